@@ -1,0 +1,215 @@
+/*
+ * hsb_oracle_impl.h -- precision-generic body of the CPU oracle.
+ * Included twice by hsb_oracle.c with REAL = double and REAL = float.
+ * TEST INFRASTRUCTURE ONLY (see hsb_oracle.c for the readings it follows).
+ */
+
+/* sgn(x) of Eq. (eq_fd) and of the spin readout s_i = sgn(x_i): +1 for x >= 0
+ * (including -0.0), -1 otherwise. */
+static REAL SFX(sgn)(REAL x)
+{
+    return x >= (REAL)0 ? (REAL)1 : (REAL)-1;
+}
+
+/* Force of one replica: f_i = sum_j J_ij b_j with b_j = x_j (Eq. eq_fb) or
+ * b_j = sgn(x_j) (Eq. eq_fd), j ascending.  `Jint` (may be NULL) is the int8
+ * copy of +/-1/0 couplings; with it the discrete sum is formed exactly in int32. */
+static void SFX(force)(const REAL *J, const int8_t *Jint, int N, int form,
+                       const REAL *x, REAL *f, int8_t *stmp)
+{
+    if (form == 1 && Jint) {
+        for (int j = 0; j < N; ++j)
+            stmp[j] = x[j] >= (REAL)0 ? (int8_t)1 : (int8_t)-1;
+        for (int i = 0; i < N; ++i) {
+            const int8_t *row = Jint + (size_t)i * N;
+            int32_t acc = 0;
+            for (int j = 0; j < N; ++j)
+                acc += (int32_t)row[j] * (int32_t)stmp[j];
+            f[i] = (REAL)acc;
+        }
+        return;
+    }
+    for (int i = 0; i < N; ++i) {
+        const REAL *row = J + (size_t)i * N;
+        REAL acc = (REAL)0;
+        for (int j = 0; j < N; ++j) {
+            REAL b = form == 1 ? SFX(sgn)(x[j]) : x[j];
+            REAL t = row[j] * b;
+            acc = acc + t;
+        }
+        f[i] = acc;
+    }
+}
+
+/* One spin update from x(t_k), y(t_k) and the force f_i (Methods):
+ *   y~  = y + {-(a0 - a(t_k)) x + c0 f} dt          Eq. (eq_SyEuY)
+ *   x~  = x + a0 y~ dt                               Eq. (eq_SyEuX)
+ *   x'  = g(x~),  y~~ = h(x~, y~)                    Eqs. (eq_WallX, eq_WallY)
+ *   y'  = y~~ + gamma y(t_k) dt                      Eq. (eq_EuHeat)
+ * in the pinned order with q = a0*dt and g = gamma*dt. */
+static void SFX(update)(int N, REAL *x, REAL *y, const REAL *f, REAL c0, REAL pk,
+                        REAL dt, REAL q, REAL g)
+{
+    for (int i = 0; i < N; ++i) {
+        REAL x0 = x[i];
+        REAL y0 = y[i];
+        REAL u = c0 * f[i];
+        REAL v = pk * x0;
+        REAL w = u - v;
+        REAL wd = w * dt;
+        REAL yt = y0 + wd;
+        REAL qy = q * yt;
+        REAL xt = x0 + qy;
+        REAL xn, ytt;
+        if (xt > (REAL)1) {
+            xn = (REAL)1;
+            ytt = (REAL)0;
+        } else if (xt < (REAL)-1) {
+            xn = (REAL)-1;
+            ytt = (REAL)0;
+        } else {
+            xn = xt;
+            ytt = yt;
+        }
+        REAL gy = g * y0;
+        x[i] = xn;
+        y[i] = ytt + gy;
+    }
+}
+
+static REAL *SFX(widen)(const float *J, int N)
+{
+    REAL *Jr = (REAL *)malloc(sizeof(REAL) * (size_t)N * (size_t)N);
+    if (!Jr)
+        return NULL;
+    for (size_t e = 0; e < (size_t)N * (size_t)N; ++e)
+        Jr[e] = (REAL)J[e];
+    return Jr;
+}
+
+/* One time step for `nrep` replicas, state x, y laid out [nrep][N].  The
+ * constants are given already rounded to REAL; p_k = a0 - a(t_k).  f_out
+ * (may be NULL) receives the forces [nrep][N]. */
+int SFX(oracle_step)(const float *J, int N, int nrep, REAL *x, REAL *y, int form,
+                     REAL pk, REAL c0, REAL dt, REAL q, REAL g, REAL *f_out)
+{
+    if (N < 1 || nrep < 0)
+        return -1;
+    REAL *Jr = SFX(widen)(J, N);
+    REAL *f = (REAL *)malloc(sizeof(REAL) * (size_t)N);
+    int8_t *stmp = (int8_t *)malloc((size_t)N);
+    if (!Jr || !f || !stmp) {
+        free(Jr);
+        free(f);
+        free(stmp);
+        return -2;
+    }
+    for (int r = 0; r < nrep; ++r) {
+        REAL *xr = x + (size_t)r * N;
+        REAL *yr = y + (size_t)r * N;
+        SFX(force)(Jr, NULL, N, form, xr, f, stmp);
+        if (f_out)
+            memcpy(f_out + (size_t)r * N, f, sizeof(REAL) * (size_t)N);
+        SFX(update)(N, xr, yr, f, c0, pk, dt, q, g);
+    }
+    free(Jr);
+    free(f);
+    free(stmp);
+    return 0;
+}
+
+/* Whole run for the replicas listed in rep_ids (replica r only depends on
+ * seed, instance, r and i, so any subset reproduces the full run).
+ * Outputs, each [nrep] or [nrep][N]: best_e, best_s (spins at the best
+ * evaluation step), x_out / y_out (state after `steps` updates, may be NULL),
+ * e_trace (energy at every evaluation step, [nrep][oracle_num_evals], may be
+ * NULL). */
+int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, uint64_t seed,
+                    int nrep, const int32_t *rep_ids, int8_t *best_s, double *best_e,
+                    REAL *x_out, REAL *y_out, double *e_trace, int nthreads)
+{
+    if (N < 1 || steps < 1 || nrep < 0 || p->eval_every < 0)
+        return -1;
+    REAL *Jr = SFX(widen)(J, N);
+    REAL *pk = (REAL *)malloc(sizeof(REAL) * (size_t)steps);
+    int8_t *Jint = NULL;
+    int use_int = p->form == 1 && !p->force_plain_sum && oracle_is_pm1(J, N);
+    if (use_int) {
+        Jint = (int8_t *)malloc((size_t)N * (size_t)N);
+        if (Jint)
+            for (size_t e = 0; e < (size_t)N * (size_t)N; ++e)
+                Jint[e] = (int8_t)J[e];
+    }
+    if (!Jr || !pk || (use_int && !Jint)) {
+        free(Jr);
+        free(pk);
+        free(Jint);
+        return -2;
+    }
+    const REAL c0 = (REAL)p->c0;
+    const REAL dt = (REAL)p->dt;
+    const REAL q = (REAL)(p->a0 * p->dt);
+    const REAL g = (REAL)(p->gamma * p->dt);
+    for (int k = 0; k < steps; ++k)
+        pk[k] = (REAL)oracle_pump_factor(p->a0, k, steps);
+    const int n_evals = (p->eval_every > 0 ? (steps - 1) / p->eval_every : 0) + 1;
+    int failed = 0;
+
+#ifdef _OPENMP
+    int nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt) reduction(| : failed)
+#else
+    (void)nthreads;
+#endif
+    for (int t = 0; t < nrep; ++t) {
+        uint32_t r = (uint32_t)rep_ids[t];
+        REAL *x = (REAL *)malloc(sizeof(REAL) * (size_t)N);
+        REAL *y = (REAL *)malloc(sizeof(REAL) * (size_t)N);
+        REAL *f = (REAL *)malloc(sizeof(REAL) * (size_t)N);
+        int8_t *s = (int8_t *)malloc((size_t)N);
+        int8_t *stmp = (int8_t *)malloc((size_t)N);
+        if (!x || !y || !f || !s || !stmp) {
+            failed = 1;
+        } else {
+            for (int i = 0; i < N; ++i) {
+                x[i] = (REAL)oracle_init_value(seed, p->instance, r, (uint32_t)i, 0, p->init_half_width);
+                y[i] = (REAL)oracle_init_value(seed, p->instance, r, (uint32_t)i, 1, p->init_half_width);
+            }
+            double best = INFINITY;
+            int ev = 0;
+            for (int k = 0; k <= steps; ++k) {
+                int is_eval = (k == steps) || (p->eval_every > 0 && k > 0 && k % p->eval_every == 0);
+                if (is_eval) {
+                    for (int i = 0; i < N; ++i)
+                        s[i] = x[i] >= (REAL)0 ? (int8_t)1 : (int8_t)-1;
+                    double e = oracle_ising_energy(J, N, s);
+                    if (e_trace)
+                        e_trace[(size_t)t * n_evals + ev] = e;
+                    ++ev;
+                    if (e < best) {
+                        best = e;
+                        memcpy(best_s + (size_t)t * N, s, (size_t)N);
+                    }
+                }
+                if (k == steps)
+                    break;
+                SFX(force)(Jr, Jint, N, p->form, x, f, stmp);
+                SFX(update)(N, x, y, f, c0, pk[k], dt, q, g);
+            }
+            best_e[t] = best;
+            if (x_out)
+                memcpy(x_out + (size_t)t * N, x, sizeof(REAL) * (size_t)N);
+            if (y_out)
+                memcpy(y_out + (size_t)t * N, y, sizeof(REAL) * (size_t)N);
+        }
+        free(x);
+        free(y);
+        free(f);
+        free(s);
+        free(stmp);
+    }
+    free(Jr);
+    free(pk);
+    free(Jint);
+    return failed ? -2 : 0;
+}

@@ -1,0 +1,402 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something other than itself: values worked
+out by hand from the Methods equations (tests/golden), the MAX-CUT identity of
+Eq. (eq_Cut), exhaustive enumeration, published SplitMix64 outputs, the
+conserved quadratic form of the symplectic-Euler map (per eigenmode of J), the
+closed-form linear map of the heated update without walls, the gamma = 0
+reduction to plain bSB / dSB and the wall invariants.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    with open(os.path.join(GOLDEN, name)) as fh:
+        return json.load(fh)
+
+
+# ------------------------------------------------------------------ RNG ----
+
+def test_splitmix64_published_outputs():
+    # First four outputs of SplitMix64 seeded with 0, as published with the
+    # generator's reference implementation (Steele, Lea & Flood 2014 / Vigna).
+    want = [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F, 0xF88BB8A8724C81EC]
+    assert [oracle.splitmix64(0, n) for n in (1, 2, 3, 4)] == want
+
+
+def test_init_values_open_interval_and_grid():
+    x, y = oracle.init_values(7, 0, range(4), 500, 1.0)
+    for a in (x, y):
+        assert np.all(np.abs(a) < 1.0)
+        # L = 1: values are odd multiples of 2^-24
+        k = a.astype(np.float64) * 2.0**24
+        assert np.all(k == np.round(k))
+        assert np.all(np.mod(np.round(k), 2) == 1)
+    x2, _ = oracle.init_values(7, 0, range(2), 500, 0.1)
+    assert np.all(np.abs(x2) < 0.1)
+
+
+def test_init_values_uniform():
+    scipy_stats = pytest.importorskip("scipy.stats")
+    x, y = oracle.init_values(11, 3, range(8), 1000, 1.0)
+    v = np.concatenate([x.ravel(), y.ravel()]).astype(np.float64)
+    res = scipy_stats.kstest(v, "uniform", args=(-1.0, 2.0))
+    assert res.pvalue > 1e-3
+    # different streams (seed, instance, replica, component) differ
+    x3, _ = oracle.init_values(11, 4, range(1), 1000, 1.0)
+    assert not np.array_equal(x3[0], x[0])
+    assert not np.array_equal(x[0], y[0])
+
+
+# --------------------------------------------------------------- energy ----
+
+def test_energy_hand_values_and_cut_identity():
+    g = _golden("worked_steps.json")["energies"]
+    for case in g["cases"]:
+        J = np.array(case["J"], np.float32)
+        for s, e, c in zip(case["states"], case["E"], case["C"]):
+            s = np.array(s, np.int8)
+            assert oracle.ising_energy(J, s) == e
+            assert oracle.cut_value(J, s) == c
+        e0, _ = oracle.brute_force(J)
+        assert e0 == case["E_ground"]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_energy_equals_cut_relation(seed):
+    # Eq. (eq_Cut): C = -E/2 - (1/4) sum_ij J_ij, with C counted edge by edge.
+    J = synth.sk_gauss(9, seed)
+    rng = np.random.default_rng(seed)
+    for _ in range(5):
+        s = rng.choice(np.array([-1, 1], np.int8), size=9)
+        cut = 0.0
+        for i in range(9):
+            for j in range(9):
+                if s[i] != s[j]:
+                    cut += -float(J[i, j]) / 2.0  # w_ij counted from both ends, halved
+        E = oracle.ising_energy(J, s)
+        assert E == pytest.approx(-2.0 * (cut + 0.25 * float(J.astype(np.float64).sum())), abs=1e-9)
+        assert oracle.cut_value(J, s) == pytest.approx(cut, abs=1e-9)
+
+
+def test_energy_single_flip_identity():
+    # Flipping spin i changes E by 2 s_i h_i with the local field h_i = sum_j J_ij s_j.
+    J = synth.sk_pm1(15, 4)
+    rng = np.random.default_rng(4)
+    s = rng.choice(np.array([-1, 1], np.int8), size=15)
+    E = oracle.ising_energy(J, s)
+    for i in range(15):
+        h = float(J[i].astype(np.float64) @ s.astype(np.float64))
+        t = s.copy()
+        t[i] = -t[i]
+        assert oracle.ising_energy(J, t) - E == 2.0 * s[i] * h
+
+
+@pytest.mark.parametrize("n,seed", [(6, 0), (9, 1), (11, 2)])
+def test_brute_force_matches_python_enumeration(n, seed):
+    J = synth.sk_pm1(n, seed)
+    best = math.inf
+    for bits in itertools.product((1, -1), repeat=n):
+        s = np.array(bits, np.float64)
+        # number of unsatisfied bonds form: E = sum_{i<j} -J_ij s_i s_j
+        e = 0.0
+        for i in range(n):
+            for j in range(i + 1, n):
+                e -= float(J[i, j]) * s[i] * s[j]
+        best = min(best, e)
+    e0, s0 = oracle.brute_force(J)
+    assert e0 == best
+    assert oracle.ising_energy(J, s0) == e0
+
+
+# ---------------------------------------------------------- worked steps ---
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_worked_steps(precision):
+    g = _golden("worked_steps.json")
+    for case in g["cases"]:
+        J = np.array(case["J"], np.float32)
+        x1, y1, f = oracle.step(J, case["x"], case["y"], case["form"], case["pk"], case["c0"],
+                                case["dt"], case["q"], case["g"], precision)
+        tol = case.get("tolerance", 0.0)
+        if precision == "f32" and tol:
+            tol = 1e-6
+        np.testing.assert_allclose(f[0], case["f"], rtol=0, atol=tol, err_msg=case["name"])
+        np.testing.assert_allclose(x1[0], case["x_next"], rtol=0, atol=tol, err_msg=case["name"])
+        np.testing.assert_allclose(y1[0], case["y_next"], rtol=0, atol=tol, err_msg=case["name"])
+
+
+# ------------------------------------------------------- dynamics pins ----
+
+def _modes(J):
+    lam, V = np.linalg.eigh(J.astype(np.float64))
+    return lam, V
+
+
+def test_quadratic_form_conserved_per_eigenmode():
+    # gamma = 0, constant p, no wall hit: in eigenmode m of J the update is the
+    # symplectic Euler map of a harmonic oscillator with P_m = (p - c0 lam_m) dt
+    # and q = a0 dt, which conserves P x^2 + q y^2 - P q x y exactly.
+    n = 8
+    J = synth.sk_pm1(n, 5)
+    lam, V = _modes(J)
+    p, c0, dt, a0 = 1.0, 0.03, 0.5, 1.0
+    q = a0 * dt
+    P = (p - c0 * lam) * dt
+    assert np.all(P > 0) and np.all(P * q < 4)
+    rng = np.random.default_rng(0)
+    x = rng.uniform(-0.01, 0.01, n)
+    y = rng.uniform(-0.01, 0.01, n)
+
+    def Q(x, y):
+        xm, ym = V.T @ x, V.T @ y
+        return P * xm**2 + q * ym**2 - P * q * xm * ym
+
+    q0 = Q(x, y)
+    for _ in range(300):
+        x, y, _ = oracle.step(J, x, y, 0, p, c0, dt, q, 0.0, "f64")
+        x, y = x[0], y[0]
+        assert np.max(np.abs(x)) < 1.0
+    np.testing.assert_allclose(Q(x, y), q0, rtol=1e-11, atol=0)
+    # A sign error on the force would make P_m = (p + c0 lam_m) dt: not conserved.
+    Pw = (p + c0 * lam) * dt
+    xm, ym = V.T @ x, V.T @ y
+    assert not np.allclose(Pw * xm**2 + q * ym**2 - Pw * q * xm * ym, q0, rtol=1e-6)
+
+
+def test_heated_update_is_linear_map_per_eigenmode():
+    # Without walls, one heated step maps each eigenmode (x_m, y_m) by
+    # [[1 - q P_m, q], [-P_m, 1 + g]] with g = gamma dt (Eqs. eq_SyEuY,
+    # eq_SyEuX, eq_EuHeat).
+    n = 7
+    J = synth.sk_gauss(n, 3)
+    lam, V = _modes(J)
+    p, c0, dt, a0, gamma = 0.8, 0.05, 0.7, 1.0, 0.3
+    q, g = a0 * dt, gamma * dt
+    rng = np.random.default_rng(1)
+    x = rng.uniform(-1e-3, 1e-3, n)
+    y = rng.uniform(-1e-3, 1e-3, n)
+    xm, ym = V.T @ x, V.T @ y
+    steps = 25
+    for _ in range(steps):
+        x, y, _ = oracle.step(J, x, y, 0, p, c0, dt, q, g, "f64")
+        x, y = x[0], y[0]
+    assert np.max(np.abs(x)) < 1.0
+    for m in range(n):
+        Pm = (p - c0 * lam[m]) * dt
+        M = np.array([[1 - q * Pm, q], [-Pm, 1 + g]])
+        want = np.linalg.matrix_power(M, steps) @ np.array([xm[m], ym[m]])
+        got = np.array([V[:, m] @ x, V[:, m] @ y])
+        np.testing.assert_allclose(got, want, rtol=1e-9, atol=1e-15)
+
+
+def test_two_spin_normal_modes():
+    # N = 2, J12 = 1: u = x1 + x2 and v = x1 - x2 decouple with
+    # P_u = (p - c0) dt and P_v = (p + c0) dt (eigenvalues +1 and -1 of J).
+    J = np.array([[0, 1], [1, 0]], np.float32)
+    p, c0, dt, gamma = 0.6, 0.2, 0.9, 0.1
+    q, g = dt, gamma * dt
+    x = np.array([0.01, -0.003])
+    y = np.array([-0.002, 0.004])
+    u0 = np.array([x[0] + x[1], y[0] + y[1]])
+    v0 = np.array([x[0] - x[1], y[0] - y[1]])
+    steps = 12
+    for _ in range(steps):
+        x, y, _ = oracle.step(J, x, y, 0, p, c0, dt, q, g, "f64")
+        x, y = x[0], y[0]
+    for P, m0, got in (((p - c0) * dt, u0, [x[0] + x[1], y[0] + y[1]]),
+                       ((p + c0) * dt, v0, [x[0] - x[1], y[0] - y[1]])):
+        M = np.array([[1 - q * P, q], [-P, 1 + g]])
+        np.testing.assert_allclose(got, np.linalg.matrix_power(M, steps) @ m0, rtol=1e-10)
+
+
+def test_heating_uses_momentum_before_the_step():
+    # Eq. (eq_EuHeat): y(t_{k+1}) = y~~ + gamma y(t_k) dt; the heated and the
+    # plain (gamma = 0) step from the same state differ in y by g*y(t_k) only.
+    J = synth.sk_gauss(10, 8)
+    rng = np.random.default_rng(2)
+    x = rng.uniform(-1, 1, (3, 10))
+    y = rng.uniform(-1, 1, (3, 10))
+    args = (0, 0.4, 0.3, 1.1, 1.1)
+    xh, yh, _ = oracle.step(J, x, y, *args, 0.25, precision="f64")
+    xp, yp, _ = oracle.step(J, x, y, *args, 0.0, precision="f64")
+    np.testing.assert_array_equal(xh, xp)
+    np.testing.assert_allclose(yh - yp, 0.25 * y, rtol=1e-12, atol=1e-15)
+
+
+def _plain_sb_f32(J, x, y, steps, c0, dt, a0, form):
+    """Plain bSB / dSB (no heating) as in Goto et al. 2021, written with numpy
+    float32 element-wise operations; the discrete force of +/-1 couplings is an
+    exact integer product."""
+    x = x.astype(np.float32).copy()
+    y = y.astype(np.float32).copy()
+    c0 = np.float32(c0)
+    dtf = np.float32(dt)
+    q = np.float32(a0 * dt)
+    Ji = J.astype(np.int64)
+    for k in range(steps):
+        pk = np.float32(a0 - (a0 * k) / steps)
+        if form == 1:
+            s = np.where(x >= 0, 1, -1).astype(np.int64)
+            f = (s @ Ji.T).astype(np.float32)
+        else:
+            raise NotImplementedError
+        ynew = y + (c0 * f - pk * x) * dtf
+        xnew = x + q * ynew
+        hit = np.abs(xnew) > 1
+        xnew = np.where(hit, np.sign(xnew), xnew).astype(np.float32)
+        ynew = np.where(hit, np.float32(0), ynew).astype(np.float32)
+        x, y = xnew, ynew
+    return x, y
+
+
+def test_gamma_zero_reduces_to_plain_dsb_bit_exact():
+    n, steps, reps = 40, 150, [0, 3, 9]
+    J = synth.sk_pm1(n, 12)
+    c0 = oracle.c0_from_c1(J, 0.6)
+    prm = oracle.make_params(1, c0, 1.1, 0.0, eval_every=0)
+    out = oracle.run(J, prm, steps, 77, reps, "f32")
+    x0, y0 = oracle.init_values(77, 0, reps, n, 1.0)
+    xp, yp = _plain_sb_f32(J, x0, y0, steps, c0, 1.1, 1.0, 1)
+    np.testing.assert_array_equal(out["x"], xp)
+    np.testing.assert_array_equal(out["y"], yp)
+
+
+def test_gamma_zero_reduces_to_plain_bsb_f64():
+    # Plain bSB in binary64 with Python loops in the same summation order.
+    n, steps = 6, 60
+    J = synth.sk_gauss(n, 13)
+    c0, dt, a0 = 0.3, 0.7, 1.0
+    prm = oracle.make_params(0, c0, dt, 0.0, eval_every=0)
+    out = oracle.run(J, prm, steps, 5, [2], "f64")
+    x0, y0 = oracle.init_values(5, 0, [2], n, 1.0)
+    x = [float(v) for v in x0[0]]
+    y = [float(v) for v in y0[0]]
+    Jd = J.astype(np.float64)
+    for k in range(steps):
+        pk = a0 - (a0 * k) / steps
+        f = []
+        for i in range(n):
+            acc = 0.0
+            for j in range(n):
+                acc = acc + float(Jd[i, j]) * x[j]
+            f.append(acc)
+        for i in range(n):
+            yt = y[i] + (c0 * f[i] - pk * x[i]) * dt
+            xt = x[i] + (a0 * dt) * yt
+            if abs(xt) > 1:
+                x[i], y[i] = math.copysign(1.0, xt), 0.0
+            else:
+                x[i], y[i] = xt, yt
+    np.testing.assert_array_equal(out["x"][0], np.array(x))
+    np.testing.assert_array_equal(out["y"][0], np.array(y))
+
+
+def test_wall_invariants_along_a_trajectory():
+    n = 30
+    J = synth.sk_pm1(n, 21)
+    c0 = oracle.c0_from_c1(J, 0.9)
+    dt, a0, gamma = 1.1, 1.0, 0.5
+    q, g = a0 * dt, gamma * dt
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, (2, n))
+    y = rng.uniform(-1, 1, (2, n))
+    steps, clamps = 200, 0
+    for k in range(steps):
+        pk = oracle.pump_factor(a0, k, steps)
+        x1, y1, f = oracle.step(J, x, y, 0, pk, c0, dt, q, g, "f64")
+        assert np.all(np.abs(x1) <= 1.0)
+        # recompute the unclamped position to find the clamped spins
+        yt = y + (c0 * f - pk * x) * dt
+        xt = x + q * yt
+        hit = np.abs(xt) > 1
+        clamps += int(hit.sum())
+        assert np.all(np.abs(x1[hit]) == 1.0)
+        assert np.all(np.sign(x1[hit]) == np.sign(xt[hit]))
+        np.testing.assert_allclose(y1[hit], g * y[hit], rtol=0, atol=0)
+        x, y = x1, y1
+    assert clamps > 0
+
+
+# -------------------------------------------------------- run protocol ----
+
+def test_replica_independence_and_determinism():
+    n, steps = 50, 300
+    J = synth.sk_pm1(n, 2)
+    c0 = oracle.c0_from_c1(J, 0.7)
+    prm = oracle.make_params(1, c0, 1.1, 0.06, eval_every=50)
+    a = oracle.run(J, prm, steps, 123, range(6), "f32", nthreads=1)
+    b = oracle.run(J, prm, steps, 123, [4, 1], "f32", nthreads=2)
+    c = oracle.run(J, prm, steps, 123, range(6), "f32", nthreads=4)
+    for key in ("x", "y", "best_s", "best_e"):
+        np.testing.assert_array_equal(a[key][[4, 1]], b[key])
+        np.testing.assert_array_equal(a[key], c[key])
+    d = oracle.run(J, prm, steps, 124, range(6), "f32")
+    assert not np.array_equal(a["x"], d["x"])
+
+
+def test_int_force_shortcut_equals_plain_sum():
+    n, steps = 64, 120
+    J = synth.sk_pm1(n, 6)
+    c0 = oracle.c0_from_c1(J, 0.7)
+    for prec in ("f32", "f64"):
+        fast = oracle.run(J, oracle.make_params(1, c0, 1.1, 0.06, eval_every=20), steps, 9,
+                          range(4), prec)
+        slow = oracle.run(J, oracle.make_params(1, c0, 1.1, 0.06, eval_every=20,
+                                                force_plain_sum=True), steps, 9, range(4), prec)
+        for key in ("x", "y", "best_s", "best_e"):
+            np.testing.assert_array_equal(fast[key], slow[key])
+
+
+def test_best_tracking_and_eval_cadence():
+    n, steps, ev = 40, 400, 100
+    J = synth.sk_pm1(n, 3)
+    c0 = oracle.c0_from_c1(J, 0.7)
+    prm = oracle.make_params(1, c0, 1.1, 0.06, eval_every=ev)
+    out = oracle.run(J, prm, steps, 3, range(5), "f32", want_trace=True)
+    tr = out["e_trace"]
+    assert tr.shape == (5, 4)  # t = 100, 200, 300, 400
+    np.testing.assert_array_equal(out["best_e"], tr.min(axis=1))
+    for r in range(5):
+        assert oracle.ising_energy(J, out["best_s"][r]) == out["best_e"][r]
+        # the final evaluation is sgn(x(t_Ns))
+        s_fin = np.where(out["x"][r] >= 0, 1, -1).astype(np.int8)
+        assert oracle.ising_energy(J, s_fin) == tr[r, -1]
+    last = oracle.run(J, oracle.make_params(1, c0, 1.1, 0.06, eval_every=0), steps, 3,
+                      range(5), "f32")
+    np.testing.assert_array_equal(last["best_e"], tr[:, -1])
+
+
+@pytest.mark.parametrize("form,gamma", [(1, 0.06), (0, 0.5)])
+def test_small_instances_reach_brute_force_ground_state(form, gamma):
+    n = 14
+    J = synth.sk_pm1(n, 30)
+    e0, _ = oracle.brute_force(J)
+    c0 = oracle.c0_from_c1(J, 0.7 if form else 0.9)
+    prm = oracle.make_params(form, c0, 1.1, gamma, eval_every=10)
+    out = oracle.run(J, prm, 300, 1, range(32), "f64")
+    assert np.all(out["best_e"] >= e0)
+    assert out["best_e"].min() == e0
+
+
+def test_pump_schedule_and_c0():
+    assert oracle.pump_factor(1.0, 0, 2000) == 1.0
+    assert oracle.pump_factor(1.0, 1000, 2000) == 0.5
+    assert oracle.pump_factor(1.0, 1999, 2000) == pytest.approx(1 / 2000, rel=1e-12)
+    J = synth.sk_pm1(100, 0)
+    assert oracle.sigma_j(J) == 1.0
+    assert oracle.c0_from_c1(J, 0.5) == 0.5 / 10.0
+    G = synth.sk_gauss(300, 0)
+    s = oracle.sigma_j(G)
+    assert 0.9 < s < 1.1
