@@ -1,0 +1,356 @@
+#!/usr/bin/env python
+"""Benchmark of the heated simulated bifurcation hot path on GB300.
+
+One benchmark step is one whole run of the library's hot path over one batch
+of synthetic input: seeded initial state, `sb_steps` heated discrete SB time
+steps of R replicas (force J sgn(X) on the tensor cores, fused update, walls,
+heating, pump schedule), energy evaluation every 100 steps with best tracking,
+and the final evaluation.  Workload: one +/-1 Sherrington-Kirkpatrick instance
+with N = 2000 spins (seeded stand-in for K2000), R = 1024 replicas, 2000 steps,
+the paper's tuned HdSB parameters (dt = 1.1, c1 = 0.7, gamma = 0.06).
+
+Metric: replica-spin-steps/s = N * R * sb_steps / time.
+
+Output: one JSON line (rank 0).  `--impl reference` times the CPU oracle on
+the host cores instead (the reference arm of this pipeline).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "replica-spin-steps/s and % of dense tensor roofline at N=2000, R=1024 vs plain FP32 GPU"
+UNIT = "replica-spin-steps/s"
+WORKLOAD = dict(name="HdSB SK +/-1 N=2000 R=1024 2000 steps FP8", N=2000, J_seed=1, R=1024,
+                sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1, gamma=0.06,
+                init_half_width=1.0, eval_every=100, a0=1.0)
+L2_FLUSH_BYTES = 256 << 20
+TC_SOURCE = os.path.join(ROOT, "paper_2203_08361_gb300", "csrc", "hsb_tc.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def _dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _config(extra=None):
+    w = WORKLOAD
+    cfg = {"workload": w["name"], "N": w["N"], "R": w["R"], "sb_steps": w["sb_steps"],
+           "form": w["form"], "prec": w["prec"], "dt": w["dt"], "c1": w["c1"],
+           "gamma": w["gamma"], "eval_every": w["eval_every"], "J": f"sk_pm1(seed={w['J_seed']})"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# ----------------------------------------------------------- CPU oracle ---
+
+def oracle_sample(reps: int, sb_steps: int, nthreads: int):
+    """Runs the binary32 oracle (as it stands) on a sample of the workload and
+    returns (replica-spin-steps/s, seconds)."""
+    import oracle
+    import synth
+    w = WORKLOAD
+    J = synth.sk_pm1(w["N"], w["J_seed"])
+    op = oracle.make_params(1, oracle.c0_from_c1(J, w["c1"]), w["dt"], w["gamma"],
+                            a0=w["a0"], init_half_width=w["init_half_width"],
+                            eval_every=w["eval_every"])
+    t0 = time.perf_counter()
+    oracle.run(J, op, sb_steps, 1, range(reps), "f32", nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return w["N"] * reps * sb_steps / dt, dt
+
+
+def cpu_baseline(target_s: float = 12.0):
+    cores = os.cpu_count() or 1
+    reps = max(cores, 8)
+    rate, t = oracle_sample(reps, 10, cores)  # calibration
+    steps = int(max(20, min(WORKLOAD["sb_steps"], target_s * rate / (WORKLOAD["N"] * reps))))
+    rate, t = oracle_sample(reps, steps, cores)
+    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} replicas x {steps} of the {WORKLOAD['sb_steps']} steps "
+                      f"(N={WORKLOAD['N']}), binary32 oracle, {cores} threads, {t:.1f} s"}
+
+
+def run_reference(args):
+    world, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    reps = max(cores, 8)
+    sb = 100
+    for _ in range(args.warmup):
+        oracle_sample(reps, sb, cores)
+    times = []
+    for _ in range(args.steps):
+        _, t = oracle_sample(reps, sb, cores)
+        times.append(t)
+    total = sum(times)
+    value = WORKLOAD["N"] * reps * sb * args.steps / total
+    sample = f"{reps} replicas x {sb} steps of the workload per step (binary32 oracle, {cores} threads)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config({"sample": sample}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.dev)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ GPU arm ----
+
+def _traffic_for_current_kernel():
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            rec = json.load(fh)
+        with open(TC_SOURCE, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+        if rec.get("source_sha256_16") == sha:
+            return rec.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mp = json.load(fh)
+        return mp, "measured"
+    except (OSError, ValueError):
+        return {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "hbm_gbs": 6800.0}, \
+            "fallback"
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2203_08361_gb300 as hsb
+    import synth
+
+    world, rank, local = _dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    w = WORKLOAD
+    N, R, S = w["N"], w["R"], w["sb_steps"]
+    J = synth.sk_pm1(N, w["J_seed"])
+    p = hsb.params(w["form"], w["prec"], a0=w["a0"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
+                   init_half_width=w["init_half_width"], eval_every=w["eval_every"])
+    seed = 1000 + rank  # independent replicas on every rank
+    stream = torch.cuda.Stream()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    spins = torch.empty((R, N), dtype=torch.int8, device="cuda")
+    energy = torch.empty(R, dtype=torch.float64, device="cuda")
+
+    solver = hsb.Solver(J)
+    solver.set_stream(stream.cuda_stream)
+
+    def one_run():
+        solver.run_device(p, R, S, seed, spins.data_ptr(), energy.data_ptr())
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            one_run()
+        solver.synchronize()
+        launches_per_run = solver.run_stats()
+
+        # ---- device-resident timed region: K runs, L2 flushed between runs
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(torch.cuda.current_device())
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            starts[i].record(stream)
+            one_run()
+            ends[i].record(stream)
+        solver.synchronize()
+        torch.cuda.synchronize()
+        clock_rec = clocks.stop()
+        if world > 1:
+            dist.barrier()
+        elapsed_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+
+        # ---- step-kernel timing: the same launches, graph-replayed, no evaluations
+        k0 = torch.cuda.Event(enable_timing=True)
+        k1 = torch.cuda.Event(enable_timing=True)
+        reps_k = 2
+        solver.advance_device(p, R, S, 0, S)  # capture + warm
+        solver.synchronize()
+        k0.record(stream)
+        for _ in range(reps_k):
+            solver.advance_device(p, R, S, 0, S)
+        k1.record(stream)
+        solver.synchronize()
+        step_kernel_ms = k0.elapsed_time(k1) / (reps_k * S)
+
+    t_max = elapsed_ms
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * N * R * S * args.steps / (t_max / 1000.0)
+
+    # ---- end to end through the C ABI with host buffers (rank-local)
+    pin_J = torch.from_numpy(J).pin_memory()
+    out_s = torch.empty((R, N), dtype=torch.int8).pin_memory()
+    out_e = torch.empty(R, dtype=torch.float64).pin_memory()
+    import ctypes as C
+    lib = hsb.load()
+
+    def e2e_step():
+        st = lib.hsb_set_couplings(C.c_void_p(solver.h), C.c_void_p(pin_J.data_ptr()))
+        if st != 0:
+            raise hsb.HsbError(st, lib.hsb_last_error().decode())
+        st = lib.hsb_run(C.c_void_p(solver.h), C.byref(p), R, S, C.c_uint64(seed),
+                         C.c_void_p(out_s.data_ptr()), C.c_void_p(out_e.data_ptr()))
+        if st != 0:
+            raise hsb.HsbError(st, lib.hsb_last_error().decode())
+
+    e2e_step()
+    e2e_iters = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(e2e_iters):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / e2e_iters
+    e2e_value = N * R * S / e2e_s * world
+    solver.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    flops_per_launch = 2.0 * N * N * R
+    achieved = flops_per_launch / (step_kernel_ms / 1000.0) / 1e12
+    mp, src = _peaks()
+    peak = 2.0 * float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops")))
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": _traffic_for_current_kernel(),
+                "kernel": "tc_fp8_step_kernel", "launch_ms": step_kernel_ms,
+                "peak_source": f"FP8 dense = 2 x bf16 sustained of {src} peaks (nominal "
+                               "FP8/BF16 ratio 4.5/2.25)",
+                "flops_per_launch": flops_per_launch}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "fp8", "data": "synthetic",
+            "config": _config({"l2": "256 MiB buffer written between timed runs (outside the "
+                                     "per-run CUDA-event intervals)",
+                               "parallelism": f"replicas only: {world} x {R} independent "
+                                              "replicas"}),
+            "roofline": roofline, "clocks": clock_rec,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * N * 4),
+                    "d2h_bytes_per_step": int(R * N + R * 8)},
+            "gpu_launches": int(launches_per_run * args.steps)}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["hsb", "reference"], default="hsb")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

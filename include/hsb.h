@@ -1,0 +1,187 @@
+/*
+ * hsb.h -- C ABI of the GB300 heated simulated bifurcation library (libhsb.so).
+ *
+ * Heated simulated bifurcation (HbSB / HdSB) searches for low-energy states of
+ * the Ising problem
+ *     E = -1/2 sum_i sum_j J_ij s_i s_j,  s_i = +/-1,  J_ij = J_ji,  J_ii = 0
+ * (Kanao & Goto, arXiv 2203.08361, Eq. (eq_Ising)) by integrating, for R
+ * independent replicas, the equations of motion
+ *     dx_i/dt = a0 y_i,
+ *     dy_i/dt = -[a0 - a(t)] x_i + c0 f_i + gamma y_i          Eqs. (eq_PosHeat), (eq_MomHeat)
+ * with f_i = sum_j J_ij x_j (ballistic, Eq. (eq_fb)) or
+ *      f_i = sum_j J_ij sgn(x_j) (discrete, Eq. (eq_fd)),
+ * discretised as in the Methods section: symplectic Euler on the terms other
+ * than gamma*y (Eqs. (eq_SyEuY), (eq_SyEuX)), perfectly inelastic walls at
+ * x = +/-1 (Eqs. (eq_WallX), (eq_WallY)) and an Euler heating step that uses
+ * the momentum before the step (Eq. (eq_EuHeat)).  a(t) rises linearly from 0
+ * to a0; c0 = c1 / (sqrt(N) sigma_J) (Results, "SB with thermal fluctuation").
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an hsb_status and never aborts the process.  On an
+ *     error, hsb_last_error() returns a message for the calling thread.
+ *   - There is no CPU fallback: without a CUDA device every compute call
+ *     returns HSB_E_NODEVICE.
+ *   - Arrays are dense and row-major; "spins x replicas" state is stored one
+ *     replica per row: element (r, i) of an R x N array is at r*N + i.
+ *   - Host pointers are caller-owned and are not retained after the call
+ *     returns.  Device pointers (the *_device variants) must stay valid until
+ *     the work queued on the handle's stream has completed.
+ *   - A handle is not thread-safe: calls on one handle must not overlap.
+ *     Distinct handles are independent.
+ *
+ * Evaluation protocol (Results, K2000 and 700-spin studies): the energy of
+ * s = sgn(x(t_k)) is evaluated at t_k for k = m*eval_every (m >= 1, k < steps)
+ * and at the final time k = steps; eval_every = 0 evaluates the final time
+ * only.  The best (strictly lowest, earliest on ties) energy and its spins are
+ * returned per replica.  sgn(x) = +1 for x >= 0 (including -0.0).
+ */
+#ifndef HSB_H
+#define HSB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HSB_API_VERSION 1
+
+#if defined(__GNUC__)
+#define HSB_API __attribute__((visibility("default")))
+#else
+#define HSB_API
+#endif
+
+typedef struct hsb_ctx *hsb_handle; /* opaque, library-owned */
+
+typedef enum {
+    HSB_OK = 0,
+    HSB_E_INVAL = 1,       /* bad argument (size, null pointer, parameter range) */
+    HSB_E_ASYM = 2,        /* J is not exactly symmetric */
+    HSB_E_DIAG = 3,        /* J has a nonzero diagonal entry */
+    HSB_E_NOMEM = 4,       /* device or host allocation failed */
+    HSB_E_CUDA = 5,        /* a CUDA runtime call or kernel failed */
+    HSB_E_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    HSB_E_UNSUPPORTED = 7, /* precision not valid for these couplings / form */
+    HSB_E_NODEVICE = 8     /* no usable CUDA device */
+} hsb_status;
+
+typedef enum {
+    HSB_BALLISTIC = 0, /* f = J x        (HbSB when gamma > 0), Eq. (eq_fb) */
+    HSB_DISCRETE = 1   /* f = J sgn(x)   (HdSB when gamma > 0), Eq. (eq_fd) */
+} hsb_form;
+
+typedef enum {
+    /* discrete form with J in {-1,0,+1}: FP8; otherwise BF16X3 */
+    HSB_PREC_AUTO = 0,
+    /* plain FP32 on CUDA cores: force sums are fused multiply-adds over j
+       ascending, so trajectories equal the binary32 oracle's bit for bit */
+    HSB_PREC_FP32 = 1,
+    /* tcgen05 tensor cores, J and sgn(x) in FP8 e4m3, FP32 accumulation.
+       Exact (integer forces); discrete form with J in {-1,0,+1} only. */
+    HSB_PREC_FP8 = 2,
+    /* tcgen05 tensor cores, J = J_hi + J_lo and x = x_hi + x_lo in BF16,
+       J_hi x_hi + J_lo x_hi + J_hi x_lo accumulated in FP32 */
+    HSB_PREC_BF16X3 = 3
+} hsb_prec;
+
+typedef struct {
+    int form;               /* hsb_form */
+    int prec;               /* hsb_prec */
+    double a0;              /* a0 > 0 (paper: 1) */
+    double c1;              /* c0 = c1 / (sqrt(N) sigma_J) when c0 <= 0 */
+    double c0;              /* interaction scale; > 0 overrides c1 */
+    double dt;              /* time step Delta t > 0 */
+    double gamma;           /* heating rate >= 0 (0: plain bSB / dSB) */
+    double init_half_width; /* x0, y0 uniform in (-L, L); paper L = 1 */
+    int eval_every;         /* >= 0; 100 in the K2000 study, 0 = final only */
+    int trace_every;        /* reserved, must be 0 */
+    uint32_t instance;      /* random stream of the instance (x0, y0) */
+    uint32_t reserved[7];   /* must be zero */
+} hsb_params;
+
+/* Fills *p with the paper's tuned HdSB settings (Fig. 1 caption): discrete
+ * form, AUTO precision, a0 = 1, c1 = 0.7, dt = 1.1, gamma = 0.06, L = 1,
+ * eval_every = 100. */
+HSB_API hsb_status hsb_params_default(hsb_params *p);
+
+/* Library ABI version (HSB_API_VERSION). */
+HSB_API int hsb_version(void);
+
+/* Creates a handle for the couplings J (host, float32, N x N, row-major),
+ * copying them to the current CUDA device.  J must be exactly symmetric with a
+ * zero diagonal (Eq. (eq_Ising)); otherwise HSB_E_ASYM / HSB_E_DIAG.  N >= 2.
+ * Work is queued on a private stream of the handle until hsb_set_stream(). */
+HSB_API hsb_status hsb_create(const float *J, int N, hsb_handle *out);
+
+/* Destroys the handle and frees its device memory (waits for its stream).
+ * NULL is ignored. */
+HSB_API void hsb_destroy(hsb_handle h);
+
+/* Sets the CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream())
+ * on which the handle queues its work; NULL selects the handle's private
+ * stream again. */
+HSB_API hsb_status hsb_set_stream(hsb_handle h, void *cuda_stream);
+
+/* Number of spins N and whether J is in {-1, 0, +1} (the FP8 path applies). */
+HSB_API hsb_status hsb_info(hsb_handle h, int *N, int *is_pm1);
+
+/* Runs `steps` >= 1 heated SB steps for replicas r = 0..R-1 (R >= 1) from the
+ * seeded initial state and returns, per replica, the best evaluated energy
+ * best_energy[r] (float64) and its spins best_spins[r*N + i] (+1 / -1).
+ * Both outputs are caller-owned HOST buffers; the call blocks until they are
+ * written.  Replica r's result depends only on (J, params, steps, seed, r),
+ * not on R. */
+HSB_API hsb_status hsb_run(hsb_handle h, const hsb_params *p, int R, int steps, uint64_t seed,
+                   int8_t *best_spins, double *best_energy);
+
+/* As hsb_run, but the outputs are DEVICE pointers (best_spins R*N int8,
+ * best_energy R float64) and the call only queues the work on the handle's
+ * stream and returns. */
+HSB_API hsb_status hsb_run_device(hsb_handle h, const hsb_params *p, int R, int steps, uint64_t seed,
+                          int8_t *best_spins, double *best_energy);
+
+/* Copies x(t_steps), y(t_steps) of the last run on this handle (R x N float32
+ * each, host) into x and y (either may be NULL).  Blocks. */
+HSB_API hsb_status hsb_get_state(hsb_handle h, float *x, float *y);
+
+/* Advances a given state: applies the updates k = k_begin .. k_end-1 of a
+ * `steps`-step pump schedule (0 <= k_begin <= k_end <= steps) to x, y (host,
+ * R x N float32, read and overwritten).  No energy is evaluated.  Used for
+ * one-step accuracy checks and for resuming a run from a saved state: the
+ * schedule uses the absolute k, so splitting a run gives the same result. */
+HSB_API hsb_status hsb_advance(hsb_handle h, const hsb_params *p, int R, int steps, int k_begin,
+                       int k_end, float *x, float *y);
+
+/* Continues the state that the last hsb_run / hsb_run_device /
+ * hsb_advance_device left on the device (same R and precision): queues the
+ * updates k = k_begin .. k_end-1 of a `steps`-step pump schedule on the
+ * handle's stream, without energy evaluation and without host copies.
+ * Resuming with k_begin equal to the previous call's end step continues the
+ * trajectory exactly; the step loop is graph-captured once per range. */
+HSB_API hsb_status hsb_advance_device(hsb_handle h, const hsb_params *p, int R, int steps, int k_begin,
+                              int k_end);
+
+/* Replaces the couplings of the handle by a new instance of the same N (host,
+ * float32, N x N, row-major; validated as in hsb_create).  Device buffers and
+ * captured step loops are kept, so solving many instances of one size pays
+ * the set-up once.  Blocks until the copy is done. */
+HSB_API hsb_status hsb_set_couplings(hsb_handle h, const float *J);
+
+/* Number of kernels the last hsb_run / hsb_run_device / hsb_advance_device
+ * queued on the device. */
+HSB_API hsb_status hsb_run_stats(hsb_handle h, long long *kernel_launches);
+
+/* Waits for the work queued on the handle's stream and reports a device-side
+ * failure of it (HSB_E_TIMEOUT when a bounded wait inside a kernel gave up). */
+HSB_API hsb_status hsb_synchronize(hsb_handle h);
+
+/* Thread-local message of the last failed call on this thread ("" if none). */
+HSB_API const char *hsb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HSB_H */

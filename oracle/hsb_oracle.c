@@ -32,7 +32,9 @@
  *     (no fused multiply-add; build with -ffp-contract=off):
  *       u = c0*f; v = p_k*x; w = u - v; yt = y + w*dt; xt = x + q*yt;
  *       walls; y' = ytt + g*y(t_k)         with q = a0*dt and g = gamma*dt.
- *   - the force sum runs over j in ascending order.  When every coupling is
+ *   - the force sum runs over j in ascending order; in binary64 each term is
+ *     a product and an add, in binary32 each term is one fused multiply-add
+ *     (fmaf, a single rounding).  When every coupling is
  *     -1, 0 or +1 and the form is discrete, the sum is a sum of integers of
  *     magnitude < 2^24 and is formed in int32: the result is the exact sum,
  *     identical to the sequential floating-point sum in either precision.

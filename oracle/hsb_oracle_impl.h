@@ -11,6 +11,19 @@ static REAL SFX(sgn)(REAL x)
     return x >= (REAL)0 ? (REAL)1 : (REAL)-1;
 }
 
+/* One term of the running force sum.  binary64: acc + J*b with two
+ * roundings.  binary32: one fused multiply-add, fmaf(J, b, acc), rounded once
+ * (C99 fmaf is correctly rounded); this is the binary32 reading of the sum. */
+static REAL SFX(accumulate)(REAL acc, REAL jv, REAL b)
+{
+    if (sizeof(REAL) == sizeof(float))
+        return (REAL)fmaf((float)jv, (float)b, (float)acc);
+    {
+        REAL t = jv * b;
+        return acc + t;
+    }
+}
+
 /* Force of one replica: f_i = sum_j J_ij b_j with b_j = x_j (Eq. eq_fb) or
  * b_j = sgn(x_j) (Eq. eq_fd), j ascending.  `Jint` (may be NULL) is the int8
  * copy of +/-1/0 couplings; with it the discrete sum is formed exactly in int32. */
@@ -34,8 +47,7 @@ static void SFX(force)(const REAL *J, const int8_t *Jint, int N, int form,
         REAL acc = (REAL)0;
         for (int j = 0; j < N; ++j) {
             REAL b = form == 1 ? SFX(sgn)(x[j]) : x[j];
-            REAL t = row[j] * b;
-            acc = acc + t;
+            acc = SFX(accumulate)(acc, row[j], b);
         }
         f[i] = acc;
     }

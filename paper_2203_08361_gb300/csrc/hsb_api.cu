@@ -1,0 +1,814 @@
+// hsb_api.cu -- C ABI and host runtime of libhsb (declared in include/hsb.h).
+//
+// Host side of the heated SB run (Kanao & Goto, arXiv 2203.08361): argument
+// validation, coupling conversion, device buffers, the per-run constants
+// (Methods; Results "SB with thermal fluctuation"), and the step loop, which
+// is captured once into a CUDA graph per run shape and replayed.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "hsb.h"
+#include "hsb_internal.cuh"
+
+using namespace hsb;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+hsb_status set_error(hsb_status s, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+hsb_status cuda_error(cudaError_t e, const char *what)
+{
+    if (e == cudaErrorMemoryAllocation)
+        return set_error(HSB_E_NOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return set_error(HSB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess)                           \
+            return cuda_error(e_, what);                 \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess)
+            ok = true;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+// Everything that determines the captured step loop.
+struct GraphKey {
+    int prec, form, R, Rp, steps, eval_every, pm1;
+    float c0, dt, q, g;
+    double a0;
+    uint64_t buffers_gen;
+    bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof *this) == 0; }
+};
+
+struct RunCfg {
+    int prec, form, R, Rp, steps, eval_every;
+    double a0;
+    StepConsts c;
+    std::vector<float> pk;  // p_k = a0 - a(t_k), k = 0..steps-1, rounded once
+};
+
+}  // namespace
+
+struct hsb_ctx {
+    int N = 0, Np = 0, device = 0, pm1 = 0;
+    double sigma = 0.0;
+    cudaStream_t work = nullptr;     // where work is queued (user's or own)
+    cudaStream_t own = nullptr;      // private stream (default work stream, capture stream)
+    float *J32 = nullptr;            // [Np][Np]
+    uint8_t *J8 = nullptr;           // [Np][Np], FP8 e4m3, created on first FP8 run
+    // run buffers, sized for Rcap padded replicas
+    int Rcap = 0;
+    float *X[2] = {nullptr, nullptr};
+    float *Y = nullptr;
+    uint8_t *S8[2] = {nullptr, nullptr};
+    float *Epart = nullptr;
+    double *Ebest = nullptr;
+    double *Efinal = nullptr;
+    int8_t *Sbest = nullptr;
+    int *err = nullptr;
+    uint64_t buffers_gen = 0;
+    TcPlan *plan = nullptr;
+    // graph cache: the whole run, and the step range of hsb_advance_device
+    bool graph_valid = false;
+    GraphKey gkey{};
+    cudaGraphExec_t gexec = nullptr;
+    bool adv_valid = false;
+    GraphKey adv_key{};
+    int adv_k0 = 0, adv_k1 = 0, adv_par = 0;
+    cudaGraphExec_t adv_exec = nullptr;
+    // device state left by the last call, for hsb_get_state / hsb_advance_device
+    int last_R = 0, last_x = 0;  // which X buffer holds x (FP32 path)
+    int state_par = 0;           // ping/pong buffer holding the current state
+    bool have_state = false;
+    long long launches = 0;      // kernels queued by the last run
+};
+
+namespace {
+
+void free_run_buffers(hsb_ctx *h)
+{
+    if (h->plan) {
+        tc_plan_destroy(h->plan);
+        h->plan = nullptr;
+    }
+    cudaFree(h->X[0]);
+    cudaFree(h->X[1]);
+    cudaFree(h->Y);
+    cudaFree(h->S8[0]);
+    cudaFree(h->S8[1]);
+    cudaFree(h->Epart);
+    cudaFree(h->Ebest);
+    cudaFree(h->Efinal);
+    cudaFree(h->Sbest);
+    h->X[0] = h->X[1] = h->Y = nullptr;
+    h->S8[0] = h->S8[1] = nullptr;
+    h->Epart = nullptr;
+    h->Ebest = h->Efinal = nullptr;
+    h->Sbest = nullptr;
+    h->Rcap = 0;
+    h->have_state = false;
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    h->graph_valid = false;
+    if (h->adv_exec) {
+        cudaGraphExecDestroy(h->adv_exec);
+        h->adv_exec = nullptr;
+    }
+    h->adv_valid = false;
+}
+
+hsb_status ensure_buffers(hsb_ctx *h, int Rp, int R)
+{
+    // Every buffer is sized for Rcap >= Rp >= R padded replicas.
+    (void)R;
+    if (Rp <= h->Rcap && h->X[0])
+        return HSB_OK;
+    free_run_buffers(h);
+    const size_t elems = (size_t)Rp * h->Np;
+    CK(cudaMalloc(&h->X[0], elems * sizeof(float)), "cudaMalloc X");
+    CK(cudaMalloc(&h->X[1], elems * sizeof(float)), "cudaMalloc X");
+    CK(cudaMalloc(&h->Y, elems * sizeof(float)), "cudaMalloc Y");
+    CK(cudaMalloc(&h->S8[0], elems), "cudaMalloc S8");
+    CK(cudaMalloc(&h->S8[1], elems), "cudaMalloc S8");
+    CK(cudaMalloc(&h->Epart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Epart");
+    CK(cudaMalloc(&h->Ebest, (size_t)Rp * sizeof(double)), "cudaMalloc Ebest");
+    CK(cudaMalloc(&h->Efinal, (size_t)Rp * sizeof(double)), "cudaMalloc Efinal");
+    CK(cudaMalloc(&h->Sbest, (size_t)Rp * h->N), "cudaMalloc Sbest");
+    h->Rcap = Rp;
+    h->buffers_gen++;
+    return HSB_OK;
+}
+
+hsb_status ensure_fp8(hsb_ctx *h)
+{
+    if (!h->J8) {
+        CK(cudaMalloc(&h->J8, (size_t)h->Np * h->Np), "cudaMalloc J8");
+        CK(launch_j_to_fp8(h->work, h->J32, h->Np, h->J8), "j_to_fp8");
+    }
+    if (!h->plan) {
+        CK(tc_fp8_plan_create(&h->plan, h->J8, h->S8[0], h->S8[1], h->Np, h->Rcap),
+           "tc_fp8_plan_create");
+    }
+    return HSB_OK;
+}
+
+hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunCfg *cfg)
+{
+    if (!p)
+        return set_error(HSB_E_INVAL, "params is NULL");
+    if (R < 1)
+        return set_error(HSB_E_INVAL, "R must be >= 1 (got %d)", R);
+    if (steps < 1)
+        return set_error(HSB_E_INVAL, "steps must be >= 1 (got %d)", steps);
+    if (p->form != HSB_BALLISTIC && p->form != HSB_DISCRETE)
+        return set_error(HSB_E_INVAL, "form must be HSB_BALLISTIC or HSB_DISCRETE");
+    if (!(p->a0 > 0.0) || !(p->dt > 0.0) || !(p->gamma >= 0.0) || !(p->init_half_width > 0.0))
+        return set_error(HSB_E_INVAL, "need a0 > 0, dt > 0, gamma >= 0, init_half_width > 0");
+    if (!(p->c0 > 0.0) && !(p->c1 > 0.0))
+        return set_error(HSB_E_INVAL, "need c0 > 0 or c1 > 0");
+    if (p->eval_every < 0 || p->trace_every != 0)
+        return set_error(HSB_E_INVAL, "eval_every must be >= 0 and trace_every 0");
+    if ((long long)R * h->N > (1LL << 40))
+        return set_error(HSB_E_INVAL, "R*N too large");
+    int prec = p->prec;
+    if (prec == HSB_PREC_AUTO)
+        prec = (p->form == HSB_DISCRETE && h->pm1) ? HSB_PREC_FP8 : HSB_PREC_FP32;
+    if (prec == HSB_PREC_FP8 && !(p->form == HSB_DISCRETE && h->pm1))
+        return set_error(HSB_E_UNSUPPORTED,
+                         "FP8 needs the discrete form and couplings in {-1, 0, +1}");
+    if (prec == HSB_PREC_BF16X3)
+        return set_error(HSB_E_UNSUPPORTED, "BF16X3 precision is not available in this build");
+    if (prec != HSB_PREC_FP32 && prec != HSB_PREC_FP8)
+        return set_error(HSB_E_INVAL, "unknown precision %d", p->prec);
+    cfg->prec = prec;
+    cfg->form = p->form;
+    cfg->R = R;
+    cfg->Rp = round_up(R, kTileR);
+    cfg->steps = steps;
+    cfg->eval_every = p->eval_every;
+    cfg->a0 = p->a0;
+    // c0 = c1 / (sqrt(N) sigma_J) (Results; sigma_J = 1 for +/-1 couplings)
+    const double c0 = p->c0 > 0.0 ? p->c0 : p->c1 / (sqrt((double)h->N) * h->sigma);
+    cfg->c.c0 = (float)c0;
+    cfg->c.dt = (float)p->dt;
+    cfg->c.q = (float)(p->a0 * p->dt);
+    cfg->c.g = (float)(p->gamma * p->dt);
+    cfg->pk.resize(steps);
+    for (int k = 0; k < steps; ++k) {
+        // a(t_k) = a0 k / Ns, linear from 0 to a0 (Results); p_k = a0 - a(t_k)
+        double t = p->a0 * (double)k;
+        t = t / (double)steps;
+        cfg->pk[k] = (float)(p->a0 - t);
+    }
+    return HSB_OK;
+}
+
+bool is_eval_step(const RunCfg &c, int k)
+{
+    return c.eval_every > 0 && k > 0 && k < c.steps && k % c.eval_every == 0;
+}
+
+// One step k of the loop (update from t_k to t_{k+1}); evaluates E(t_k) first
+// when k is an evaluation step.  `cur` selects the ping/pong buffer holding
+// the state at t_k (X for the FP32 path, the FP8 operand S8 otherwise).
+hsb_status enqueue_step(hsb_ctx *h, cudaStream_t st, const RunCfg &c, int k, int cur,
+                        bool allow_eval)
+{
+    const bool ev = allow_eval && is_eval_step(c, k);
+    const int nblk = h->Np / kTileM;
+    if (c.prec == HSB_PREC_FP32) {
+        if (ev && c.form == HSB_BALLISTIC)
+            CK(launch_simt_step(st, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[cur], nullptr,
+                                h->Y, 0.f, c.c, h->Epart),
+               "energy kernel");
+        CK(launch_simt_step(st, c.form, false, ev && c.form == HSB_DISCRETE, h->J32, h->N, h->Np,
+                            c.Rp, h->X[cur], h->X[cur ^ 1], h->Y, c.pk[k], c.c, h->Epart),
+           "fp32 step kernel");
+        if (ev)
+            CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[cur], nullptr,
+                                  h->Ebest, h->Sbest),
+               "best kernel");
+    } else {  // FP8: S8[cur] -> S8[cur^1], X and Y in place
+        CK(launch_tc_fp8_step(st, h->plan, cur, ev, false, h->N, h->X[0], h->Y, c.pk[k], c.c,
+                              h->Epart, h->S8[cur ^ 1], h->err),
+           "fp8 step kernel");
+        if (ev)
+            CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, h->S8[cur],
+                                  h->Ebest, h->Sbest),
+               "best kernel");
+    }
+    return HSB_OK;
+}
+
+// Final evaluation at t_steps, best update and (general J) binary64 energies.
+hsb_status enqueue_final(hsb_ctx *h, cudaStream_t st, const RunCfg &c)
+{
+    const int nblk = h->Np / kTileM;
+    const int cur = c.steps & 1;
+    if (c.prec == HSB_PREC_FP32) {
+        CK(launch_simt_step(st, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[cur], nullptr,
+                            h->Y, 0.f, c.c, h->Epart),
+           "energy kernel");
+        CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[cur], nullptr,
+                              h->Ebest, h->Sbest),
+           "best kernel");
+    } else {
+        CK(launch_tc_fp8_step(st, h->plan, cur, true, true, h->N, h->X[0], h->Y, 0.f, c.c,
+                              h->Epart, nullptr, h->err),
+           "fp8 energy kernel");
+        CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, h->S8[cur],
+                              h->Ebest, h->Sbest),
+           "best kernel");
+    }
+    if (!h->pm1)
+        CK(launch_final_energy_f64(st, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efinal),
+           "final energy kernel");
+    return HSB_OK;
+}
+
+// Kernels one run queues: init, the steps, the energy evaluations of the
+// ballistic form, the best updates, the final evaluation and (general J) the
+// binary64 energies.
+long long count_launches(const hsb_ctx *h, const RunCfg &c)
+{
+    long long evals = c.eval_every > 0 ? (c.steps - 1) / c.eval_every : 0;
+    long long n = 1 + c.steps + evals /* best */ + 2 /* final energy + best */;
+    if (c.form == HSB_BALLISTIC && c.prec == HSB_PREC_FP32)
+        n += evals;
+    if (!h->pm1)
+        n += 1;
+    return n;
+}
+
+hsb_status build_graph(hsb_ctx *h, const RunCfg &c, const GraphKey &key)
+{
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    h->graph_valid = false;
+    CK(cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal), "begin capture");
+    hsb_status s = HSB_OK;
+    for (int k = 0; k < c.steps && s == HSB_OK; ++k)
+        s = enqueue_step(h, h->own, c, k, k & 1, true);
+    if (s == HSB_OK)
+        s = enqueue_final(h, h->own, c);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->own, &graph);
+    if (s != HSB_OK) {
+        if (graph)
+            cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess)
+        return cuda_error(e, "end capture");
+    e = cudaGraphInstantiate(&h->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess)
+        return cuda_error(e, "graph instantiate");
+    h->gkey = key;
+    h->graph_valid = true;
+    return HSB_OK;
+}
+
+hsb_status prepare(hsb_ctx *h, const RunCfg &c)
+{
+    hsb_status s = ensure_buffers(h, c.Rp, c.R);
+    if (s != HSB_OK)
+        return s;
+    if (c.prec == HSB_PREC_FP8) {
+        s = ensure_fp8(h);
+        if (s != HSB_OK)
+            return s;
+    }
+    return HSB_OK;
+}
+
+GraphKey make_key(const hsb_ctx *h, const RunCfg &c);
+
+// Queues a whole run (init, graph of the step loop) on the work stream.
+hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_params *p)
+{
+    hsb_status s = prepare(h, c);
+    if (s != HSB_OK)
+        return s;
+    const GraphKey key = make_key(h, c);
+    if (!h->graph_valid || !(h->gkey == key)) {
+        s = build_graph(h, c, key);
+        if (s != HSB_OK)
+            return s;
+    }
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->work), "memset err");
+    CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R, c.Rp,
+                   h->X[0], h->Y, c.prec == HSB_PREC_FP8 ? h->S8[0] : nullptr, h->Ebest),
+       "init kernel");
+    CK(cudaGraphLaunch(h->gexec, h->work), "graph launch");
+    h->last_R = c.R;
+    h->last_x = c.prec == HSB_PREC_FP32 ? (c.steps & 1) : 0;
+    h->state_par = c.steps & 1;
+    h->have_state = true;
+    h->launches = count_launches(h, c);
+    return HSB_OK;
+}
+
+GraphKey make_key(const hsb_ctx *h, const RunCfg &c)
+{
+    GraphKey key;
+    memset(&key, 0, sizeof key);
+    key.prec = c.prec;
+    key.form = c.form;
+    key.R = c.R;
+    key.Rp = c.Rp;
+    key.steps = c.steps;
+    key.eval_every = c.eval_every;
+    key.pm1 = h->pm1;
+    key.c0 = c.c.c0;
+    key.dt = c.c.dt;
+    key.q = c.c.q;
+    key.g = c.c.g;
+    key.a0 = c.a0;
+    key.buffers_gen = h->buffers_gen;
+    return key;
+}
+
+hsb_status check_device_error(hsb_ctx *h)
+{
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->work), "read err");
+    CK(cudaStreamSynchronize(h->work), "synchronize");
+    if (e == kErrTimeout)
+        return set_error(HSB_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (e != 0)
+        return set_error(HSB_E_CUDA, "device error code %d", e);
+    return HSB_OK;
+}
+
+}  // namespace
+
+// =================================================================== ABI ===
+
+extern "C" {
+
+int hsb_version(void) { return HSB_API_VERSION; }
+
+const char *hsb_last_error(void) { return g_last_error.c_str(); }
+
+hsb_status hsb_params_default(hsb_params *p)
+{
+    if (!p)
+        return set_error(HSB_E_INVAL, "params is NULL");
+    memset(p, 0, sizeof *p);
+    p->form = HSB_DISCRETE;
+    p->prec = HSB_PREC_AUTO;
+    p->a0 = 1.0;
+    p->c1 = 0.7;
+    p->c0 = 0.0;
+    p->dt = 1.1;
+    p->gamma = 0.06;
+    p->init_half_width = 1.0;
+    p->eval_every = 100;
+    p->trace_every = 0;
+    p->instance = 0;
+    return HSB_OK;
+}
+
+hsb_status hsb_create(const float *J, int N, hsb_handle *out)
+{
+    if (!out)
+        return set_error(HSB_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (!J)
+        return set_error(HSB_E_INVAL, "J is NULL");
+    if (N < 2 || N > (1 << 20))
+        return set_error(HSB_E_INVAL, "N must be in [2, 2^20] (got %d)", N);
+    // Eq. (eq_Ising): J_ij = J_ji and J_ii = 0.
+    int pm1 = 1;
+    double sum2 = 0.0;
+    for (int i = 0; i < N; ++i) {
+        if (J[(size_t)i * N + i] != 0.0f)
+            return set_error(HSB_E_DIAG, "J[%d][%d] = %g is not zero", i, i,
+                             (double)J[(size_t)i * N + i]);
+        for (int j = 0; j < N; ++j) {
+            const float v = J[(size_t)i * N + j];
+            if (!(v == J[(size_t)j * N + i]))
+                return set_error(HSB_E_ASYM, "J[%d][%d] != J[%d][%d]", i, j, j, i);
+            if (!(v == 1.0f || v == -1.0f || v == 0.0f))
+                pm1 = 0;
+            // sigma_J^2 = sum_ij J_ij^2 / (N(N-1)), summed row by row in binary64
+            const double d = (double)v;
+            sum2 += d * d;
+        }
+    }
+    if (!(sum2 > 0.0))
+        return set_error(HSB_E_INVAL, "J is all zero");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return set_error(HSB_E_NODEVICE, "no CUDA device");
+    }
+    hsb_ctx *h = new hsb_ctx();
+    cudaGetDevice(&h->device);
+    h->N = N;
+    h->Np = round_up(N, kTileM);
+    h->pm1 = pm1;
+    h->sigma = sqrt(sum2 / ((double)N * (double)(N - 1)));
+    hsb_status s = HSB_OK;
+    do {
+        cudaError_t e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            s = cuda_error(e, "stream create");
+            break;
+        }
+        h->work = h->own;
+        e = cudaMalloc(&h->err, sizeof(int));
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(h->err, 0, sizeof(int), h->work);
+        if (e != cudaSuccess) {
+            s = cuda_error(e, "cudaMalloc err");
+            break;
+        }
+        const size_t np = (size_t)h->Np;
+        e = cudaMalloc(&h->J32, np * np * sizeof(float));
+        if (e != cudaSuccess) {
+            s = cuda_error(e, "cudaMalloc J");
+            break;
+        }
+        e = cudaMemsetAsync(h->J32, 0, np * np * sizeof(float), h->work);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(h->J32, np * sizeof(float), J, (size_t)N * sizeof(float),
+                                  (size_t)N * sizeof(float), (size_t)N, cudaMemcpyHostToDevice,
+                                  h->work);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(h->work);
+        if (e != cudaSuccess) {
+            s = cuda_error(e, "copy J");
+            break;
+        }
+    } while (0);
+    if (s != HSB_OK) {
+        hsb_destroy(h);
+        return s;
+    }
+    *out = h;
+    return HSB_OK;
+}
+
+void hsb_destroy(hsb_handle h)
+{
+    if (!h)
+        return;
+    DeviceGuard g(h->device);
+    if (h->work)
+        cudaStreamSynchronize(h->work);
+    free_run_buffers(h);
+    cudaFree(h->J32);
+    cudaFree(h->J8);
+    cudaFree(h->err);
+    if (h->own)
+        cudaStreamDestroy(h->own);
+    delete h;
+}
+
+hsb_status hsb_set_stream(hsb_handle h, void *cuda_stream)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    h->work = cuda_stream ? (cudaStream_t)cuda_stream : h->own;
+    return HSB_OK;
+}
+
+hsb_status hsb_info(hsb_handle h, int *N, int *is_pm1)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (N)
+        *N = h->N;
+    if (is_pm1)
+        *is_pm1 = h->pm1;
+    return HSB_OK;
+}
+
+hsb_status hsb_run_device(hsb_handle h, const hsb_params *p, int R, int steps, uint64_t seed,
+                          int8_t *best_spins, double *best_energy)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (!best_spins || !best_energy)
+        return set_error(HSB_E_INVAL, "output pointer is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok)
+        return set_error(HSB_E_NODEVICE, "cannot select the handle's device");
+    RunCfg c;
+    hsb_status s = resolve(h, p, R, steps, &c);
+    if (s != HSB_OK)
+        return s;
+    s = enqueue_run(h, c, seed, p);
+    if (s != HSB_OK)
+        return s;
+    CK(cudaMemcpyAsync(best_spins, h->Sbest, (size_t)R * h->N, cudaMemcpyDeviceToDevice, h->work),
+       "copy spins");
+    CK(cudaMemcpyAsync(best_energy, h->pm1 ? h->Ebest : h->Efinal, (size_t)R * sizeof(double),
+                       cudaMemcpyDeviceToDevice, h->work),
+       "copy energies");
+    return HSB_OK;
+}
+
+hsb_status hsb_run(hsb_handle h, const hsb_params *p, int R, int steps, uint64_t seed,
+                   int8_t *best_spins, double *best_energy)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (!best_spins || !best_energy)
+        return set_error(HSB_E_INVAL, "output pointer is NULL");
+    DeviceGuard g(h->device);
+    if (!g.ok)
+        return set_error(HSB_E_NODEVICE, "cannot select the handle's device");
+    RunCfg c;
+    hsb_status s = resolve(h, p, R, steps, &c);
+    if (s != HSB_OK)
+        return s;
+    s = enqueue_run(h, c, seed, p);
+    if (s != HSB_OK)
+        return s;
+    CK(cudaMemcpyAsync(best_spins, h->Sbest, (size_t)R * h->N, cudaMemcpyDeviceToHost, h->work),
+       "copy spins");
+    CK(cudaMemcpyAsync(best_energy, h->pm1 ? h->Ebest : h->Efinal, (size_t)R * sizeof(double),
+                       cudaMemcpyDeviceToHost, h->work),
+       "copy energies");
+    return check_device_error(h);
+}
+
+hsb_status hsb_get_state(hsb_handle h, float *x, float *y)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (!h->have_state)
+        return set_error(HSB_E_INVAL, "no run on this handle yet");
+    DeviceGuard g(h->device);
+    const size_t row = (size_t)h->N * sizeof(float);
+    const size_t pitch = (size_t)h->Np * sizeof(float);
+    if (x)
+        CK(cudaMemcpy2DAsync(x, row, h->X[h->last_x], pitch, row, (size_t)h->last_R,
+                             cudaMemcpyDeviceToHost, h->work),
+           "copy x");
+    if (y)
+        CK(cudaMemcpy2DAsync(y, row, h->Y, pitch, row, (size_t)h->last_R, cudaMemcpyDeviceToHost,
+                             h->work),
+           "copy y");
+    CK(cudaStreamSynchronize(h->work), "synchronize");
+    return HSB_OK;
+}
+
+hsb_status hsb_advance(hsb_handle h, const hsb_params *p, int R, int steps, int k_begin,
+                       int k_end, float *x, float *y)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (!x || !y)
+        return set_error(HSB_E_INVAL, "state pointer is NULL");
+    if (k_begin < 0 || k_end < k_begin || k_end > steps)
+        return set_error(HSB_E_INVAL, "need 0 <= k_begin <= k_end <= steps");
+    DeviceGuard g(h->device);
+    if (!g.ok)
+        return set_error(HSB_E_NODEVICE, "cannot select the handle's device");
+    RunCfg c;
+    hsb_status s = resolve(h, p, R, steps, &c);
+    if (s != HSB_OK)
+        return s;
+    s = prepare(h, c);
+    if (s != HSB_OK)
+        return s;
+    const size_t row = (size_t)h->N * sizeof(float);
+    const size_t pitch = (size_t)h->Np * sizeof(float);
+    const size_t elems = (size_t)c.Rp * h->Np;
+    // FP32 path: step k reads X[k & 1]; FP8 path: X[0] in place, S8[k & 1].
+    const int xin = c.prec == HSB_PREC_FP32 ? (k_begin & 1) : 0;
+    CK(cudaMemsetAsync(h->X[xin], 0, elems * sizeof(float), h->work), "memset x");
+    CK(cudaMemsetAsync(h->Y, 0, elems * sizeof(float), h->work), "memset y");
+    CK(cudaMemcpy2DAsync(h->X[xin], pitch, x, row, row, (size_t)R, cudaMemcpyHostToDevice,
+                         h->work),
+       "copy x");
+    CK(cudaMemcpy2DAsync(h->Y, pitch, y, row, row, (size_t)R, cudaMemcpyHostToDevice, h->work),
+       "copy y");
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->work), "memset err");
+    if (c.prec == HSB_PREC_FP8)
+        CK(launch_sign_to_fp8(h->work, h->X[0], h->N, h->Np, c.Rp, h->S8[k_begin & 1]),
+           "sign kernel");
+    for (int k = k_begin; k < k_end; ++k) {
+        s = enqueue_step(h, h->work, c, k, k & 1, false);
+        if (s != HSB_OK)
+            return s;
+    }
+    const int xout = c.prec == HSB_PREC_FP32 ? (k_end & 1) : 0;
+    CK(cudaMemcpy2DAsync(x, row, h->X[xout], pitch, row, (size_t)R, cudaMemcpyDeviceToHost,
+                         h->work),
+       "copy x back");
+    CK(cudaMemcpy2DAsync(y, row, h->Y, pitch, row, (size_t)R, cudaMemcpyDeviceToHost, h->work),
+       "copy y back");
+    h->have_state = false;
+    return check_device_error(h);
+}
+
+hsb_status hsb_advance_device(hsb_handle h, const hsb_params *p, int R, int steps, int k_begin,
+                              int k_end)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (k_begin < 0 || k_end < k_begin || k_end > steps)
+        return set_error(HSB_E_INVAL, "need 0 <= k_begin <= k_end <= steps");
+    DeviceGuard g(h->device);
+    if (!g.ok)
+        return set_error(HSB_E_NODEVICE, "cannot select the handle's device");
+    RunCfg c;
+    hsb_status s = resolve(h, p, R, steps, &c);
+    if (s != HSB_OK)
+        return s;
+    if (!h->have_state || h->last_R != R || c.Rp > h->Rcap)
+        return set_error(HSB_E_INVAL, "no device state of %d replicas on this handle", R);
+    s = prepare(h, c);
+    if (s != HSB_OK)
+        return s;
+    const GraphKey key = make_key(h, c);
+    const int par = h->state_par;
+    if (!h->adv_valid || !(h->adv_key == key) || h->adv_k0 != k_begin || h->adv_k1 != k_end ||
+        h->adv_par != par) {
+        if (h->adv_exec) {
+            cudaGraphExecDestroy(h->adv_exec);
+            h->adv_exec = nullptr;
+        }
+        h->adv_valid = false;
+        CK(cudaStreamBeginCapture(h->own, cudaStreamCaptureModeThreadLocal), "begin capture");
+        for (int k = k_begin; k < k_end && s == HSB_OK; ++k)
+            s = enqueue_step(h, h->own, c, k, (par + (k - k_begin)) & 1, false);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(h->own, &graph);
+        if (s != HSB_OK) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            return s;
+        }
+        if (e != cudaSuccess)
+            return cuda_error(e, "end capture");
+        e = cudaGraphInstantiate(&h->adv_exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess)
+            return cuda_error(e, "graph instantiate");
+        h->adv_key = key;
+        h->adv_k0 = k_begin;
+        h->adv_k1 = k_end;
+        h->adv_par = par;
+        h->adv_valid = true;
+    }
+    if (k_end > k_begin)
+        CK(cudaGraphLaunch(h->adv_exec, h->work), "graph launch");
+    const int n = k_end - k_begin;
+    h->state_par = (par + n) & 1;
+    if (c.prec == HSB_PREC_FP32)
+        h->last_x = h->state_par;
+    h->launches = n;
+    return HSB_OK;
+}
+
+hsb_status hsb_set_couplings(hsb_handle h, const float *J)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (!J)
+        return set_error(HSB_E_INVAL, "J is NULL");
+    const int N = h->N;
+    int pm1 = 1;
+    double sum2 = 0.0;
+    for (int i = 0; i < N; ++i) {
+        if (J[(size_t)i * N + i] != 0.0f)
+            return set_error(HSB_E_DIAG, "J[%d][%d] = %g is not zero", i, i,
+                             (double)J[(size_t)i * N + i]);
+        for (int j = 0; j < N; ++j) {
+            const float v = J[(size_t)i * N + j];
+            if (!(v == J[(size_t)j * N + i]))
+                return set_error(HSB_E_ASYM, "J[%d][%d] != J[%d][%d]", i, j, j, i);
+            if (!(v == 1.0f || v == -1.0f || v == 0.0f))
+                pm1 = 0;
+            const double d = (double)v;
+            sum2 += d * d;
+        }
+    }
+    if (!(sum2 > 0.0))
+        return set_error(HSB_E_INVAL, "J is all zero");
+    DeviceGuard g(h->device);
+    if (!g.ok)
+        return set_error(HSB_E_NODEVICE, "cannot select the handle's device");
+    const size_t np = (size_t)h->Np;
+    CK(cudaMemcpy2DAsync(h->J32, np * sizeof(float), J, (size_t)N * sizeof(float),
+                         (size_t)N * sizeof(float), (size_t)N, cudaMemcpyHostToDevice, h->work),
+       "copy J");
+    h->pm1 = pm1;
+    h->sigma = sqrt(sum2 / ((double)N * (double)(N - 1)));
+    if (h->J8) {
+        if (pm1) {
+            CK(launch_j_to_fp8(h->work, h->J32, h->Np, h->J8), "j_to_fp8");
+        } else {
+            if (h->plan) {
+                tc_plan_destroy(h->plan);
+                h->plan = nullptr;
+            }
+            cudaFree(h->J8);
+            h->J8 = nullptr;
+        }
+    }
+    CK(cudaStreamSynchronize(h->work), "synchronize");
+    return HSB_OK;
+}
+
+hsb_status hsb_run_stats(hsb_handle h, long long *kernel_launches)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (kernel_launches)
+        *kernel_launches = h->launches;
+    return HSB_OK;
+}
+
+hsb_status hsb_synchronize(hsb_handle h)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    DeviceGuard g(h->device);
+    return check_device_error(h);
+}
+
+}  // extern "C"

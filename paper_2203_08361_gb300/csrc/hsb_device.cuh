@@ -1,0 +1,78 @@
+// hsb_device.cuh -- device helpers shared by the kernels of libhsb: the
+// counter-based initial-state generator, the FP8 sign encoding and the fused
+// spin update of the Methods section.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hsb_internal.cuh"
+
+namespace hsb {
+
+// FP8 e4m3 encodings of +1 and -1 (sign 0/1, biased exponent 7, mantissa 0).
+constexpr uint8_t kFp8PlusOne = 0x38;
+constexpr uint8_t kFp8MinusOne = 0xB8;
+
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): output number n (n >= 1) of
+// the generator started from `state` is the finaliser of state + n * GAMMA.
+__device__ __forceinline__ uint64_t splitmix64_out(uint64_t state, uint64_t n)
+{
+    uint64_t z = state + n * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+// Uniform value in (-L, L): draw u = output (1 + r*2^32 + 2i + comp) of the
+// instance stream, m = top 24 bits, value = fl32((2m + 1 - 2^24) * scale)
+// with scale = fl32(L * 2^-24).  2m + 1 - 2^24 is an odd integer below 2^24
+// in magnitude, exact in binary32, so the value takes one rounding.
+__device__ __forceinline__ float init_uniform(uint64_t s_inst, uint32_t r, uint32_t i, int comp,
+                                              float scale)
+{
+    const uint64_t n = 1u + ((uint64_t)r << 32) + 2u * (uint64_t)i + (uint64_t)comp;
+    const uint64_t u = splitmix64_out(s_inst, n);
+    const int m = (int)(u >> 40);
+    const float v = (float)(2 * m + 1 - 16777216);
+    return __fmul_rn(v, scale);
+}
+
+// sgn(x) as an FP8 byte; +1 for x >= 0 (including -0.0).
+__device__ __forceinline__ uint8_t fp8_sign(float x)
+{
+    return x >= 0.f ? kFp8PlusOne : kFp8MinusOne;
+}
+
+// One spin update (Methods):
+//   y~  = y + {-(a0 - a(t_k)) x + c0 f} dt        Eq. (eq_SyEuY)
+//   x~  = x + a0 y~ dt                             Eq. (eq_SyEuX)
+//   x'  = g(x~), y~~ = h(x~, y~)                   Eqs. (eq_WallX), (eq_WallY)
+//   y'  = y~~ + gamma y(t_k) dt                    Eq. (eq_EuHeat)
+// Every operation is one binary32 rounding in this fixed order (no fused
+// multiply-add): u = c0 f; v = p_k x; w = u - v; yt = y + w dt; xt = x + q yt;
+// walls (strict |x~| > 1); y' = ytt + g y(t_k).
+__device__ __forceinline__ void sb_update(float f, float x0, float y0, float pk,
+                                          const StepConsts &c, float &xn, float &yn)
+{
+    const float u = __fmul_rn(c.c0, f);
+    const float v = __fmul_rn(pk, x0);
+    const float w = __fsub_rn(u, v);
+    const float wd = __fmul_rn(w, c.dt);
+    const float yt = __fadd_rn(y0, wd);
+    const float qy = __fmul_rn(c.q, yt);
+    const float xt = __fadd_rn(x0, qy);
+    float ytt = yt;
+    xn = xt;
+    if (xt > 1.f) {
+        xn = 1.f;
+        ytt = 0.f;
+    } else if (xt < -1.f) {
+        xn = -1.f;
+        ytt = 0.f;
+    }
+    const float gy = __fmul_rn(c.g, y0);
+    yn = __fadd_rn(ytt, gy);
+}
+
+}  // namespace hsb

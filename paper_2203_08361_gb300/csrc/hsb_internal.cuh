@@ -1,0 +1,81 @@
+// hsb_internal.cuh -- declarations shared by the translation units of libhsb.
+//
+// Device layout (all buffers padded; Np = N rounded up to 128, Rp = R rounded
+// up to 128; padded spins have zero couplings and zero state):
+//   J32  [Np][Np] float32    couplings (final energies, FP32 path)
+//   J8   [Np][Np] uint8      FP8 e4m3 couplings (+1 = 0x38, -1 = 0xB8, 0 = 0x00)
+//   X[b] [Rp][Np] float32    positions, one replica per row (b = ping/pong
+//                            buffer for the FP32 path, which reads x of every
+//                            spin while it writes the next step)
+//   Y    [Rp][Np] float32    momenta (updated in place by the owning thread)
+//   S8[b][Rp][Np] uint8      sgn(x) in FP8, the tensor-core B operand
+//   Epart[Np/128][Rp] float  per row-block partial sums of s_i f_i
+//   Ebest[R] double, Sbest[R][N] int8   best energy / spins so far
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hsb {
+
+constexpr int kTileM = 128;  // spins per row block
+constexpr int kTileR = 128;  // replica padding granule
+
+// Scalar constants of one run, each rounded once from binary64 to binary32
+// (c0, dt, q = a0*dt, g = gamma*dt).  p_k is passed per step.
+struct StepConsts {
+    float c0;
+    float dt;
+    float q;
+    float g;
+};
+
+// Error word written by kernels whose bounded waits gave up.
+enum : int { kErrNone = 0, kErrTimeout = 1, kErrBadLaunch = 2 };
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// ---- hsb_simt.cu -------------------------------------------------------
+// Initial state (Results: x_i, y_i uniform in (-L, L)); also the FP8 operand
+// S8 = sgn(x0) when s8 != nullptr.  Ebest <- +inf.
+cudaError_t launch_init(cudaStream_t st, uint64_t seed, uint32_t instance, float half_width,
+                        int N, int Np, int R, int Rp, float *X, float *Y, uint8_t *S8,
+                        double *Ebest);
+
+// One plain-FP32 step (force by fused multiply-adds over j ascending, then the
+// pinned update).  energy != 0 also writes Epart from s(t_k) and f (discrete
+// form only).  energy_only computes Epart for s = sgn(Xcur) without updating.
+cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool energy,
+                             const float *J32, int N, int Np, int Rp, const float *Xcur,
+                             float *Xnext, float *Y, float pk, StepConsts c, float *Epart);
+
+// Best tracking after an evaluation: E_r = -1/2 sum_blocks Epart; if E_r <
+// Ebest[r] store it with the spins sgn(x) read from X (fp32) or S8 (fp8).
+cudaError_t launch_best_update(cudaStream_t st, const float *Epart, int nblk, int N, int Np,
+                               int R, int Rp, const float *X, const uint8_t *S8,
+                               double *Ebest, int8_t *Sbest);
+
+// Energy of the final best spins in binary64 (Eq. (eq_Ising)) for general J.
+cudaError_t launch_final_energy_f64(cudaStream_t st, const float *J32, int N, int Np, int R,
+                                    const int8_t *Sbest, double *Eout);
+
+// sgn(X) -> FP8 operand (used when a state is loaded from the host).
+cudaError_t launch_sign_to_fp8(cudaStream_t st, const float *X, int N, int Np, int Rp,
+                               uint8_t *S8);
+
+// float32 couplings -> FP8 e4m3 (+/-1/0 only).
+cudaError_t launch_j_to_fp8(cudaStream_t st, const float *J32, int Np, uint8_t *J8);
+
+// ---- hsb_tc.cu -----------------------------------------------------------
+// tcgen05 FP8 step: F = J8 * S8cur^T on the tensor cores (FP32 accumulation
+// in tensor memory), fused update; writes S8next, X and Y in place, and Epart
+// on evaluation steps.  Requires Np % 128 == 0 and Rp % 128 == 0.
+struct TcPlan;  // opaque per-shape launch plan (tensor maps)
+cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S8a,
+                               const uint8_t *S8b, int Np, int Rp);
+void tc_plan_destroy(TcPlan *p);
+cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
+                               bool energy_only, int N, float *X, float *Y, float pk,
+                               StepConsts c, float *Epart, uint8_t *S8next, int *err);
+
+}  // namespace hsb

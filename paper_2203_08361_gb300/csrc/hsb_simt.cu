@@ -1,0 +1,350 @@
+// hsb_simt.cu -- CUDA-core kernels of libhsb: seeded initial state, the plain
+// FP32 step (the comparison form), energy evaluation, best tracking, the
+// binary64 final energy and operand conversions.
+//
+// Paper: Kanao & Goto, arXiv 2203.08361.  Methods, Eqs. (eq_SyEuY),
+// (eq_SyEuX), (eq_WallX), (eq_WallY), (eq_EuHeat); forces Eqs. (eq_fb),
+// (eq_fd); energy Eq. (eq_Ising).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hsb_device.cuh"
+#include "hsb_internal.cuh"
+
+namespace hsb {
+
+// ------------------------------------------------------------------ init ---
+
+// x_i, y_i uniform in (-L, L) (Results, "SB with thermal fluctuation"), drawn
+// from a counter-based SplitMix64 stream so that replica r's values depend on
+// (seed, instance, r, i) only.
+__global__ void init_kernel(uint64_t seed, uint32_t instance, float scale, int N, int Np, int R,
+                            int Rp, float *__restrict__ X, float *__restrict__ Y,
+                            uint8_t *__restrict__ S8, double *__restrict__ Ebest)
+{
+    const size_t total = (size_t)Rp * Np;
+    const uint64_t s_inst = splitmix64_out(seed, (uint64_t)instance + 1u);
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t r = (uint32_t)(e / Np);
+        const uint32_t i = (uint32_t)(e % Np);
+        float x = 0.f, y = 0.f;
+        uint8_t s = 0;
+        if ((int)i < N) {
+            x = init_uniform(s_inst, r, i, 0, scale);
+            y = init_uniform(s_inst, r, i, 1, scale);
+            s = fp8_sign(x);
+        }
+        X[e] = x;
+        Y[e] = y;
+        if (S8)
+            S8[e] = s;
+        if (e < (size_t)R)
+            Ebest[e] = INFINITY;
+    }
+}
+
+cudaError_t launch_init(cudaStream_t st, uint64_t seed, uint32_t instance, float half_width,
+                        int N, int Np, int R, int Rp, float *X, float *Y, uint8_t *S8,
+                        double *Ebest)
+{
+    // scale = fl32(L * 2^-24), one rounding from binary64
+    const float scale = (float)((double)half_width / 16777216.0);
+    const size_t total = (size_t)Rp * Np;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    init_kernel<<<blocks, 256, 0, st>>>(seed, instance, scale, N, Np, R, Rp, X, Y, S8, Ebest);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- plain FP32 step ---
+//
+// Tile: 128 spins (rows of J) x 128 replicas, 256 threads, 8 x 8 outputs per
+// thread, K slices of 8 double-buffered in shared memory.  Every output keeps
+// one accumulator updated by fmaf over k ascending, the binary32 reading of
+// the force sum.  B operand element (r, k) is x_k of replica r (ballistic) or
+// sgn(x_k) (discrete and energy evaluation), formed while staging the tile.
+
+template <int FORM, bool ENERGY_ONLY>
+__global__ void __launch_bounds__(256, 1)
+simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
+                 const float *__restrict__ Xcur, float *__restrict__ Xnext,
+                 float *__restrict__ Y, float pk, StepConsts c, int energy,
+                 float *__restrict__ Epart)
+{
+    constexpr bool kSign = (FORM == 1) || ENERGY_ONLY;
+    __shared__ __align__(16) float As[2][8][128];
+    __shared__ __align__(16) float Bs[2][8][128];
+    __shared__ float Ered[16][129];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15;
+    const int ty = tid >> 4;
+    const int m0 = blockIdx.x * 128;
+    const int r0 = blockIdx.y * 128;
+
+    const int lrow = tid >> 1;
+    const int lk = (tid & 1) * 4;
+    const float *Ap = J + (size_t)(m0 + lrow) * Np + lk;
+    const float *Bp = Xcur + (size_t)(r0 + lrow) * Np + lk;
+
+    auto bval = [](float v) { return kSign ? (v >= 0.f ? 1.f : -1.f) : v; };
+
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b)
+            acc[a][b] = 0.f;
+
+    float4 ra = *reinterpret_cast<const float4 *>(Ap);
+    float4 rb = *reinterpret_cast<const float4 *>(Bp);
+    As[0][lk + 0][lrow] = ra.x;
+    As[0][lk + 1][lrow] = ra.y;
+    As[0][lk + 2][lrow] = ra.z;
+    As[0][lk + 3][lrow] = ra.w;
+    Bs[0][lk + 0][lrow] = bval(rb.x);
+    Bs[0][lk + 1][lrow] = bval(rb.y);
+    Bs[0][lk + 2][lrow] = bval(rb.z);
+    Bs[0][lk + 3][lrow] = bval(rb.w);
+    __syncthreads();
+
+    const int nk = Np / 8;
+    for (int kt = 0; kt < nk; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < nk) {
+            ra = *reinterpret_cast<const float4 *>(Ap + (size_t)(kt + 1) * 8);
+            rb = *reinterpret_cast<const float4 *>(Bp + (size_t)(kt + 1) * 8);
+        }
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[cur][kk][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[cur][kk][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[cur][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[cur][kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b)
+                    acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        if (kt + 1 < nk) {
+            const int nxt = cur ^ 1;
+            As[nxt][lk + 0][lrow] = ra.x;
+            As[nxt][lk + 1][lrow] = ra.y;
+            As[nxt][lk + 2][lrow] = ra.z;
+            As[nxt][lk + 3][lrow] = ra.w;
+            Bs[nxt][lk + 0][lrow] = bval(rb.x);
+            Bs[nxt][lk + 1][lrow] = bval(rb.y);
+            Bs[nxt][lk + 2][lrow] = bval(rb.z);
+            Bs[nxt][lk + 3][lrow] = bval(rb.w);
+        }
+        __syncthreads();
+    }
+
+    // Epilogue: thread owns rows {ty*4+a, 64+ty*4+a} and replicas
+    // {tx*4+b, 64+tx*4+b}; one float4 of x and y per (replica, row group).
+    float ep[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int col = (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
+        const size_t rowbase = (size_t)(r0 + col) * Np + m0;
+        float e = 0.f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ibase = h * 64 + ty * 4;
+            const float4 x4 = *reinterpret_cast<const float4 *>(Xcur + rowbase + ibase);
+            const float xv[4] = {x4.x, x4.y, x4.z, x4.w};
+            if (ENERGY_ONLY || energy) {
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float f = acc[h * 4 + a][b];
+                    if (m0 + ibase + a < N)
+                        e += (xv[a] >= 0.f ? f : -f);
+                }
+            }
+            if (!ENERGY_ONLY) {
+                const float4 y4 = *reinterpret_cast<const float4 *>(Y + rowbase + ibase);
+                const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+                float xo[4], yo[4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+                    sb_update(acc[h * 4 + a][b], xv[a], yv[a], pk, c, xo[a], yo[a]);
+                *reinterpret_cast<float4 *>(Xnext + rowbase + ibase) =
+                    make_float4(xo[0], xo[1], xo[2], xo[3]);
+                *reinterpret_cast<float4 *>(Y + rowbase + ibase) =
+                    make_float4(yo[0], yo[1], yo[2], yo[3]);
+            }
+        }
+        ep[b] = e;
+    }
+    if (ENERGY_ONLY || energy) {
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int col = (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
+            Ered[ty][col] = ep[b];
+        }
+        __syncthreads();
+        if (tid < 128) {
+            float s = 0.f;
+            for (int t = 0; t < 16; ++t)
+                s += Ered[t][tid];
+            Epart[(size_t)blockIdx.x * Rp + r0 + tid] = s;
+        }
+    }
+}
+
+cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool energy,
+                             const float *J32, int N, int Np, int Rp, const float *Xcur,
+                             float *Xnext, float *Y, float pk, StepConsts c, float *Epart)
+{
+    dim3 grid(Np / 128, Rp / 128);
+    if (energy_only)
+        simt_step_kernel<1, true><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
+                                                         1, Epart);
+    else if (form == 1)
+        simt_step_kernel<1, false><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
+                                                          energy ? 1 : 0, Epart);
+    else
+        simt_step_kernel<0, false><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
+                                                          0, Epart);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ best tracking ---
+
+// E_r = -1/2 sum_b Epart[b][r] (binary64 sum over row blocks in order); a
+// strictly lower energy replaces the best and copies sgn(x(t_k)).
+__global__ void best_update_kernel(const float *__restrict__ Epart, int nblk, int N, int Np,
+                                   int Rp, const float *__restrict__ X,
+                                   const uint8_t *__restrict__ S8, double *__restrict__ Ebest,
+                                   int8_t *__restrict__ Sbest)
+{
+    const int r = blockIdx.x;
+    __shared__ int take;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b)
+            s += (double)Epart[(size_t)b * Rp + r];
+        const double E = -0.5 * s;
+        take = E < Ebest[r];
+        if (take)
+            Ebest[r] = E;
+    }
+    __syncthreads();
+    if (!take)
+        return;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        int8_t sp;
+        if (X)
+            sp = X[(size_t)r * Np + i] >= 0.f ? 1 : -1;
+        else
+            sp = S8[(size_t)r * Np + i] == kFp8PlusOne ? 1 : -1;
+        Sbest[(size_t)r * N + i] = sp;
+    }
+}
+
+cudaError_t launch_best_update(cudaStream_t st, const float *Epart, int nblk, int N, int Np,
+                               int R, int Rp, const float *X, const uint8_t *S8,
+                               double *Ebest, int8_t *Sbest)
+{
+    best_update_kernel<<<R, 256, 0, st>>>(Epart, nblk, N, Np, Rp, X, S8, Ebest, Sbest);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- binary64 energy ---
+
+// Eq. (eq_Ising) for general couplings: E = -1/2 sum_i s_i sum_j J_ij s_j,
+// every term exact in binary64 (+/-J_ij), one warp per row, fixed reduction
+// order.  One block per replica.
+__global__ void __launch_bounds__(256)
+final_energy_f64_kernel(const float *__restrict__ J, int N, int Np,
+                        const int8_t *__restrict__ Sbest, double *__restrict__ Eout)
+{
+    extern __shared__ int8_t s_sh[];
+    __shared__ double red[8];
+    const int r = blockIdx.x;
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        s_sh[i] = Sbest[(size_t)r * N + i];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int i = warp; i < N; i += 8) {
+        const float *row = J + (size_t)i * Np;
+        double a = 0.0;
+        for (int j = lane; j < N; j += 32) {
+            const double v = (double)row[j];
+            a += s_sh[j] > 0 ? v : -v;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            a += __shfl_down_sync(0xffffffffu, a, off);
+        if (lane == 0)
+            acc += s_sh[i] > 0 ? a : -a;
+    }
+    if (lane == 0)
+        red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w)
+            s += red[w];
+        Eout[r] = -0.5 * s;
+    }
+}
+
+cudaError_t launch_final_energy_f64(cudaStream_t st, const float *J32, int N, int Np, int R,
+                                    const int8_t *Sbest, double *Eout)
+{
+    final_energy_f64_kernel<<<R, 256, (size_t)N, st>>>(J32, N, Np, Sbest, Eout);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- conversions ---
+
+__global__ void sign_to_fp8_kernel(const float *__restrict__ X, int N, int Np, size_t total,
+                                   uint8_t *__restrict__ S8)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e % Np);
+        S8[e] = i < N ? fp8_sign(X[e]) : (uint8_t)0;
+    }
+}
+
+cudaError_t launch_sign_to_fp8(cudaStream_t st, const float *X, int N, int Np, int Rp,
+                               uint8_t *S8)
+{
+    const size_t total = (size_t)Rp * Np;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    sign_to_fp8_kernel<<<blocks, 256, 0, st>>>(X, N, Np, total, S8);
+    return cudaGetLastError();
+}
+
+__global__ void j_to_fp8_kernel(const float *__restrict__ J, size_t total, uint8_t *__restrict__ J8)
+{
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const float v = J[e];
+        J8[e] = v > 0.f ? kFp8PlusOne : (v < 0.f ? kFp8MinusOne : (uint8_t)0);
+    }
+}
+
+cudaError_t launch_j_to_fp8(cudaStream_t st, const float *J32, int Np, uint8_t *J8)
+{
+    const size_t total = (size_t)Np * Np;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    j_to_fp8_kernel<<<blocks, 256, 0, st>>>(J32, total, J8);
+    return cudaGetLastError();
+}
+
+}  // namespace hsb

@@ -1,0 +1,63 @@
+"""The C ABI library loads and exports every symbol include/hsb.h declares;
+host-side validation and the no-device behaviour need no GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2203_08361_gb300 as hsb
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "hsb.h")) as fh:
+        text = fh.read()
+    return sorted(set(re.findall(r"HSB_API[^;(]*?\b(hsb_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = hsb.load()
+    declared = _declared()
+    assert declared == sorted(hsb.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_version_and_defaults():
+    assert hsb.version() == 1
+    p = hsb.params()
+    assert (p.form, p.prec) == (hsb.HSB_DISCRETE, hsb.HSB_PREC_AUTO)
+    # the paper's tuned HdSB settings (Fig. 1 caption), a0 = 1 (Results)
+    assert (p.a0, p.c1, p.dt, p.gamma, p.init_half_width, p.eval_every) == \
+        (1.0, 0.7, 1.1, 0.06, 1.0, 100)
+    assert C.sizeof(hsb.Params) == 96
+
+
+def test_create_validates_couplings_on_the_host():
+    J = synth.sk_pm1(8, 0)
+    bad = J.copy()
+    bad[0, 1] = -bad[0, 1]
+    with pytest.raises(hsb.HsbError) as e:
+        hsb.create(bad)
+    assert e.value.status == 2  # HSB_E_ASYM
+    bad = J.copy()
+    bad[3, 3] = 1.0
+    with pytest.raises(hsb.HsbError) as e:
+        hsb.create(bad)
+    assert e.value.status == 3  # HSB_E_DIAG
+    with pytest.raises(hsb.HsbError) as e:
+        hsb.create(np.zeros((1, 1), np.float32))
+    assert e.value.status == 1  # HSB_E_INVAL
+
+
+def test_no_cpu_fallback_without_a_device():
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(hsb.HsbError) as e:
+        hsb.create(synth.sk_pm1(8, 0))
+    assert e.value.status == 8  # HSB_E_NODEVICE
