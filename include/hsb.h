@@ -98,7 +98,11 @@ typedef struct {
     int eval_every;         /* >= 0; 100 in the K2000 study, 0 = final only */
     int trace_every;        /* reserved, must be 0 */
     uint32_t instance;      /* random stream of the instance (x0, y0) */
-    uint32_t reserved[7];   /* must be zero */
+    int schedule;           /* FP8 step loop: 0 = automatic (persistent kernel
+                               when its grid fits on the device), 1 = persistent
+                               kernel only (HSB_E_UNSUPPORTED if it cannot fit),
+                               2 = one kernel launch per step */
+    uint32_t reserved[6];   /* must be zero */
 } hsb_params;
 
 /* Fills *p with the paper's tuned HdSB settings (Fig. 1 caption): discrete

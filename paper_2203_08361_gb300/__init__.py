@@ -25,6 +25,7 @@ STATUS = {0: "HSB_OK", 1: "HSB_E_INVAL", 2: "HSB_E_ASYM", 3: "HSB_E_DIAG", 4: "H
 PREC = {"auto": HSB_PREC_AUTO, "fp32": HSB_PREC_FP32, "fp8": HSB_PREC_FP8,
         "bf16x3": HSB_PREC_BF16X3}
 FORM = {"ballistic": HSB_BALLISTIC, "discrete": HSB_DISCRETE}
+SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2}
 
 # Every symbol include/hsb.h declares.
 EXPORTS = ["hsb_params_default", "hsb_version", "hsb_create", "hsb_destroy", "hsb_set_stream",
@@ -53,7 +54,8 @@ class Params(C.Structure):
         ("eval_every", C.c_int),
         ("trace_every", C.c_int),
         ("instance", C.c_uint32),
-        ("reserved", C.c_uint32 * 7),
+        ("schedule", C.c_int),
+        ("reserved", C.c_uint32 * 6),
     ]
 
 
@@ -126,6 +128,8 @@ def params(form="discrete", prec="auto", **kw) -> Params:
     _check(load().hsb_params_default(C.byref(p)))
     p.form = FORM[form] if isinstance(form, str) else int(form)
     p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    if isinstance(kw.get("schedule"), str):
+        kw["schedule"] = SCHEDULE[kw["schedule"]]
     for k, v in kw.items():
         if not hasattr(p, k):
             raise AttributeError(f"hsb_params has no field {k!r}")

@@ -16,8 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhsb.so")
-SOURCES = ["hsb_api.cu", "hsb_simt.cu", "hsb_tc.cu"]
-HEADERS = ["hsb_internal.cuh", "hsb_device.cuh"]
+SOURCES = ["hsb_api.cu", "hsb_simt.cu", "hsb_tc.cu", "hsb_persist.cu"]
+HEADERS = ["hsb_internal.cuh", "hsb_device.cuh", "hsb_ptx.cuh"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

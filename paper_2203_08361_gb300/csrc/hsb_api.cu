@@ -74,7 +74,7 @@ struct GraphKey {
 };
 
 struct RunCfg {
-    int prec, form, R, Rp, steps, eval_every;
+    int prec, form, R, Rp, steps, eval_every, schedule;
     double a0;
     StepConsts c;
     std::vector<float> pk;  // p_k = a0 - a(t_k), k = 0..steps-1, rounded once
@@ -101,6 +101,17 @@ struct hsb_ctx {
     int *err = nullptr;
     uint64_t buffers_gen = 0;
     TcPlan *plan = nullptr;
+    // persistent FP8 schedule: flags, p_k table, per-evaluation partials and
+    // spin snapshots
+    int *flags = nullptr;
+    size_t flags_cap = 0;
+    float *pk_dev = nullptr;
+    int pk_cap = 0, pk_steps = -1;
+    double pk_a0 = 0.0;
+    float *Eeval = nullptr;
+    size_t eeval_cap = 0;
+    uint8_t *Snap = nullptr;
+    size_t snap_cap = 0;
     // graph cache: the whole run, and the step range of hsb_advance_device
     bool graph_valid = false;
     GraphKey gkey{};
@@ -203,6 +214,8 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_INVAL, "need c0 > 0 or c1 > 0");
     if (p->eval_every < 0 || p->trace_every != 0)
         return set_error(HSB_E_INVAL, "eval_every must be >= 0 and trace_every 0");
+    if (p->schedule < 0 || p->schedule > 2)
+        return set_error(HSB_E_INVAL, "schedule must be 0, 1 or 2");
     if ((long long)R * h->N > (1LL << 40))
         return set_error(HSB_E_INVAL, "R*N too large");
     int prec = p->prec;
@@ -221,6 +234,7 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
     cfg->Rp = round_up(R, kTileR);
     cfg->steps = steps;
     cfg->eval_every = p->eval_every;
+    cfg->schedule = p->schedule;
     cfg->a0 = p->a0;
     // c0 = c1 / (sqrt(N) sigma_J) (Results; sigma_J = 1 for +/-1 couplings)
     const double c0 = p->c0 > 0.0 ? p->c0 : p->c1 / (sqrt((double)h->N) * h->sigma);
@@ -264,8 +278,8 @@ hsb_status enqueue_step(hsb_ctx *h, cudaStream_t st, const RunCfg &c, int k, int
                                   h->Ebest, h->Sbest),
                "best kernel");
     } else {  // FP8: S8[cur] -> S8[cur^1], X and Y in place
-        CK(launch_tc_fp8_step(st, h->plan, cur, ev, false, h->N, h->X[0], h->Y, c.pk[k], c.c,
-                              h->Epart, h->S8[cur ^ 1], h->err),
+        CK(launch_tc_fp8_step(st, h->plan, cur, ev, false, h->N, c.Rp, h->X[0], h->Y, c.pk[k],
+                              c.c, h->Epart, h->S8[cur ^ 1], h->err),
            "fp8 step kernel");
         if (ev)
             CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, h->S8[cur],
@@ -288,7 +302,7 @@ hsb_status enqueue_final(hsb_ctx *h, cudaStream_t st, const RunCfg &c)
                               h->Ebest, h->Sbest),
            "best kernel");
     } else {
-        CK(launch_tc_fp8_step(st, h->plan, cur, true, true, h->N, h->X[0], h->Y, 0.f, c.c,
+        CK(launch_tc_fp8_step(st, h->plan, cur, true, true, h->N, c.Rp, h->X[0], h->Y, 0.f, c.c,
                               h->Epart, nullptr, h->err),
            "fp8 energy kernel");
         CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, h->S8[cur],
@@ -361,12 +375,135 @@ hsb_status prepare(hsb_ctx *h, const RunCfg &c)
 
 GraphKey make_key(const hsb_ctx *h, const RunCfg &c);
 
+int num_evals(const RunCfg &c)
+{
+    return (c.eval_every > 0 ? (c.steps - 1) / c.eval_every : 0) + 1;
+}
+
+// Whether the FP8 step loop runs as one persistent kernel.
+hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
+{
+    *out = false;
+    if (c.prec != HSB_PREC_FP8 || c.schedule == 2)
+        return HSB_OK;
+    const bool fits = tc_persistent_fits(h->Np, c.Rp);
+    if (!fits && c.schedule == 1)
+        return set_error(HSB_E_UNSUPPORTED,
+                         "the persistent kernel's %d x %d grid does not fit on the device",
+                         h->Np / kTileM, c.Rp / kTileR);
+    *out = fits;
+    return HSB_OK;
+}
+
+template <typename T>
+hsb_status grow(T **ptr, size_t *cap, size_t n, const char *what)
+{
+    if (*cap >= n && *ptr)
+        return HSB_OK;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    CK(cudaMalloc(ptr, n * sizeof(T)), what);
+    *cap = n;
+    return HSB_OK;
+}
+
+// Device p_k table of the run (uploaded when steps or a0 change).
+hsb_status ensure_pk(hsb_ctx *h, const RunCfg &c)
+{
+    if (h->pk_steps == c.steps && h->pk_a0 == c.a0 && h->pk_dev)
+        return HSB_OK;
+    if (h->pk_cap < c.steps) {
+        cudaFree(h->pk_dev);
+        h->pk_dev = nullptr;
+        h->pk_cap = 0;
+        CK(cudaMalloc(&h->pk_dev, (size_t)c.steps * sizeof(float)), "cudaMalloc pk");
+        h->pk_cap = c.steps;
+    }
+    CK(cudaMemcpyAsync(h->pk_dev, c.pk.data(), (size_t)c.steps * sizeof(float),
+                       cudaMemcpyHostToDevice, h->work),
+       "copy pk");
+    CK(cudaStreamSynchronize(h->work), "synchronize");
+    h->pk_steps = c.steps;
+    h->pk_a0 = c.a0;
+    return HSB_OK;
+}
+
+// Queues the persistent kernel for updates [k_begin, k_begin + nsteps) of the
+// run's schedule, starting from operand buffer par0.
+hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nsteps,
+                              bool evaluate, int par0)
+{
+    const int nblk = h->Np / kTileM;
+    const int nrb = c.Rp / kTileR;
+    const int ne = evaluate ? num_evals(c) : 0;
+    hsb_status s = ensure_pk(h, c);
+    if (s == HSB_OK)
+        s = grow(&h->flags, &h->flags_cap, (size_t)nblk * nrb, "cudaMalloc flags");
+    if (s == HSB_OK && evaluate)
+        s = grow(&h->Eeval, &h->eeval_cap, (size_t)ne * nblk * c.Rp, "cudaMalloc Eeval");
+    if (s == HSB_OK && evaluate)
+        s = grow(&h->Snap, &h->snap_cap, (size_t)ne * c.Rp * h->Np, "cudaMalloc snapshots");
+    if (s != HSB_OK)
+        return s;
+    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * sizeof(int), h->work), "memset flags");
+    PersistArgs a;
+    memset(&a, 0, sizeof a);
+    a.N = h->N;
+    a.Np = h->Np;
+    a.Rp = c.Rp;
+    a.nblk = nblk;
+    a.nrb = nrb;
+    a.k_begin = k_begin;
+    a.nsteps = nsteps;
+    a.final_pass = evaluate ? 1 : 0;
+    a.eval_every = evaluate ? c.eval_every : 0;
+    a.steps_total = c.steps;
+    a.n_evals = ne;
+    a.par0 = par0;
+    a.pk = h->pk_dev;
+    a.c = c.c;
+    a.X = h->X[0];
+    a.Y = h->Y;
+    a.S8a = h->S8[0];
+    a.S8b = h->S8[1];
+    a.flags = h->flags;
+    a.Epart = h->Eeval;
+    a.Snap = h->Snap;
+    a.err = h->err;
+    CK(launch_tc_fp8_persistent(h->work, h->plan, a), "persistent fp8 kernel");
+    if (evaluate)
+        CK(launch_select_best(h->work, h->Eeval, h->Snap, ne, nblk, h->N, h->Np, c.R, c.Rp,
+                              h->Ebest, h->Sbest),
+           "select best kernel");
+    return HSB_OK;
+}
+
 // Queues a whole run (init, graph of the step loop) on the work stream.
 hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_params *p)
 {
     hsb_status s = prepare(h, c);
     if (s != HSB_OK)
         return s;
+    bool persistent = false;
+    s = use_persistent(h, c, &persistent);
+    if (s != HSB_OK)
+        return s;
+    if (persistent) {
+        CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->work), "memset err");
+        CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R,
+                       c.Rp, h->X[0], h->Y, h->S8[0], h->Ebest),
+           "init kernel");
+        s = enqueue_persistent(h, c, 0, c.steps, true, 0);
+        if (s != HSB_OK)
+            return s;
+        h->last_R = c.R;
+        h->last_x = 0;
+        h->state_par = c.steps & 1;
+        h->have_state = true;
+        h->launches = 3;
+        return HSB_OK;
+    }
     const GraphKey key = make_key(h, c);
     if (!h->graph_valid || !(h->gkey == key)) {
         s = build_graph(h, c, key);
@@ -539,6 +676,10 @@ void hsb_destroy(hsb_handle h)
     cudaFree(h->J32);
     cudaFree(h->J8);
     cudaFree(h->err);
+    cudaFree(h->flags);
+    cudaFree(h->pk_dev);
+    cudaFree(h->Eeval);
+    cudaFree(h->Snap);
     if (h->own)
         cudaStreamDestroy(h->own);
     delete h;
@@ -669,10 +810,22 @@ hsb_status hsb_advance(hsb_handle h, const hsb_params *p, int R, int steps, int 
     if (c.prec == HSB_PREC_FP8)
         CK(launch_sign_to_fp8(h->work, h->X[0], h->N, h->Np, c.Rp, h->S8[k_begin & 1]),
            "sign kernel");
-    for (int k = k_begin; k < k_end; ++k) {
-        s = enqueue_step(h, h->work, c, k, k & 1, false);
-        if (s != HSB_OK)
-            return s;
+    bool persistent = false;
+    s = use_persistent(h, c, &persistent);
+    if (s != HSB_OK)
+        return s;
+    if (persistent) {
+        if (k_end > k_begin) {
+            s = enqueue_persistent(h, c, k_begin, k_end - k_begin, false, k_begin & 1);
+            if (s != HSB_OK)
+                return s;
+        }
+    } else {
+        for (int k = k_begin; k < k_end; ++k) {
+            s = enqueue_step(h, h->work, c, k, k & 1, false);
+            if (s != HSB_OK)
+                return s;
+        }
     }
     const int xout = c.prec == HSB_PREC_FP32 ? (k_end & 1) : 0;
     CK(cudaMemcpy2DAsync(x, row, h->X[xout], pitch, row, (size_t)R, cudaMemcpyDeviceToHost,
@@ -703,8 +856,22 @@ hsb_status hsb_advance_device(hsb_handle h, const hsb_params *p, int R, int step
     s = prepare(h, c);
     if (s != HSB_OK)
         return s;
-    const GraphKey key = make_key(h, c);
     const int par = h->state_par;
+    bool persistent = false;
+    s = use_persistent(h, c, &persistent);
+    if (s != HSB_OK)
+        return s;
+    if (persistent) {
+        if (k_end > k_begin) {
+            s = enqueue_persistent(h, c, k_begin, k_end - k_begin, false, par);
+            if (s != HSB_OK)
+                return s;
+        }
+        h->state_par = (par + (k_end - k_begin)) & 1;
+        h->launches = k_end > k_begin ? 1 : 0;
+        return HSB_OK;
+    }
+    const GraphKey key = make_key(h, c);
     if (!h->adv_valid || !(h->adv_key == key) || h->adv_k0 != k_begin || h->adv_k1 != k_end ||
         h->adv_par != par) {
         if (h->adv_exec) {

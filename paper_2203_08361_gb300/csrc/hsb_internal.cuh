@@ -13,6 +13,7 @@
 //   Ebest[R] double, Sbest[R][N] int8   best energy / spins so far
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -67,15 +68,48 @@ cudaError_t launch_sign_to_fp8(cudaStream_t st, const float *X, int N, int Np, i
 cudaError_t launch_j_to_fp8(cudaStream_t st, const float *J32, int Np, uint8_t *J8);
 
 // ---- hsb_tc.cu -----------------------------------------------------------
+// TMA tensor maps of the FP8 operands: J8 [Np][Np] and the two S8 ping/pong
+// buffers [Rcap][Np], 128-byte boxes with the 128-byte swizzle.
+struct TcPlan {
+    CUtensorMap mapA;
+    CUtensorMap mapB[2];
+    int Np, Rp;  // Rp: replica capacity the maps were encoded for
+};
+
 // tcgen05 FP8 step: F = J8 * S8cur^T on the tensor cores (FP32 accumulation
 // in tensor memory), fused update; writes S8next, X and Y in place, and Epart
 // on evaluation steps.  Requires Np % 128 == 0 and Rp % 128 == 0.
-struct TcPlan;  // opaque per-shape launch plan (tensor maps)
 cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S8a,
                                const uint8_t *S8b, int Np, int Rp);
 void tc_plan_destroy(TcPlan *p);
 cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
-                               bool energy_only, int N, float *X, float *Y, float pk,
+                               bool energy_only, int N, int Rp, float *X, float *Y, float pk,
                                StepConsts c, float *Epart, uint8_t *S8next, int *err);
+
+// ---- hsb_persist.cu --------------------------------------------------------
+// Arguments of the persistent FP8 kernel: `nsteps` updates starting at global
+// step k_begin of a `steps_total`-step schedule, then (final_pass) one
+// energy-only pass.  The operand of the first update is in S8a (par0 = 0) or
+// S8b (par0 = 1).  Evaluations e = 0..n_evals-1 write Epart[e][nblk][Rp] and
+// the spin snapshot Snap[e][Rp][Np].  flags[nblk][nrb] must be zero at launch.
+struct PersistArgs {
+    int N, Np, Rp, nblk, nrb;
+    int k_begin, nsteps, final_pass, eval_every, steps_total, n_evals, par0;
+    const float *pk;
+    StepConsts c;
+    float *X, *Y;
+    uint8_t *S8a, *S8b;
+    int *flags;
+    float *Epart;
+    uint8_t *Snap;
+    int *err;
+};
+
+// True when the nblk x nrb grid of the persistent kernel can be co-resident.
+bool tc_persistent_fits(int Np, int Rp);
+cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const PersistArgs &a);
+cudaError_t launch_select_best(cudaStream_t st, const float *Epart, const uint8_t *Snap,
+                               int n_evals, int nblk, int N, int Np, int R, int Rp,
+                               double *Ebest, int8_t *Sbest);
 
 }  // namespace hsb

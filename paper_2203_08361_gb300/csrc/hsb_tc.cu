@@ -323,12 +323,6 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
 
 // ------------------------------------------------------------- host side ---
 
-struct TcPlan {
-    CUtensorMap mapA;
-    CUtensorMap mapB[2];
-    int Np, Rp;
-};
-
 namespace {
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
@@ -400,14 +394,16 @@ cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S
 void tc_plan_destroy(TcPlan *p) { delete p; }
 
 cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
-                               bool energy_only, int N, float *X, float *Y, float pk,
+                               bool energy_only, int N, int Rp, float *X, float *Y, float pk,
                                StepConsts c, float *Epart, uint8_t *S8next, int *err)
 {
-    if (!plan)
+    // Rp (this run's padded replica count) may be below the capacity the
+    // tensor maps were encoded for; Epart rows are Rp long.
+    if (!plan || Rp % kBN != 0 || Rp > plan->Rp)
         return cudaErrorInvalidValue;
-    dim3 grid(plan->Np / kBM, plan->Rp / kBN);
+    dim3 grid(plan->Np / kBM, Rp / kBN);
     tc_fp8_step_kernel<<<grid, kThreads, kSmemBytes, st>>>(
-        plan->mapA, plan->mapB[parity & 1], N, plan->Np, plan->Rp, X, Y, S8next, pk, c,
+        plan->mapA, plan->mapB[parity & 1], N, plan->Np, Rp, X, Y, S8next, pk, c,
         energy ? 1 : 0, energy_only ? 1 : 0, Epart, err);
     return cudaGetLastError();
 }

@@ -31,16 +31,18 @@ def _assert_same(got_x, got_y, spins, energy, ref, rows=None):
     np.testing.assert_array_equal(energy[sel], ref["best_e"])
 
 
-@pytest.mark.parametrize("prec", ["fp8", "fp32"])
-@pytest.mark.parametrize("n,R", [(128, 128), (300, 40), (257, 130), (2, 3)])
-def test_discrete_pm1_bit_exact(prec, n, R):
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
+                                           ("fp32", "auto")])
+@pytest.mark.parametrize("n,R", [(128, 128), (300, 40), (257, 130), (2, 3), (700, 300)])
+def test_discrete_pm1_bit_exact(prec, schedule, n, R):
     J = synth.sk_pm1(n, 1000 + n)
     steps, seed, ev = 150, 7, 40
-    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=ev)
+    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=ev,
+                   schedule=schedule)
     with hsb.Solver(J) as s:
         spins, energy = s.run(p, R, steps, seed)
         x, y = s.get_state(R)
-        assert s.run_stats() > steps
+        assert s.run_stats() >= 3
     ref = oracle.run(J, _oparams(J, 1, 0.7, 1.1, 0.06, ev), steps, seed, range(R), "f32")
     _assert_same(x, y, spins, energy, ref)
 
@@ -82,14 +84,15 @@ def test_small_ballistic_pm1_workload_fp32():
     assert abs(np.mean(energy) - np.mean(e0)) < 0.05 * abs(np.mean(e0))
 
 
-@pytest.mark.parametrize("prec", ["fp8", "fp32"])
-def test_one_step_and_split_runs(prec):
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
+                                           ("fp32", "auto")])
+def test_one_step_and_split_runs(prec, schedule):
     n, R, steps = 260, 70, 50
     J = synth.sk_pm1(n, 4)
     rng = np.random.default_rng(0)
     x0 = rng.uniform(-1, 1, (R, n)).astype(np.float32)
     y0 = rng.uniform(-1, 1, (R, n)).astype(np.float32)
-    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06)
+    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, schedule=schedule)
     c0 = oracle.c0_from_c1(J, 0.7)
     with hsb.Solver(J) as s:
         x1, y1 = s.advance(p, steps, 10, 11, x0, y0)
@@ -119,9 +122,9 @@ def test_fp8_force_is_the_exact_integer_product(n):
     with hsb.Solver(J) as s:
         x1, y1 = s.advance(p, 4, 0, 1, x0, y0)
     f = np.rint(y1.astype(np.float64) / 2.0**-20).astype(np.int64)
-    s_ = np.where(x0 >= 0, 1, -1).astype(np.int64)
-    Ji = J.astype(np.int8)
-    want = np.stack([(Ji.astype(np.int64) @ s_[r]) for r in range(R)])
+    s_ = np.where(x0 >= 0, 1, -1).astype(np.float32)
+    # float32 sums of +/-1 terms below 2^24 are exact in any order
+    want = np.rint(s_ @ J.T).astype(np.int64)
     np.testing.assert_array_equal(f, want)
     assert f[0, 0] == n - 1
 
@@ -156,14 +159,20 @@ def test_full_size_fp8_equals_fp32_and_is_independent_of_R():
     steps, seed = 400, 2
     with hsb.Solver(J) as s:
         sa, ea = s.run(p, 1024, steps, seed)
-        xa, _ = s.get_state(1024)
+        xa, ya = s.get_state(1024)
         p32 = hsb.params("discrete", "fp32", c1=0.7, dt=1.1, gamma=0.06, eval_every=100)
         sb, eb = s.run(p32, 1024, steps, seed)
-        xb, _ = s.get_state(1024)
+        xb, yb = s.get_state(1024)
+        pps = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
+                         schedule="per_step")
+        sd, ed = s.run(pps, 1024, steps, seed)
+        xd, yd = s.get_state(1024)
         sc, ec = s.run(p, 8, steps, seed)
-    np.testing.assert_array_equal(sa, sb)
-    np.testing.assert_array_equal(ea, eb)
-    np.testing.assert_array_equal(xa, xb)
+    for other_s, other_e, other_x, other_y in ((sb, eb, xb, yb), (sd, ed, xd, yd)):
+        np.testing.assert_array_equal(sa, other_s)
+        np.testing.assert_array_equal(ea, other_e)
+        np.testing.assert_array_equal(xa, other_x)
+        np.testing.assert_array_equal(ya, other_y)
     np.testing.assert_array_equal(sa[:8], sc)
     np.testing.assert_array_equal(ea[:8], ec)
 
