@@ -352,9 +352,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hsb", "reference"], default="hsb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sb-steps", type=int, default=None,
+                    help="override the SB steps per run (profiling of small cases only; "
+                         "the headline workload is 2000)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.sb_steps:
+        WORKLOAD["sb_steps"] = int(args.sb_steps)
+        WORKLOAD["name"] = WORKLOAD["name"].replace("2000 steps", f"{args.sb_steps} steps")
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -71,9 +71,12 @@ cudaError_t launch_j_to_fp8(cudaStream_t st, const float *J32, int Np, uint8_t *
 // TMA tensor maps of the FP8 operands: J8 [Np][Np] and the two S8 ping/pong
 // buffers [Rcap][Np], 128-byte boxes with the 128-byte swizzle.
 struct TcPlan {
-    CUtensorMap mapA;
-    CUtensorMap mapB[2];
-    int Np, Rp;  // Rp: replica capacity the maps were encoded for
+    CUtensorMap mapA;      // 2-D J8, box 128 B x 128 rows
+    CUtensorMap mapB[2];   // 2-D S8a / S8b, box 128 B x 128 rows
+    CUtensorMap mapA3;     // 3-D J8 (128 B, rows, K chunks), box 128 x 128 x 2
+    CUtensorMap mapB3[2];  // 3-D S8a / S8b, box 128 x 128 x 2
+    CUtensorMap mapSt[2];  // 2-D S8a / S8b for tile stores, no swizzle, box 128 x 128
+    int Np, Rp;            // Rp: replica capacity the maps were encoded for
 };
 
 // tcgen05 FP8 step: F = J8 * S8cur^T on the tensor cores (FP32 accumulation

@@ -11,17 +11,20 @@
 // so a step moves only J and the FP8 spin operand S = sgn(x) through L2:
 //   warp 0      producer: polls the per-tile "published" flags of the step's
 //               operand (one flag per 128-spin chunk, all lanes at once),
-//               then TMA-loads J (128 x 128 bytes) and S chunks into a ring of
-//               shared-memory stages, in the order the chunks become ready
-//               (the FP8 products are exact integers, so the summation order
-//               does not change the force);
+//               then TMA-loads J and S two K chunks at a time (3-D boxes of
+//               128 x 128 x 2 bytes: one 32 KB copy each, which moves data
+//               into the SM faster than two 16 KB copies) into a ring of
+//               shared-memory stages, in the order the chunk pairs become
+//               ready (the FP8 products are exact integers, so the summation
+//               order does not change the force);
 //   warp 1      allocates 512 tensor-memory columns, issues tcgen05.mma
 //               (kind::f8f6f4, M = N = 128, K = 32) from one lane;
-//   warps 2-9   epilogue, two warps per 32-lane quadrant (64 replicas each):
+//   warps 2-17  epilogue, four warps per 32-lane quadrant (32 replicas each,
+//               moved through tensor memory 16 columns at a time):
 //               accumulator, x and y from tensor memory, the pinned spin
-//               update, x and y back to tensor memory, sgn(x') as FP8 into the
-//               other operand buffer, then a gpu-scope release of the tile's
-//               flag.  On evaluation steps also the per-replica partial sums
+//               update, x and y back to tensor memory, sgn(x') as FP8 into a shared-memory
+//               tile that one TMA store writes to the other operand buffer,
+//               then a gpu-scope release of the tile's flag.  On evaluation steps also the per-replica partial sums
 //               of s_i f_i and a snapshot of s = sgn(x(t_k)).
 // A final pass after the last update evaluates E(t_Ns).  The best evaluation
 // per replica is chosen afterwards by select_best_kernel.
@@ -47,10 +50,12 @@ namespace {
 constexpr int kPM = 128;
 constexpr int kPN = 128;
 constexpr int kPK = 128;
-constexpr int kPStages = 6;
-constexpr int kPStageA = kPM * kPK;
-constexpr int kPStageB = kPN * kPK;
-constexpr int kEpiWarps = 8;
+constexpr int kPChunks = 2;  // K chunks of 128 per stage
+constexpr int kPStages = 3;
+constexpr int kPStageA = kPChunks * kPM * kPK;
+constexpr int kPStageB = kPChunks * kPN * kPK;
+constexpr int kPTileS = kPN * kPM;  // FP8 spin tile [replica][spin] for the store
+constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kPThreads = 64 + kEpiThreads;
 constexpr uint32_t kPTmemCols = 512;
@@ -69,7 +74,8 @@ struct __align__(8) PShared {
     float red[4][kPN];
 };
 
-constexpr size_t kPSmem = 1024 + (size_t)kPStages * (kPStageA + kPStageB) + sizeof(PShared);
+constexpr size_t kPSmem =
+    1024 + (size_t)kPStages * (kPStageA + kPStageB) + kPTileS + sizeof(PShared);
 
 // Barrier among the epilogue warps that also ORs a predicate over them, so
 // that a decision to leave the step loop is the same in every epilogue warp.
@@ -94,14 +100,17 @@ __device__ __forceinline__ void epi_bar() { ptx::named_bar(1, kEpiThreads); }
 __global__ void __launch_bounds__(kPThreads, 1)
 tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                          const __grid_constant__ CUtensorMap tmapB0,
-                         const __grid_constant__ CUtensorMap tmapB1, const PersistArgs a)
+                         const __grid_constant__ CUtensorMap tmapB1,
+                         const __grid_constant__ CUtensorMap tmapSt0,
+                         const __grid_constant__ CUtensorMap tmapSt1, const PersistArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = base;
     uint8_t *sB = base + (size_t)kPStages * kPStageA;
-    PShared *sh = reinterpret_cast<PShared *>(sB + (size_t)kPStages * kPStageB);
+    uint8_t *sS = sB + (size_t)kPStages * kPStageB;
+    PShared *sh = reinterpret_cast<PShared *>(sS + kPTileS);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -126,6 +135,8 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         ptx::prefetch_tmap(&tmapA);
         ptx::prefetch_tmap(&tmapB0);
         ptx::prefetch_tmap(&tmapB1);
+        ptx::prefetch_tmap(&tmapSt0);
+        ptx::prefetch_tmap(&tmapSt1);
     }
     if (warp == 1)
         ptx::tmem_alloc(&sh->tmem_base, kPTmemCols);
@@ -136,11 +147,15 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
 
     if (warp == 0) {
         // ---------------------------------------------------------- producer
+        // K chunks are fetched in pairs (2p, 2p+1); a chunk past the end reads
+        // as zero, so an odd chunk count adds zero products only.
+        const int npairs = (nblk + 1) >> 1;
         uint32_t g = 0;
         bool fail = false;
         for (int kl = 0; kl < passes && !fail; ++kl) {
             const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? &tmapB1 : &tmapB0;
             uint32_t pending = nblk >= 32 ? 0xFFFFFFFFu : ((1u << nblk) - 1u);
+            uint32_t have = 0;  // chunks seen published, not yet loaded
             const unsigned long long t0 = ptx::globaltimer();
             while (pending) {
                 bool ready = false;
@@ -148,14 +163,24 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                     ready = ptx::ld_acquire_gpu(&a.flags[lane * a.nrb + rb]) >= kl;
                 const uint32_t rmask = __ballot_sync(0xFFFFFFFFu, ready);
                 __syncwarp();
-                if (rmask) {
+                have |= rmask;
+                pending &= ~rmask;
+                // a pair can be loaded when both of its chunks are published
+                uint32_t pmask = 0;
+                for (int pp = 0; pp < npairs; ++pp) {
+                    const uint32_t need = (2 * pp + 1 < nblk) ? (3u << (2 * pp)) : (1u << (2 * pp));
+                    if ((have & need) == need)
+                        pmask |= 1u << pp;
+                }
+                if (pmask) {
                     if (lane == 0) {
                         ptx::fence_proxy_async_global();
-                        for (int t = 0; t < nblk; ++t) {
-                            int kc = mb + t;
-                            if (kc >= nblk)
-                                kc -= nblk;
-                            if (!((rmask >> kc) & 1u))
+                        const int p0 = mb >> 1;
+                        for (int t = 0; t < npairs; ++t) {
+                            int pp = p0 + t;
+                            if (pp >= npairs)
+                                pp -= npairs;
+                            if (!((pmask >> pp) & 1u))
                                 continue;
                             const int s = (int)(g % kPStages);
                             const uint32_t ph = (g / kPStages) & 1u;
@@ -164,14 +189,16 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                                 break;
                             }
                             ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
-                            ptx::tma_load_2d(sA + (size_t)s * kPStageA, &tmapA, kc * kPK, m0,
+                            ptx::tma_load_3d(sA + (size_t)s * kPStageA, &tmapA, 0, m0, 2 * pp,
                                              &sh->full[s]);
-                            ptx::tma_load_2d(sB + (size_t)s * kPStageB, mapB, kc * kPK, r0,
+                            ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp,
                                              &sh->full[s]);
                             ++g;
                         }
                     }
-                    pending &= ~rmask;
+                    for (int pp = 0; pp < npairs; ++pp)
+                        if ((pmask >> pp) & 1u)
+                            have &= ~((2 * pp + 1 < nblk) ? (3u << (2 * pp)) : (1u << (2 * pp)));
                     fail = __shfl_sync(0xFFFFFFFFu, fail, 0);
                     g = __shfl_sync(0xFFFFFFFFu, g, 0);
                     if (fail)
@@ -207,7 +234,8 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                     ptx::tc_fence_after();
                 }
                 bool ok = true;
-                for (int t = 0; t < nblk; ++t) {
+                const int npairs = (nblk + 1) >> 1;
+                for (int t = 0; t < npairs; ++t) {
                     const int s = (int)(g % kPStages);
                     const uint32_t ph = (g / kPStages) & 1u;
                     if (!ptx::mbar_wait(&sh->full[s], ph, &sh->abort, a.err)) {
@@ -215,13 +243,16 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t a0 = ptx::smem_u32(sA + (size_t)s * kPStageA);
-                    const uint32_t b0 = ptx::smem_u32(sB + (size_t)s * kPStageB);
 #pragma unroll
-                    for (int kk = 0; kk < kPK / 32; ++kk)
-                        ptx::mma_fp8(tmem + kColAcc, ptx::sw128_desc(a0 + kk * 32),
-                                     ptx::sw128_desc(b0 + kk * 32), kIdesc,
-                                     (t | kk) != 0 ? 1u : 0u);
+                    for (int c = 0; c < kPChunks; ++c) {
+                        const uint32_t a0 = ptx::smem_u32(sA + (size_t)s * kPStageA + c * kPM * kPK);
+                        const uint32_t b0 = ptx::smem_u32(sB + (size_t)s * kPStageB + c * kPN * kPK);
+#pragma unroll
+                        for (int kk = 0; kk < kPK / 32; ++kk)
+                            ptx::mma_fp8(tmem + kColAcc, ptx::sw128_desc(a0 + kk * 32),
+                                         ptx::sw128_desc(b0 + kk * 32), kIdesc,
+                                         (t | c | kk) != 0 ? 1u : 0u);
+                    }
                     ptx::mma_commit(&sh->empty[s]);
                     ++g;
                 }
@@ -232,10 +263,10 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const int ew = warp - 2;            // 0..7
+        const int ew = warp - 2;            // 0..15
         const int q = warp & 3;             // tensor-memory lane quadrant
-        const int c0 = (ew >> 2) * 64;      // first of this warp's 64 replica columns
-        const int et = threadIdx.x - 64;    // 0..255
+        const int c0 = (ew >> 2) * 32;      // first of this warp's 32 replica columns
+        const int et = threadIdx.x - 64;    // 0..511
         const int i = m0 + q * 32 + lane;   // spin of this thread
         const bool live = i < a.N;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
@@ -243,20 +274,22 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
 
         // initial state of the tile into tensor memory
 #pragma unroll
-        for (int cb = 0; cb < 2; ++cb) {
-            uint32_t xr[32], yr[32];
+        for (int h = 0; h < 2; ++h) {
+            uint32_t xr[16], yr[16];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const size_t e = (size_t)(r0 + c0 + cb * 32 + j) * a.Np + i;
+            for (int j = 0; j < 16; ++j) {
+                const size_t e = (size_t)(r0 + c0 + h * 16 + j) * a.Np + i;
                 xr[j] = __float_as_uint(a.X[e]);
                 yr[j] = __float_as_uint(a.Y[e]);
             }
-            ptx::tmem_st32(tmem + lane_off + kColX + c0 + cb * 32, xr);
-            ptx::tmem_st32(tmem + lane_off + kColY + c0 + cb * 32, yr);
+            ptx::tmem_st16(tmem + lane_off + kColX + c0 + h * 16, xr);
+            ptx::tmem_st16(tmem + lane_off + kColY + c0 + h * 16, yr);
         }
         ptx::tmem_st_wait();
 
         bool left = false;
+        uint8_t *srow = sS + q * 32 + lane;  // this spin's byte in row `col` of the tile
+        float pk_next = a.nsteps > 0 ? a.pk[a.k_begin] : 0.f;
         for (int kl = 0; kl < passes; ++kl) {
             const bool final_pass = kl == a.nsteps;
             const int k = a.k_begin + kl;
@@ -265,6 +298,9 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 e = a.n_evals - 1;
             else if (a.eval_every > 0 && k > 0 && k < a.steps_total && k % a.eval_every == 0)
                 e = k / a.eval_every - 1;
+            const float pk = final_pass ? 0.f : pk_next;
+            if (kl + 1 < a.nsteps)
+                pk_next = a.pk[k + 1];  // p_k of the next pass, off the critical path
 
             const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
             if (epi_bar_or(!ok)) {
@@ -272,58 +308,58 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 break;
             }
             ptx::tc_fence_after();
-            uint32_t f[2][32];
-            ptx::tmem_ld32(tmem + lane_off + kColAcc + c0, f[0]);
-            ptx::tmem_ld32(tmem + lane_off + kColAcc + c0 + 32, f[1]);
-            ptx::tmem_ld_wait();
-            ptx::tc_fence_before();
-            epi_bar();
-            if (et == 0)
-                ptx::mbar_arrive(&sh->tmem_empty);  // the next step's MMA may overwrite
-
-            const float pk = final_pass ? 0.f : a.pk[k];
-            uint8_t *Snext = ((a.par0 + kl + 1) & 1) ? a.S8b : a.S8a;
 #pragma unroll
-            for (int cb = 0; cb < 2; ++cb) {
-                uint32_t xr[32], yr[32];
-                ptx::tmem_ld32(tmem + lane_off + kColX + c0 + cb * 32, xr);
-                ptx::tmem_ld32(tmem + lane_off + kColY + c0 + cb * 32, yr);
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t col0 = (uint32_t)(c0 + h * 16);
+                uint32_t f[16], xr[16], yr[16];
+                ptx::tmem_ld16(tmem + lane_off + kColAcc + col0, f);
+                ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
+                ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
                 ptx::tmem_ld_wait();
+                if (e >= 0) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = c0 + cb * 32 + j;
-                    const size_t eidx = (size_t)(r0 + col) * a.Np + i;
-                    const float fj = __uint_as_float(f[cb][j]);
-                    const float x0 = __uint_as_float(xr[j]);
-                    const float y0 = __uint_as_float(yr[j]);
-                    if (e >= 0) {
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = col0 + j;
+                        const float fj = __uint_as_float(f[j]);
+                        const float x0 = __uint_as_float(xr[j]);
                         float term = live ? (x0 >= 0.f ? fj : -fj) : 0.f;
 #pragma unroll
                         for (int off = 16; off > 0; off >>= 1)
                             term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
                         if (lane == 0)
                             sh->red[q][col] = term;
-                        a.Snap[(size_t)e * plane + eidx] = live ? fp8_sign(x0) : (uint8_t)0;
-                    }
-                    if (!final_pass) {
-                        float xn, yn;
-                        sb_update(fj, x0, y0, pk, a.c, xn, yn);
-                        xr[j] = __float_as_uint(xn);
-                        yr[j] = __float_as_uint(yn);
-                        Snext[eidx] = live ? fp8_sign(xn) : (uint8_t)0;
+                        a.Snap[(size_t)e * plane + (size_t)(r0 + col) * a.Np + i] =
+                            live ? fp8_sign(x0) : (uint8_t)0;
                     }
                 }
                 if (!final_pass) {
-                    ptx::tmem_st32(tmem + lane_off + kColX + c0 + cb * 32, xr);
-                    ptx::tmem_st32(tmem + lane_off + kColY + c0 + cb * 32, yr);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float xn, yn;
+                        sb_update(__uint_as_float(f[j]), __uint_as_float(xr[j]),
+                                  __uint_as_float(yr[j]), pk, a.c, xn, yn);
+                        xr[j] = __float_as_uint(xn);
+                        yr[j] = __float_as_uint(yn);
+                        srow[(col0 + j) * kPM] = live ? fp8_sign(xn) : (uint8_t)0;
+                    }
+                    ptx::tmem_st16(tmem + lane_off + kColX + col0, xr);
+                    ptx::tmem_st16(tmem + lane_off + kColY + col0, yr);
                 }
             }
+            ptx::tc_fence_before();
             if (!final_pass) {
                 ptx::tmem_st_wait();
-                ptx::fence_proxy_async_global();
+                ptx::fence_proxy_async_smem();  // tile writes before the TMA store reads them
             }
             epi_bar();
+            if (et == 0)
+                ptx::mbar_arrive(&sh->tmem_empty);  // accumulator read: the next MMA may start
             if (!final_pass && et == 0) {
+                // S(t_{k+1}) of this tile: one tile store, then publish the flag
+                ptx::tma_store_2d(((a.par0 + kl + 1) & 1) ? &tmapSt1 : &tmapSt0, m0, r0, sS);
+                ptx::bulk_commit();
+                ptx::bulk_wait_all();
+                ptx::fence_proxy_async_global();
                 ptx::fence_acq_rel_gpu();
                 ptx::st_release_gpu(&a.flags[mb * a.nrb + rb], kl + 1);
             }
@@ -336,14 +372,14 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         // final state back to global memory
         if (!left) {
 #pragma unroll
-            for (int cb = 0; cb < 2; ++cb) {
-                uint32_t xr[32], yr[32];
-                ptx::tmem_ld32(tmem + lane_off + kColX + c0 + cb * 32, xr);
-                ptx::tmem_ld32(tmem + lane_off + kColY + c0 + cb * 32, yr);
+            for (int h = 0; h < 2; ++h) {
+                uint32_t xr[16], yr[16];
+                ptx::tmem_ld16(tmem + lane_off + kColX + c0 + h * 16, xr);
+                ptx::tmem_ld16(tmem + lane_off + kColY + c0 + h * 16, yr);
                 ptx::tmem_ld_wait();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const size_t eidx = (size_t)(r0 + c0 + cb * 32 + j) * a.Np + i;
+                for (int j = 0; j < 16; ++j) {
+                    const size_t eidx = (size_t)(r0 + c0 + h * 16 + j) * a.Np + i;
                     a.X[eidx] = __uint_as_float(xr[j]);
                     a.Y[eidx] = __uint_as_float(yr[j]);
                 }
@@ -429,8 +465,8 @@ cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tc_fp8_persistent_kernel, plan->mapA, plan->mapB[0],
-                              plan->mapB[1], a);
+    return cudaLaunchKernelEx(&cfg, tc_fp8_persistent_kernel, plan->mapA3, plan->mapB3[0],
+                              plan->mapB3[1], plan->mapSt[0], plan->mapSt[1], a);
 }
 
 cudaError_t launch_select_best(cudaStream_t st, const float *Epart, const uint8_t *Snap,

@@ -345,8 +345,10 @@ EncodeTiledFn get_encode_fn()
 }
 
 // 2-D uint8 map over a row-major [rows][cols] array, box = 128 bytes x box_rows,
-// 128-byte swizzle (the layout the matrix descriptors above describe).
-bool encode_u8(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols, uint32_t box_rows)
+// with the 128-byte swizzle (the layout the matrix descriptors describe) or
+// without swizzle (plain tile stores).
+bool encode_u8(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols, uint32_t box_rows,
+               bool swizzle = true)
 {
     EncodeTiledFn fn = get_encode_fn();
     if (!fn)
@@ -358,6 +360,30 @@ bool encode_u8(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols, ui
     const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(ptr), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// 3-D view of the same [rows][cols] byte array: (byte within a 128-byte K
+// chunk, row, K chunk) with strides (1, cols, 128).  One box of
+// 128 x box_rows x chunks lands in shared memory as `chunks` consecutive
+// 128-byte-swizzled [box_rows][128] tiles, so a single copy fetches several K
+// chunks.  Chunks past the end read as zero.
+bool encode_u8_3d(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols,
+                  uint32_t box_rows, uint32_t chunks)
+{
+    EncodeTiledFn fn = get_encode_fn();
+    if (!fn)
+        return false;
+    if ((reinterpret_cast<uintptr_t>(ptr) & 15u) != 0 || (cols % 128u) != 0)
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)kBK, rows, cols / kBK};
+    const cuuint64_t strides[2] = {cols, (cuuint64_t)kBK};
+    const cuuint32_t box[3] = {(cuuint32_t)kBK, box_rows, chunks};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(ptr), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -376,7 +402,12 @@ cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S
     p->Rp = Rp;
     if (!encode_u8(&p->mapA, J8, (uint64_t)Np, (uint64_t)Np, kBM) ||
         !encode_u8(&p->mapB[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN) ||
-        !encode_u8(&p->mapB[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN)) {
+        !encode_u8(&p->mapB[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN) ||
+        !encode_u8_3d(&p->mapA3, J8, (uint64_t)Np, (uint64_t)Np, kBM, 2) ||
+        !encode_u8_3d(&p->mapB3[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN, 2) ||
+        !encode_u8_3d(&p->mapB3[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN, 2) ||
+        !encode_u8(&p->mapSt[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN, false) ||
+        !encode_u8(&p->mapSt[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN, false)) {
         delete p;
         return cudaErrorInvalidValue;
     }
