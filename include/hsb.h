@@ -177,6 +177,34 @@ HSB_API hsb_status hsb_set_couplings(hsb_handle h, const float *J);
  * queued on the device. */
 HSB_API hsb_status hsb_run_stats(hsb_handle h, long long *kernel_launches);
 
+/* Plain FP32 heated SB run (as hsb_run with HSB_PREC_FP32) that allocates
+ * nothing.  The paper has no counterpart: this entry point serves callers
+ * that cannot allocate device memory on demand -- code running under a fixed
+ * device-memory budget owned by another allocator (a framework's caching
+ * pool, a serving process sized at start-up), or code that must not call
+ * cudaMalloc / cudaFree because those calls synchronize the device and stall
+ * the work of other streams.
+ *   J            DEVICE, float32, N x N row-major couplings (symmetric, zero
+ *                diagonal; not validated, the caller owns them)
+ *   best_spins   DEVICE, int8, R x N (+1 / -1), written
+ *   best_energy  DEVICE, float64, R, written (binary64 Eq. (eq_Ising))
+ *   cuda_stream  cudaStream_t on which all work is queued (NULL: legacy
+ *                default stream); the call returns once the work is queued.
+ * Limits: 2 <= N <= 512 and 1 <= R <= 256; larger sizes return HSB_E_INVAL.
+ * p->c0 must be given (> 0): the couplings stay on the device, so the c1
+ * normalisation is not applied; p->prec and p->schedule are ignored.
+ * Every intermediate buffer lives in one file-scope device array of about
+ * 2.6 MB that each GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the previous call's contents (the
+ * call rewrites every part it reads first): calls whose work overlaps on the
+ * GPU -- on different streams, or from different threads -- race and give
+ * wrong results, so serialise them. */
+HSB_API hsb_status hsb_run_fp32_noalloc(const float *J, int N, const hsb_params *p, int R,
+                                        int steps, uint64_t seed, int8_t *best_spins,
+                                        double *best_energy, void *cuda_stream);
+
 /* Waits for the work queued on the handle's stream and reports a device-side
  * failure of it (HSB_E_TIMEOUT when a bounded wait inside a kernel gave up). */
 HSB_API hsb_status hsb_synchronize(hsb_handle h);

@@ -31,7 +31,7 @@ SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2}
 EXPORTS = ["hsb_params_default", "hsb_version", "hsb_create", "hsb_destroy", "hsb_set_stream",
            "hsb_info", "hsb_run", "hsb_run_device", "hsb_get_state", "hsb_advance",
            "hsb_advance_device", "hsb_set_couplings", "hsb_run_stats", "hsb_synchronize",
-           "hsb_last_error"]
+           "hsb_run_fp32_noalloc", "hsb_last_error"]
 
 
 class HsbError(RuntimeError):
@@ -104,6 +104,8 @@ def load():
         lib.hsb_run_stats.argtypes = [H, C.POINTER(C.c_longlong)]
         lib.hsb_synchronize.restype = I
         lib.hsb_synchronize.argtypes = [H]
+        lib.hsb_run_fp32_noalloc.restype = I
+        lib.hsb_run_fp32_noalloc.argtypes = [P, I, C.POINTER(Params), I, I, C.c_uint64, P, P, P]
         _lib = lib
         return lib
 
@@ -216,6 +218,15 @@ def run_stats(h: int) -> int:
     n = C.c_longlong()
     _check(load().hsb_run_stats(C.c_void_p(h), C.byref(n)))
     return int(n.value)
+
+
+def run_fp32_noalloc(J_ptr: int, N: int, p: Params, R: int, steps: int, seed: int,
+                     spins_ptr: int, energy_ptr: int, stream_ptr: int | None = None) -> None:
+    """hsb_run_fp32_noalloc: device couplings and outputs, fixed scratch, no allocation."""
+    _check(load().hsb_run_fp32_noalloc(C.c_void_p(J_ptr), int(N), C.byref(p), int(R),
+                                       int(steps), C.c_uint64(seed & (2**64 - 1)),
+                                       C.c_void_p(spins_ptr), C.c_void_p(energy_ptr),
+                                       C.c_void_p(stream_ptr or 0)))
 
 
 def synchronize(h: int) -> None:

@@ -21,16 +21,16 @@ using namespace hsb;
 
 namespace {
 
-thread_local std::string g_last_error;
+// Message of the last failed call on this thread (fixed storage, so that
+// reporting an error never allocates).
+thread_local char g_last_error[512];
 
 hsb_status set_error(hsb_status s, const char *fmt, ...)
 {
-    char buf[512];
     va_list ap;
     va_start(ap, fmt);
-    vsnprintf(buf, sizeof buf, fmt, ap);
+    vsnprintf(g_last_error, sizeof g_last_error, fmt, ap);
     va_end(ap);
-    g_last_error = buf;
     return s;
 }
 
@@ -557,13 +557,20 @@ hsb_status check_device_error(hsb_ctx *h)
 
 }  // namespace
 
+namespace hsb {
+hsb_status report_error(hsb_status s, const char *msg)
+{
+    return set_error(s, "%s", msg);
+}
+}  // namespace hsb
+
 // =================================================================== ABI ===
 
 extern "C" {
 
 int hsb_version(void) { return HSB_API_VERSION; }
 
-const char *hsb_last_error(void) { return g_last_error.c_str(); }
+const char *hsb_last_error(void) { return g_last_error; }
 
 hsb_status hsb_params_default(hsb_params *p)
 {
