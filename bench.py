@@ -273,6 +273,34 @@ def run_gpu(args):
         solver.synchronize()
         loop_ms = k0.elapsed_time(k1) / reps_k
 
+    # ---- the plain FP32 GPU form on the same workload (CUDA cores, fused
+    # multiply-add force): its trajectories are identical to the FP8 path's,
+    # so the speedup compares runs of equal final-energy accuracy
+    def fp32_comparison():
+        p32 = hsb.params(w["form"], "fp32", a0=w["a0"], c1=w["c1"], dt=w["dt"],
+                         gamma=w["gamma"], init_half_width=w["init_half_width"],
+                         eval_every=w["eval_every"])
+        spins32 = torch.empty_like(spins)
+        energy32 = torch.empty_like(energy)
+        with torch.cuda.stream(stream):
+            solver.run_device(p32, R, S, seed, spins32.data_ptr(), energy32.data_ptr())
+            solver.synchronize()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            fp32_runs = 2
+            f0.record(stream)
+            for _ in range(fp32_runs):
+                solver.run_device(p32, R, S, seed, spins32.data_ptr(), energy32.data_ptr())
+            f1.record(stream)
+            solver.synchronize()
+            ms = f0.elapsed_time(f1) / fp32_runs
+            one_run()
+            solver.synchronize()
+        same = bool(torch.equal(spins, spins32) and torch.equal(energy, energy32))
+        return ms, same
+
+    fp32_ms, identical = (None, None) if args.no_fp32_baseline else fp32_comparison()
+
     t_max = elapsed_ms
     if world > 1:
         t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
@@ -336,7 +364,12 @@ def run_gpu(args):
             "roofline": roofline, "clocks": clock_rec,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(N * N * 4),
                     "d2h_bytes_per_step": int(R * N + R * 8)},
-            "gpu_launches": int(launches_per_run * args.steps)}
+            "gpu_launches": int(launches_per_run * args.steps),
+            "fp32_gpu_baseline": None if fp32_ms is None else {
+                "value": N * R * S / (fp32_ms / 1000.0), "unit": UNIT, "ms_per_run": fp32_ms,
+                "speedup_fp8": (t_max / args.steps) and fp32_ms / (t_max / args.steps),
+                "identical_results": identical,
+                "kernel": "simt_step_kernel (plain FP32, CUDA cores)"}}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -352,6 +385,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["hsb", "reference"], default="hsb")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32-baseline", action="store_true",
+                    help="skip the plain FP32 GPU comparison (e.g. for launch-list captures)")
     ap.add_argument("--sb-steps", type=int, default=None,
                     help="override the SB steps per run (profiling of small cases only; "
                          "the headline workload is 2000)")
