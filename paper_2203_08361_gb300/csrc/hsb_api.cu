@@ -110,6 +110,10 @@ struct hsb_ctx {
     double pk_a0 = 0.0;
     float *Eeval = nullptr;
     size_t eeval_cap = 0;
+    // split-BF16 path: couplings [J_hi | J_lo], operand ping/pong, plan
+    void *Jcat = nullptr;
+    void *Xcat[2] = {nullptr, nullptr};
+    Bf16Plan *bplan = nullptr;
     uint8_t *Snap = nullptr;
     size_t snap_cap = 0;
     // graph cache: the whole run, and the step range of hsb_advance_device
@@ -135,6 +139,13 @@ void free_run_buffers(hsb_ctx *h)
         tc_plan_destroy(h->plan);
         h->plan = nullptr;
     }
+    if (h->bplan) {
+        bf16_plan_destroy(h->bplan);
+        h->bplan = nullptr;
+    }
+    cudaFree(h->Xcat[0]);
+    cudaFree(h->Xcat[1]);
+    h->Xcat[0] = h->Xcat[1] = nullptr;
     cudaFree(h->X[0]);
     cudaFree(h->X[1]);
     cudaFree(h->Y);
@@ -198,6 +209,25 @@ hsb_status ensure_fp8(hsb_ctx *h)
     return HSB_OK;
 }
 
+hsb_status ensure_bf16(hsb_ctx *h)
+{
+    const size_t np = (size_t)h->Np;
+    if (!h->Jcat) {
+        CK(cudaMalloc(&h->Jcat, np * 2 * np * 2), "cudaMalloc Jcat");
+        CK(launch_split_couplings(h->work, h->J32, h->Np, h->Jcat), "split couplings");
+    }
+    for (int b = 0; b < 2; ++b)
+        if (!h->Xcat[b]) {
+            CK(cudaMalloc(&h->Xcat[b], (size_t)h->Rcap * 2 * np * 2), "cudaMalloc Xcat");
+            CK(cudaMemsetAsync(h->Xcat[b], 0, (size_t)h->Rcap * 2 * np * 2, h->work),
+               "memset Xcat");
+        }
+    if (!h->bplan)
+        CK(bf16_plan_create(&h->bplan, h->Jcat, h->Xcat[0], h->Xcat[1], h->Np, h->Rcap),
+           "bf16_plan_create");
+    return HSB_OK;
+}
+
 hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunCfg *cfg)
 {
     if (!p)
@@ -219,14 +249,21 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
     if ((long long)R * h->N > (1LL << 40))
         return set_error(HSB_E_INVAL, "R*N too large");
     int prec = p->prec;
-    if (prec == HSB_PREC_AUTO)
-        prec = (p->form == HSB_DISCRETE && h->pm1) ? HSB_PREC_FP8 : HSB_PREC_FP32;
+    const int Rp_ = round_up(R, kTileR);
+    if (prec == HSB_PREC_AUTO) {
+        if (p->form == HSB_DISCRETE && h->pm1)
+            prec = HSB_PREC_FP8;
+        else
+            prec = tc_bf16_persistent_fits(h->Np, Rp_) ? HSB_PREC_BF16X3 : HSB_PREC_FP32;
+    }
     if (prec == HSB_PREC_FP8 && !(p->form == HSB_DISCRETE && h->pm1))
         return set_error(HSB_E_UNSUPPORTED,
                          "FP8 needs the discrete form and couplings in {-1, 0, +1}");
-    if (prec == HSB_PREC_BF16X3)
-        return set_error(HSB_E_UNSUPPORTED, "BF16X3 precision is not available in this build");
-    if (prec != HSB_PREC_FP32 && prec != HSB_PREC_FP8)
+    if (prec == HSB_PREC_BF16X3 && !tc_bf16_persistent_fits(h->Np, Rp_))
+        return set_error(HSB_E_UNSUPPORTED,
+                         "BF16X3 runs as one persistent kernel; its %d x %d grid does not fit",
+                         h->Np / kTileM, Rp_ / kTileR);
+    if (prec != HSB_PREC_FP32 && prec != HSB_PREC_FP8 && prec != HSB_PREC_BF16X3)
         return set_error(HSB_E_INVAL, "unknown precision %d", p->prec);
     cfg->prec = prec;
     cfg->form = p->form;
@@ -370,6 +407,11 @@ hsb_status prepare(hsb_ctx *h, const RunCfg &c)
         if (s != HSB_OK)
             return s;
     }
+    if (c.prec == HSB_PREC_BF16X3) {
+        s = ensure_bf16(h);
+        if (s != HSB_OK)
+            return s;
+    }
     return HSB_OK;
 }
 
@@ -479,12 +521,96 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     return HSB_OK;
 }
 
+// Queues the split-BF16 persistent kernel for updates [k_begin, k_begin +
+// nsteps) from operand buffer par0 (state in X[0], Y).
+hsb_status enqueue_bf16(hsb_ctx *h, const RunCfg &c, int k_begin, int nsteps, int par0)
+{
+    const int nblk = h->Np / kTileM;
+    const int nrb = c.Rp / kTileR;
+    hsb_status s = ensure_pk(h, c);
+    if (s == HSB_OK)
+        s = grow(&h->flags, &h->flags_cap, (size_t)nblk * nrb, "cudaMalloc flags");
+    if (s != HSB_OK)
+        return s;
+    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * sizeof(int), h->work), "memset flags");
+    PersistArgs a;
+    memset(&a, 0, sizeof a);
+    a.N = h->N;
+    a.Np = h->Np;
+    a.Rp = c.Rp;
+    a.nblk = nblk;
+    a.nrb = nrb;
+    a.k_begin = k_begin;
+    a.nsteps = nsteps;
+    a.final_pass = 0;
+    a.steps_total = c.steps;
+    a.par0 = par0;
+    a.pk = h->pk_dev;
+    a.c = c.c;
+    a.X = h->X[0];
+    a.Y = h->Y;
+    a.flags = h->flags;
+    a.err = h->err;
+    CK(launch_tc_bf16x3_persistent(h->work, h->bplan, c.form, a), "persistent bf16x3 kernel");
+    return HSB_OK;
+}
+
+// Whole split-BF16 run: the step loop is cut at the evaluation steps; each
+// evaluation is the plain-FP32 energy pass over sgn(x) (exact for +/-1
+// couplings, binary32 fused multiply-adds otherwise) and a best update.
+hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_params *p)
+{
+    const int nblk = h->Np / kTileM;
+    CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->work), "memset err");
+    CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R, c.Rp,
+                   h->X[0], h->Y, nullptr, h->Ebest),
+       "init kernel");
+    CK(launch_split_state(h->work, h->X[0], h->N, h->Np, c.Rp, c.form, h->Xcat[0]),
+       "split state");
+    int par = 0, k = 0;
+    long long launches = 2;
+    while (k < c.steps) {
+        int kb = c.steps;
+        if (c.eval_every > 0) {
+            const int next = (k / c.eval_every + 1) * c.eval_every;
+            if (next < c.steps)
+                kb = next;
+        }
+        hsb_status s = enqueue_bf16(h, c, k, kb - k, par);
+        if (s != HSB_OK)
+            return s;
+        par = (par + (kb - k)) & 1;
+        k = kb;
+        // evaluation of s(t_k): at an evaluation step, and at the end
+        CK(launch_simt_step(h->work, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[0], nullptr,
+                            h->Y, 0.f, c.c, h->Epart),
+           "energy kernel");
+        CK(launch_best_update(h->work, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[0], nullptr,
+                              h->Ebest, h->Sbest),
+           "best kernel");
+        launches += 3;
+    }
+    if (!h->pm1) {
+        CK(launch_final_energy_f64(h->work, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efinal),
+           "final energy kernel");
+        launches += 1;
+    }
+    h->last_R = c.R;
+    h->last_x = 0;
+    h->state_par = par;
+    h->have_state = true;
+    h->launches = launches;
+    return HSB_OK;
+}
+
 // Queues a whole run (init, graph of the step loop) on the work stream.
 hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_params *p)
 {
     hsb_status s = prepare(h, c);
     if (s != HSB_OK)
         return s;
+    if (c.prec == HSB_PREC_BF16X3)
+        return enqueue_run_bf16(h, c, seed, p);
     bool persistent = false;
     s = use_persistent(h, c, &persistent);
     if (s != HSB_OK)
@@ -682,6 +808,7 @@ void hsb_destroy(hsb_handle h)
     free_run_buffers(h);
     cudaFree(h->J32);
     cudaFree(h->J8);
+    cudaFree(h->Jcat);
     cudaFree(h->err);
     cudaFree(h->flags);
     cudaFree(h->pk_dev);
@@ -817,6 +944,23 @@ hsb_status hsb_advance(hsb_handle h, const hsb_params *p, int R, int steps, int 
     if (c.prec == HSB_PREC_FP8)
         CK(launch_sign_to_fp8(h->work, h->X[0], h->N, h->Np, c.Rp, h->S8[k_begin & 1]),
            "sign kernel");
+    if (c.prec == HSB_PREC_BF16X3) {
+        CK(launch_split_state(h->work, h->X[0], h->N, h->Np, c.Rp, c.form, h->Xcat[0]),
+           "split state");
+        if (k_end > k_begin) {
+            s = enqueue_bf16(h, c, k_begin, k_end - k_begin, 0);
+            if (s != HSB_OK)
+                return s;
+        }
+        CK(cudaMemcpy2DAsync(x, row, h->X[0], pitch, row, (size_t)R, cudaMemcpyDeviceToHost,
+                             h->work),
+           "copy x back");
+        CK(cudaMemcpy2DAsync(y, row, h->Y, pitch, row, (size_t)R, cudaMemcpyDeviceToHost,
+                             h->work),
+           "copy y back");
+        h->have_state = false;
+        return check_device_error(h);
+    }
     bool persistent = false;
     s = use_persistent(h, c, &persistent);
     if (s != HSB_OK)
@@ -864,6 +1008,16 @@ hsb_status hsb_advance_device(hsb_handle h, const hsb_params *p, int R, int step
     if (s != HSB_OK)
         return s;
     const int par = h->state_par;
+    if (c.prec == HSB_PREC_BF16X3) {
+        if (k_end > k_begin) {
+            s = enqueue_bf16(h, c, k_begin, k_end - k_begin, par);
+            if (s != HSB_OK)
+                return s;
+        }
+        h->state_par = (par + (k_end - k_begin)) & 1;
+        h->launches = k_end > k_begin ? 1 : 0;
+        return HSB_OK;
+    }
     bool persistent = false;
     s = use_persistent(h, c, &persistent);
     if (s != HSB_OK)
@@ -964,6 +1118,8 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
             h->J8 = nullptr;
         }
     }
+    if (h->Jcat)
+        CK(launch_split_couplings(h->work, h->J32, h->Np, h->Jcat), "split couplings");
     CK(cudaStreamSynchronize(h->work), "synchronize");
     return HSB_OK;
 }

@@ -115,4 +115,20 @@ cudaError_t launch_select_best(cudaStream_t st, const float *Epart, const uint8_
                                int n_evals, int nblk, int N, int Np, int R, int Rp,
                                double *Ebest, int8_t *Sbest);
 
+// ---- hsb_persist_bf16.cu ---------------------------------------------------
+// Split-BF16 persistent kernel for general couplings (form 0 ballistic, 1
+// discrete).  Jcat: [Np][2 Np] BF16 [J_hi | J_lo]; operand buffers Xcat[b]:
+// [Rcap][2 Np] BF16 [x_hi | x_lo] (ballistic) or [sgn x | unused] (discrete).
+// The kernel runs a.nsteps updates without evaluation (a.final_pass == 0).
+struct Bf16Plan;
+cudaError_t bf16_plan_create(Bf16Plan **out, const void *Jcat, const void *Xcat0,
+                             const void *Xcat1, int Np, int Rp);
+void bf16_plan_destroy(Bf16Plan *p);
+cudaError_t launch_split_couplings(cudaStream_t st, const float *J32, int Np, void *Jcat);
+cudaError_t launch_split_state(cudaStream_t st, const float *X, int N, int Np, int Rp, int form,
+                               void *Xcat);
+bool tc_bf16_persistent_fits(int Np, int Rp);
+cudaError_t launch_tc_bf16x3_persistent(cudaStream_t st, const Bf16Plan *plan, int form,
+                                        const PersistArgs &a);
+
 }  // namespace hsb

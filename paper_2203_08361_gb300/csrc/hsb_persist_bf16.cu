@@ -1,0 +1,537 @@
+// hsb_persist_bf16.cu -- persistent tcgen05 kernel for heated SB with general
+// (e.g. Gaussian) couplings: the force J x (ballistic, Eq. (eq_fb)) or
+// J sgn(x) (discrete, Eq. (eq_fd)) as split-BF16 products with FP32
+// accumulation, fused with the Methods update (Kanao & Goto, arXiv 2203.08361).
+//
+// Split precision: J = J_hi + J_lo and x = x_hi + x_lo with BF16 parts
+// (hi = bf16(v), lo = bf16(v - hi); v - hi is exact in binary32).  The force
+//     F = J_hi x_hi + J_lo x_hi + J_hi x_lo
+// drops only J_lo x_lo and the rounding of the lo parts, about 3 * 2^-18 of
+// |J_ij x_j| per term; accumulation is FP32 in tensor memory.  In the discrete
+// form the operand sgn(x) is exact in BF16 and F = J_hi s + J_lo s.
+//
+// Layout: J and the operand are stored as [hi | lo] planes side by side, a
+// [rows][2 * Np] BF16 array, so one 3-D TMA box (64 K elements x 128 rows x
+// 2 planes, 128-byte swizzle) fetches both planes of a K chunk in one copy.
+//
+// Structure as in hsb_persist.cu (one 128 x 128 tile per CTA for the whole
+// launch, x and y in tensor memory, per-tile published flags, bounded waits),
+// with two differences: K chunks are consumed in a fixed order per CTA (own
+// row block first, then ascending with wrap-around), because BF16 products
+// are not exact and the sum must not depend on timing; and there is no
+// evaluation inside the kernel -- the host splits a run at evaluation steps.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hsb_device.cuh"
+#include "hsb_internal.cuh"
+#include "hsb_ptx.cuh"
+
+namespace hsb {
+
+namespace {
+
+constexpr int kQM = 128;        // spins per tile
+constexpr int kQN = 128;        // replicas per tile
+constexpr int kQKE = 64;        // K elements per chunk (128 bytes of BF16)
+constexpr int kQStages = 2;
+constexpr int kQPlane = kQM * 128;           // one 128 x 128-byte plane, 16 KB
+constexpr int kQStageA = 2 * kQPlane;        // hi + lo
+constexpr int kQStageB = 2 * kQPlane;        // hi + lo (discrete form uses one plane)
+constexpr int kQTile = kQN * kQM * 2;        // BF16 [replica][spin] store tile, 32 KB
+constexpr int kQEpiWarps = 16;
+constexpr int kQEpiThreads = 32 * kQEpiWarps;
+constexpr int kQThreads = 64 + kQEpiThreads;
+constexpr uint32_t kQTmemCols = 512;
+constexpr uint32_t kQColAcc = 0;
+constexpr uint32_t kQColX = 128;
+constexpr uint32_t kQColY = 256;
+
+// Instruction descriptor, kind::f16 with A = B = BF16 (format 1 at bits 7-9
+// and 10-12), D = F32 (bits 4-5 = 1), K-major, N >> 3 at 17-22, M >> 4 at 24-28.
+constexpr uint32_t kQIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kQN >> 3) << 17) |
+                             ((uint32_t)(kQM >> 4) << 24);
+
+struct __align__(8) QShared {
+    uint64_t full[kQStages];
+    uint64_t empty[kQStages];
+    uint64_t accfull;
+    uint64_t tmem_empty;
+    uint32_t tmem_base;
+    int abort;
+};
+
+constexpr size_t kQSmem =
+    1024 + (size_t)kQStages * (kQStageA + kQStageB) + 2 * (size_t)kQTile + sizeof(QShared);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kQIdesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ bool qbar_or(bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(kQEpiThreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void qbar() { ptx::named_bar(1, kQEpiThreads); }
+
+}  // namespace
+
+template <int FORM>
+__global__ void __launch_bounds__(kQThreads, 1)
+tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
+                            const __grid_constant__ CUtensorMap tmapB0,
+                            const __grid_constant__ CUtensorMap tmapB1,
+                            const __grid_constant__ CUtensorMap tmapSt0,
+                            const __grid_constant__ CUtensorMap tmapSt1, const PersistArgs a)
+{
+    constexpr int kBPlanes = FORM == 0 ? 2 : 1;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sA = base;
+    uint8_t *sB = base + (size_t)kQStages * kQStageA;
+    uint8_t *sT = sB + (size_t)kQStages * kQStageB;  // store tiles: hi, then lo
+    QShared *sh = reinterpret_cast<QShared *>(sT + 2 * (size_t)kQTile);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int mb = blockIdx.x;
+    const int rb = blockIdx.y;
+    const int m0 = mb * kQM;
+    const int r0 = rb * kQN;
+    const int nblk = a.nblk;
+    const int nchunks = a.Np / kQKE;  // two per row block
+    const int passes = a.nsteps;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kQStages; ++s) {
+            ptx::mbar_init(&sh->full[s], 1);
+            ptx::mbar_init(&sh->empty[s], 1);
+        }
+        ptx::mbar_init(&sh->accfull, 1);
+        ptx::mbar_init(&sh->tmem_empty, 1);
+        sh->abort = 0;
+        ptx::mbar_init_fence();
+    }
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tmap(&tmapJ);
+        ptx::prefetch_tmap(&tmapB0);
+        ptx::prefetch_tmap(&tmapB1);
+        ptx::prefetch_tmap(&tmapSt0);
+        ptx::prefetch_tmap(&tmapSt1);
+    }
+    if (warp == 1)
+        ptx::tmem_alloc(&sh->tmem_base, kQTmemCols);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool fail = false;
+            for (int kl = 0; kl < passes && !fail; ++kl) {
+                const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? &tmapB1 : &tmapB0;
+                const unsigned long long t0 = ptx::globaltimer();
+                for (int t = 0; t < nblk && !fail; ++t) {
+                    int kb = mb + t;  // fixed order: own row block first
+                    if (kb >= nblk)
+                        kb -= nblk;
+                    // wait until row block kb has published the operand of this pass
+                    while (ptx::ld_acquire_gpu(&a.flags[kb * a.nrb + rb]) < kl) {
+                        if (*(volatile int *)&sh->abort ||
+                            ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
+                            *(volatile int *)&sh->abort = 1;
+                            atomicExch(a.err, kErrTimeout);
+                            fail = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    if (fail)
+                        break;
+                    ptx::fence_proxy_async_global();
+                    for (int h = 0; h < 2; ++h) {
+                        const int c = 2 * kb + h;
+                        const int s = (int)(g % kQStages);
+                        const uint32_t ph = (g / kQStages) & 1u;
+                        if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err)) {
+                            fail = true;
+                            break;
+                        }
+                        ptx::mbar_expect_tx(&sh->full[s],
+                                            (uint32_t)(kQStageA + kBPlanes * kQPlane));
+                        ptx::tma_load_3d(sA + (size_t)s * kQStageA, &tmapJ, c * kQKE, m0, 0,
+                                         &sh->full[s]);
+                        ptx::tma_load_3d(sB + (size_t)s * kQStageB, mapB, c * kQKE, r0, 0,
+                                         &sh->full[s]);
+                        ++g;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // --------------------------------------------------------------- MMA
+        if (lane == 0) {
+            uint32_t g = 0;
+            for (int kl = 0; kl < passes; ++kl) {
+                if (kl > 0) {
+                    if (!ptx::mbar_wait(&sh->tmem_empty, (uint32_t)(kl - 1) & 1u, &sh->abort,
+                                        a.err))
+                        break;
+                    ptx::tc_fence_after();
+                }
+                bool ok = true;
+                for (int t = 0; t < nchunks; ++t) {
+                    const int s = (int)(g % kQStages);
+                    const uint32_t ph = (g / kQStages) & 1u;
+                    if (!ptx::mbar_wait(&sh->full[s], ph, &sh->abort, a.err)) {
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t ahi = ptx::smem_u32(sA + (size_t)s * kQStageA);
+                    const uint32_t alo = ahi + kQPlane;
+                    const uint32_t bhi = ptx::smem_u32(sB + (size_t)s * kQStageB);
+                    const uint32_t blo = bhi + kQPlane;
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t off = kk * 32;
+                        mma_bf16(tmem + kQColAcc, ptx::sw128_desc(ahi + off),
+                                 ptx::sw128_desc(bhi + off), (t | kk) != 0 ? 1u : 0u);
+                        mma_bf16(tmem + kQColAcc, ptx::sw128_desc(alo + off),
+                                 ptx::sw128_desc(bhi + off), 1u);
+                        if (FORM == 0)
+                            mma_bf16(tmem + kQColAcc, ptx::sw128_desc(ahi + off),
+                                     ptx::sw128_desc(blo + off), 1u);
+                    }
+                    ptx::mma_commit(&sh->empty[s]);
+                    ++g;
+                }
+                if (!ok)
+                    break;
+                ptx::mma_commit(&sh->accfull);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int ew = warp - 2;
+        const int q = warp & 3;
+        const int c0 = (ew >> 2) * 32;
+        const int et = threadIdx.x - 64;
+        const int i = m0 + q * 32 + lane;
+        const bool live = i < a.N;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        __nv_bfloat16 *tHi = reinterpret_cast<__nv_bfloat16 *>(sT) + q * 32 + lane;
+        __nv_bfloat16 *tLo = reinterpret_cast<__nv_bfloat16 *>(sT + kQTile) + q * 32 + lane;
+
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            uint32_t xr[16], yr[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const size_t e = (size_t)(r0 + c0 + h * 16 + j) * a.Np + i;
+                xr[j] = __float_as_uint(a.X[e]);
+                yr[j] = __float_as_uint(a.Y[e]);
+            }
+            ptx::tmem_st16(tmem + lane_off + kQColX + c0 + h * 16, xr);
+            ptx::tmem_st16(tmem + lane_off + kQColY + c0 + h * 16, yr);
+        }
+        ptx::tmem_st_wait();
+
+        bool left = false;
+        float pk_next = passes > 0 ? a.pk[a.k_begin] : 0.f;
+        for (int kl = 0; kl < passes; ++kl) {
+            const int k = a.k_begin + kl;
+            const float pk = pk_next;
+            if (kl + 1 < passes)
+                pk_next = a.pk[k + 1];
+            const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
+            if (qbar_or(!ok)) {
+                left = true;
+                break;
+            }
+            ptx::tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t col0 = (uint32_t)(c0 + h * 16);
+                uint32_t f[16], xr[16], yr[16];
+                ptx::tmem_ld16(tmem + lane_off + kQColAcc + col0, f);
+                ptx::tmem_ld16(tmem + lane_off + kQColX + col0, xr);
+                ptx::tmem_ld16(tmem + lane_off + kQColY + col0, yr);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float xn, yn;
+                    sb_update(__uint_as_float(f[j]), __uint_as_float(xr[j]),
+                              __uint_as_float(yr[j]), pk, a.c, xn, yn);
+                    xr[j] = __float_as_uint(xn);
+                    yr[j] = __float_as_uint(yn);
+                    const int col = col0 + j;
+                    if (FORM == 0) {
+                        // x' = hi + lo, hi = bf16(x'), lo = bf16(x' - hi)
+                        const __nv_bfloat16 hi = __float2bfloat16_rn(xn);
+                        const __nv_bfloat16 lo =
+                            __float2bfloat16_rn(__fsub_rn(xn, __bfloat162float(hi)));
+                        tHi[col * kQM] = live ? hi : __float2bfloat16_rn(0.f);
+                        tLo[col * kQM] = live ? lo : __float2bfloat16_rn(0.f);
+                    } else {
+                        tHi[col * kQM] = __float2bfloat16_rn(live ? (xn >= 0.f ? 1.f : -1.f) : 0.f);
+                    }
+                }
+                ptx::tmem_st16(tmem + lane_off + kQColX + col0, xr);
+                ptx::tmem_st16(tmem + lane_off + kQColY + col0, yr);
+            }
+            ptx::tc_fence_before();
+            ptx::tmem_st_wait();
+            ptx::fence_proxy_async_smem();
+            qbar();
+            if (et == 0) {
+                ptx::mbar_arrive(&sh->tmem_empty);
+                const CUtensorMap *st = ((a.par0 + kl + 1) & 1) ? &tmapSt1 : &tmapSt0;
+                ptx::tma_store_2d(st, m0, r0, sT);
+                if (FORM == 0)
+                    ptx::tma_store_2d(st, a.Np + m0, r0, sT + kQTile);
+                ptx::bulk_commit();
+                ptx::bulk_wait_all();
+                ptx::fence_proxy_async_global();
+                ptx::fence_acq_rel_gpu();
+                ptx::st_release_gpu(&a.flags[mb * a.nrb + rb], kl + 1);
+            }
+        }
+        if (!left) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t xr[16], yr[16];
+                ptx::tmem_ld16(tmem + lane_off + kQColX + c0 + h * 16, xr);
+                ptx::tmem_ld16(tmem + lane_off + kQColY + c0 + h * 16, yr);
+                ptx::tmem_ld_wait();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const size_t eidx = (size_t)(r0 + c0 + h * 16 + j) * a.Np + i;
+                    a.X[eidx] = __uint_as_float(xr[j]);
+                    a.Y[eidx] = __uint_as_float(yr[j]);
+                }
+            }
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 1)
+        ptx::tmem_dealloc(tmem, kQTmemCols);
+}
+
+// ------------------------------------------------------------- host side ---
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 3-D load map over a [rows][2 * Np] BF16 [hi | lo] array: (K element, row,
+// plane) with strides (2, 4 * Np, 2 * Np) bytes; box 64 x 128 x planes.
+bool encode_planes(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t Np, uint32_t planes)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0)
+        return false;
+    const cuuint64_t dims[3] = {Np, rows, 2};
+    const cuuint64_t strides[2] = {4 * Np, 2 * Np};
+    const cuuint32_t box[3] = {(cuuint32_t)kQKE, 128, planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 2-D store map over the same array: box 128 spins x 128 replicas, no swizzle.
+bool encode_store(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t Np)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0)
+        return false;
+    const cuuint64_t dims[2] = {2 * Np, rows};
+    const cuuint64_t strides[1] = {4 * Np};
+    const cuuint32_t box[2] = {128, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// J -> [J_hi | J_lo] BF16 planes, zero padding.
+__global__ void split_couplings_kernel(const float *__restrict__ J32, int Np,
+                                       __nv_bfloat16 *__restrict__ Jcat)
+{
+    const size_t total = (size_t)Np * Np;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = e / Np, c = e % Np;
+        const float v = J32[e];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(v, __bfloat162float(hi)));
+        Jcat[r * 2 * Np + c] = hi;
+        Jcat[r * 2 * Np + Np + c] = lo;
+    }
+}
+
+// Operand of the first step: [x_hi | x_lo] (ballistic) or [sgn x | 0]
+// (discrete) from the state X, zero for padded spins.
+__global__ void split_state_kernel(const float *__restrict__ X, int N, int Np, int Rp, int form,
+                                   __nv_bfloat16 *__restrict__ Xcat)
+{
+    const size_t total = (size_t)Rp * Np;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = e / Np, i = e % Np;
+        const float x = X[e];
+        __nv_bfloat16 hi, lo = __float2bfloat16_rn(0.f);
+        if ((int)i >= N) {
+            hi = __float2bfloat16_rn(0.f);
+        } else if (form == 0) {
+            hi = __float2bfloat16_rn(x);
+            lo = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(hi)));
+        } else {
+            hi = __float2bfloat16_rn(x >= 0.f ? 1.f : -1.f);
+        }
+        Xcat[r * 2 * Np + i] = hi;
+        Xcat[r * 2 * Np + Np + i] = lo;
+    }
+}
+
+}  // namespace
+
+struct Bf16Plan {
+    CUtensorMap mapJ;
+    CUtensorMap mapB[2][2];  // [form][buffer]: 2 planes (ballistic) / 1 plane (discrete)
+    CUtensorMap mapSt[2];
+    int Np, Rp;
+};
+
+cudaError_t bf16_plan_create(Bf16Plan **out, const void *Jcat, const void *Xcat0,
+                             const void *Xcat1, int Np, int Rp)
+{
+    *out = nullptr;
+    if (Np % 128 != 0 || Rp % 128 != 0)
+        return cudaErrorInvalidValue;
+    Bf16Plan *p = new Bf16Plan();
+    p->Np = Np;
+    p->Rp = Rp;
+    const void *xb[2] = {Xcat0, Xcat1};
+    bool ok = encode_planes(&p->mapJ, Jcat, (uint64_t)Np, (uint64_t)Np, 2);
+    for (int b = 0; b < 2 && ok; ++b) {
+        ok = encode_planes(&p->mapB[0][b], xb[b], (uint64_t)Rp, (uint64_t)Np, 2) &&
+             encode_planes(&p->mapB[1][b], xb[b], (uint64_t)Rp, (uint64_t)Np, 1) &&
+             encode_store(&p->mapSt[b], xb[b], (uint64_t)Rp, (uint64_t)Np);
+    }
+    if (!ok) {
+        delete p;
+        return cudaErrorInvalidValue;
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+void bf16_plan_destroy(Bf16Plan *p) { delete p; }
+
+cudaError_t launch_split_couplings(cudaStream_t st, const float *J32, int Np, void *Jcat)
+{
+    split_couplings_kernel<<<152 * 8, 256, 0, st>>>(J32, Np,
+                                                    static_cast<__nv_bfloat16 *>(Jcat));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_state(cudaStream_t st, const float *X, int N, int Np, int Rp, int form,
+                               void *Xcat)
+{
+    split_state_kernel<<<152 * 8, 256, 0, st>>>(X, N, Np, Rp, form,
+                                                static_cast<__nv_bfloat16 *>(Xcat));
+    return cudaGetLastError();
+}
+
+bool tc_bf16_persistent_fits(int Np, int Rp)
+{
+    const int nblk = Np / kQM, nrb = Rp / kQN;
+    if (nblk < 1 || nrb < 1)
+        return false;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return false;
+    if (cudaFuncSetAttribute(tc_bf16x3_persistent_kernel<0>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(tc_bf16x3_persistent_kernel<1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem) != cudaSuccess)
+        return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_bf16x3_persistent_kernel<0>,
+                                                      kQThreads, kQSmem) != cudaSuccess)
+        return false;
+    return (long long)nblk * nrb <= (long long)per_sm * sms;
+}
+
+cudaError_t launch_tc_bf16x3_persistent(cudaStream_t st, const Bf16Plan *plan, int form,
+                                        const PersistArgs &a)
+{
+    if (!plan || a.Np != plan->Np || a.Rp > plan->Rp || a.Rp % kQN != 0 || a.nsteps < 1 ||
+        a.final_pass != 0 || (form != 0 && form != 1))
+        return cudaErrorInvalidValue;
+    auto kern = form == 0 ? tc_bf16x3_persistent_kernel<0> : tc_bf16x3_persistent_kernel<1>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQSmem);
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.nblk, a.nrb, 1);
+    cfg.blockDim = dim3(kQThreads, 1, 1);
+    cfg.dynamicSmemBytes = kQSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, plan->mapJ, plan->mapB[form][0], plan->mapB[form][1],
+                              plan->mapSt[0], plan->mapSt[1], a);
+}
+
+}  // namespace hsb
