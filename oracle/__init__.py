@@ -61,6 +61,7 @@ class Params(C.Structure):
         ("init_half_width", C.c_double),
         ("instance", C.c_uint32),
         ("force_plain_sum", C.c_int),
+        ("trace_every", C.c_int),
     ]
 
 
@@ -90,6 +91,8 @@ def _load():
         lib.oracle_pump_factor.argtypes = [C.c_double, C.c_int, C.c_int]
         lib.oracle_num_evals.restype = C.c_int
         lib.oracle_num_evals.argtypes = [C.c_int, C.c_int]
+        lib.oracle_num_traced.restype = C.c_int
+        lib.oracle_num_traced.argtypes = [C.c_int, C.c_int]
         lib.oracle_is_pm1.restype = C.c_int
         lib.oracle_is_pm1.argtypes = [P, C.c_int]
         for sfx, real in (("f64", C.c_double), ("f32", C.c_float)):
@@ -99,7 +102,7 @@ def _load():
             rn = getattr(lib, f"oracle_run_{sfx}")
             rn.restype = C.c_int
             rn.argtypes = [P, C.c_int, C.POINTER(Params), C.c_int, C.c_uint64, C.c_int, P, P, P,
-                           P, P, P, C.c_int]
+                           P, P, P, P, P, C.c_int]
         _lib = lib
         return lib
 
@@ -223,10 +226,15 @@ def step(J, x, y, form: int, pk: float, c0: float, dt: float, q: float, g: float
 
 def make_params(form: int, c0: float, dt: float, gamma: float, a0: float = 1.0,
                 init_half_width: float = 1.0, eval_every: int = 100, instance: int = 0,
-                force_plain_sum: bool = False) -> Params:
+                force_plain_sum: bool = False, trace_every: int = 0) -> Params:
     return Params(form=int(form), eval_every=int(eval_every), a0=float(a0), c0=float(c0),
                   dt=float(dt), gamma=float(gamma), init_half_width=float(init_half_width),
-                  instance=int(instance), force_plain_sum=int(bool(force_plain_sum)))
+                  instance=int(instance), force_plain_sum=int(bool(force_plain_sum)),
+                  trace_every=int(trace_every))
+
+
+def num_traced(steps: int, trace_every: int) -> int:
+    return int(_load().oracle_num_traced(steps, trace_every))
 
 
 def run(J, params: Params, steps: int, seed: int, reps, precision: str = "f64",
@@ -247,10 +255,16 @@ def run(J, params: Params, steps: int, seed: int, reps, precision: str = "f64",
     y = np.zeros((nrep, n), real)
     ne = num_evals(steps, params.eval_every)
     trace = np.zeros((nrep, ne), np.float64) if want_trace else None
+    nt = num_traced(steps, params.trace_every)
+    tr_e = np.zeros((nrep, nt), np.float64) if nt else None
+    tr_t = np.zeros((nrep, nt), np.float64) if nt else None
     fn = getattr(_load(), f"oracle_run_{precision}")
     rc = fn(_ptr(J), n, C.byref(params), int(steps), C.c_uint64(seed & (2**64 - 1)), nrep,
             _ptr(reps), _ptr(best_s), _ptr(best_e), _ptr(x), _ptr(y),
-            _ptr(trace) if trace is not None else None, int(nthreads))
+            _ptr(trace) if trace is not None else None,
+            _ptr(tr_e) if tr_e is not None else None,
+            _ptr(tr_t) if tr_t is not None else None, int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle_run failed ({rc})")
-    return {"best_e": best_e, "best_s": best_s, "x": x, "y": y, "e_trace": trace}
+    return {"best_e": best_e, "best_s": best_s, "x": x, "y": y, "e_trace": trace,
+            "trace_e": tr_e, "trace_t": tr_t}

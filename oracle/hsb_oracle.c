@@ -201,7 +201,14 @@ typedef struct {
     double init_half_width; /* x0, y0 uniform in (-L, L) (paper: L = 1) */
     uint32_t instance;      /* RNG stream of the instance */
     int force_plain_sum;    /* 1: never take the int32 force shortcut */
+    int trace_every;        /* > 0: record E(t_k) and T_inst(t_k) for k = m*trace_every < Ns */
 } oracle_params;
+
+/* Number of traced times of a run: t_k for k = m*trace_every < Ns. */
+int oracle_num_traced(int steps, int trace_every)
+{
+    return trace_every > 0 ? (steps - 1) / trace_every + 1 : 0;
+}
 
 /* ----------------------------------------- precision-generic routines --- */
 

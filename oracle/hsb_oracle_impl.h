@@ -135,10 +135,13 @@ int SFX(oracle_step)(const float *J, int N, int nrep, REAL *x, REAL *y, int form
  * Outputs, each [nrep] or [nrep][N]: best_e, best_s (spins at the best
  * evaluation step), x_out / y_out (state after `steps` updates, may be NULL),
  * e_trace (energy at every evaluation step, [nrep][oracle_num_evals], may be
- * NULL). */
+ * NULL), trace_e / trace_t (Ising energy, Eq. (eq_Ising), and instantaneous
+ * temperature T_inst = (1/N) sum_i y_i^2, Eq. (eq_TInst), at the traced times
+ * t_k, k = m*trace_every < Ns, [nrep][oracle_num_traced]; may be NULL). */
 int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, uint64_t seed,
                     int nrep, const int32_t *rep_ids, int8_t *best_s, double *best_e,
-                    REAL *x_out, REAL *y_out, double *e_trace, int nthreads)
+                    REAL *x_out, REAL *y_out, double *e_trace, double *trace_e,
+                    double *trace_t, int nthreads)
 {
     if (N < 1 || steps < 1 || nrep < 0 || p->eval_every < 0)
         return -1;
@@ -165,6 +168,7 @@ int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, ui
     for (int k = 0; k < steps; ++k)
         pk[k] = (REAL)oracle_pump_factor(p->a0, k, steps);
     const int n_evals = (p->eval_every > 0 ? (steps - 1) / p->eval_every : 0) + 1;
+    const int n_traced = oracle_num_traced(steps, p->trace_every);
     int failed = 0;
 
 #ifdef _OPENMP
@@ -205,6 +209,18 @@ int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, ui
                 }
                 if (k == steps)
                     break;
+                if (p->trace_every > 0 && k % p->trace_every == 0) {
+                    const size_t at = (size_t)t * n_traced + (size_t)(k / p->trace_every);
+                    for (int i = 0; i < N; ++i)
+                        s[i] = x[i] >= (REAL)0 ? (int8_t)1 : (int8_t)-1;
+                    if (trace_e)
+                        trace_e[at] = oracle_ising_energy(J, N, s);
+                    double t2 = 0.0;
+                    for (int i = 0; i < N; ++i)
+                        t2 += (double)y[i] * (double)y[i];
+                    if (trace_t)
+                        trace_t[at] = t2 / (double)N;
+                }
                 SFX(force)(Jr, Jint, N, p->form, x, f, stmp);
                 SFX(update)(N, x, y, f, c0, pk[k], dt, q, g);
             }

@@ -400,3 +400,24 @@ def test_pump_schedule_and_c0():
     G = synth.sk_gauss(300, 0)
     s = oracle.sigma_j(G)
     assert 0.9 < s < 1.1
+
+
+def test_trace_energy_and_instantaneous_temperature():
+    # Eq. (eq_TInst): T_inst = (1/N) sum_i y_i^2; at t_0 it is the mean square
+    # of the initial momenta; traced energies at evaluation times equal the
+    # evaluation energies.
+    n, steps = 40, 120
+    J = synth.sk_pm1(n, 8)
+    c0 = oracle.c0_from_c1(J, 0.7)
+    prm = oracle.make_params(1, c0, 1.1, 0.06, eval_every=30, trace_every=10)
+    out = oracle.run(J, prm, steps, 4, range(3), "f64", want_trace=True)
+    assert out["trace_e"].shape == (3, 12)
+    _, y0 = oracle.init_values(4, 0, range(3), n, 1.0)
+    np.testing.assert_allclose(out["trace_t"][:, 0], (y0.astype(np.float64) ** 2).mean(axis=1),
+                               rtol=1e-14)
+    x0, _ = oracle.init_values(4, 0, range(3), n, 1.0)
+    for r in range(3):
+        s0 = np.where(x0[r] >= 0, 1, -1).astype(np.int8)
+        assert out["trace_e"][r, 0] == oracle.ising_energy(J, s0)
+    # evaluations at t = 30, 60, 90 are traced at indices 3, 6, 9
+    np.testing.assert_array_equal(out["trace_e"][:, [3, 6, 9]], out["e_trace"][:, :3])
