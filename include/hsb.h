@@ -96,7 +96,11 @@ typedef struct {
     double gamma;           /* heating rate >= 0 (0: plain bSB / dSB) */
     double init_half_width; /* x0, y0 uniform in (-L, L); paper L = 1 */
     int eval_every;         /* >= 0; 100 in the K2000 study, 0 = final only */
-    int trace_every;        /* reserved, must be 0 */
+    int trace_every;        /* >= 0; > 0 records, at t_k for k = m*trace_every < steps,
+                               the minimum and mean Ising energy over replicas and
+                               the mean instantaneous temperature (1/N) sum y^2
+                               (Eq. (eq_TInst)); see hsb_get_trace.  FP32 and FP8
+                               (one launch per step) only */
     uint32_t instance;      /* random stream of the instance (x0, y0) */
     int schedule;           /* FP8 step loop: 0 = automatic (persistent kernel
                                when its grid fits on the device), 1 = persistent
@@ -166,6 +170,14 @@ HSB_API hsb_status hsb_advance(hsb_handle h, const hsb_params *p, int R, int ste
  * trajectory exactly; the step loop is graph-captured once per range. */
 HSB_API hsb_status hsb_advance_device(hsb_handle h, const hsb_params *p, int R, int steps, int k_begin,
                               int k_end);
+
+/* Copies the trace of the last run (params.trace_every > 0): entry m holds
+ * {min_r E_r, mean_r E_r, mean_r T_inst,r} at t_k, k = m*trace_every, as 3
+ * doubles, E of s = sgn(x(t_k)) (Eq. (eq_Ising)) and T_inst = (1/N) sum_i
+ * y_i(t_k)^2 (Eq. (eq_TInst)).  Writes min(max_entries, length) entries to
+ * buf (host, 3 doubles each) and the trace length to *entries (may be NULL).
+ * Blocks. */
+HSB_API hsb_status hsb_get_trace(hsb_handle h, double *buf, size_t max_entries, size_t *entries);
 
 /* Replaces the couplings of the handle by a new instance of the same N (host,
  * float32, N x N, row-major; validated as in hsb_create).  Device buffers and

@@ -31,7 +31,7 @@ SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2}
 EXPORTS = ["hsb_params_default", "hsb_version", "hsb_create", "hsb_destroy", "hsb_set_stream",
            "hsb_info", "hsb_run", "hsb_run_device", "hsb_get_state", "hsb_advance",
            "hsb_advance_device", "hsb_set_couplings", "hsb_run_stats", "hsb_synchronize",
-           "hsb_run_fp32_noalloc", "hsb_last_error"]
+           "hsb_run_fp32_noalloc", "hsb_get_trace", "hsb_last_error"]
 
 
 class HsbError(RuntimeError):
@@ -104,6 +104,8 @@ def load():
         lib.hsb_run_stats.argtypes = [H, C.POINTER(C.c_longlong)]
         lib.hsb_synchronize.restype = I
         lib.hsb_synchronize.argtypes = [H]
+        lib.hsb_get_trace.restype = I
+        lib.hsb_get_trace.argtypes = [H, P, C.c_size_t, C.POINTER(C.c_size_t)]
         lib.hsb_run_fp32_noalloc.restype = I
         lib.hsb_run_fp32_noalloc.argtypes = [P, I, C.POINTER(Params), I, I, C.c_uint64, P, P, P]
         _lib = lib
@@ -213,6 +215,16 @@ def set_couplings(h: int, J: np.ndarray) -> None:
     _check(load().hsb_set_couplings(C.c_void_p(h), _ptr(J)))
 
 
+def get_trace(h: int):
+    """hsb_get_trace: float64 [n, 3] = (min E, mean E, mean T_inst) per traced time."""
+    n = C.c_size_t()
+    _check(load().hsb_get_trace(C.c_void_p(h), None, 0, C.byref(n)))
+    buf = np.zeros((n.value, 3), np.float64)
+    if n.value:
+        _check(load().hsb_get_trace(C.c_void_p(h), _ptr(buf), n.value, C.byref(n)))
+    return buf
+
+
 def run_stats(h: int) -> int:
     """Kernels queued by the last run on the handle."""
     n = C.c_longlong()
@@ -260,6 +272,9 @@ class Solver:
 
     def run_stats(self):
         return run_stats(self.h)
+
+    def get_trace(self):
+        return get_trace(self.h)
 
     def set_stream(self, stream_ptr):
         set_stream(self.h, stream_ptr)

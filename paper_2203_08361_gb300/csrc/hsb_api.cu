@@ -66,7 +66,7 @@ struct DeviceGuard {
 
 // Everything that determines the captured step loop.
 struct GraphKey {
-    int prec, form, R, Rp, steps, eval_every, pm1;
+    int prec, form, R, Rp, steps, eval_every, trace_every, pm1;
     float c0, dt, q, g;
     double a0;
     uint64_t buffers_gen;
@@ -74,7 +74,7 @@ struct GraphKey {
 };
 
 struct RunCfg {
-    int prec, form, R, Rp, steps, eval_every, schedule;
+    int prec, form, R, Rp, steps, eval_every, trace_every, schedule;
     double a0;
     StepConsts c;
     std::vector<float> pk;  // p_k = a0 - a(t_k), k = 0..steps-1, rounded once
@@ -95,6 +95,9 @@ struct hsb_ctx {
     float *Y = nullptr;
     uint8_t *S8[2] = {nullptr, nullptr};
     float *Epart = nullptr;
+    float *Tpart = nullptr;  // [nblk][Rp] sums of y^2 for the trace
+    double *trace = nullptr; // [n_traced][3] {min E, mean E, mean T_inst}
+    size_t trace_cap = 0, trace_len = 0;
     double *Ebest = nullptr;
     double *Efinal = nullptr;
     int8_t *Sbest = nullptr;
@@ -152,12 +155,14 @@ void free_run_buffers(hsb_ctx *h)
     cudaFree(h->S8[0]);
     cudaFree(h->S8[1]);
     cudaFree(h->Epart);
+    cudaFree(h->Tpart);
     cudaFree(h->Ebest);
     cudaFree(h->Efinal);
     cudaFree(h->Sbest);
     h->X[0] = h->X[1] = h->Y = nullptr;
     h->S8[0] = h->S8[1] = nullptr;
     h->Epart = nullptr;
+    h->Tpart = nullptr;
     h->Ebest = h->Efinal = nullptr;
     h->Sbest = nullptr;
     h->Rcap = 0;
@@ -188,6 +193,7 @@ hsb_status ensure_buffers(hsb_ctx *h, int Rp, int R)
     CK(cudaMalloc(&h->S8[0], elems), "cudaMalloc S8");
     CK(cudaMalloc(&h->S8[1], elems), "cudaMalloc S8");
     CK(cudaMalloc(&h->Epart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Epart");
+    CK(cudaMalloc(&h->Tpart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Tpart");
     CK(cudaMalloc(&h->Ebest, (size_t)Rp * sizeof(double)), "cudaMalloc Ebest");
     CK(cudaMalloc(&h->Efinal, (size_t)Rp * sizeof(double)), "cudaMalloc Efinal");
     CK(cudaMalloc(&h->Sbest, (size_t)Rp * h->N), "cudaMalloc Sbest");
@@ -242,8 +248,8 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_INVAL, "need a0 > 0, dt > 0, gamma >= 0, init_half_width > 0");
     if (!(p->c0 > 0.0) && !(p->c1 > 0.0))
         return set_error(HSB_E_INVAL, "need c0 > 0 or c1 > 0");
-    if (p->eval_every < 0 || p->trace_every != 0)
-        return set_error(HSB_E_INVAL, "eval_every must be >= 0 and trace_every 0");
+    if (p->eval_every < 0 || p->trace_every < 0)
+        return set_error(HSB_E_INVAL, "eval_every and trace_every must be >= 0");
     if (p->schedule < 0 || p->schedule > 2)
         return set_error(HSB_E_INVAL, "schedule must be 0, 1 or 2");
     if ((long long)R * h->N > (1LL << 40))
@@ -265,12 +271,17 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
                          h->Np / kTileM, Rp_ / kTileR);
     if (prec != HSB_PREC_FP32 && prec != HSB_PREC_FP8 && prec != HSB_PREC_BF16X3)
         return set_error(HSB_E_INVAL, "unknown precision %d", p->prec);
+    if (p->trace_every > 0 && prec == HSB_PREC_BF16X3)
+        return set_error(HSB_E_UNSUPPORTED, "the trace needs the FP32 or FP8 precision");
+    if (p->trace_every > 0 && prec == HSB_PREC_FP8 && p->schedule == 1)
+        return set_error(HSB_E_UNSUPPORTED, "the trace runs on the one-launch-per-step schedule");
     cfg->prec = prec;
     cfg->form = p->form;
     cfg->R = R;
     cfg->Rp = round_up(R, kTileR);
     cfg->steps = steps;
     cfg->eval_every = p->eval_every;
+    cfg->trace_every = p->trace_every;
     cfg->schedule = p->schedule;
     cfg->a0 = p->a0;
     // c0 = c1 / (sqrt(N) sigma_J) (Results; sigma_J = 1 for +/-1 couplings)
@@ -301,28 +312,36 @@ hsb_status enqueue_step(hsb_ctx *h, cudaStream_t st, const RunCfg &c, int k, int
                         bool allow_eval)
 {
     const bool ev = allow_eval && is_eval_step(c, k);
+    // traced time t_k: energy and T_inst of the state before this update
+    const bool tr = allow_eval && c.trace_every > 0 && k % c.trace_every == 0;
+    const bool en = ev || tr;
+    float *tpart = tr ? h->Tpart : nullptr;
     const int nblk = h->Np / kTileM;
     if (c.prec == HSB_PREC_FP32) {
-        if (ev && c.form == HSB_BALLISTIC)
+        if (en && c.form == HSB_BALLISTIC)
             CK(launch_simt_step(st, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[cur], nullptr,
-                                h->Y, 0.f, c.c, h->Epart),
+                                h->Y, 0.f, c.c, h->Epart, nullptr),
                "energy kernel");
-        CK(launch_simt_step(st, c.form, false, ev && c.form == HSB_DISCRETE, h->J32, h->N, h->Np,
-                            c.Rp, h->X[cur], h->X[cur ^ 1], h->Y, c.pk[k], c.c, h->Epart),
+        CK(launch_simt_step(st, c.form, false, en && c.form == HSB_DISCRETE, h->J32, h->N, h->Np,
+                            c.Rp, h->X[cur], h->X[cur ^ 1], h->Y, c.pk[k], c.c, h->Epart, tpart),
            "fp32 step kernel");
         if (ev)
             CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[cur], nullptr,
                                   h->Ebest, h->Sbest),
                "best kernel");
     } else {  // FP8: S8[cur] -> S8[cur^1], X and Y in place
-        CK(launch_tc_fp8_step(st, h->plan, cur, ev, false, h->N, c.Rp, h->X[0], h->Y, c.pk[k],
-                              c.c, h->Epart, h->S8[cur ^ 1], h->err),
+        CK(launch_tc_fp8_step(st, h->plan, cur, en, false, h->N, c.Rp, h->X[0], h->Y, c.pk[k],
+                              c.c, h->Epart, tpart, h->S8[cur ^ 1], h->err),
            "fp8 step kernel");
         if (ev)
             CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, h->S8[cur],
                                   h->Ebest, h->Sbest),
                "best kernel");
     }
+    if (tr)
+        CK(launch_trace_reduce(st, h->Epart, h->Tpart, nblk, h->N, c.R, c.Rp,
+                               h->trace + 3 * (size_t)(k / c.trace_every)),
+           "trace kernel");
     return HSB_OK;
 }
 
@@ -333,14 +352,14 @@ hsb_status enqueue_final(hsb_ctx *h, cudaStream_t st, const RunCfg &c)
     const int cur = c.steps & 1;
     if (c.prec == HSB_PREC_FP32) {
         CK(launch_simt_step(st, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[cur], nullptr,
-                            h->Y, 0.f, c.c, h->Epart),
+                            h->Y, 0.f, c.c, h->Epart, nullptr),
            "energy kernel");
         CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[cur], nullptr,
                               h->Ebest, h->Sbest),
            "best kernel");
     } else {
         CK(launch_tc_fp8_step(st, h->plan, cur, true, true, h->N, c.Rp, h->X[0], h->Y, 0.f, c.c,
-                              h->Epart, nullptr, h->err),
+                              h->Epart, nullptr, nullptr, h->err),
            "fp8 energy kernel");
         CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, h->S8[cur],
                               h->Ebest, h->Sbest),
@@ -361,6 +380,12 @@ long long count_launches(const hsb_ctx *h, const RunCfg &c)
     long long n = 1 + c.steps + evals /* best */ + 2 /* final energy + best */;
     if (c.form == HSB_BALLISTIC && c.prec == HSB_PREC_FP32)
         n += evals;
+    if (c.trace_every > 0) {
+        const long long traced = (c.steps - 1) / c.trace_every + 1;
+        n += traced;  // trace reductions
+        if (c.form == HSB_BALLISTIC && c.prec == HSB_PREC_FP32)
+            n += traced;  // energy passes at traced times (shared with evaluations)
+    }
     if (!h->pm1)
         n += 1;
     return n;
@@ -426,7 +451,7 @@ int num_evals(const RunCfg &c)
 hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
 {
     *out = false;
-    if (c.prec != HSB_PREC_FP8 || c.schedule == 2)
+    if (c.prec != HSB_PREC_FP8 || c.schedule == 2 || c.trace_every > 0)
         return HSB_OK;
     const bool fits = tc_persistent_fits(h->Np, c.Rp);
     if (!fits && c.schedule == 1)
@@ -583,7 +608,7 @@ hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hs
         k = kb;
         // evaluation of s(t_k): at an evaluation step, and at the end
         CK(launch_simt_step(h->work, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[0], nullptr,
-                            h->Y, 0.f, c.c, h->Epart),
+                            h->Y, 0.f, c.c, h->Epart, nullptr),
            "energy kernel");
         CK(launch_best_update(h->work, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[0], nullptr,
                               h->Ebest, h->Sbest),
@@ -600,6 +625,7 @@ hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hs
     h->state_par = par;
     h->have_state = true;
     h->launches = launches;
+    h->trace_len = 0;
     return HSB_OK;
 }
 
@@ -628,7 +654,22 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
         h->state_par = c.steps & 1;
         h->have_state = true;
         h->launches = 3;
+        h->trace_len = 0;
         return HSB_OK;
+    }
+    if (c.trace_every > 0) {
+        const size_t need = 3 * (size_t)((c.steps - 1) / c.trace_every + 1);
+        if (h->trace_cap < need) {
+            cudaFree(h->trace);
+            h->trace = nullptr;
+            h->trace_cap = 0;
+            CK(cudaMalloc(&h->trace, need * sizeof(double)), "cudaMalloc trace");
+            h->trace_cap = need;
+            h->graph_valid = false;  // the captured loop holds the trace pointer
+        }
+        h->trace_len = need / 3;
+    } else {
+        h->trace_len = 0;
     }
     const GraphKey key = make_key(h, c);
     if (!h->graph_valid || !(h->gkey == key)) {
@@ -659,6 +700,7 @@ GraphKey make_key(const hsb_ctx *h, const RunCfg &c)
     key.Rp = c.Rp;
     key.steps = c.steps;
     key.eval_every = c.eval_every;
+    key.trace_every = c.trace_every;
     key.pm1 = h->pm1;
     key.c0 = c.c.c0;
     key.dt = c.c.dt;
@@ -809,6 +851,7 @@ void hsb_destroy(hsb_handle h)
     cudaFree(h->J32);
     cudaFree(h->J8);
     cudaFree(h->Jcat);
+    cudaFree(h->trace);
     cudaFree(h->err);
     cudaFree(h->flags);
     cudaFree(h->pk_dev);
@@ -1120,6 +1163,24 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
     }
     if (h->Jcat)
         CK(launch_split_couplings(h->work, h->J32, h->Np, h->Jcat), "split couplings");
+    CK(cudaStreamSynchronize(h->work), "synchronize");
+    return HSB_OK;
+}
+
+hsb_status hsb_get_trace(hsb_handle h, double *buf, size_t max_entries, size_t *entries)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    const size_t n = h->trace_len < max_entries ? h->trace_len : max_entries;
+    if (entries)
+        *entries = h->trace_len;
+    if (n == 0)
+        return HSB_OK;
+    if (!buf)
+        return set_error(HSB_E_INVAL, "buf is NULL");
+    DeviceGuard g(h->device);
+    CK(cudaMemcpyAsync(buf, h->trace, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->work),
+       "copy trace");
     CK(cudaStreamSynchronize(h->work), "synchronize");
     return HSB_OK;
 }

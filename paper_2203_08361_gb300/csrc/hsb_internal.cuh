@@ -46,9 +46,15 @@ cudaError_t launch_init(cudaStream_t st, uint64_t seed, uint32_t instance, float
 // One plain-FP32 step (force by fused multiply-adds over j ascending, then the
 // pinned update).  energy != 0 also writes Epart from s(t_k) and f (discrete
 // form only).  energy_only computes Epart for s = sgn(Xcur) without updating.
+// Tpart (may be NULL): per row block sums of y_i(t_k)^2 for the trace.
 cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool energy,
                              const float *J32, int N, int Np, int Rp, const float *Xcur,
-                             float *Xnext, float *Y, float pk, StepConsts c, float *Epart);
+                             float *Xnext, float *Y, float pk, StepConsts c, float *Epart,
+                             float *Tpart);
+
+// Trace entry {min_r E_r, mean_r E_r, mean_r T_inst,r} from Epart / Tpart.
+cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,
+                                int N, int R, int Rp, double *out);
 
 // Best tracking after an evaluation: E_r = -1/2 sum_blocks Epart; if E_r <
 // Ebest[r] store it with the spins sgn(x) read from X (fp32) or S8 (fp8).
@@ -87,7 +93,8 @@ cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S
 void tc_plan_destroy(TcPlan *p);
 cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
                                bool energy_only, int N, int Rp, float *X, float *Y, float pk,
-                               StepConsts c, float *Epart, uint8_t *S8next, int *err);
+                               StepConsts c, float *Epart, float *Tpart, uint8_t *S8next,
+                               int *err);
 
 // ---- hsb_persist.cu --------------------------------------------------------
 // Arguments of the persistent FP8 kernel: `nsteps` updates starting at global

@@ -151,16 +151,17 @@ extern "C" HSB_API hsb_status hsb_run_fp32_noalloc(const float *J, int N, const 
         const bool ev = p->eval_every > 0 && k > 0 && k % p->eval_every == 0;
         if (ev && p->form == HSB_BALLISTIC)
             e = launch_simt_step(st, 1, true, true, Jp, N, Np, Rp, X[cur], nullptr, Y, 0.f, c,
-                                 Epart);
+                                 Epart, nullptr);
         if (e == cudaSuccess)
             e = launch_simt_step(st, p->form, false, ev && p->form == HSB_DISCRETE, Jp, N, Np, Rp,
-                                 X[cur], X[cur ^ 1], Y, pk, c, Epart);
+                                 X[cur], X[cur ^ 1], Y, pk, c, Epart, nullptr);
         if (e == cudaSuccess && ev)
             e = launch_best_update(st, Epart, nblk, N, Np, R, Rp, X[cur], nullptr, Ebest, Sbest);
     }
     const int fin = steps & 1;
     if (e == cudaSuccess)
-        e = launch_simt_step(st, 1, true, true, Jp, N, Np, Rp, X[fin], nullptr, Y, 0.f, c, Epart);
+        e = launch_simt_step(st, 1, true, true, Jp, N, Np, Rp, X[fin], nullptr, Y, 0.f, c, Epart,
+                             nullptr);
     if (e == cudaSuccess)
         e = launch_best_update(st, Epart, nblk, N, Np, R, Rp, X[fin], nullptr, Ebest, Sbest);
     if (e == cudaSuccess)

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, 1)
 simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
                  const float *__restrict__ Xcur, float *__restrict__ Xnext,
                  float *__restrict__ Y, float pk, StepConsts c, int energy,
-                 float *__restrict__ Epart)
+                 float *__restrict__ Epart, float *__restrict__ Tpart)
 {
     constexpr bool kSign = (FORM == 1) || ENERGY_ONLY;
     __shared__ __align__(16) float As[2][8][128];
@@ -148,12 +148,12 @@ simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
 
     // Epilogue: thread owns rows {ty*4+a, 64+ty*4+a} and replicas
     // {tx*4+b, 64+tx*4+b}; one float4 of x and y per (replica, row group).
-    float ep[8];
+    float ep[8], tp[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
         const int col = (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
         const size_t rowbase = (size_t)(r0 + col) * Np + m0;
-        float e = 0.f;
+        float e = 0.f, t2 = 0.f;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int ibase = h * 64 + ty * 4;
@@ -170,6 +170,11 @@ simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
             if (!ENERGY_ONLY) {
                 const float4 y4 = *reinterpret_cast<const float4 *>(Y + rowbase + ibase);
                 const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+                if (Tpart) {
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+                        t2 = __fadd_rn(t2, __fmul_rn(yv[a], yv[a]));
+                }
                 float xo[4], yo[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
@@ -181,6 +186,23 @@ simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
             }
         }
         ep[b] = e;
+        tp[b] = t2;
+    }
+    if (!ENERGY_ONLY && Tpart) {
+        // sum_i y_i(t_k)^2 of this row block per replica (Eq. eq_TInst)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int col = (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
+            Ered[ty][col] = tp[b];
+        }
+        __syncthreads();
+        if (tid < 128) {
+            float sacc = 0.f;
+            for (int t = 0; t < 16; ++t)
+                sacc += Ered[t][tid];
+            Tpart[(size_t)blockIdx.x * Rp + r0 + tid] = sacc;
+        }
+        __syncthreads();
     }
     if (ENERGY_ONLY || energy) {
 #pragma unroll
@@ -200,18 +222,65 @@ simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
 
 cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool energy,
                              const float *J32, int N, int Np, int Rp, const float *Xcur,
-                             float *Xnext, float *Y, float pk, StepConsts c, float *Epart)
+                             float *Xnext, float *Y, float pk, StepConsts c, float *Epart,
+                             float *Tpart)
 {
     dim3 grid(Np / 128, Rp / 128);
     if (energy_only)
         simt_step_kernel<1, true><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
-                                                         1, Epart);
+                                                         1, Epart, nullptr);
     else if (form == 1)
         simt_step_kernel<1, false><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
-                                                          energy ? 1 : 0, Epart);
+                                                          energy ? 1 : 0, Epart, Tpart);
     else
         simt_step_kernel<0, false><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
-                                                          0, Epart);
+                                                          0, Epart, Tpart);
+    return cudaGetLastError();
+}
+
+// One trace entry (traced time t_k): over replicas r < R, E_r = -1/2 sum_b
+// Epart[b][r] and T_r = (1/N) sum_b Tpart[b][r] (binary64, blocks in order);
+// out = {min_r E_r, mean_r E_r, mean_r T_r}.  One block, fixed reduction order.
+__global__ void __launch_bounds__(1024)
+trace_reduce_kernel(const float *__restrict__ Epart, const float *__restrict__ Tpart, int nblk,
+                    int N, int R, int Rp, double *__restrict__ out)
+{
+    __shared__ double smin[1024], ssum[1024], stt[1024];
+    double mn = INFINITY, se = 0.0, st = 0.0;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        double e = 0.0, t = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            e += (double)Epart[(size_t)b * Rp + r];
+            t += (double)Tpart[(size_t)b * Rp + r];
+        }
+        e = -0.5 * e;
+        mn = fmin(mn, e);
+        se += e;
+        st += t / (double)N;
+    }
+    smin[threadIdx.x] = mn;
+    ssum[threadIdx.x] = se;
+    stt[threadIdx.x] = st;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+            ssum[threadIdx.x] += ssum[threadIdx.x + w];
+            stt[threadIdx.x] += stt[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = smin[0];
+        out[1] = ssum[0] / (double)R;
+        out[2] = stt[0] / (double)R;
+    }
+}
+
+cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,
+                                int N, int R, int Rp, double *out)
+{
+    trace_reduce_kernel<<<1, 1024, 0, st>>>(Epart, Tpart, nblk, N, R, Rp, out);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ struct __align__(8) TcShared {
     uint32_t tmem_base;
     int abort;
     float red[4][kBN];
+    float tred[4][kBN];
 };
 
 constexpr size_t kSmemBytes = 1024 /* alignment slack */ + (size_t)kStages * (kStageA + kStageB) +
@@ -195,7 +196,7 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                    const __grid_constant__ CUtensorMap tmapB, int N, int Np, int Rp,
                    float *__restrict__ X, float *__restrict__ Y, uint8_t *__restrict__ S8next,
                    float pk, StepConsts c, int energy, int energy_only,
-                   float *__restrict__ Epart, int *__restrict__ err)
+                   float *__restrict__ Epart, float *__restrict__ Tpart, int *__restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -287,7 +288,17 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                         term = live ? (x0 >= 0.f ? f[j] : -f[j]) : 0.f;
                     if (!energy_only) {
                         float xn, yn;
-                        sb_update(f[j], x0, Y[e], pk, c, xn, yn);
+                        const float y0 = Y[e];
+                        if (Tpart) {
+                            // y_i(t_k)^2 of this row block, summed over lanes (Eq. eq_TInst)
+                            float t2 = __fmul_rn(y0, y0);
+#pragma unroll
+                            for (int off = 16; off > 0; off >>= 1)
+                                t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+                            if (lane == 0)
+                                sh->tred[q][col] = t2;
+                        }
+                        sb_update(f[j], x0, y0, pk, c, xn, yn);
                         X[e] = xn;
                         Y[e] = yn;
                         S8next[e] = live ? fp8_sign(xn) : (uint8_t)0;
@@ -302,12 +313,16 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                 }
             }
         }
-        if (energy || energy_only) {
+        if (energy || energy_only || Tpart) {
             epilogue_bar();
             const int t = threadIdx.x - 64;  // 0..127
-            if (ok && t < kBN) {
+            if (ok && t < kBN && (energy || energy_only)) {
                 const float s = sh->red[0][t] + sh->red[1][t] + sh->red[2][t] + sh->red[3][t];
                 Epart[(size_t)blockIdx.x * Rp + r0 + t] = s;
+            }
+            if (ok && t < kBN && Tpart && !energy_only) {
+                const float s = sh->tred[0][t] + sh->tred[1][t] + sh->tred[2][t] + sh->tred[3][t];
+                Tpart[(size_t)blockIdx.x * Rp + r0 + t] = s;
             }
         }
     }
@@ -426,7 +441,8 @@ void tc_plan_destroy(TcPlan *p) { delete p; }
 
 cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
                                bool energy_only, int N, int Rp, float *X, float *Y, float pk,
-                               StepConsts c, float *Epart, uint8_t *S8next, int *err)
+                               StepConsts c, float *Epart, float *Tpart, uint8_t *S8next,
+                               int *err)
 {
     // Rp (this run's padded replica count) may be below the capacity the
     // tensor maps were encoded for; Epart rows are Rp long.
@@ -435,7 +451,7 @@ cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, 
     dim3 grid(plan->Np / kBM, Rp / kBN);
     tc_fp8_step_kernel<<<grid, kThreads, kSmemBytes, st>>>(
         plan->mapA, plan->mapB[parity & 1], N, plan->Np, Rp, X, Y, S8next, pk, c,
-        energy ? 1 : 0, energy_only ? 1 : 0, Epart, err);
+        energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err);
     return cudaGetLastError();
 }
 

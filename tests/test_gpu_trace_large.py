@@ -1,0 +1,75 @@
+"""The per-step trace and the large-instance workload on the GPU.
+
+Trace: at t_k (k = m * trace_every) the minimum and mean Ising energy over
+replicas (Eq. eq_Ising) and the mean instantaneous temperature T_inst =
+(1/N) sum_i y_i^2 (Eq. eq_TInst).  For +/-1 couplings and the discrete form
+the energies are exact integers and must equal the oracle's; T_inst is a
+binary32 sum of squares per 128-spin block added in binary64, compared to the
+oracle's binary64 value within 1e-6 relative.
+
+Large instance: N = 16384 +/-1 SK (FP8 couplings 268 MB, beyond the 126 MB L2),
+R = 4096, FP8 on the one-launch-per-step schedule; sampled replicas are checked
+bit for bit against the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_08361_gb300 as hsb
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle_trace(J, c1, steps, seed, reps, trace_every, eval_every=0):
+    c0 = oracle.c0_from_c1(J, c1)
+    op = oracle.make_params(1, c0, 1.1, 0.06, eval_every=eval_every, trace_every=trace_every)
+    return oracle.run(J, op, steps, seed, reps, "f32", nthreads=0)
+
+
+@pytest.mark.parametrize("prec", ["fp8", "fp32"])
+def test_trace_matches_oracle(prec):
+    n, R, steps, te = 300, 40, 100, 10
+    J = synth.sk_pm1(n, 17)
+    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=25, trace_every=te)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, steps, 6)
+        tr = s.get_trace()
+        x, y = s.get_state(R)
+    ref = _oracle_trace(J, 0.7, steps, 6, range(R), te, eval_every=25)
+    assert tr.shape == (steps // te, 3)
+    np.testing.assert_array_equal(tr[:, 0], ref["trace_e"].min(axis=0))
+    np.testing.assert_array_equal(tr[:, 1], ref["trace_e"].mean(axis=0))
+    np.testing.assert_allclose(tr[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6)
+    # the trace does not change the trajectory
+    np.testing.assert_array_equal(x, ref["x"])
+    np.testing.assert_array_equal(energy, ref["best_e"])
+
+
+def test_large_instance_fp8_sampled_replicas_and_trace():
+    n, steps, seed = 16384, 40, 11
+    J = synth.sk_pm1(n, 3)
+    p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=0, trace_every=1)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, 4096, steps, seed)
+        x_all, _ = s.get_state(4096)
+        tr_all = s.get_trace()
+        spins2, energy2 = s.run(p, 2, steps, seed)
+        x2, y2 = s.get_state(2)
+        tr2 = s.get_trace()
+    # replica independence at full size
+    np.testing.assert_array_equal(x_all[:2], x2)
+    np.testing.assert_array_equal(spins[:2], spins2)
+    # two replicas against the oracle, bit for bit, with their trace
+    ref = _oracle_trace(J, 0.7, steps, seed, [0, 1], 1)
+    np.testing.assert_array_equal(x2, ref["x"])
+    np.testing.assert_array_equal(y2, ref["y"])
+    np.testing.assert_array_equal(energy2, ref["best_e"])
+    np.testing.assert_array_equal(tr2[:, 0], ref["trace_e"].min(axis=0))
+    np.testing.assert_array_equal(tr2[:, 1], ref["trace_e"].mean(axis=0))
+    np.testing.assert_allclose(tr2[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6)
+    # full trace: integer energies, min <= mean, T_inst of U(-1,1) momenta ~ 1/3 at t_0
+    assert tr_all.shape == (steps, 3)
+    assert np.all(tr_all[:, 0] == np.round(tr_all[:, 0]))
+    assert np.all(tr_all[:, 0] <= tr_all[:, 1])
+    assert abs(tr_all[0, 2] - 1.0 / 3.0) < 1e-3
