@@ -150,6 +150,21 @@ HSB_API hsb_status hsb_run(hsb_handle h, const hsb_params *p, int R, int steps, 
 HSB_API hsb_status hsb_run_device(hsb_handle h, const hsb_params *p, int R, int steps, uint64_t seed,
                           int8_t *best_spins, double *best_energy);
 
+/* Runs `count` instances (handles hs[0..count-1], each with its own N) with
+ * the same parameters, R replicas and steps, and returns each instance's best
+ * spins (best_spins[b], host, R x N_b int8) and energies (best_energy[b],
+ * host, R float64).  Instance b draws its initial state from the random
+ * stream p->instance + b, so its result equals hsb_run on hs[b] with
+ * instance = p->instance + b.  For the discrete form with couplings in
+ * {-1, 0, +1} (FP8), R rounded up to 32 at most 256 and N rounded up to 128
+ * times that at most 128 KiB, all instances run in one kernel launch that
+ * takes them from a queue, largest first, one CTA per instance; otherwise
+ * the instances run one after another.  All handles must be on one device;
+ * the work is queued on hs[0]'s stream.  Blocks. */
+HSB_API hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, int R,
+                                 int steps, uint64_t seed, int8_t *const *best_spins,
+                                 double *const *best_energy);
+
 /* Copies x(t_steps), y(t_steps) of the last run on this handle (R x N float32
  * each, host) into x and y (either may be NULL).  Blocks. */
 HSB_API hsb_status hsb_get_state(hsb_handle h, float *x, float *y);

@@ -31,7 +31,7 @@ SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2}
 EXPORTS = ["hsb_params_default", "hsb_version", "hsb_create", "hsb_destroy", "hsb_set_stream",
            "hsb_info", "hsb_run", "hsb_run_device", "hsb_get_state", "hsb_advance",
            "hsb_advance_device", "hsb_set_couplings", "hsb_run_stats", "hsb_synchronize",
-           "hsb_run_fp32_noalloc", "hsb_get_trace", "hsb_last_error"]
+           "hsb_run_fp32_noalloc", "hsb_get_trace", "hsb_run_batch", "hsb_last_error"]
 
 
 class HsbError(RuntimeError):
@@ -104,6 +104,8 @@ def load():
         lib.hsb_run_stats.argtypes = [H, C.POINTER(C.c_longlong)]
         lib.hsb_synchronize.restype = I
         lib.hsb_synchronize.argtypes = [H]
+        lib.hsb_run_batch.restype = I
+        lib.hsb_run_batch.argtypes = [P, I, C.POINTER(Params), I, I, C.c_uint64, P, P]
         lib.hsb_get_trace.restype = I
         lib.hsb_get_trace.argtypes = [H, P, C.c_size_t, C.POINTER(C.c_size_t)]
         lib.hsb_run_fp32_noalloc.restype = I
@@ -213,6 +215,20 @@ def set_couplings(h: int, J: np.ndarray) -> None:
     """hsb_set_couplings: new instance of the same N for an existing handle."""
     J = np.ascontiguousarray(J, dtype=np.float32)
     _check(load().hsb_set_couplings(C.c_void_p(h), _ptr(J)))
+
+
+def run_batch(handles, p: Params, R: int, steps: int, seed: int):
+    """hsb_run_batch: list of (best_spins int8 [R, N_b], best_energy float64 [R])."""
+    count = len(handles)
+    ns = [info(h)[0] for h in handles]
+    spins = [np.empty((R, n), np.int8) for n in ns]
+    energy = [np.empty(R, np.float64) for _ in ns]
+    harr = (C.c_void_p * count)(*handles)
+    sarr = (C.c_void_p * count)(*[a.ctypes.data for a in spins])
+    earr = (C.c_void_p * count)(*[a.ctypes.data for a in energy])
+    _check(load().hsb_run_batch(harr, count, C.byref(p), int(R), int(steps),
+                                C.c_uint64(seed & (2**64 - 1)), sarr, earr))
+    return list(zip(spins, energy))
 
 
 def get_trace(h: int):

@@ -11,6 +11,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -1192,6 +1193,139 @@ hsb_status hsb_run_stats(hsb_handle h, long long *kernel_launches)
     if (kernel_launches)
         *kernel_launches = h->launches;
     return HSB_OK;
+}
+
+hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, int R, int steps,
+                         uint64_t seed, int8_t *const *best_spins, double *const *best_energy)
+{
+    if (!hs || count < 1 || !best_spins || !best_energy)
+        return set_error(HSB_E_INVAL, "hsb_run_batch: null argument or count < 1");
+    if (!p)
+        return set_error(HSB_E_INVAL, "params is NULL");
+    for (int b = 0; b < count; ++b) {
+        if (!hs[b] || !best_spins[b] || !best_energy[b])
+            return set_error(HSB_E_INVAL, "hsb_run_batch: null handle or output %d", b);
+        if (hs[b]->device != hs[0]->device)
+            return set_error(HSB_E_INVAL, "hsb_run_batch: all handles must share one device");
+    }
+    // The batched kernel applies to the discrete form with +/-1 couplings in
+    // FP8; any other case runs the instances one after another.
+    bool batched = p->form == HSB_DISCRETE &&
+                   (p->prec == HSB_PREC_AUTO || p->prec == HSB_PREC_FP8) && p->trace_every == 0;
+    for (int b = 0; b < count && batched; ++b)
+        batched = hs[b]->pm1 && batch_shape_ok(hs[b]->Np, R);
+    if (!batched) {
+        for (int b = 0; b < count; ++b) {
+            hsb_params pb = *p;
+            pb.instance = p->instance + (uint32_t)b;
+            hsb_status s = hsb_run(hs[b], &pb, R, steps, seed, best_spins[b], best_energy[b]);
+            if (s != HSB_OK)
+                return s;
+        }
+        return HSB_OK;
+    }
+    DeviceGuard g(hs[0]->device);
+    if (!g.ok)
+        return set_error(HSB_E_NODEVICE, "cannot select the handles' device");
+    std::vector<BatchInst> insts((size_t)count);
+    RunCfg c0cfg;
+    for (int b = 0; b < count; ++b) {
+        hsb_ctx *h = hs[b];
+        hsb_params pb = *p;
+        pb.prec = HSB_PREC_FP8;
+        pb.instance = p->instance + (uint32_t)b;
+        RunCfg c;
+        hsb_status s = resolve(h, &pb, R, steps, &c);
+        if (s != HSB_OK)
+            return s;
+        s = prepare(h, c);
+        if (s != HSB_OK)
+            return s;
+        if (b == 0)
+            c0cfg = c;
+        BatchInst &in = insts[(size_t)b];
+        memset(&in, 0, sizeof in);
+        in.X = h->X[0];
+        in.Y = h->Y;
+        in.S8a = h->S8[0];
+        in.S8b = h->S8[1];
+        in.Ebest = h->Ebest;
+        in.Sbest = h->Sbest;
+        in.c0 = c.c.c0;
+        in.N = h->N;
+        in.Np = h->Np;
+        in.R = R;
+        in.BN = round_up(R, 32);
+        in.instance = pb.instance;
+        CK(batch_fill_maps(&in, h->J8, h->S8[0], h->S8[1], h->Np, h->Rcap), "batch maps");
+    }
+    // largest instances first
+    std::vector<int> order((size_t)count);
+    for (int b = 0; b < count; ++b)
+        order[(size_t)b] = b;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return insts[(size_t)x].Np > insts[(size_t)y].Np; });
+    std::vector<BatchInst> sorted((size_t)count);
+    for (int b = 0; b < count; ++b)
+        sorted[(size_t)b] = insts[(size_t)order[(size_t)b]];
+    CK(cudaDeviceSynchronize(), "synchronize");  // couplings converted on each handle's stream
+
+    BatchInst *d_insts = nullptr;
+    unsigned int *d_queue = nullptr;
+    float *d_pk = nullptr;
+    cudaStream_t st = hs[0]->work;
+    hsb_status status = HSB_OK;
+    cudaError_t e = cudaMalloc(&d_insts, sizeof(BatchInst) * (size_t)count);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d_queue, sizeof(unsigned int));
+    if (e == cudaSuccess)
+        e = cudaMalloc(&d_pk, sizeof(float) * (size_t)steps);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_insts, sorted.data(), sizeof(BatchInst) * (size_t)count,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d_pk, c0cfg.pk.data(), sizeof(float) * (size_t)steps,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemset(d_queue, 0, sizeof(unsigned int));
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(hs[0]->err, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        BatchArgs a;
+        memset(&a, 0, sizeof a);
+        a.count = count;
+        a.queue = d_queue;
+        a.steps = steps;
+        a.eval_every = p->eval_every;
+        a.pk = d_pk;
+        a.dt = c0cfg.c.dt;
+        a.q = c0cfg.c.q;
+        a.g = c0cfg.c.g;
+        a.scale = (float)(p->init_half_width / 16777216.0);
+        a.seed = seed;
+        a.err = hs[0]->err;
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hs[0]->device);
+        e = launch_tc_fp8_batch(st, d_insts, a, std::min(count, std::max(sms, 1)));
+    }
+    for (int b = 0; b < count && e == cudaSuccess; ++b) {
+        hsb_ctx *h = hs[b];
+        e = cudaMemcpyAsync(best_spins[b], h->Sbest, (size_t)R * h->N, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(best_energy[b], h->Ebest, (size_t)R * sizeof(double),
+                                cudaMemcpyDeviceToHost, st);
+        h->have_state = false;
+        h->launches = 1;
+    }
+    if (e != cudaSuccess)
+        status = cuda_error(e, "batched run");
+    else
+        status = check_device_error(hs[0]);
+    cudaStreamSynchronize(st);
+    cudaFree(d_insts);
+    cudaFree(d_queue);
+    cudaFree(d_pk);
+    return status;
 }
 
 hsb_status hsb_synchronize(hsb_handle h)

@@ -1,0 +1,423 @@
+// hsb_batch.cu -- many heated discrete SB problems (+/-1 couplings, FP8) of
+// uneven size in one launch: a work queue of instances, one CTA per instance
+// at a time, largest first.
+//
+// Per instance the whole step loop (Kanao & Goto, arXiv 2203.08361: force
+// Eq. (eq_fd), Methods update, evaluations every `eval_every` steps and at the
+// end, best kept) runs inside one CTA, so no CTA waits on another:
+//   - the spin operand S = sgn(x) of all N spins x BN replicas (FP8, at most
+//     128 KB) stays in shared memory for the step; the new signs go to the
+//     other global buffer and are fetched back with one TMA copy at the step
+//     boundary (the old ones are read by every row block of the step);
+//   - J streams through shared memory two 128-wide K chunks per TMA copy
+//     (3-D box, 32 KB); instances are small enough that J stays in L2;
+//   - for each 128-spin row block one tcgen05.mma chain (M = 128, N = BN)
+//     accumulates F = J S in tensor memory, double-buffered so that the next
+//     block's MMA overlaps the epilogue of this one;
+//   - the epilogue (8 warps) applies the pinned update to x, y in global
+//     memory, writes sgn(x') as FP8, and on evaluation steps adds s_i f_i into
+//     per-replica integer sums; after the step the best energy and spins of
+//     each replica are updated in place (exact integers, strict <).
+// Every wait is bounded; a wait that gives up raises the error word and the
+// CTA stops taking instances.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "hsb_device.cuh"
+#include "hsb_internal.cuh"
+#include "hsb_ptx.cuh"
+
+namespace hsb {
+
+namespace {
+
+constexpr int kTM = 128;                 // spins per row block
+constexpr int kMaxBN = 256;              // replica columns per instance
+constexpr int kMaxS = 128 * 1024;        // resident spin operand bytes (BN * Np)
+constexpr int kGStages = 2;
+constexpr int kGStageA = 2 * kTM * 128;  // two K chunks of J, 32 KB
+constexpr int kGEpiWarps = 8;
+constexpr int kGEpiThreads = 32 * kGEpiWarps;
+constexpr int kGThreads = 64 + kGEpiThreads;
+
+struct __align__(8) GShared {
+    uint64_t full[kGStages];
+    uint64_t empty[kGStages];
+    uint64_t s_full;        // resident S of the step has arrived
+    uint64_t step_done;     // epilogue finished a step (or the initial state)
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint32_t tmem_base;
+    int abort;
+    int inst;               // current instance index (-1: none left)
+    int esum[kMaxBN];       // per-replica sum of s_i f_i of the step (exact)
+    int improved[kMaxBN];
+};
+
+constexpr size_t kGSmem = 1024 + (size_t)kMaxS + (size_t)kGStages * kGStageA + sizeof(GShared);
+static_assert(kGSmem <= 232448, "shared memory per CTA is limited to 227 KB");
+
+__device__ __forceinline__ void gbar() { ptx::named_bar(1, kGEpiThreads); }
+
+__device__ __forceinline__ bool gbar_or(bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(kGEpiThreads)
+        : "memory");
+    return r != 0;
+}
+
+__device__ __forceinline__ void mma_fp8_n(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t acc)
+{
+    ptx::mma_fp8(tmem_d, adesc, bdesc, idesc, acc);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kGThreads, 1)
+tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint8_t *sS = base;                      // resident operand [chunk][BN][128]
+    uint8_t *sA = base + kMaxS;              // J stages
+    GShared *sh = reinterpret_cast<GShared *>(sA + (size_t)kGStages * kGStageA);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kGStages; ++s) {
+            ptx::mbar_init(&sh->full[s], 1);
+            ptx::mbar_init(&sh->empty[s], 1);
+        }
+        ptx::mbar_init(&sh->s_full, 1);
+        ptx::mbar_init(&sh->step_done, 1);
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&sh->acc_full[b], 1);
+            ptx::mbar_init(&sh->acc_empty[b], 1);
+        }
+        sh->abort = 0;
+        ptx::mbar_init_fence();
+    }
+    if (warp == 1)
+        ptx::tmem_alloc(&sh->tmem_base, 512);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = sh->tmem_base;
+
+    // running counters of each role, continued across instances
+    uint32_t g = 0;       // J stages (producer, MMA)
+    uint32_t tile = 0;    // accumulator tiles (MMA, epilogue)
+    uint32_t sdone = 0;   // step_done phases (producer waits, epilogue arrives)
+    uint32_t sfull = 0;   // s_full phases (producer arrives via TMA, MMA waits)
+
+    for (;;) {
+        if (threadIdx.x == 0)
+            sh->inst = *(volatile int *)&sh->abort ? -1 : (int)atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const int idx = sh->inst;
+        if (idx < 0 || idx >= a.count)
+            break;
+        const BatchInst &in = insts[idx];
+        const int N = in.N, Np = in.Np, BN = in.BN, R = in.R;
+        const int nblk = Np / kTM;
+        const int npairs = (nblk + 1) >> 1;
+        const int passes = a.steps + 1;  // updates, then the final evaluation
+
+        if (warp == 0) {
+            // ------------------------------------------------------ producer
+            if (lane == 0) {
+                ptx::prefetch_tmap(&in.mapA);
+                bool fail = false;
+                for (int k = 0; k < passes && !fail; ++k) {
+                    // the operand of step k is complete once the previous step's
+                    // epilogue (or the initial state) is done
+                    if (!ptx::mbar_wait(&sh->step_done, sdone & 1u, &sh->abort, a.err))
+                        break;
+                    ++sdone;
+                    ptx::fence_proxy_async_global();
+                    ptx::mbar_expect_tx(&sh->s_full, (uint32_t)(BN * Np));
+                    ptx::tma_load_3d(sS, &in.mapS[k & 1], 0, 0, 0, &sh->s_full);
+                    for (int mb = 0; mb < nblk && !fail; ++mb)
+                        for (int p = 0; p < npairs; ++p) {
+                            const int s = (int)(g % kGStages);
+                            const uint32_t ph = (g / kGStages) & 1u;
+                            if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err)) {
+                                fail = true;
+                                break;
+                            }
+                            ptx::mbar_expect_tx(&sh->full[s], (uint32_t)kGStageA);
+                            ptx::tma_load_3d(sA + (size_t)s * kGStageA, &in.mapA, 0, mb * kTM,
+                                             2 * p, &sh->full[s]);
+                            ++g;
+                        }
+                }
+            }
+        } else if (warp == 1) {
+            // ----------------------------------------------------------- MMA
+            if (lane == 0) {
+                const uint32_t idesc = ptx::idesc_e4m3_f32(kTM, BN);
+                const uint32_t sbase = ptx::smem_u32(sS);
+                bool ok = true;
+                for (int k = 0; k < passes && ok; ++k) {
+                    if (!ptx::mbar_wait(&sh->s_full, sfull & 1u, &sh->abort, a.err))
+                        break;
+                    ++sfull;
+                    ptx::tc_fence_after();
+                    for (int mb = 0; mb < nblk && ok; ++mb) {
+                        const uint32_t buf = tile & 1u;
+                        if (!ptx::mbar_wait(&sh->acc_empty[buf], ((tile >> 1) & 1u) ^ 1u,
+                                            &sh->abort, a.err)) {
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint32_t dcol = tmem + buf * (uint32_t)BN;
+                        for (int p = 0; p < npairs; ++p) {
+                            const int s = (int)(g % kGStages);
+                            const uint32_t ph = (g / kGStages) & 1u;
+                            if (!ptx::mbar_wait(&sh->full[s], ph, &sh->abort, a.err)) {
+                                ok = false;
+                                break;
+                            }
+                            ptx::tc_fence_after();
+                            for (int c = 0; c < 2; ++c) {
+                                const int kc = 2 * p + c;
+                                if (kc >= nblk)
+                                    break;
+                                const uint32_t a0 =
+                                    ptx::smem_u32(sA + (size_t)s * kGStageA + c * kTM * 128);
+                                const uint32_t b0 = sbase + (uint32_t)(kc * BN * 128);
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk)
+                                    mma_fp8_n(dcol, ptx::sw128_desc(a0 + kk * 32),
+                                              ptx::sw128_desc(b0 + kk * 32), idesc,
+                                              (p | c | kk) != 0 ? 1u : 0u);
+                            }
+                            ptx::mma_commit(&sh->empty[s]);
+                            ++g;
+                        }
+                        if (!ok)
+                            break;
+                        ptx::mma_commit(&sh->acc_full[buf]);
+                        ++tile;
+                    }
+                }
+            }
+        } else {
+            // ------------------------------------------------------ epilogue
+            const int et = threadIdx.x - 64;           // 0..255
+            const int q = warp & 3;                    // lane quadrant
+            const int half = (warp - 2) >> 2;          // column half
+            const int cw = BN / 2;                     // columns per warp (multiple of 16)
+            const int cbase = half * cw;
+            const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+            const uint64_t s_inst = splitmix64_out(a.seed, (uint64_t)in.instance + 1u);
+
+            // initial state: x, y uniform in (-L, L), S = sgn(x), best = +inf
+            for (size_t e = et; e < (size_t)BN * Np; e += kGEpiThreads) {
+                const int r = (int)(e / Np), i = (int)(e % Np);
+                float x = 0.f, y = 0.f;
+                uint8_t sg = 0;
+                if (i < N) {
+                    x = init_uniform(s_inst, (uint32_t)r, (uint32_t)i, 0, a.scale);
+                    y = init_uniform(s_inst, (uint32_t)r, (uint32_t)i, 1, a.scale);
+                    sg = fp8_sign(x);
+                }
+                in.X[e] = x;
+                in.Y[e] = y;
+                in.S8a[e] = sg;
+            }
+            for (int r = et; r < R; r += kGEpiThreads)
+                in.Ebest[r] = INFINITY;
+            for (int r = et; r < kMaxBN; r += kGEpiThreads)
+                sh->esum[r] = 0;
+            ptx::fence_proxy_async_global();
+            gbar();
+            if (et == 0)
+                ptx::mbar_arrive(&sh->step_done);
+
+            StepConsts c;
+            c.c0 = in.c0;
+            c.dt = a.dt;
+            c.q = a.q;
+            c.g = a.g;
+            bool left = false;
+            for (int k = 0; k < passes && !left; ++k) {
+                const bool final_pass = k == a.steps;
+                const bool ev = final_pass ||
+                                (a.eval_every > 0 && k > 0 && k % a.eval_every == 0);
+                const float pk = final_pass ? 0.f : a.pk[k];
+                const uint8_t *Sold = (k & 1) ? in.S8b : in.S8a;
+                uint8_t *Snew = (k & 1) ? in.S8a : in.S8b;
+                for (int mb = 0; mb < nblk; ++mb) {
+                    const uint32_t buf = tile & 1u;
+                    const bool ok = ptx::mbar_wait(&sh->acc_full[buf], (tile >> 1) & 1u,
+                                                   &sh->abort, a.err);
+                    if (gbar_or(!ok)) {
+                        left = true;
+                        break;
+                    }
+                    ++tile;
+                    ptx::tc_fence_after();
+                    const int i = mb * kTM + q * 32 + lane;
+                    const bool live = i < N;
+                    for (int cb = 0; cb < cw; cb += 16) {
+                        uint32_t f[16];
+                        ptx::tmem_ld16(tmem + buf * (uint32_t)BN + lane_off + (uint32_t)(cbase + cb),
+                                       f);
+                        ptx::tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int r = cbase + cb + j;
+                            const size_t e = (size_t)r * Np + i;
+                            const float fj = __uint_as_float(f[j]);
+                            const float x0 = in.X[e];
+                            if (ev) {
+                                int term = live ? (x0 >= 0.f ? (int)fj : -(int)fj) : 0;
+#pragma unroll
+                                for (int off = 16; off > 0; off >>= 1)
+                                    term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
+                                if (lane == 0)
+                                    atomicAdd(&sh->esum[r], term);
+                            }
+                            if (!final_pass) {
+                                float xn, yn;
+                                sb_update(fj, x0, in.Y[e], pk, c, xn, yn);
+                                in.X[e] = xn;
+                                in.Y[e] = yn;
+                                Snew[e] = live ? fp8_sign(xn) : (uint8_t)0;
+                            }
+                        }
+                    }
+                    ptx::tc_fence_before();
+                    gbar();
+                    if (et == 0)
+                        ptx::mbar_arrive(&sh->acc_empty[buf]);
+                }
+                if (left)
+                    break;
+                // end of step k: best update from the evaluation of s(t_k)
+                if (ev) {
+                    for (int r = et; r < R; r += kGEpiThreads) {
+                        const double E = -0.5 * (double)sh->esum[r];
+                        const int take = E < in.Ebest[r];
+                        if (take)
+                            in.Ebest[r] = E;
+                        sh->improved[r] = take;
+                    }
+                    gbar();
+                    const int w = warp - 2;
+                    for (int r = w; r < R; r += kGEpiWarps)
+                        if (sh->improved[r])
+                            for (int i = lane; i < N; i += 32)
+                                in.Sbest[(size_t)r * N + i] =
+                                    Sold[(size_t)r * Np + i] == kFp8PlusOne ? (int8_t)1 : (int8_t)-1;
+                    for (int r = et; r < kMaxBN; r += kGEpiThreads)
+                        sh->esum[r] = 0;
+                }
+                ptx::fence_proxy_async_global();
+                gbar();
+                // one arrival per pass the producer waits for: the initial state
+                // and steps 0..steps-1 (the final evaluation pass has no successor)
+                if (et == 0 && !final_pass)
+                    ptx::mbar_arrive(&sh->step_done);
+            }
+        }
+        __syncthreads();
+        if (*(volatile int *)&sh->abort)
+            break;
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    if (warp == 1)
+        ptx::tmem_dealloc(tmem, 512);
+}
+
+// ------------------------------------------------------------- host side ---
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                   const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                   const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn batch_encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// 3-D view of a [rows][cols] byte array as (byte in a 128-byte K chunk, row,
+// chunk), box 128 x box_rows x box_chunks, 128-byte swizzle.
+bool encode_chunks(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols,
+                   uint32_t box_rows, uint32_t box_chunks)
+{
+    EncodeTiledFn fn = batch_encode_fn();
+    if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0 || cols % 128u != 0)
+        return false;
+    const cuuint64_t dims[3] = {128, rows, cols / 128};
+    const cuuint64_t strides[2] = {cols, 128};
+    const cuuint32_t box[3] = {128, box_rows, box_chunks};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void *>(ptr), dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool batch_shape_ok(int Np, int R)
+{
+    const int BN = round_up(R, 32);
+    return R >= 1 && BN <= kMaxBN && Np % kTM == 0 && Np / 128 <= 256 && BN * Np <= kMaxS;
+}
+
+cudaError_t batch_fill_maps(BatchInst *in, const uint8_t *J8, const uint8_t *S8a,
+                            const uint8_t *S8b, int Np, int Rcap)
+{
+    const int BN = in->BN;
+    if (!encode_chunks(&in->mapA, J8, (uint64_t)Np, (uint64_t)Np, kTM, 2) ||
+        !encode_chunks(&in->mapS[0], S8a, (uint64_t)Rcap, (uint64_t)Np, (uint32_t)BN,
+                       (uint32_t)(Np / 128)) ||
+        !encode_chunks(&in->mapS[1], S8b, (uint64_t)Rcap, (uint64_t)Np, (uint32_t)BN,
+                       (uint32_t)(Np / 128)))
+        return cudaErrorInvalidValue;
+    return cudaSuccess;
+}
+
+cudaError_t launch_tc_fp8_batch(cudaStream_t st, const BatchInst *d_insts, const BatchArgs &a,
+                                int ctas)
+{
+    cudaError_t e = cudaFuncSetAttribute(tc_fp8_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
+    if (e != cudaSuccess)
+        return e;
+    tc_fp8_batch_kernel<<<ctas, kGThreads, kGSmem, st>>>(d_insts, a);
+    return cudaGetLastError();
+}
+
+}  // namespace hsb

@@ -138,4 +138,36 @@ bool tc_bf16_persistent_fits(int Np, int Rp);
 cudaError_t launch_tc_bf16x3_persistent(cudaStream_t st, const Bf16Plan *plan, int form,
                                         const PersistArgs &a);
 
+// ---- hsb_batch.cu -----------------------------------------------------------
+// One instance of a batched FP8 run (a device array of these is read by the
+// kernel; aligned as its tensor maps require).
+struct BatchInst {
+    CUtensorMap mapA;     // J8 as (128 B, rows, K chunk), box 128 x 128 x 2
+    CUtensorMap mapS[2];  // S8a / S8b as (128 B, rows, chunk), box 128 x BN x Np/128
+    float *X, *Y;         // [Rcap][Np] state
+    uint8_t *S8a, *S8b;   // [Rcap][Np] FP8 operand ping/pong
+    double *Ebest;        // [R]
+    int8_t *Sbest;        // [R][N]
+    float c0;
+    int N, Np, R, BN;     // BN = R rounded up to 32
+    uint32_t instance;    // random stream of the instance
+};
+
+struct BatchArgs {
+    int count;             // instances in the queue
+    unsigned int *queue;   // next instance to take (zero at launch)
+    int steps, eval_every;
+    const float *pk;       // [steps] p_k = a0 - a(t_k)
+    float dt, q, g;        // binary32 constants shared by the batch
+    float scale;           // fl32(L * 2^-24) of the initial distribution
+    uint64_t seed;
+    int *err;
+};
+
+bool batch_shape_ok(int Np, int R);
+cudaError_t batch_fill_maps(BatchInst *in, const uint8_t *J8, const uint8_t *S8a,
+                            const uint8_t *S8b, int Np, int Rcap);
+cudaError_t launch_tc_fp8_batch(cudaStream_t st, const BatchInst *d_insts, const BatchArgs &a,
+                                int ctas);
+
 }  // namespace hsb

@@ -76,6 +76,7 @@ struct __align__(8) PShared {
 
 constexpr size_t kPSmem =
     1024 + (size_t)kPStages * (kPStageA + kPStageB) + kPTileS + sizeof(PShared);
+static_assert(kPSmem <= 232448, "shared memory per CTA is limited to 227 KB");
 
 // Barrier among the epilogue warps that also ORs a predicate over them, so
 // that a decision to leave the step loop is the same in every epilogue warp.

@@ -66,6 +66,7 @@ struct __align__(8) QShared {
 
 constexpr size_t kQSmem =
     1024 + (size_t)kQStages * (kQStageA + kQStageB) + 2 * (size_t)kQTile + sizeof(QShared);
+static_assert(kQSmem <= 232448, "shared memory per CTA is limited to 227 KB");
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
                                          uint32_t accumulate)

@@ -52,6 +52,7 @@ struct __align__(8) TcShared {
 
 constexpr size_t kSmemBytes = 1024 /* alignment slack */ + (size_t)kStages * (kStageA + kStageB) +
                               sizeof(TcShared);
+static_assert(kSmemBytes <= 232448, "shared memory per CTA is limited to 227 KB");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

@@ -1,0 +1,56 @@
+"""Batched heated discrete SB over many instances of uneven size (FP8, one
+launch): every instance's best spins and energies must equal those of a
+separate run of the same instance (same random stream), and the oracle's on
+sampled instances."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_08361_gb300 as hsb
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch_vs_single(sizes, R, steps, ev, seed, check_oracle=()):
+    Js = [synth.sk_pm1(n, 500 + b) for b, n in enumerate(sizes)]
+    solvers = [hsb.Solver(J) for J in Js]
+    p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=ev)
+    try:
+        out = hsb.run_batch([s.h for s in solvers], p, R, steps, seed)
+        for b, s in enumerate(solvers):
+            pb = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=ev,
+                            instance=b)
+            spins, energy = s.run(pb, R, steps, seed)
+            np.testing.assert_array_equal(out[b][0], spins, err_msg=f"instance {b}")
+            np.testing.assert_array_equal(out[b][1], energy, err_msg=f"instance {b}")
+        for b in check_oracle:
+            J = Js[b]
+            op = oracle.make_params(1, oracle.c0_from_c1(J, 0.7), 1.1, 0.06, eval_every=ev,
+                                    instance=b)
+            ref = oracle.run(J, op, steps, seed, range(R), "f32")
+            np.testing.assert_array_equal(out[b][0], ref["best_s"])
+            np.testing.assert_array_equal(out[b][1], ref["best_e"])
+    finally:
+        for s in solvers:
+            s.close()
+    return out
+
+
+def test_batch_small_uneven_instances():
+    # ragged sizes (one 128-row block up to several, odd block counts) and R
+    _batch_vs_single([100, 128, 257, 300, 511, 700, 129, 2, 640], 40, 150, 30, 3,
+                     check_oracle=(0, 2, 7))
+
+
+def test_batch_more_instances_than_ctas_per_cta_reuse():
+    # 400 small instances: every CTA takes several instances in turn
+    sizes = [int(v) for v in synth.batch_sizes(400, 7, lo=2, hi=260)]
+    _batch_vs_single(sizes, 32, 60, 20, 5, check_oracle=(0, 399))
+
+
+def test_batch_uneven_workload_full_size():
+    # 256 SK instances, N uniform in [100, 2000], R = 64, 2000 steps, eval every
+    # 100: one batched launch against 256 separate runs.
+    sizes = synth.batch_sizes(256, 4)
+    _batch_vs_single(sizes, 64, 2000, 100, 9, check_oracle=(sizes.index(min(sizes)),))
