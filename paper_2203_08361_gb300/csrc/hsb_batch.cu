@@ -264,6 +264,17 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                 uint8_t *Snew = (k & 1) ? in.S8a : in.S8b;
                 for (int mb = 0; mb < nblk; ++mb) {
                     const uint32_t buf = tile & 1u;
+                    const int i = mb * kTM + q * 32 + lane;
+                    const bool live = i < N;
+                    // x, y of the first 16 columns are fetched before the
+                    // accumulator is ready, so the loads overlap the MMA
+                    float xr[16], yr[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const size_t e = (size_t)(cbase + j) * Np + i;
+                        xr[j] = in.X[e];
+                        yr[j] = in.Y[e];
+                    }
                     const bool ok = ptx::mbar_wait(&sh->acc_full[buf], (tile >> 1) & 1u,
                                                    &sh->abort, a.err);
                     if (gbar_or(!ok)) {
@@ -272,19 +283,26 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     }
                     ++tile;
                     ptx::tc_fence_after();
-                    const int i = mb * kTM + q * 32 + lane;
-                    const bool live = i < N;
                     for (int cb = 0; cb < cw; cb += 16) {
                         uint32_t f[16];
                         ptx::tmem_ld16(tmem + buf * (uint32_t)BN + lane_off + (uint32_t)(cbase + cb),
                                        f);
+                        // next chunk's x, y in flight while this chunk computes
+                        float xn[16], yn[16];
+                        const bool more = cb + 16 < cw;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const size_t e = (size_t)(cbase + cb + 16 + j) * Np + i;
+                            xn[j] = more ? in.X[e] : 0.f;
+                            yn[j] = more ? in.Y[e] : 0.f;
+                        }
                         ptx::tmem_ld_wait();
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int r = cbase + cb + j;
                             const size_t e = (size_t)r * Np + i;
                             const float fj = __uint_as_float(f[j]);
-                            const float x0 = in.X[e];
+                            const float x0 = xr[j];
                             if (ev) {
                                 int term = live ? (x0 >= 0.f ? (int)fj : -(int)fj) : 0;
 #pragma unroll
@@ -294,12 +312,17 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                                     atomicAdd(&sh->esum[r], term);
                             }
                             if (!final_pass) {
-                                float xn, yn;
-                                sb_update(fj, x0, in.Y[e], pk, c, xn, yn);
-                                in.X[e] = xn;
-                                in.Y[e] = yn;
-                                Snew[e] = live ? fp8_sign(xn) : (uint8_t)0;
+                                float xo, yo;
+                                sb_update(fj, x0, yr[j], pk, c, xo, yo);
+                                in.X[e] = xo;
+                                in.Y[e] = yo;
+                                Snew[e] = live ? fp8_sign(xo) : (uint8_t)0;
                             }
+                        }
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            xr[j] = xn[j];
+                            yr[j] = yn[j];
                         }
                     }
                     ptx::tc_fence_before();
