@@ -105,7 +105,10 @@ typedef struct {
     int schedule;           /* FP8 step loop: 0 = automatic (persistent kernel
                                when its grid fits on the device), 1 = persistent
                                kernel only (HSB_E_UNSUPPORTED if it cannot fit),
-                               2 = one kernel launch per step */
+                               2 = one kernel launch per step, 3 = persistent
+                               kernel with the CTA's rows of J held on chip for
+                               the whole run (N <= 2048, else
+                               HSB_E_UNSUPPORTED) */
     uint32_t reserved[6];   /* must be zero */
 } hsb_params;
 

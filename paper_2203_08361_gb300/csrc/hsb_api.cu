@@ -251,8 +251,8 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_INVAL, "need c0 > 0 or c1 > 0");
     if (p->eval_every < 0 || p->trace_every < 0)
         return set_error(HSB_E_INVAL, "eval_every and trace_every must be >= 0");
-    if (p->schedule < 0 || p->schedule > 2)
-        return set_error(HSB_E_INVAL, "schedule must be 0, 1 or 2");
+    if (p->schedule < 0 || p->schedule > 3)
+        return set_error(HSB_E_INVAL, "schedule must be 0, 1, 2 or 3");
     if ((long long)R * h->N > (1LL << 40))
         return set_error(HSB_E_INVAL, "R*N too large");
     int prec = p->prec;
@@ -274,7 +274,7 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_INVAL, "unknown precision %d", p->prec);
     if (p->trace_every > 0 && prec == HSB_PREC_BF16X3)
         return set_error(HSB_E_UNSUPPORTED, "the trace needs the FP32 or FP8 precision");
-    if (p->trace_every > 0 && prec == HSB_PREC_FP8 && p->schedule == 1)
+    if (p->trace_every > 0 && prec == HSB_PREC_FP8 && (p->schedule == 1 || p->schedule == 3))
         return set_error(HSB_E_UNSUPPORTED, "the trace runs on the one-launch-per-step schedule");
     cfg->prec = prec;
     cfg->form = p->form;
@@ -454,8 +454,9 @@ hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
     *out = false;
     if (c.prec != HSB_PREC_FP8 || c.schedule == 2 || c.trace_every > 0)
         return HSB_OK;
-    const bool fits = tc_persistent_fits(h->Np, c.Rp);
-    if (!fits && c.schedule == 1)
+    const bool fits = c.schedule == 3 ? tc_resident_fits(h->Np, c.Rp)
+                                      : tc_persistent_fits(h->Np, c.Rp);
+    if (!fits && (c.schedule == 1 || c.schedule == 3))
         return set_error(HSB_E_UNSUPPORTED,
                          "the persistent kernel's %d x %d grid does not fit on the device",
                          h->Np / kTileM, c.Rp / kTileR);
@@ -539,7 +540,11 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     a.Epart = h->Eeval;
     a.Snap = h->Snap;
     a.err = h->err;
-    CK(launch_tc_fp8_persistent(h->work, h->plan, a), "persistent fp8 kernel");
+    // schedule 3: J resident on chip; otherwise J streamed every step
+    if (c.schedule == 3)
+        CK(launch_tc_fp8_resident(h->work, h->plan, h->J8, a), "resident fp8 kernel");
+    else
+        CK(launch_tc_fp8_persistent(h->work, h->plan, a), "persistent fp8 kernel");
     if (evaluate)
         CK(launch_select_best(h->work, h->Eeval, h->Snap, ne, nblk, h->N, h->Np, c.R, c.Rp,
                               h->Ebest, h->Sbest),

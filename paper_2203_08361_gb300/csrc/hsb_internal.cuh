@@ -115,6 +115,11 @@ struct PersistArgs {
     int *err;
 };
 
+// Resident-J variant (hsb_persist_ar.cu): N <= 2048, same arguments.
+bool tc_resident_fits(int Np, int Rp);
+cudaError_t launch_tc_fp8_resident(cudaStream_t st, const TcPlan *plan, const uint8_t *J8,
+                                   const PersistArgs &a);
+
 // True when the nblk x nrb grid of the persistent kernel can be co-resident.
 bool tc_persistent_fits(int Np, int Rp);
 cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const PersistArgs &a);

@@ -226,6 +226,10 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
     } else if (warp == 1) {
         // --------------------------------------------------------------- MMA
         if (lane == 0) {
+            // descriptors of stage 0; a stage or K step further is a plain
+            // add on the 14-bit start-address field (addresses < 256 KB)
+            const uint64_t adesc0 = ptx::sw128_desc(ptx::smem_u32(sA));
+            const uint64_t bdesc0 = ptx::sw128_desc(ptx::smem_u32(sB));
             uint32_t g = 0;
             for (int kl = 0; kl < passes; ++kl) {
                 if (kl > 0) {
@@ -244,14 +248,15 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                         break;
                     }
                     ptx::tc_fence_after();
+                    const uint64_t ad = adesc0 + (uint64_t)((s * kPStageA) >> 4);
+                    const uint64_t bd = bdesc0 + (uint64_t)((s * kPStageB) >> 4);
 #pragma unroll
                     for (int c = 0; c < kPChunks; ++c) {
-                        const uint32_t a0 = ptx::smem_u32(sA + (size_t)s * kPStageA + c * kPM * kPK);
-                        const uint32_t b0 = ptx::smem_u32(sB + (size_t)s * kPStageB + c * kPN * kPK);
 #pragma unroll
                         for (int kk = 0; kk < kPK / 32; ++kk)
-                            ptx::mma_fp8(tmem + kColAcc, ptx::sw128_desc(a0 + kk * 32),
-                                         ptx::sw128_desc(b0 + kk * 32), kIdesc,
+                            ptx::mma_fp8(tmem + kColAcc,
+                                         ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4),
+                                         bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4), kIdesc,
                                          (t | c | kk) != 0 ? 1u : 0u);
                     }
                     ptx::mma_commit(&sh->empty[s]);
@@ -303,7 +308,13 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             if (kl + 1 < a.nsteps)
                 pk_next = a.pk[k + 1];  // p_k of the next pass, off the critical path
 
+            // x and y of the first 16 columns: the MMA does not write them
+            uint32_t xpre[16], ypre[16];
+            ptx::tmem_ld16(tmem + lane_off + kColX + c0, xpre);
+            ptx::tmem_ld16(tmem + lane_off + kColY + c0, ypre);
             const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
+            ptx::tmem_ld_wait(xpre);
+            ptx::tmem_ld_wait(ypre);
             if (epi_bar_or(!ok)) {
                 left = true;
                 break;
@@ -314,9 +325,19 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 const uint32_t col0 = (uint32_t)(c0 + h * 16);
                 uint32_t f[16], xr[16], yr[16];
                 ptx::tmem_ld16(tmem + lane_off + kColAcc + col0, f);
-                ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
-                ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
-                ptx::tmem_ld_wait();
+                if (h == 0) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        xr[j] = xpre[j];
+                        yr[j] = ypre[j];
+                    }
+                } else {
+                    ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
+                    ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
+                    ptx::tmem_ld_wait(xr);
+                    ptx::tmem_ld_wait(yr);
+                }
+                ptx::tmem_ld_wait(f);
                 if (e >= 0) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -361,7 +382,6 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 ptx::bulk_commit();
                 ptx::bulk_wait_all();
                 ptx::fence_proxy_async_global();
-                ptx::fence_acq_rel_gpu();
                 ptx::st_release_gpu(&a.flags[mb * a.nrb + rb], kl + 1);
             }
             if (e >= 0 && et < kPN) {

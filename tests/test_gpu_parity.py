@@ -31,9 +31,10 @@ def _assert_same(got_x, got_y, spins, energy, ref, rows=None):
     np.testing.assert_array_equal(energy[sel], ref["best_e"])
 
 
-@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
-                                           ("fp32", "auto")])
-@pytest.mark.parametrize("n,R", [(128, 128), (300, 40), (257, 130), (2, 3), (700, 300)])
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "resident"),
+                                           ("fp8", "per_step"), ("fp32", "auto")])
+@pytest.mark.parametrize("n,R", [(128, 128), (300, 40), (257, 130), (2, 3), (700, 300),
+                                 (1100, 130), (2048, 128)])
 def test_discrete_pm1_bit_exact(prec, schedule, n, R):
     J = synth.sk_pm1(n, 1000 + n)
     steps, seed, ev = 150, 7, 40
@@ -84,8 +85,8 @@ def test_small_ballistic_pm1_workload_fp32():
     assert abs(np.mean(energy) - np.mean(e0)) < 0.05 * abs(np.mean(e0))
 
 
-@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
-                                           ("fp32", "auto")])
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "resident"),
+                                           ("fp8", "per_step"), ("fp32", "auto")])
 def test_one_step_and_split_runs(prec, schedule):
     n, R, steps = 260, 70, 50
     J = synth.sk_pm1(n, 4)
@@ -167,8 +168,13 @@ def test_full_size_fp8_equals_fp32_and_is_independent_of_R():
                          schedule="per_step")
         sd, ed = s.run(pps, 1024, steps, seed)
         xd, yd = s.get_state(1024)
+        pst = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
+                         schedule="resident")
+        sg, eg = s.run(pst, 1024, steps, seed)
+        xg, yg = s.get_state(1024)
         sc, ec = s.run(p, 8, steps, seed)
-    for other_s, other_e, other_x, other_y in ((sb, eb, xb, yb), (sd, ed, xd, yd)):
+    for other_s, other_e, other_x, other_y in ((sb, eb, xb, yb), (sd, ed, xd, yd),
+                                               (sg, eg, xg, yg)):
         np.testing.assert_array_equal(sa, other_s)
         np.testing.assert_array_equal(ea, other_e)
         np.testing.assert_array_equal(xa, other_x)
@@ -221,6 +227,16 @@ def test_unsupported_precision_and_argument_errors():
     with hsb.Solver(J) as s:
         with pytest.raises(hsb.HsbError) as e:
             s.run(hsb.params("ballistic", "fp8"), 4, 10, 0)
+        assert e.value.status == 7
+        # the per-step trace runs on the one-launch-per-step schedule only
+        for sched in ("persistent", "resident"):
+            with pytest.raises(hsb.HsbError) as e:
+                s.run(hsb.params("discrete", "fp8", trace_every=1, schedule=sched), 4, 10, 0)
+            assert e.value.status == 7
+    # J held on chip needs N <= 2048
+    with hsb.Solver(synth.sk_pm1(2100, 0)) as s:
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("discrete", "fp8", schedule="resident"), 128, 4, 0)
         assert e.value.status == 7
 
 
