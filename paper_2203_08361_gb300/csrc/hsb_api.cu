@@ -291,6 +291,7 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
     cfg->c.dt = (float)p->dt;
     cfg->c.q = (float)(p->a0 * p->dt);
     cfg->c.g = (float)(p->gamma * p->dt);
+    cfg->c.nz = -0.0f;
     cfg->pk.resize(steps);
     for (int k = 0; k < steps; ++k) {
         // a(t_k) = a0 k / Ns, linear from 0 to a0 (Results); p_k = a0 - a(t_k)

@@ -75,4 +75,82 @@ __device__ __forceinline__ void sb_update(float f, float x0, float y0, float pk,
     yn = __fadd_rn(ytt, gy);
 }
 
+// ---- two updates at once on packed binary32 pairs (lo, hi) -----------------
+// The arithmetic uses add/sub/fma.rn.f32x2 and gives the same bits as two
+// sb_update calls.  Each product a*b is computed as fma(a, b, z) with z = -0.0
+// supplied at run time (StepConsts::nz): the sum is exactly a*b for every
+// product (a zero product keeps its sign), rounded once, and because z is not
+// a compile-time constant the compiler cannot turn the product back into a
+// multiply and fuse it into the following add, which it does for plain
+// mul/add.rn.f32x2 pairs.
+
+__device__ __forceinline__ uint64_t f2_pack(float lo, float hi)
+{
+    return ((uint64_t)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+__device__ __forceinline__ uint64_t f2_pack_bits(uint32_t lo, uint32_t hi)
+{
+    return ((uint64_t)hi << 32) | lo;
+}
+__device__ __forceinline__ float f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// StepConsts broadcast to both halves of a pair.
+struct StepConsts2 {
+    uint64_t c0, dt, q, g, z;
+};
+
+__device__ __forceinline__ StepConsts2 step_consts2(const StepConsts &c)
+{
+    StepConsts2 k;
+    k.c0 = f2_pack(c.c0, c.c0);
+    k.dt = f2_pack(c.dt, c.dt);
+    k.q = f2_pack(c.q, c.q);
+    k.g = f2_pack(c.g, c.g);
+    k.z = f2_pack(c.nz, c.nz);
+    return k;
+}
+
+// sb_update on the pairs (f, x0, y0) with p_k broadcast in pk2; the walls
+// are applied per element.  Returns x' per element and y' as a pair.
+__device__ __forceinline__ void sb_update2(uint64_t f, uint64_t x0, uint64_t y0, uint64_t pk2,
+                                           const StepConsts2 &k, float &xn_lo, float &xn_hi,
+                                           uint64_t &yn)
+{
+    const uint64_t u = f2_fma(k.c0, f, k.z);
+    const uint64_t v = f2_fma(pk2, x0, k.z);
+    const uint64_t w = f2_sub(u, v);
+    const uint64_t wd = f2_fma(w, k.dt, k.z);
+    const uint64_t yt = f2_add(y0, wd);
+    const uint64_t qy = f2_fma(k.q, yt, k.z);
+    const uint64_t xt = f2_add(x0, qy);
+    const float xt0 = f2_lo(xt), xt1 = f2_hi(xt);
+    // walls: |x~| > 1 -> x' = sgn(x~), y~~ = 0 (Eqs. eq_WallX, eq_WallY)
+    xn_lo = fminf(fmaxf(xt0, -1.f), 1.f);
+    xn_hi = fminf(fmaxf(xt1, -1.f), 1.f);
+    const float ytt0 = fabsf(xt0) > 1.f ? 0.f : f2_lo(yt);
+    const float ytt1 = fabsf(xt1) > 1.f ? 0.f : f2_hi(yt);
+    const uint64_t gy = f2_fma(k.g, y0, k.z);
+    yn = f2_add(f2_pack(ytt0, ytt1), gy);
+}
+
 }  // namespace hsb

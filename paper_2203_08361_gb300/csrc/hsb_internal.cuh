@@ -29,6 +29,7 @@ struct StepConsts {
     float dt;
     float q;
     float g;
+    float nz;  // -0.0f, set at run time (see sb_update2)
 };
 
 // Error word written by kernels whose bounded waits gave up.

@@ -133,6 +133,7 @@ extern "C" HSB_API hsb_status hsb_run_fp32_noalloc(const float *J, int N, const 
     c.dt = (float)p->dt;
     c.q = (float)(p->a0 * p->dt);
     c.g = (float)(p->gamma * p->dt);
+    c.nz = -0.0f;
     const int nblk = Np / kTileM;
 
     // The scratch keeps the previous call's contents: the padded couplings,

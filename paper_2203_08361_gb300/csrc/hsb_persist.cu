@@ -295,6 +295,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
 
         bool left = false;
         uint8_t *srow = sS + q * 32 + lane;  // this spin's byte in row `col` of the tile
+        const StepConsts2 k2 = step_consts2(a.c);
         float pk_next = a.nsteps > 0 ? a.pk[a.k_begin] : 0.f;
         for (int kl = 0; kl < passes; ++kl) {
             const bool final_pass = kl == a.nsteps;
@@ -305,6 +306,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             else if (a.eval_every > 0 && k > 0 && k < a.steps_total && k % a.eval_every == 0)
                 e = k / a.eval_every - 1;
             const float pk = final_pass ? 0.f : pk_next;
+            const uint64_t pk2 = f2_pack(pk, pk);
             if (kl + 1 < a.nsteps)
                 pk_next = a.pk[k + 1];  // p_k of the next pass, off the critical path
 
@@ -355,14 +357,19 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                     }
                 }
                 if (!final_pass) {
+                    // two replicas per packed binary32 operation
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        float xn, yn;
-                        sb_update(__uint_as_float(f[j]), __uint_as_float(xr[j]),
-                                  __uint_as_float(yr[j]), pk, a.c, xn, yn);
-                        xr[j] = __float_as_uint(xn);
-                        yr[j] = __float_as_uint(yn);
-                        srow[(col0 + j) * kPM] = live ? fp8_sign(xn) : (uint8_t)0;
+                    for (int j = 0; j < 16; j += 2) {
+                        float xn0, xn1;
+                        uint64_t yn;
+                        sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
+                                   f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xn0, xn1, yn);
+                        xr[j] = __float_as_uint(xn0);
+                        xr[j + 1] = __float_as_uint(xn1);
+                        yr[j] = (uint32_t)yn;
+                        yr[j + 1] = (uint32_t)(yn >> 32);
+                        srow[(col0 + j) * kPM] = live ? fp8_sign(xn0) : (uint8_t)0;
+                        srow[(col0 + j + 1) * kPM] = live ? fp8_sign(xn1) : (uint8_t)0;
                     }
                     ptx::tmem_st16(tmem + lane_off + kColX + col0, xr);
                     ptx::tmem_st16(tmem + lane_off + kColY + col0, yr);
