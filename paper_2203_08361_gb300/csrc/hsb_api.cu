@@ -509,14 +509,15 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     const int ne = evaluate ? num_evals(c) : 0;
     hsb_status s = ensure_pk(h, c);
     if (s == HSB_OK)
-        s = grow(&h->flags, &h->flags_cap, (size_t)nblk * nrb, "cudaMalloc flags");
+        s = grow(&h->flags, &h->flags_cap, (size_t)nblk * nrb * kFlagStride, "cudaMalloc flags");
     if (s == HSB_OK && evaluate)
         s = grow(&h->Eeval, &h->eeval_cap, (size_t)ne * nblk * c.Rp, "cudaMalloc Eeval");
     if (s == HSB_OK && evaluate)
         s = grow(&h->Snap, &h->snap_cap, (size_t)ne * c.Rp * h->Np, "cudaMalloc snapshots");
     if (s != HSB_OK)
         return s;
-    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * sizeof(int), h->work), "memset flags");
+    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * kFlagStride * sizeof(int), h->work),
+       "memset flags");
     PersistArgs a;
     memset(&a, 0, sizeof a);
     a.N = h->N;
@@ -561,10 +562,11 @@ hsb_status enqueue_bf16(hsb_ctx *h, const RunCfg &c, int k_begin, int nsteps, in
     const int nrb = c.Rp / kTileR;
     hsb_status s = ensure_pk(h, c);
     if (s == HSB_OK)
-        s = grow(&h->flags, &h->flags_cap, (size_t)nblk * nrb, "cudaMalloc flags");
+        s = grow(&h->flags, &h->flags_cap, (size_t)nblk * nrb * kFlagStride, "cudaMalloc flags");
     if (s != HSB_OK)
         return s;
-    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * sizeof(int), h->work), "memset flags");
+    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * kFlagStride * sizeof(int), h->work),
+       "memset flags");
     PersistArgs a;
     memset(&a, 0, sizeof a);
     a.N = h->N;
@@ -1307,6 +1309,7 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
         a.dt = c0cfg.c.dt;
         a.q = c0cfg.c.q;
         a.g = c0cfg.c.g;
+        a.nz = -0.0f;
         a.scale = (float)(p->init_half_width / 16777216.0);
         a.seed = seed;
         a.err = hs[0]->err;

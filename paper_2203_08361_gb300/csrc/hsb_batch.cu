@@ -254,12 +254,15 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
             c.dt = a.dt;
             c.q = a.q;
             c.g = a.g;
+            c.nz = a.nz;
+            const StepConsts2 k2 = step_consts2(c);
             bool left = false;
             for (int k = 0; k < passes && !left; ++k) {
                 const bool final_pass = k == a.steps;
                 const bool ev = final_pass ||
                                 (a.eval_every > 0 && k > 0 && k % a.eval_every == 0);
                 const float pk = final_pass ? 0.f : a.pk[k];
+                const uint64_t pk2 = f2_pack(pk, pk);
                 const uint8_t *Sold = (k & 1) ? in.S8b : in.S8a;
                 uint8_t *Snew = (k & 1) ? in.S8a : in.S8b;
                 for (int mb = 0; mb < nblk; ++mb) {
@@ -297,26 +300,34 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                             yn[j] = more ? in.Y[e] : 0.f;
                         }
                         ptx::tmem_ld_wait();
+                        if (ev) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int r = cbase + cb + j;
-                            const size_t e = (size_t)r * Np + i;
-                            const float fj = __uint_as_float(f[j]);
-                            const float x0 = xr[j];
-                            if (ev) {
-                                int term = live ? (x0 >= 0.f ? (int)fj : -(int)fj) : 0;
+                            for (int j = 0; j < 16; ++j) {
+                                const int r = cbase + cb + j;
+                                const float fj = __uint_as_float(f[j]);
+                                int term = live ? (xr[j] >= 0.f ? (int)fj : -(int)fj) : 0;
 #pragma unroll
                                 for (int off = 16; off > 0; off >>= 1)
                                     term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
                                 if (lane == 0)
                                     atomicAdd(&sh->esum[r], term);
                             }
-                            if (!final_pass) {
-                                float xo, yo;
-                                sb_update(fj, x0, yr[j], pk, c, xo, yo);
-                                in.X[e] = xo;
-                                in.Y[e] = yo;
-                                Snew[e] = live ? fp8_sign(xo) : (uint8_t)0;
+                        }
+                        if (!final_pass) {
+                            // two replicas per packed binary32 operation
+#pragma unroll
+                            for (int j = 0; j < 16; j += 2) {
+                                const size_t e = (size_t)(cbase + cb + j) * Np + i;
+                                float xo0, xo1;
+                                uint64_t yo;
+                                sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack(xr[j], xr[j + 1]),
+                                           f2_pack(yr[j], yr[j + 1]), pk2, k2, xo0, xo1, yo);
+                                in.X[e] = xo0;
+                                in.X[e + Np] = xo1;
+                                in.Y[e] = f2_lo(yo);
+                                in.Y[e + Np] = f2_hi(yo);
+                                Snew[e] = live ? fp8_sign(xo0) : (uint8_t)0;
+                                Snew[e + Np] = live ? fp8_sign(xo1) : (uint8_t)0;
                             }
                         }
 #pragma unroll

@@ -32,6 +32,15 @@ struct StepConsts {
     float nz;  // -0.0f, set at run time (see sb_update2)
 };
 
+// Published-step flags of the persistent kernels: one int per (row block,
+// replica block) tile, each on its own 128-byte line, so that the 16 CTAs
+// polling one tile's flag do not queue behind the polls of other tiles.
+constexpr int kFlagStride = 32;
+__host__ __device__ constexpr int flag_index(int mb, int rb, int nrb)
+{
+    return (mb * nrb + rb) * kFlagStride;
+}
+
 // Error word written by kernels whose bounded waits gave up.
 enum : int { kErrNone = 0, kErrTimeout = 1, kErrBadLaunch = 2 };
 
@@ -165,6 +174,7 @@ struct BatchArgs {
     int steps, eval_every;
     const float *pk;       // [steps] p_k = a0 - a(t_k)
     float dt, q, g;        // binary32 constants shared by the batch
+    float nz;              // -0.0f (run-time zero addend of the packed products)
     float scale;           // fl32(L * 2^-24) of the initial distribution
     uint64_t seed;
     int *err;

@@ -220,7 +220,7 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
             while (pending) {
                 bool ready = false;
                 if (lane < nblk && ((pending >> lane) & 1u))
-                    ready = ptx::ld_acquire_gpu(&a.flags[lane * a.nrb + rb]) >= kl;
+                    ready = ptx::ld_acquire_gpu(&a.flags[flag_index(lane, rb, a.nrb)]) >= kl;
                 const uint32_t rmask = __ballot_sync(0xFFFFFFFFu, ready);
                 if (rmask) {
                     if (lane == 0) {
@@ -355,6 +355,7 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
     } else {
         // ---------------------------------------------------------- epilogue
         const size_t plane = (size_t)a.Rp * a.Np;
+        const StepConsts2 k2 = step_consts2(a.c);
         float pk_next = a.nsteps > 0 ? a.pk[a.k_begin] : 0.f;
         bool left = false;
         for (int kl = 0; kl < passes; ++kl) {
@@ -366,6 +367,7 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
             else if (a.eval_every > 0 && k > 0 && k < a.steps_total && k % a.eval_every == 0)
                 e = k / a.eval_every - 1;
             const float pk = final_pass ? 0.f : pk_next;
+            const uint64_t pk2 = f2_pack(pk, pk);
             if (kl + 1 < a.nsteps)
                 pk_next = a.pk[k + 1];
             // sgn(x') of (i, r0 + c0 + j) goes to byte j * Np of this pointer
@@ -412,14 +414,20 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
                     }
                 }
                 if (!final_pass) {
+                    // two replicas per packed binary32 operation
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        float xn, yn;
-                        sb_update(__uint_as_float(f[j]), xs[h * 16 + j], __uint_as_float(yr[j]),
-                                  pk, a.c, xn, yn);
-                        xs[h * 16 + j] = xn;
-                        yr[j] = __float_as_uint(yn);
-                        sdst[(size_t)(h * 16 + j) * a.Np] = live ? fp8_sign(xn) : (uint8_t)0;
+                    for (int j = 0; j < 16; j += 2) {
+                        float xn0, xn1;
+                        uint64_t yn;
+                        sb_update2(f2_pack_bits(f[j], f[j + 1]),
+                                   f2_pack(xs[h * 16 + j], xs[h * 16 + j + 1]),
+                                   f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xn0, xn1, yn);
+                        xs[h * 16 + j] = xn0;
+                        xs[h * 16 + j + 1] = xn1;
+                        yr[j] = (uint32_t)yn;
+                        yr[j + 1] = (uint32_t)(yn >> 32);
+                        sdst[(size_t)(h * 16 + j) * a.Np] = live ? fp8_sign(xn0) : (uint8_t)0;
+                        sdst[(size_t)(h * 16 + j + 1) * a.Np] = live ? fp8_sign(xn1) : (uint8_t)0;
                     }
                     ptx::tmem_st16(tmem + lane_off + kRColY + col0, yr);
                 }
@@ -434,7 +442,7 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
                 // every epilogue thread's S stores precede the barrier; the
                 // gpu-scope release (cumulative) publishes them with the flag
                 ptx::fence_proxy_async_global();
-                ptx::st_release_gpu(&a.flags[mb * a.nrb + rb], kl + 1);
+                ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
             }
             if (e >= 0 && et < kRN) {
                 const float s = sh->red[0][et] + sh->red[1][et] + sh->red[2][et] + sh->red[3][et];

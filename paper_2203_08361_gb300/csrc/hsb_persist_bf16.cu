@@ -161,7 +161,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                     if (kb >= nblk)
                         kb -= nblk;
                     // wait until row block kb has published the operand of this pass
-                    while (ptx::ld_acquire_gpu(&a.flags[kb * a.nrb + rb]) < kl) {
+                    while (ptx::ld_acquire_gpu(&a.flags[flag_index(kb, rb, a.nrb)]) < kl) {
                         if (*(volatile int *)&sh->abort ||
                             ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
                             *(volatile int *)&sh->abort = 1;
@@ -263,10 +263,12 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
         ptx::tmem_st_wait();
 
         bool left = false;
+        const StepConsts2 k2 = step_consts2(a.c);
         float pk_next = passes > 0 ? a.pk[a.k_begin] : 0.f;
         for (int kl = 0; kl < passes; ++kl) {
             const int k = a.k_begin + kl;
             const float pk = pk_next;
+            const uint64_t pk2 = f2_pack(pk, pk);
             if (kl + 1 < passes)
                 pk_next = a.pk[k + 1];
             const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
@@ -283,13 +285,20 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                 ptx::tmem_ld16(tmem + lane_off + kQColX + col0, xr);
                 ptx::tmem_ld16(tmem + lane_off + kQColY + col0, yr);
                 ptx::tmem_ld_wait();
+                // two replicas per packed binary32 operation
+                float xnv[16];
+#pragma unroll
+                for (int j = 0; j < 16; j += 2) {
+                    uint64_t yn;
+                    sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
+                               f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xnv[j], xnv[j + 1], yn);
+                    yr[j] = (uint32_t)yn;
+                    yr[j + 1] = (uint32_t)(yn >> 32);
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    float xn, yn;
-                    sb_update(__uint_as_float(f[j]), __uint_as_float(xr[j]),
-                              __uint_as_float(yr[j]), pk, a.c, xn, yn);
+                    const float xn = xnv[j];
                     xr[j] = __float_as_uint(xn);
-                    yr[j] = __float_as_uint(yn);
                     const int col = col0 + j;
                     if (FORM == 0) {
                         // x' = hi + lo, hi = bf16(x'), lo = bf16(x' - hi)
@@ -318,8 +327,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                 ptx::bulk_commit();
                 ptx::bulk_wait_all();
                 ptx::fence_proxy_async_global();
-                ptx::fence_acq_rel_gpu();
-                ptx::st_release_gpu(&a.flags[mb * a.nrb + rb], kl + 1);
+                ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
             }
         }
         if (!left) {
