@@ -8,31 +8,39 @@
 // Each CTA owns one tile of 128 spins x 128 replicas for the whole run.  The
 // tile's positions x and momenta y stay in tensor memory next to the FP32
 // accumulator (columns 0-127 accumulator, 128-255 x, 256-383 y; lane = spin),
-// so a step moves only J and the FP8 spin operand S = sgn(x) through L2:
-//   warp 0      producer: polls the per-tile "published" flags of the step's
-//               operand (one flag per 128-spin chunk, all lanes at once),
-//               then TMA-loads J and S two K chunks at a time (3-D boxes of
-//               128 x 128 x 2 bytes: one 32 KB copy each, which moves data
-//               into the SM faster than two 16 KB copies) into a ring of
-//               shared-memory stages, in the order the chunk pairs become
-//               ready (the FP8 products are exact integers, so the summation
-//               order does not change the force);
-//   warp 1      allocates 512 tensor-memory columns, issues tcgen05.mma
-//               (kind::f8f6f4, M = N = 128, K = 32) from one lane;
-//   warps 2-17  epilogue, four warps per 32-lane quadrant (32 replicas each,
-//               moved through tensor memory 16 columns at a time):
-//               accumulator, x and y from tensor memory, the pinned spin
-//               update, x and y back to tensor memory, sgn(x') as FP8 into a shared-memory
-//               tile that one TMA store writes to the other operand buffer,
-//               then a gpu-scope release of the tile's flag.  On evaluation steps also the per-replica partial sums
-//               of s_i f_i and a snapshot of s = sgn(x(t_k)).
+// so a step moves only J and the FP8 spin operand S = sgn(x) through L2.  One step of a tile is a dependency chain (the force needs the
+// sign tiles of every row block), so the roles are arranged to shorten it:
+//   warp 0      poller: reads the per-tile "published" flags of the step's
+//               operand (one flag per 128-spin chunk, all lanes at once) and
+//               appends the K-chunk pairs, in the order they become ready, to
+//               a ring in shared memory (the FP8 products are exact integers,
+//               so the summation order does not change the force);
+//   warps 1-2   TMA issuers: load g of the ring is issued by warp 1 + g % 2,
+//               as two 32 KB 3-D boxes (J and S, 128 x 128 x 2 bytes) into
+//               stage g % 3.  Bulk copies from one thread complete one after
+//               another, so two issuing threads double the ingress of an SM;
+//   warp 3      MMA: issues tcgen05.mma (kind::f8f6f4, M = N = 128, K = 32)
+//               from an elected lane of the converged warp (warp-uniform
+//               operands issue faster than from one divergent thread).  With
+//               kMmaWarps = 2, pair t goes to warp 3 + t % 2 and its own
+//               accumulator (split K); the partial forces are exact integers,
+//               so their binary32 sum is the exact force;
+//   warps 4-19  epilogue, four warps per 32-lane quadrant (32 replicas each,
+//               moved through tensor memory 16 columns at a time): the
+//               accumulator(s), x and y from tensor memory, the pinned spin
+//               update, x and y back to tensor memory, sgn(x') as FP8 into a
+//               padded shared-memory tile that each warp copies to the other
+//               operand buffer with 16-byte stores; then one thread releases
+//               the tile's flag at gpu scope.  On evaluation steps also the
+//               per-replica partial sums of s_i f_i and a snapshot of
+//               s = sgn(x(t_k)).
 // A final pass after the last update evaluates E(t_Ns).  The best evaluation
 // per replica is chosen afterwards by select_best_kernel.
 //
 // All CTAs must be co-resident (cooperative launch).  Every wait is bounded:
-// mbarrier and flag waits give up after a wall-clock budget, raise the CTA's
-// abort flag and the error word; epilogue warps decide to leave through a
-// barrier reduction, so they never wait at a named barrier for a warp that
+// mbarrier, ring and flag waits give up after a wall-clock budget, raise the
+// CTA's abort flag and the error word; epilogue warps decide to leave through
+// a barrier reduction, so they never wait at a named barrier for a warp that
 // has left.  Tensor memory is freed on every exit path.
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -54,29 +62,39 @@ constexpr int kPChunks = 2;  // K chunks of 128 per stage
 constexpr int kPStages = 3;
 constexpr int kPStageA = kPChunks * kPM * kPK;
 constexpr int kPStageB = kPChunks * kPN * kPK;
-constexpr int kPTileS = kPN * kPM;  // FP8 spin tile [replica][spin] for the store
+constexpr int kPTileRow = kPM + 16;          // padded row of the sign tile (bytes)
+constexpr int kPTileS = kPN * kPTileRow;     // FP8 sign tile [replica][spin]
+constexpr int kIssuers = 2;
+constexpr int kMmaWarps = 1;  // 2 splits K over two accumulators
+constexpr int kFirstMma = 1 + kIssuers;
+constexpr int kFirstEpi = kFirstMma + kMmaWarps;
 constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = 32 * kEpiWarps;
-constexpr int kPThreads = 64 + kEpiThreads;
+constexpr int kPThreads = 32 * kFirstEpi + kEpiThreads;
+constexpr int kOrder = 32;                   // ring of pair ids in load order
 constexpr uint32_t kPTmemCols = 512;
-constexpr uint32_t kColAcc = 0;
-constexpr uint32_t kColX = 128;
-constexpr uint32_t kColY = 256;
+constexpr uint32_t kColAcc0 = 0;
+constexpr uint32_t kColAcc1 = 128;                 // used when kMmaWarps == 2
+constexpr uint32_t kColX = 128 * kMmaWarps;
+constexpr uint32_t kColY = kColX + 128;
 constexpr uint32_t kIdesc = ptx::idesc_e4m3_f32(kPM, kPN);
 
 struct __align__(8) PShared {
     uint64_t full[kPStages];
     uint64_t empty[kPStages];
-    uint64_t accfull;
-    uint64_t tmem_empty;
+    uint64_t accfull;     // one arrival per MMA warp
+    uint64_t tmem_empty;  // the epilogue has read both accumulators
     uint32_t tmem_base;
     int abort;
-    float red[4][kPN];
+    int avail;            // ring entries written so far (all passes)
+    int order[kOrder];    // pair of load g at order[g % kOrder]
+    float red[2][4][kPN]; // per-quadrant energy partials, by pass parity
 };
 
 constexpr size_t kPSmem =
     1024 + (size_t)kPStages * (kPStageA + kPStageB) + kPTileS + sizeof(PShared);
 static_assert(kPSmem <= 232448, "shared memory per CTA is limited to 227 KB");
+static_assert(kPThreads <= 1024, "too many threads per CTA");
 
 // Barrier among the epilogue warps that also ORs a predicate over them, so
 // that a decision to leave the step loop is the same in every epilogue warp.
@@ -96,14 +114,45 @@ __device__ __forceinline__ bool epi_bar_or(bool pred)
 
 __device__ __forceinline__ void epi_bar() { ptx::named_bar(1, kEpiThreads); }
 
+// Bounded wait by every lane of a warp; false in all lanes if any gave up.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *abort, int *err)
+{
+    const bool ok = ptx::mbar_wait(bar, parity, abort, err);
+    return __all_sync(0xFFFFFFFFu, ok);
+}
+
+// tcgen05.mma (both operands in shared memory) issued by one elected lane of
+// a converged warp; the operand values are warp-uniform.
+__device__ __forceinline__ void mma_fp8_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %3, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %4, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(kIdesc)
+        : "memory");
+}
+
+// tcgen05.commit from one elected lane: arrives on `bar` when the MMAs this
+// lane issued have completed.
+__device__ __forceinline__ void commit_elect(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            ptx::smem_u32(bar))
+        : "memory");
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kPThreads, 1)
 tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                          const __grid_constant__ CUtensorMap tmapB0,
-                         const __grid_constant__ CUtensorMap tmapB1,
-                         const __grid_constant__ CUtensorMap tmapSt0,
-                         const __grid_constant__ CUtensorMap tmapSt1, const PersistArgs a)
+                         const __grid_constant__ CUtensorMap tmapB1, const PersistArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -120,6 +169,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
     const int m0 = mb * kPM;
     const int r0 = rb * kPN;
     const int nblk = a.nblk;
+    const int npairs = (nblk + 1) >> 1;
     const int passes = a.nsteps + a.final_pass;
 
     if (threadIdx.x == 0) {
@@ -127,19 +177,18 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             ptx::mbar_init(&sh->full[s], 1);
             ptx::mbar_init(&sh->empty[s], 1);
         }
-        ptx::mbar_init(&sh->accfull, 1);
+        ptx::mbar_init(&sh->accfull, kMmaWarps);
         ptx::mbar_init(&sh->tmem_empty, 1);
         sh->abort = 0;
+        sh->avail = 0;
         ptx::mbar_init_fence();
     }
-    if (warp == 0 && lane == 0) {
+    if (warp == 1 && lane == 0) {
         ptx::prefetch_tmap(&tmapA);
         ptx::prefetch_tmap(&tmapB0);
         ptx::prefetch_tmap(&tmapB1);
-        ptx::prefetch_tmap(&tmapSt0);
-        ptx::prefetch_tmap(&tmapSt1);
     }
-    if (warp == 1)
+    if (warp == kFirstMma)
         ptx::tmem_alloc(&sh->tmem_base, kPTmemCols);
     ptx::tc_fence_before();
     __syncthreads();
@@ -147,64 +196,47 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
     const uint32_t tmem = sh->tmem_base;
 
     if (warp == 0) {
-        // ---------------------------------------------------------- producer
+        // ------------------------------------------------------------ poller
         // K chunks are fetched in pairs (2p, 2p+1); a chunk past the end reads
-        // as zero, so an odd chunk count adds zero products only.
-        const int npairs = (nblk + 1) >> 1;
-        uint32_t g = 0;
+        // as zero, so an odd chunk count adds zero products only.  A pair is
+        // appended once both of its chunks are published for the pass.
+        int G = 0;
         bool fail = false;
         for (int kl = 0; kl < passes && !fail; ++kl) {
-            const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? &tmapB1 : &tmapB0;
             uint32_t pending = nblk >= 32 ? 0xFFFFFFFFu : ((1u << nblk) - 1u);
-            uint32_t have = 0;  // chunks seen published, not yet loaded
+            uint32_t have = 0;
+            uint32_t left = npairs >= 32 ? 0xFFFFFFFFu : ((1u << npairs) - 1u);
             const unsigned long long t0 = ptx::globaltimer();
             int idle = 0;
-            while (pending) {
+            while (left) {
                 bool ready = false;
                 if (lane < nblk && ((pending >> lane) & 1u))
                     ready = ptx::ld_acquire_gpu(&a.flags[flag_index(lane, rb, a.nrb)]) >= kl;
                 const uint32_t rmask = __ballot_sync(0xFFFFFFFFu, ready);
-                __syncwarp();
                 have |= rmask;
                 pending &= ~rmask;
-                // a pair can be loaded when both of its chunks are published
                 uint32_t pmask = 0;
                 for (int pp = 0; pp < npairs; ++pp) {
                     const uint32_t need = (2 * pp + 1 < nblk) ? (3u << (2 * pp)) : (1u << (2 * pp));
-                    if ((have & need) == need)
+                    if (((left >> pp) & 1u) && (have & need) == need)
                         pmask |= 1u << pp;
                 }
                 if (pmask) {
                     if (lane == 0) {
-                        ptx::fence_proxy_async_global();
+                        // own pair first, then the following ones cyclically
                         const int p0 = mb >> 1;
                         for (int t = 0; t < npairs; ++t) {
                             int pp = p0 + t;
                             if (pp >= npairs)
                                 pp -= npairs;
-                            if (!((pmask >> pp) & 1u))
-                                continue;
-                            const int s = (int)(g % kPStages);
-                            const uint32_t ph = (g / kPStages) & 1u;
-                            if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err)) {
-                                fail = true;
-                                break;
-                            }
-                            ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
-                            ptx::tma_load_3d(sA + (size_t)s * kPStageA, &tmapA, 0, m0, 2 * pp,
-                                             &sh->full[s]);
-                            ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp,
-                                             &sh->full[s]);
-                            ++g;
+                            if ((pmask >> pp) & 1u)
+                                sh->order[(G++) % kOrder] = pp;
                         }
+                        __threadfence_block();
+                        *(volatile int *)&sh->avail = G;
                     }
-                    for (int pp = 0; pp < npairs; ++pp)
-                        if ((pmask >> pp) & 1u)
-                            have &= ~((2 * pp + 1 < nblk) ? (3u << (2 * pp)) : (1u << (2 * pp)));
-                    fail = __shfl_sync(0xFFFFFFFFu, fail, 0);
-                    g = __shfl_sync(0xFFFFFFFFu, g, 0);
-                    if (fail)
-                        break;
+                    G = __shfl_sync(0xFFFFFFFFu, G, 0);
+                    left &= ~pmask;
                 } else {
                     int give_up = 0;
                     if (lane == 0) {
@@ -225,58 +257,101 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 }
             }
         }
-    } else if (warp == 1) {
-        // --------------------------------------------------------------- MMA
+    } else if (warp <= kIssuers) {
+        // ------------------------------------------------------- TMA issuers
         if (lane == 0) {
-            // descriptors of stage 0; a stage or K step further is a plain
-            // add on the 14-bit start-address field (addresses < 256 KB)
-            const uint64_t adesc0 = ptx::sw128_desc(ptx::smem_u32(sA));
-            const uint64_t bdesc0 = ptx::sw128_desc(ptx::smem_u32(sB));
-            uint32_t g = 0;
-            for (int kl = 0; kl < passes; ++kl) {
-                if (kl > 0) {
-                    if (!ptx::mbar_wait(&sh->tmem_empty, (uint32_t)(kl - 1) & 1u, &sh->abort,
-                                        a.err))
-                        break;
-                    ptx::tc_fence_after();
-                }
-                bool ok = true;
-                const int npairs = (nblk + 1) >> 1;
-                for (int t = 0; t < npairs; ++t) {
-                    const int s = (int)(g % kPStages);
-                    const uint32_t ph = (g / kPStages) & 1u;
-                    if (!ptx::mbar_wait(&sh->full[s], ph, &sh->abort, a.err)) {
-                        ok = false;
-                        break;
+            const int iw = warp - 1;
+            const int total = passes * npairs;
+            for (int g = iw; g < total; g += kIssuers) {
+                const int kl = g / npairs;
+                if (*(volatile int *)&sh->avail <= g) {
+                    const unsigned long long t0 = ptx::globaltimer();
+                    int spins = 0;
+                    bool fail = false;
+                    while (*(volatile int *)&sh->avail <= g) {
+                        if (*(volatile int *)&sh->abort) {
+                            fail = true;
+                            break;
+                        }
+                        if ((++spins & 63) == 0 &&
+                            ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
+                            *(volatile int *)&sh->abort = 1;
+                            atomicExch(a.err, kErrTimeout);
+                            fail = true;
+                            break;
+                        }
+                        __nanosleep(20);
                     }
-                    ptx::tc_fence_after();
-                    const uint64_t ad = adesc0 + (uint64_t)((s * kPStageA) >> 4);
-                    const uint64_t bd = bdesc0 + (uint64_t)((s * kPStageB) >> 4);
-#pragma unroll
-                    for (int c = 0; c < kPChunks; ++c) {
-#pragma unroll
-                        for (int kk = 0; kk < kPK / 32; ++kk)
-                            ptx::mma_fp8(tmem + kColAcc,
-                                         ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4),
-                                         bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4), kIdesc,
-                                         (t | c | kk) != 0 ? 1u : 0u);
-                    }
-                    ptx::mma_commit(&sh->empty[s]);
-                    ++g;
+                    if (fail)
+                        break;
                 }
-                if (!ok)
+                __threadfence_block();
+                const int pp = *(volatile int *)&sh->order[g % kOrder];
+                const int s = g % kPStages;
+                const uint32_t ph = (uint32_t)(g / kPStages) & 1u;
+                if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err))
                     break;
-                ptx::mma_commit(&sh->accfull);
+                const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? &tmapB1 : &tmapB0;
+                ptx::fence_proxy_async_global();
+                ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
+                ptx::tma_load_3d(sA + (size_t)s * kPStageA, &tmapA, 0, m0, 2 * pp, &sh->full[s]);
+                ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp, &sh->full[s]);
             }
+        }
+    } else if (warp < kFirstEpi) {
+        // --------------------------------------------------------------- MMA
+        // descriptors of stage 0; a stage or K step further is a plain add on
+        // the 14-bit start-address field (addresses < 256 KB)
+        const int mw = warp - kFirstMma;
+        const uint32_t dcol = tmem + (mw ? kColAcc1 : kColAcc0);
+        const uint64_t adesc0 = ptx::sw128_desc(ptx::smem_u32(sA));
+        const uint64_t bdesc0 = ptx::sw128_desc(ptx::smem_u32(sB));
+        for (int kl = 0; kl < passes; ++kl) {
+            if (kl > 0) {
+                if (!warp_wait(&sh->tmem_empty, (uint32_t)(kl - 1) & 1u, &sh->abort, a.err))
+                    break;
+                ptx::tc_fence_after();
+            }
+            bool ok = true;
+            int mine = 0;
+            for (int t = mw; t < npairs; t += kMmaWarps) {
+                const int g = kl * npairs + t;
+                const int s = g % kPStages;
+                const uint32_t ph = (uint32_t)(g / kPStages) & 1u;
+                if (!warp_wait(&sh->full[s], ph, &sh->abort, a.err)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint64_t ad = adesc0 + (uint64_t)((s * kPStageA) >> 4);
+                const uint64_t bd = bdesc0 + (uint64_t)((s * kPStageB) >> 4);
+#pragma unroll
+                for (int c = 0; c < kPChunks; ++c) {
+#pragma unroll
+                    for (int kk = 0; kk < kPK / 32; ++kk)
+                        mma_fp8_elect(dcol, ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4),
+                                      bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4),
+                                      (mine | c | kk) != 0 ? 1u : 0u);
+                }
+                commit_elect(&sh->empty[s]);
+                ++mine;
+            }
+            if (!ok)
+                break;
+            if (mine > 0)
+                commit_elect(&sh->accfull);
+            else if (lane == 0)
+                ptx::mbar_arrive(&sh->accfull);  // no pair of this pass for this warp
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const int ew = warp - 2;            // 0..15
+        const int ew = warp - kFirstEpi;    // 0..15
         const int q = warp & 3;             // tensor-memory lane quadrant
         const int c0 = (ew >> 2) * 32;      // first of this warp's 32 replica columns
-        const int et = threadIdx.x - 64;    // 0..511
+        const int et = threadIdx.x - 32 * kFirstEpi;  // 0..511
         const int i = m0 + q * 32 + lane;   // spin of this thread
         const bool live = i < a.N;
+        const bool two_acc = kMmaWarps > 1 && npairs > 1;  // a second accumulator has pairs
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const size_t plane = (size_t)a.Rp * a.Np;
 
@@ -296,7 +371,8 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         ptx::tmem_st_wait();
 
         bool left = false;
-        uint8_t *srow = sS + q * 32 + lane;  // this spin's byte in row `col` of the tile
+        // this spin's byte in row `col` of the sign tile
+        uint8_t *srow = sS + q * 32 + lane;
         const StepConsts2 k2 = step_consts2(a.c);
         float pk_next = a.nsteps > 0 ? a.pk[a.k_begin] : 0.f;
         for (int kl = 0; kl < passes; ++kl) {
@@ -311,6 +387,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             const uint64_t pk2 = f2_pack(pk, pk);
             if (kl + 1 < a.nsteps)
                 pk_next = a.pk[k + 1];  // p_k of the next pass, off the critical path
+            float(*red)[kPN] = sh->red[kl & 1];
 
             // x and y of the first 16 columns: the MMA does not write them
             uint32_t xpre[16], ypre[16];
@@ -328,7 +405,22 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             for (int h = 0; h < 2; ++h) {
                 const uint32_t col0 = (uint32_t)(c0 + h * 16);
                 uint32_t f[16], xr[16], yr[16];
-                ptx::tmem_ld16(tmem + lane_off + kColAcc + col0, f);
+                ptx::tmem_ld16(tmem + lane_off + kColAcc0 + col0, f);
+                if (two_acc) {
+                    // partial forces over disjoint K ranges: exact integers,
+                    // added 8 columns at a time
+#pragma unroll
+                    for (int p8 = 0; p8 < 2; ++p8) {
+                        uint32_t f1[8];
+                        ptx::tmem_ld8(tmem + lane_off + kColAcc1 + col0 + p8 * 8, f1);
+                        ptx::tmem_ld_wait(f1);
+                        ptx::tmem_ld_wait(f);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            f[p8 * 8 + j] = __float_as_uint(
+                                __fadd_rn(__uint_as_float(f[p8 * 8 + j]), __uint_as_float(f1[j])));
+                    }
+                }
                 if (h == 0) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -353,7 +445,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                         for (int off = 16; off > 0; off >>= 1)
                             term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
                         if (lane == 0)
-                            sh->red[q][col] = term;
+                            red[q][col] = term;
                         a.Snap[(size_t)e * plane + (size_t)(r0 + col) * a.Np + i] =
                             live ? fp8_sign(x0) : (uint8_t)0;
                     }
@@ -370,8 +462,8 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                         xr[j + 1] = __float_as_uint(xn1);
                         yr[j] = (uint32_t)yn;
                         yr[j + 1] = (uint32_t)(yn >> 32);
-                        srow[(col0 + j) * kPM] = live ? fp8_sign(xn0) : (uint8_t)0;
-                        srow[(col0 + j + 1) * kPM] = live ? fp8_sign(xn1) : (uint8_t)0;
+                        srow[(col0 + j) * kPTileRow] = live ? fp8_sign(xn0) : (uint8_t)0;
+                        srow[(col0 + j + 1) * kPTileRow] = live ? fp8_sign(xn1) : (uint8_t)0;
                     }
                     ptx::tmem_st16(tmem + lane_off + kColX + col0, xr);
                     ptx::tmem_st16(tmem + lane_off + kColY + col0, yr);
@@ -379,23 +471,32 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             }
             ptx::tc_fence_before();
             if (!final_pass) {
+                // this warp's 32 replicas x 32 spins of S(t_{k+1}): 16-byte
+                // stores, two per lane, into the other operand buffer
+                __syncwarp();
+                uint8_t *dst = (((a.par0 + kl + 1) & 1) ? a.S8b : a.S8a) +
+                               (size_t)(r0 + c0) * a.Np + m0 + q * 32;
+#pragma unroll
+                for (int v = lane; v < 64; v += 32) {
+                    const int row = v >> 1, off = (v & 1) * 16;
+                    const uint4 val =
+                        *reinterpret_cast<const uint4 *>(sS + (c0 + row) * kPTileRow + q * 32 + off);
+                    *reinterpret_cast<uint4 *>(dst + (size_t)row * a.Np + off) = val;
+                }
                 ptx::tmem_st_wait();
-                ptx::fence_proxy_async_smem();  // tile writes before the TMA store reads them
             }
             epi_bar();
-            if (!final_pass && et == 0) {
-                // S(t_{k+1}) of this tile: one tile store, then publish the flag
-                ptx::tma_store_2d(((a.par0 + kl + 1) & 1) ? &tmapSt1 : &tmapSt0, m0, r0, sS);
-                ptx::mbar_arrive(&sh->tmem_empty);  // accumulator read: the next MMA may start
-                ptx::bulk_commit();
-                ptx::bulk_wait_all();
-                ptx::fence_proxy_async_global();
-                ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
-            } else if (et == 0) {
-                ptx::mbar_arrive(&sh->tmem_empty);
+            if (et == 0) {
+                ptx::mbar_arrive(&sh->tmem_empty);  // both accumulators read
+                if (!final_pass) {
+                    // every epilogue thread's S stores precede the barrier; the
+                    // gpu-scope release (cumulative) publishes them with the flag
+                    ptx::fence_proxy_async_global();
+                    ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
+                }
             }
             if (e >= 0 && et < kPN) {
-                const float s = sh->red[0][et] + sh->red[1][et] + sh->red[2][et] + sh->red[3][et];
+                const float s = red[0][et] + red[1][et] + red[2][et] + red[3][et];
                 a.Epart[((size_t)e * nblk + mb) * a.Rp + r0 + et] = s;
             }
         }
@@ -421,7 +522,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (warp == 1)
+    if (warp == kFirstMma)
         ptx::tmem_dealloc(tmem, kPTmemCols);
 }
 
@@ -497,7 +598,7 @@ cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const 
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, tc_fp8_persistent_kernel, plan->mapA3, plan->mapB3[0],
-                              plan->mapB3[1], plan->mapSt[0], plan->mapSt[1], a);
+                              plan->mapB3[1], a);
 }
 
 cudaError_t launch_select_best(cudaStream_t st, const float *Epart, const uint8_t *Snap,
