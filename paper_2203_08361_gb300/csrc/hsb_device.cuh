@@ -130,6 +130,20 @@ __device__ __forceinline__ StepConsts2 step_consts2(const StepConsts &c)
     return k;
 }
 
+// x~ of a pair (Eqs. eq_SyEuY, eq_SyEuX), by the same operations as
+// sb_update2.  The walls keep the sign of x~, so sgn(x') = sgn(x~).
+__device__ __forceinline__ uint64_t sb_position2(uint64_t f, uint64_t x0, uint64_t y0, uint64_t pk2,
+                                                 const StepConsts2 &k)
+{
+    const uint64_t u = f2_fma(k.c0, f, k.z);
+    const uint64_t v = f2_fma(pk2, x0, k.z);
+    const uint64_t w = f2_sub(u, v);
+    const uint64_t wd = f2_fma(w, k.dt, k.z);
+    const uint64_t yt = f2_add(y0, wd);
+    const uint64_t qy = f2_fma(k.q, yt, k.z);
+    return f2_add(x0, qy);
+}
+
 // sb_update on the pairs (f, x0, y0) with p_k broadcast in pk2; the walls
 // are applied per element.  Returns x' per element and y' as a pair.
 __device__ __forceinline__ void sb_update2(uint64_t f, uint64_t x0, uint64_t y0, uint64_t pk2,

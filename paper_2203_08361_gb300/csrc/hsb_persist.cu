@@ -15,10 +15,11 @@
 //               appends the K-chunk pairs, in the order they become ready, to
 //               a ring in shared memory (the FP8 products are exact integers,
 //               so the summation order does not change the force);
-//   warps 1-2   TMA issuers: load g of the ring is issued by warp 1 + g % 2,
-//               as two 32 KB 3-D boxes (J and S, 128 x 128 x 2 bytes) into
-//               stage g % 3.  Bulk copies from one thread complete one after
-//               another, so two issuing threads double the ingress of an SM;
+//   warps 1-2   TMA issuers: load g of the ring fills stage g % 3 with two
+//               32 KB 3-D boxes (J and S, 128 x 128 x 2 bytes).  Bulk copies
+//               from one thread complete one after another: the boxes of the
+//               first two loads of a pass come from both warps in parallel,
+//               later loads alternate whole between the warps;
 //   warp 3      MMA: issues tcgen05.mma (kind::f8f6f4, M = N = 128, K = 32)
 //               from an elected lane of the converged warp (warp-uniform
 //               operands issue faster than from one divergent thread).  With
@@ -26,14 +27,16 @@
 //               accumulator (split K); the partial forces are exact integers,
 //               so their binary32 sum is the exact force;
 //   warps 4-19  epilogue, four warps per 32-lane quadrant (32 replicas each,
-//               moved through tensor memory 16 columns at a time): the
-//               accumulator(s), x and y from tensor memory, the pinned spin
-//               update, x and y back to tensor memory, sgn(x') as FP8 into a
-//               padded shared-memory tile that each warp copies to the other
-//               operand buffer with 16-byte stores; then one thread releases
-//               the tile's flag at gpu scope.  On evaluation steps also the
+//               moved through tensor memory 16 columns at a time), in two
+//               phases.  Phase 1 computes only x~ (sgn(x') = sgn(x~), the
+//               walls keep the sign), writes sgn as FP8 into a padded
+//               shared-memory tile that each warp copies to the other operand
+//               buffer with 16-byte stores, and one thread releases the
+//               tile's flag at gpu scope.  Phase 2, while the flags travel,
+//               repeats the pinned update in full and stores x' and y' in
+//               tensor memory; on evaluation steps it also forms the
 //               per-replica partial sums of s_i f_i and a snapshot of
-//               s = sgn(x(t_k)).
+//               s = sgn(x(t_k)).  Each warp then releases the accumulator.
 // A final pass after the last update evaluates E(t_Ns).  The best evaluation
 // per replica is chosen afterwards by select_best_kernel.
 //
@@ -83,12 +86,12 @@ struct __align__(8) PShared {
     uint64_t full[kPStages];
     uint64_t empty[kPStages];
     uint64_t accfull;     // one arrival per MMA warp
-    uint64_t tmem_empty;  // the epilogue has read both accumulators
+    uint64_t tmem_empty;  // every epilogue warp has read the accumulator(s)
     uint32_t tmem_base;
     int abort;
     int avail;            // ring entries written so far (all passes)
     int order[kOrder];    // pair of load g at order[g % kOrder]
-    float red[2][4][kPN]; // per-quadrant energy partials, by pass parity
+    float red[4][kPN];    // per-quadrant energy partials
 };
 
 constexpr size_t kPSmem =
@@ -147,6 +150,28 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
         : "memory");
 }
 
+// Force of 16 replica columns from tensor memory: the accumulator, plus the
+// second one when K is split over two MMA warps (partial forces over
+// disjoint K ranges are exact integers, added 8 columns at a time).
+__device__ __forceinline__ void load_force(uint32_t tcol, bool two_acc, uint32_t (&f)[16])
+{
+    ptx::tmem_ld16(tcol + kColAcc0, f);
+    if (two_acc) {
+#pragma unroll
+        for (int p8 = 0; p8 < 2; ++p8) {
+            uint32_t f1[8];
+            ptx::tmem_ld8(tcol + kColAcc1 + p8 * 8, f1);
+            ptx::tmem_ld_wait(f1);
+            ptx::tmem_ld_wait(f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                f[p8 * 8 + j] = __float_as_uint(
+                    __fadd_rn(__uint_as_float(f[p8 * 8 + j]), __uint_as_float(f1[j])));
+        }
+    }
+    ptx::tmem_ld_wait(f);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kPThreads, 1)
@@ -178,7 +203,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             ptx::mbar_init(&sh->empty[s], 1);
         }
         ptx::mbar_init(&sh->accfull, kMmaWarps);
-        ptx::mbar_init(&sh->tmem_empty, 1);
+        ptx::mbar_init(&sh->tmem_empty, kEpiWarps);
         sh->abort = 0;
         sh->avail = 0;
         ptx::mbar_init_fence();
@@ -259,11 +284,19 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         }
     } else if (warp <= kIssuers) {
         // ------------------------------------------------------- TMA issuers
+        // Copies from one thread complete one after another.  The first two
+        // loads of a pass are on the critical path, so their J boxes come
+        // from warp 1 and their S boxes from warp 2, in parallel; the later
+        // loads alternate whole between the warps (J and S from one thread).
         if (lane == 0) {
             const int iw = warp - 1;
             const int total = passes * npairs;
-            for (int g = iw; g < total; g += kIssuers) {
+            for (int g = 0; g < total; ++g) {
                 const int kl = g / npairs;
+                const int t = g - kl * npairs;
+                const bool split = t < 2;
+                if (!split && (t & 1) != iw)
+                    continue;
                 if (*(volatile int *)&sh->avail <= g) {
                     const unsigned long long t0 = ptx::globaltimer();
                     int spins = 0;
@@ -291,11 +324,18 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 const uint32_t ph = (uint32_t)(g / kPStages) & 1u;
                 if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err))
                     break;
-                const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? &tmapB1 : &tmapB0;
                 ptx::fence_proxy_async_global();
-                ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
-                ptx::tma_load_3d(sA + (size_t)s * kPStageA, &tmapA, 0, m0, 2 * pp, &sh->full[s]);
-                ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp, &sh->full[s]);
+                if (!split || iw == 0) {
+                    // the stage's one arrival; both boxes count against it
+                    ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
+                    ptx::tma_load_3d(sA + (size_t)s * kPStageA, &tmapA, 0, m0, 2 * pp,
+                                     &sh->full[s]);
+                }
+                if (!split || iw == 1) {
+                    const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? &tmapB1 : &tmapB0;
+                    ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp,
+                                     &sh->full[s]);
+                }
             }
         }
     } else if (warp < kFirstEpi) {
@@ -387,7 +427,6 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             const uint64_t pk2 = f2_pack(pk, pk);
             if (kl + 1 < a.nsteps)
                 pk_next = a.pk[k + 1];  // p_k of the next pass, off the critical path
-            float(*red)[kPN] = sh->red[kl & 1];
 
             // x and y of the first 16 columns: the MMA does not write them
             uint32_t xpre[16], ypre[16];
@@ -401,39 +440,69 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 break;
             }
             ptx::tc_fence_after();
+
+            if (!final_pass) {
+                // ---- phase 1: only sgn(x') = sgn(x~), published before the
+                // rest of the update (the next step of every tile waits for it)
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t col0 = (uint32_t)(c0 + h * 16);
+                    uint32_t f[16], xr[16], yr[16];
+                    load_force(tmem + lane_off + col0, two_acc, f);
+                    if (h == 0) {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            xr[j] = xpre[j];
+                            yr[j] = ypre[j];
+                        }
+                    } else {
+                        ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
+                        ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
+                        ptx::tmem_ld_wait(xr);
+                        ptx::tmem_ld_wait(yr);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        const uint64_t xt =
+                            sb_position2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
+                                         f2_pack_bits(yr[j], yr[j + 1]), pk2, k2);
+                        srow[(col0 + j) * kPTileRow] = live ? fp8_sign(f2_lo(xt)) : (uint8_t)0;
+                        srow[(col0 + j + 1) * kPTileRow] = live ? fp8_sign(f2_hi(xt)) : (uint8_t)0;
+                    }
+                }
+                // this warp's 32 replicas x 32 spins of S(t_{k+1}): 16-byte
+                // stores, two per lane, into the other operand buffer
+                __syncwarp();
+                uint8_t *dst = (((a.par0 + kl + 1) & 1) ? a.S8b : a.S8a) +
+                               (size_t)(r0 + c0) * a.Np + m0 + q * 32;
+#pragma unroll
+                for (int v = lane; v < 64; v += 32) {
+                    const int row = v >> 1, off = (v & 1) * 16;
+                    const uint4 val =
+                        *reinterpret_cast<const uint4 *>(sS + (c0 + row) * kPTileRow + q * 32 + off);
+                    *reinterpret_cast<uint4 *>(dst + (size_t)row * a.Np + off) = val;
+                }
+                epi_bar();
+                if (et == 0) {
+                    // every epilogue thread's S stores precede the barrier; the
+                    // gpu-scope release (cumulative) publishes them with the flag
+                    ptx::fence_proxy_async_global();
+                    ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
+                }
+            }
+
+            // ---- phase 2: energy of s(t_k) on evaluation passes, and the full
+            // update of x and y in tensor memory (off the critical path: the
+            // next force needs the flags of every tile first)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t col0 = (uint32_t)(c0 + h * 16);
                 uint32_t f[16], xr[16], yr[16];
-                ptx::tmem_ld16(tmem + lane_off + kColAcc0 + col0, f);
-                if (two_acc) {
-                    // partial forces over disjoint K ranges: exact integers,
-                    // added 8 columns at a time
-#pragma unroll
-                    for (int p8 = 0; p8 < 2; ++p8) {
-                        uint32_t f1[8];
-                        ptx::tmem_ld8(tmem + lane_off + kColAcc1 + col0 + p8 * 8, f1);
-                        ptx::tmem_ld_wait(f1);
-                        ptx::tmem_ld_wait(f);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            f[p8 * 8 + j] = __float_as_uint(
-                                __fadd_rn(__uint_as_float(f[p8 * 8 + j]), __uint_as_float(f1[j])));
-                    }
-                }
-                if (h == 0) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        xr[j] = xpre[j];
-                        yr[j] = ypre[j];
-                    }
-                } else {
-                    ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
-                    ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
-                    ptx::tmem_ld_wait(xr);
-                    ptx::tmem_ld_wait(yr);
-                }
-                ptx::tmem_ld_wait(f);
+                ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
+                ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
+                load_force(tmem + lane_off + col0, two_acc, f);
+                ptx::tmem_ld_wait(xr);
+                ptx::tmem_ld_wait(yr);
                 if (e >= 0) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -445,7 +514,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                         for (int off = 16; off > 0; off >>= 1)
                             term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
                         if (lane == 0)
-                            red[q][col] = term;
+                            sh->red[q][col] = term;
                         a.Snap[(size_t)e * plane + (size_t)(r0 + col) * a.Np + i] =
                             live ? fp8_sign(x0) : (uint8_t)0;
                     }
@@ -462,42 +531,23 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                         xr[j + 1] = __float_as_uint(xn1);
                         yr[j] = (uint32_t)yn;
                         yr[j + 1] = (uint32_t)(yn >> 32);
-                        srow[(col0 + j) * kPTileRow] = live ? fp8_sign(xn0) : (uint8_t)0;
-                        srow[(col0 + j + 1) * kPTileRow] = live ? fp8_sign(xn1) : (uint8_t)0;
                     }
                     ptx::tmem_st16(tmem + lane_off + kColX + col0, xr);
                     ptx::tmem_st16(tmem + lane_off + kColY + col0, yr);
                 }
             }
             ptx::tc_fence_before();
-            if (!final_pass) {
-                // this warp's 32 replicas x 32 spins of S(t_{k+1}): 16-byte
-                // stores, two per lane, into the other operand buffer
-                __syncwarp();
-                uint8_t *dst = (((a.par0 + kl + 1) & 1) ? a.S8b : a.S8a) +
-                               (size_t)(r0 + c0) * a.Np + m0 + q * 32;
-#pragma unroll
-                for (int v = lane; v < 64; v += 32) {
-                    const int row = v >> 1, off = (v & 1) * 16;
-                    const uint4 val =
-                        *reinterpret_cast<const uint4 *>(sS + (c0 + row) * kPTileRow + q * 32 + off);
-                    *reinterpret_cast<uint4 *>(dst + (size_t)row * a.Np + off) = val;
-                }
+            if (!final_pass)
                 ptx::tmem_st_wait();
-            }
-            epi_bar();
-            if (et == 0) {
-                ptx::mbar_arrive(&sh->tmem_empty);  // both accumulators read
-                if (!final_pass) {
-                    // every epilogue thread's S stores precede the barrier; the
-                    // gpu-scope release (cumulative) publishes them with the flag
-                    ptx::fence_proxy_async_global();
-                    ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
+            __syncwarp();
+            if (lane == 0)
+                ptx::mbar_arrive(&sh->tmem_empty);  // this warp has read the accumulator
+            if (e >= 0) {
+                epi_bar();
+                if (et < kPN) {
+                    const float s = sh->red[0][et] + sh->red[1][et] + sh->red[2][et] + sh->red[3][et];
+                    a.Epart[((size_t)e * nblk + mb) * a.Rp + r0 + et] = s;
                 }
-            }
-            if (e >= 0 && et < kPN) {
-                const float s = red[0][et] + red[1][et] + red[2][et] + red[3][et];
-                a.Epart[((size_t)e * nblk + mb) * a.Rp + r0 + et] = s;
             }
         }
 
