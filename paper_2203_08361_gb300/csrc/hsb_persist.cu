@@ -13,8 +13,9 @@
 //   warp 0      poller: reads the per-tile "published" flags of the step's
 //               operand (one flag per 128-spin chunk, all lanes at once) and
 //               appends the K-chunk pairs, in the order they become ready, to
-//               a ring in shared memory (the FP8 products are exact integers,
-//               so the summation order does not change the force);
+//               a ring in shared memory, arriving on the slot's mbarrier (the
+//               FP8 products are exact integers, so the summation order does
+//               not change the force);
 //   warps 1-2   TMA issuers: load g of the ring fills stage g % 3 with two
 //               32 KB 3-D boxes (J and S, 128 x 128 x 2 bytes).  Bulk copies
 //               from one thread complete one after another: the boxes of the
@@ -89,7 +90,7 @@ struct __align__(8) PShared {
     uint64_t tmem_empty;  // every epilogue warp has read the accumulator(s)
     uint32_t tmem_base;
     int abort;
-    int avail;            // ring entries written so far (all passes)
+    uint64_t ring[kOrder];  // slot g % kOrder named: one arrival per use
     int order[kOrder];    // pair of load g at order[g % kOrder]
     float red[4][kPN];    // per-quadrant energy partials
 };
@@ -204,8 +205,9 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         }
         ptx::mbar_init(&sh->accfull, kMmaWarps);
         ptx::mbar_init(&sh->tmem_empty, kEpiWarps);
+        for (int r = 0; r < kOrder; ++r)
+            ptx::mbar_init(&sh->ring[r], 1);
         sh->abort = 0;
-        sh->avail = 0;
         ptx::mbar_init_fence();
     }
     if (warp == 1 && lane == 0) {
@@ -254,11 +256,14 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                             int pp = p0 + t;
                             if (pp >= npairs)
                                 pp -= npairs;
-                            if ((pmask >> pp) & 1u)
-                                sh->order[(G++) % kOrder] = pp;
+                            if ((pmask >> pp) & 1u) {
+                                // the arrival (release) makes the entry visible
+                                // to the issuers waiting on the slot
+                                sh->order[G % kOrder] = pp;
+                                ptx::mbar_arrive(&sh->ring[G % kOrder]);
+                                ++G;
+                            }
                         }
-                        __threadfence_block();
-                        *(volatile int *)&sh->avail = G;
                     }
                     G = __shfl_sync(0xFFFFFFFFu, G, 0);
                     left &= ~pmask;
@@ -297,28 +302,10 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 const bool split = t < 2;
                 if (!split && (t & 1) != iw)
                     continue;
-                if (*(volatile int *)&sh->avail <= g) {
-                    const unsigned long long t0 = ptx::globaltimer();
-                    int spins = 0;
-                    bool fail = false;
-                    while (*(volatile int *)&sh->avail <= g) {
-                        if (*(volatile int *)&sh->abort) {
-                            fail = true;
-                            break;
-                        }
-                        if ((++spins & 63) == 0 &&
-                            ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
-                            *(volatile int *)&sh->abort = 1;
-                            atomicExch(a.err, kErrTimeout);
-                            fail = true;
-                            break;
-                        }
-                        __nanosleep(20);
-                    }
-                    if (fail)
-                        break;
-                }
-                __threadfence_block();
+                // the poller has named load g (use g / kOrder of the slot)
+                if (!ptx::mbar_wait(&sh->ring[g % kOrder], (uint32_t)(g / kOrder) & 1u, &sh->abort,
+                                    a.err))
+                    break;
                 const int pp = *(volatile int *)&sh->order[g % kOrder];
                 const int s = g % kPStages;
                 const uint32_t ph = (uint32_t)(g / kPStages) & 1u;
