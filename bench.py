@@ -77,11 +77,15 @@ def oracle_sample(reps: int, sb_steps: int, nthreads: int):
     return w["N"] * reps * sb_steps / dt, dt
 
 
-def cpu_baseline(target_s: float = 12.0):
+def cpu_baseline(target_s: float = 20.0):
     cores = os.cpu_count() or 1
     reps = max(cores, 8)
     rate, t = oracle_sample(reps, 10, cores)  # calibration
-    steps = int(max(20, min(WORKLOAD["sb_steps"], target_s * rate / (WORKLOAD["N"] * reps))))
+    # the whole step count of the workload on as many replicas (a multiple of
+    # the thread count) as fill about target_s seconds
+    steps = WORKLOAD["sb_steps"]
+    want = target_s * rate / (WORKLOAD["N"] * steps)
+    reps = int(min(WORKLOAD["R"], max(cores, round(want / cores) * cores)))
     rate, t = oracle_sample(reps, steps, cores)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} replicas x {steps} of the {WORKLOAD['sb_steps']} steps "
@@ -134,7 +138,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.dev)],
+                 "-lms", "50", "-i", str(self.dev)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
