@@ -91,13 +91,14 @@ struct TcPlan {
     CUtensorMap mapB[2];   // 2-D S8a / S8b, box 128 B x 128 rows
     CUtensorMap mapA3;     // 3-D J8 (128 B, rows, K chunks), box 128 x 128 x 2
     CUtensorMap mapB3[2];  // 3-D S8a / S8b, box 128 x 128 x 2
-    CUtensorMap mapSt[2];  // 2-D S8a / S8b for tile stores, no swizzle, box 128 x 128
+    CUtensorMap mapBw[2];  // 2-D S8a / S8b, box 128 B x 256 rows (per-step kernel)
     int Np, Rp;            // Rp: replica capacity the maps were encoded for
 };
 
 // tcgen05 FP8 step: F = J8 * S8cur^T on the tensor cores (FP32 accumulation
 // in tensor memory), fused update; writes S8next, X and Y in place, and Epart
-// on evaluation steps.  Requires Np % 128 == 0 and Rp % 128 == 0.
+// on evaluation steps.  Requires Np % 128 == 0 and Rp % 128 == 0.  A
+// persistent grid (one CTA per SM) walks 128-spin x 256-replica tiles.
 cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S8a,
                                const uint8_t *S8b, int Np, int Rp);
 void tc_plan_destroy(TcPlan *p);

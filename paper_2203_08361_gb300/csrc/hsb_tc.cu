@@ -1,4 +1,6 @@
-// hsb_tc.cu -- tensor-core (tcgen05) step kernels of libhsb for sm_103a.
+// hsb_tc.cu -- one-step tensor-core (tcgen05) kernel of libhsb for sm_103a,
+// used when the persistent step loop does not fit (large N, many tiles) and
+// for per-step traces.
 //
 // Discrete heated SB with couplings in {-1, 0, +1} (HdSB; Kanao & Goto,
 // arXiv 2203.08361, Eq. (eq_fd) and Methods): the force F = J sgn(X) of all
@@ -7,43 +9,64 @@
 // and every partial sum an integer of magnitude < 2^24, so FP32 accumulation
 // in tensor memory is exact and the force equals the integer J sgn(x).
 //
-// One CTA computes a 128-spin x 128-replica tile of F:
-//   warp 0     TMA producer: J and S tiles (128 x 128 bytes, 128-byte swizzle)
-//              into a ring of shared-memory stages;
-//   warp 1     allocates tensor memory and issues tcgen05.mma (kind::f8f6f4,
-//              M = 128, N = 128, K = 32 per instruction) from one lane;
-//   warps 2-5  epilogue: tcgen05.ld of the accumulator (one spin per lane),
-//              the pinned spin update of the Methods equations, x and y in
-//              place, sgn(x') as the next step's FP8 operand, and on
-//              evaluation steps the per-replica partial sums of s_i f_i.
-// Every mbarrier wait is bounded (a wall-clock budget); a wait that gives up
-// sets the error word, makes the other roles leave their loops, and the CTA
-// frees its tensor memory before it exits.
+// A persistent grid, one CTA per SM, walks tiles of 128 spins x 256
+// replicas, replica blocks fastest, so that the CTAs running at one time share
+// a few row blocks of J in L2 (J streams from HBM about once per step) and
+// every S chunk is reused by all of them.  Per CTA:
+//   warps 0-3  TMA issuers: warps 0 and 1 load the J box (128 rows x 128 B)
+//              of even and odd K chunks, warps 2 and 3 the S box (256 rows x
+//              128 B), into a ring of four 48 KB stages.  Copies from one
+//              thread complete one after another, so four issuing threads
+//              keep the ring full; every stage is always served by the same
+//              two issuers, so their parity waits see each phase in order;
+//   warp 4     MMA: tcgen05.mma kind::f8f6f4, M = 128, N = 256, K = 32,
+//              issued from an elected lane of the converged warp (a 128 x 256
+//              x 32 instruction keeps the tensor core busy even from one warp)
+//              into one of two 256-column accumulators, alternating by tile,
+//              so the epilogue of a tile overlaps the next tile's force;
+//   warps 5-12 epilogue, two warps per 32-lane quadrant (128 replica columns
+//              each): the accumulator, x and y of the tile from global memory,
+//              the pinned spin update, x' and y' in place, sgn(x') as the next
+//              step's FP8 operand; on evaluation steps the per-replica partial
+//              sums of s_i f_i, with a trace the sums of y_i(t_k)^2.
+// Replica columns past Rp (the last tile of an odd number of 128-replica
+// blocks) are computed from whatever the operand rows hold and never stored.
+// Every wait is bounded (a wall-clock budget); a wait that gives up sets the
+// error word and makes the other roles leave their loops; the epilogue warps
+// decide to leave through a barrier reduction, and the CTA frees its tensor
+// memory before it exits.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "hsb_device.cuh"
 #include "hsb_internal.cuh"
+#include "hsb_ptx.cuh"
 
 namespace hsb {
 
 namespace {
 
 constexpr int kBM = 128;            // spins per tile (MMA M, tensor-memory lanes)
-constexpr int kBN = 128;            // replicas per tile (MMA N, accumulator columns)
+constexpr int kBN = 256;            // replicas per tile (MMA N, accumulator columns)
 constexpr int kBK = 128;            // K bytes per stage (one 128-byte swizzle row)
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr int kStageA = kBM * kBK;  // 16 KB
-constexpr int kStageB = kBN * kBK;  // 16 KB
-constexpr int kThreads = 192;
-constexpr int kTmemCols = 128;
-constexpr unsigned long long kWaitBudgetNs = 2000000000ull;  // 2 s
+constexpr int kStageB = kBN * kBK;  // 32 KB
+constexpr int kIssuers = 4;
+constexpr int kMmaWarp = kIssuers;
+constexpr int kFirstEpi = kMmaWarp + 1;
+constexpr int kEpiWarps = 8;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kThreads = 32 * kFirstEpi + kEpiThreads;
+constexpr uint32_t kTmemCols = 2 * kBN;  // two accumulators
+constexpr uint32_t kIdesc = ptx::idesc_e4m3_f32(kBM, kBN);
 
 struct __align__(8) TcShared {
     uint64_t full[kStages];
     uint64_t empty[kStages];
-    uint64_t accfull;
+    uint64_t accfull[2];
+    uint64_t accempty[2];
     uint32_t tmem_base;
     int abort;
     float red[4][kBN];
@@ -54,150 +77,60 @@ constexpr size_t kSmemBytes = 1024 /* alignment slack */ + (size_t)kStages * (kS
                               sizeof(TcShared);
 static_assert(kSmemBytes <= 232448, "shared memory per CTA is limited to 227 KB");
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
+__device__ __forceinline__ bool epi_bar_or(bool pred)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t ok;
+    uint32_t r;
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred), "r"(kEpiThreads)
         : "memory");
-    return ok != 0;
+    return r != 0;
 }
 
-// Bounded wait for the phase with the given parity.  Returns false (and sets
-// the abort flag and the error word) when the budget runs out or another role
-// has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, TcShared *sh,
-                                          int *err)
+__device__ __forceinline__ void epi_bar() { ptx::named_bar(1, kEpiThreads); }
+
+// Bounded wait by every lane; false in all lanes if any gave up.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *abort, int *err)
 {
-    if (mbar_try_wait(bar, parity))
-        return true;
-    const unsigned long long t0 = globaltimer();
-    for (;;) {
-        if (mbar_try_wait(bar, parity))
-            return true;
-        if (*(volatile int *)&sh->abort)
-            return false;
-        if (globaltimer() - t0 > kWaitBudgetNs) {
-            *(volatile int *)&sh->abort = 1;
-            atomicExch(err, kErrTimeout);
-            return false;
-        }
-    }
+    const bool ok = ptx::mbar_wait(bar, parity, abort, err);
+    return __all_sync(0xFFFFFFFFu, ok);
 }
 
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
-                                            uint64_t *bar)
+__device__ __forceinline__ void mma_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t accumulate)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %3, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %4, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(kIdesc)
         : "memory");
 }
 
-// Shared-memory matrix descriptor (tcgen05 "matrix descriptor"): K-major tile
-// whose rows are 128 bytes with the 128-byte swizzle, 8-row groups 1024 bytes
-// apart.  Fields: start address >> 4 (bits 0-13), leading byte offset >> 4
-// (bits 16-29, unused for this layout, set to 1), stride byte offset >> 4
-// (bits 32-45), fixed value 1 (bits 46-47), swizzle mode 2 = 128-byte (bits
-// 61-63).
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1u << 16;
-    d |= (uint64_t)(1024u >> 4) << 32;
-    d |= (uint64_t)1u << 46;
-    d |= (uint64_t)2u << 61;
-    return d;
-}
-
-// Instruction descriptor of kind::f8f6f4: D = F32 (bits 4-5 = 1), A = B = E4M3
-// (bits 7-9, 10-12 = 0), both K-major, N >> 3 at bits 17-22, M >> 4 at bits
-// 24-28.
-constexpr uint32_t kIdescFp8 = (1u << 4) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_fp8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate)
+__device__ __forceinline__ void commit_elect(uint64_t *bar)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            ptx::smem_u32(bar))
         : "memory");
 }
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 lanes x 32 columns of 32-bit accumulator: register j holds column
-// (col + j) of the lane of this thread.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-        v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void epilogue_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 1)
 tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
-                   const __grid_constant__ CUtensorMap tmapB, int N, int Np, int Rp,
-                   float *__restrict__ X, float *__restrict__ Y, uint8_t *__restrict__ S8next,
-                   float pk, StepConsts c, int energy, int energy_only,
-                   float *__restrict__ Epart, float *__restrict__ Tpart, int *__restrict__ err)
+                   const __grid_constant__ CUtensorMap tmapB, int N, int Np, int Rp, int nrb,
+                   int ntiles, float *__restrict__ X, float *__restrict__ Y,
+                   uint8_t *__restrict__ S8next, float pk, StepConsts c, int energy,
+                   int energy_only, float *__restrict__ Epart, float *__restrict__ Tpart,
+                   int *__restrict__ err)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -208,133 +141,198 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kBM;
-    const int r0 = blockIdx.y * kBN;
     const int nk = Np / kBK;
+    // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&sh->full[s], 1);
-            mbar_init(&sh->empty[s], 1);
+            ptx::mbar_init(&sh->full[s], 1);
+            ptx::mbar_init(&sh->empty[s], 1);
         }
-        mbar_init(&sh->accfull, 1);
+        for (int b = 0; b < 2; ++b) {
+            ptx::mbar_init(&sh->accfull[b], 1);
+            ptx::mbar_init(&sh->accempty[b], kEpiWarps);
+        }
         sh->abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        ptx::mbar_init_fence();
     }
-    if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&sh->tmem_base)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if (warp == 0 && lane == 0) {
+        ptx::prefetch_tmap(&tmapA);
+        ptx::prefetch_tmap(&tmapB);
     }
-    tc_fence_before();
+    if (warp == kMmaWarp)
+        ptx::tmem_alloc(&sh->tmem_base, kTmemCols);
+    ptx::tc_fence_before();
     __syncthreads();
-    tc_fence_after();
+    ptx::tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
 
-    if (warp == 0) {
+    if (warp < kIssuers) {
+        // ------------------------------------------------------- TMA issuers
+        // Global chunk counter g runs over the K chunks of this CTA's tiles;
+        // issuer warp w takes g with g % 2 == w % 2 (stages w % 2, w % 2 + 2)
+        // and loads J (w < 2) or S (w >= 2).  The J issuer posts the stage's
+        // expected bytes (its one arrival); both boxes count against it.
         if (lane == 0) {
-            for (int kc = 0; kc < nk; ++kc) {
-                const int s = kc % kStages;
-                const uint32_t ph = (uint32_t)(kc / kStages) & 1u;
-                if (!mbar_wait(&sh->empty[s], ph ^ 1u, sh, err))
+            const bool isA = warp < 2;
+            const int total = my_tiles * nk;
+            for (int g = warp & 1; g < total; g += 2) {
+                const int j = g / nk;
+                const int kc = g - j * nk;
+                const int tile = blockIdx.x + j * gridDim.x;
+                const int mb = tile / nrb;
+                const int rb = tile - mb * nrb;
+                const int s = g % kStages;
+                const uint32_t ph = (uint32_t)(g / kStages) & 1u;
+                if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, err))
                     break;
-                mbar_expect_tx(&sh->full[s], (uint32_t)(kStageA + kStageB));
-                tma_load_2d(sA + (size_t)s * kStageA, &tmapA, kc * kBK, m0, &sh->full[s]);
-                tma_load_2d(sB + (size_t)s * kStageB, &tmapB, kc * kBK, r0, &sh->full[s]);
+                if (isA) {
+                    ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kStageA + kStageB));
+                    ptx::tma_load_2d(sA + (size_t)s * kStageA, &tmapA, kc * kBK, mb * kBM,
+                                     &sh->full[s]);
+                } else {
+                    ptx::tma_load_2d(sB + (size_t)s * kStageB, &tmapB, kc * kBK, rb * kBN,
+                                     &sh->full[s]);
+                }
             }
         }
-    } else if (warp == 1) {
-        if (lane == 0) {
+    } else if (warp == kMmaWarp) {
+        // --------------------------------------------------------------- MMA
+        const uint64_t adesc0 = ptx::sw128_desc(ptx::smem_u32(sA));
+        const uint64_t bdesc0 = ptx::sw128_desc(ptx::smem_u32(sB));
+        int g = 0;
+        for (int j = 0; j < my_tiles; ++j) {
+            const int b = j & 1;
+            // the epilogue has read this accumulator's previous tile
+            if (!warp_wait(&sh->accempty[b], (uint32_t)((j >> 1) & 1) ^ 1u, &sh->abort, err))
+                break;
+            ptx::tc_fence_after();
+            const uint32_t dcol = tmem + (uint32_t)(b * kBN);
             bool ok = true;
-            for (int kc = 0; kc < nk; ++kc) {
-                const int s = kc % kStages;
-                const uint32_t ph = (uint32_t)(kc / kStages) & 1u;
-                if (!mbar_wait(&sh->full[s], ph, sh, err)) {
+            for (int kc = 0; kc < nk; ++kc, ++g) {
+                const int s = g % kStages;
+                const uint32_t ph = (uint32_t)(g / kStages) & 1u;
+                if (!warp_wait(&sh->full[s], ph, &sh->abort, err)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
-                const uint32_t a0 = smem_u32(sA + (size_t)s * kStageA);
-                const uint32_t b0 = smem_u32(sB + (size_t)s * kStageB);
+                ptx::tc_fence_after();
+                const uint64_t ad = adesc0 + (uint64_t)((s * kStageA) >> 4);
+                const uint64_t bd = bdesc0 + (uint64_t)((s * kStageB) >> 4);
 #pragma unroll
                 for (int kk = 0; kk < kBK / 32; ++kk)
-                    mma_fp8(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), kIdescFp8,
-                            (kc | kk) != 0 ? 1u : 0u);
-                mma_commit(&sh->empty[s]);
+                    mma_elect(dcol, ad + (uint64_t)((kk * 32) >> 4), bd + (uint64_t)((kk * 32) >> 4),
+                              (kc | kk) != 0 ? 1u : 0u);
+                commit_elect(&sh->empty[s]);
             }
-            if (ok)
-                mma_commit(&sh->accfull);
+            if (!ok)
+                break;
+            commit_elect(&sh->accfull[b]);
         }
     } else {
-        // Epilogue warps 2..5; warp w reads tensor-memory lanes 32*(w % 4)..+31.
-        const int q = warp & 3;
-        const int row = q * 32 + lane;
-        const int i = m0 + row;
-        const bool live = i < N;
-        const bool ok = mbar_wait(&sh->accfull, 0u, sh, err);
-        tc_fence_after();
-        if (ok) {
-            for (int cb = 0; cb < kBN / 32; ++cb) {
-                float f[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cb * 32), f);
+        // ---------------------------------------------------------- epilogue
+        const int ew = warp - kFirstEpi;           // 0..7
+        const int q = warp & 3;                    // tensor-memory lane quadrant
+        const int cbase = (ew >> 2) * (kBN / 2);   // this warp's 128 replica columns
+        const int et = threadIdx.x - 32 * kFirstEpi;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const bool reduce = energy || energy_only || Tpart;
+        for (int j = 0; j < my_tiles; ++j) {
+            const int b = j & 1;
+            const int tile = blockIdx.x + j * gridDim.x;
+            const int mb = tile / nrb;
+            const int rb = tile - mb * nrb;
+            const int m0 = mb * kBM;
+            const int r0 = rb * kBN;
+            const int i = m0 + q * 32 + lane;      // spin of this thread
+            const bool live = i < N;
+            // x and y of one 32-column chunk, fetched before any store of the
+            // chunk (the first chunk before the accumulator wait): all loads
+            // of a chunk are in flight together
+            float xv[32], yv[32];
+            auto fetch = [&](int col0) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = cb * 32 + j;
-                    const size_t e = (size_t)(r0 + col) * Np + i;
-                    const float x0 = X[e];
-                    float term = 0.f;
-                    if (energy || energy_only)
-                        term = live ? (x0 >= 0.f ? f[j] : -f[j]) : 0.f;
-                    if (!energy_only) {
-                        float xn, yn;
-                        const float y0 = Y[e];
-                        if (Tpart) {
-                            // y_i(t_k)^2 of this row block, summed over lanes (Eq. eq_TInst)
-                            float t2 = __fmul_rn(y0, y0);
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int r = r0 + col0 + jj;
+                    const size_t e = (size_t)(r < Rp ? r : 0) * Np + i;
+                    xv[jj] = X[e];
+                    yv[jj] = energy_only ? 0.f : Y[e];
+                }
+            };
+            fetch(cbase);
+            const bool ok = ptx::mbar_wait(&sh->accfull[b], (uint32_t)(j >> 1) & 1u, &sh->abort,
+                                           err);
+            if (epi_bar_or(!ok))
+                break;
+            ptx::tc_fence_after();
+            for (int cb = 0; cb < kBN / 2 / 32; ++cb) {
+                const int col0 = cbase + cb * 32;
+                uint32_t fr[32];
+                ptx::tmem_ld32(tmem + lane_off + (uint32_t)(b * kBN + col0), fr);
+                if (cb > 0)
+                    fetch(col0);
+                ptx::tmem_ld_wait();
 #pragma unroll
-                            for (int off = 16; off > 0; off >>= 1)
-                                t2 += __shfl_xor_sync(0xffffffffu, t2, off);
-                            if (lane == 0)
-                                sh->tred[q][col] = t2;
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int col = col0 + jj;
+                    const int r = r0 + col;
+                    const float fj = __uint_as_float(fr[jj]);
+                    float term = 0.f, t2 = 0.f;
+                    if (r < Rp) {
+                        const size_t e = (size_t)r * Np + i;
+                        const float x0 = xv[jj];
+                        if (energy || energy_only)
+                            term = live ? (x0 >= 0.f ? fj : -fj) : 0.f;
+                        if (!energy_only) {
+                            const float y0 = yv[jj];
+                            if (Tpart)
+                                t2 = __fmul_rn(y0, y0);  // y_i(t_k)^2 (Eq. eq_TInst)
+                            float xn, yn;
+                            sb_update(fj, x0, y0, pk, c, xn, yn);
+                            X[e] = xn;
+                            Y[e] = yn;
+                            S8next[e] = live ? fp8_sign(xn) : (uint8_t)0;
                         }
-                        sb_update(f[j], x0, y0, pk, c, xn, yn);
-                        X[e] = xn;
-                        Y[e] = yn;
-                        S8next[e] = live ? fp8_sign(xn) : (uint8_t)0;
                     }
-                    if (energy || energy_only) {
+                    if (reduce) {
 #pragma unroll
-                        for (int off = 16; off > 0; off >>= 1)
-                            term += __shfl_xor_sync(0xffffffffu, term, off);
-                        if (lane == 0)
+                        for (int off = 16; off > 0; off >>= 1) {
+                            term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
+                            t2 += __shfl_xor_sync(0xFFFFFFFFu, t2, off);
+                        }
+                        if (lane == 0) {
                             sh->red[q][col] = term;
+                            sh->tred[q][col] = t2;
+                        }
                     }
                 }
             }
-        }
-        if (energy || energy_only || Tpart) {
-            epilogue_bar();
-            const int t = threadIdx.x - 64;  // 0..127
-            if (ok && t < kBN && (energy || energy_only)) {
-                const float s = sh->red[0][t] + sh->red[1][t] + sh->red[2][t] + sh->red[3][t];
-                Epart[(size_t)blockIdx.x * Rp + r0 + t] = s;
-            }
-            if (ok && t < kBN && Tpart && !energy_only) {
-                const float s = sh->tred[0][t] + sh->tred[1][t] + sh->tred[2][t] + sh->tred[3][t];
-                Tpart[(size_t)blockIdx.x * Rp + r0 + t] = s;
+            // the accumulator is read: the MMA may start the tile after next
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0)
+                ptx::mbar_arrive(&sh->accempty[b]);
+            if (reduce) {
+                epi_bar();
+                if (et < kBN && r0 + et < Rp) {
+                    if (energy || energy_only)
+                        Epart[(size_t)mb * Rp + r0 + et] =
+                            sh->red[0][et] + sh->red[1][et] + sh->red[2][et] + sh->red[3][et];
+                    if (Tpart && !energy_only)
+                        Tpart[(size_t)mb * Rp + r0 + et] =
+                            sh->tred[0][et] + sh->tred[1][et] + sh->tred[2][et] + sh->tred[3][et];
+                }
+                epi_bar();  // the next tile's partial sums overwrite red
             }
         }
     }
 
-    tc_fence_before();
+    ptx::tc_fence_before();
     __syncthreads();
-    tc_fence_after();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kTmemCols)
-                     : "memory");
+    ptx::tc_fence_after();
+    if (warp == kMmaWarp)
+        ptx::tmem_dealloc(tmem, kTmemCols);
 }
 
 // ------------------------------------------------------------- host side ---
@@ -411,19 +409,19 @@ cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S
                                const uint8_t *S8b, int Np, int Rp)
 {
     *out = nullptr;
-    if (Np % kBM != 0 || Rp % kBN != 0)
+    if (Np % kBM != 0 || Rp % 128 != 0)
         return cudaErrorInvalidValue;
     TcPlan *p = new TcPlan();
     p->Np = Np;
     p->Rp = Rp;
     if (!encode_u8(&p->mapA, J8, (uint64_t)Np, (uint64_t)Np, kBM) ||
-        !encode_u8(&p->mapB[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN) ||
-        !encode_u8(&p->mapB[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN) ||
+        !encode_u8(&p->mapB[0], S8a, (uint64_t)Rp, (uint64_t)Np, 128) ||
+        !encode_u8(&p->mapB[1], S8b, (uint64_t)Rp, (uint64_t)Np, 128) ||
         !encode_u8_3d(&p->mapA3, J8, (uint64_t)Np, (uint64_t)Np, kBM, 2) ||
-        !encode_u8_3d(&p->mapB3[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN, 2) ||
-        !encode_u8_3d(&p->mapB3[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN, 2) ||
-        !encode_u8(&p->mapSt[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN, false) ||
-        !encode_u8(&p->mapSt[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN, false)) {
+        !encode_u8_3d(&p->mapB3[0], S8a, (uint64_t)Rp, (uint64_t)Np, 128, 2) ||
+        !encode_u8_3d(&p->mapB3[1], S8b, (uint64_t)Rp, (uint64_t)Np, 128, 2) ||
+        !encode_u8(&p->mapBw[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN) ||
+        !encode_u8(&p->mapBw[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN)) {
         delete p;
         return cudaErrorInvalidValue;
     }
@@ -446,12 +444,21 @@ cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, 
                                int *err)
 {
     // Rp (this run's padded replica count) may be below the capacity the
-    // tensor maps were encoded for; Epart rows are Rp long.
-    if (!plan || Rp % kBN != 0 || Rp > plan->Rp)
+    // tensor maps were encoded for; Epart rows are Rp long.  A last tile that
+    // reaches past Rp reads operand rows that are never stored back.
+    if (!plan || Rp % 128 != 0 || Rp > plan->Rp)
         return cudaErrorInvalidValue;
-    dim3 grid(plan->Np / kBM, Rp / kBN);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int nrb = (Rp + kBN - 1) / kBN;
+    const int ntiles = (plan->Np / kBM) * nrb;
+    const int grid = ntiles < sms ? ntiles : sms;
     tc_fp8_step_kernel<<<grid, kThreads, kSmemBytes, st>>>(
-        plan->mapA, plan->mapB[parity & 1], N, plan->Np, Rp, X, Y, S8next, pk, c,
+        plan->mapA, plan->mapBw[parity & 1], N, plan->Np, Rp, nrb, ntiles, X, Y, S8next, pk, c,
         energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err);
     return cudaGetLastError();
 }
