@@ -14,12 +14,33 @@
 // [rows][2 * Np] BF16 array, so one 3-D TMA box (64 K elements x 128 rows x
 // 2 planes, 128-byte swizzle) fetches both planes of a K chunk in one copy.
 //
-// Structure as in hsb_persist.cu (one 128 x 128 tile per CTA for the whole
-// launch, x and y in tensor memory, per-tile published flags, bounded waits),
-// with two differences: K chunks are consumed in a fixed order per CTA (own
-// row block first, then ascending with wrap-around), because BF16 products
-// are not exact and the sum must not depend on timing; and there is no
-// evaluation inside the kernel -- the host splits a run at evaluation steps.
+// One 128 x 128 tile per CTA for the whole launch, x and y in tensor memory,
+// per-tile published flags and bounded waits, as in hsb_persist.cu.  K chunks
+// are consumed in a fixed order per CTA (own row block first, then ascending
+// with wrap-around), because BF16 products are not exact and the sum must not
+// depend on timing; there is no evaluation inside the kernel (the host splits
+// a run at evaluation steps).  Roles:
+//   warp 0     J issuer: TMA-loads both planes of each K chunk of J (one
+//              3-D box, 32 KB) into a ring of three stages as soon as a stage
+//              is free (J does not change, so the first chunks of a step
+//              arrive during the previous epilogue) and posts the stage's
+//              expected bytes;
+//   warp 1     operand issuer: waits for the row block's flag, then loads the
+//              same chunks of [x_hi | x_lo] (or sgn x).
+//              Copies from one thread complete one after another, so the two
+//              boxes of a stage come from two threads; each issuer takes
+//              every load in order, so its parity waits see every phase;
+//   warps 2-3  MMA (kind::f16, M = N = 128, K = 16), issued from an elected
+//              lane of the converged warp.  One warp issues an MMA of this
+//              shape about every 90 cycles, slower than the tensor core runs
+//              it, so K is split: loads in stage 1 go to warp 3 and a second
+//              accumulator, the others to warp 2 (a fixed assignment per
+//              step and chunk, so the FP32 sums do not depend on timing);
+//   warps 4-19 epilogue, in two phases.  Phase 1 computes x' (the walls are
+//              part of it), writes the next operand ([bf16(x') | bf16(x' -
+//              hi)], or sgn x') straight from registers and releases the
+//              tile's flag; phase 2 repeats the pinned update in full and
+//              stores x' and y' in tensor memory while the flags travel.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -37,18 +58,19 @@ namespace {
 constexpr int kQM = 128;        // spins per tile
 constexpr int kQN = 128;        // replicas per tile
 constexpr int kQKE = 64;        // K elements per chunk (128 bytes of BF16)
-constexpr int kQStages = 2;
+constexpr int kQStages = 3;
 constexpr int kQPlane = kQM * 128;           // one 128 x 128-byte plane, 16 KB
 constexpr int kQStageA = 2 * kQPlane;        // hi + lo
 constexpr int kQStageB = 2 * kQPlane;        // hi + lo (discrete form uses one plane)
-constexpr int kQTile = kQN * kQM * 2;        // BF16 [replica][spin] store tile, 32 KB
+constexpr int kQFirstEpi = 4;
 constexpr int kQEpiWarps = 16;
 constexpr int kQEpiThreads = 32 * kQEpiWarps;
-constexpr int kQThreads = 64 + kQEpiThreads;
+constexpr int kQThreads = 32 * kQFirstEpi + kQEpiThreads;
 constexpr uint32_t kQTmemCols = 512;
-constexpr uint32_t kQColAcc = 0;
-constexpr uint32_t kQColX = 128;
-constexpr uint32_t kQColY = 256;
+constexpr uint32_t kQColAcc0 = 0;
+constexpr uint32_t kQColAcc1 = 128;
+constexpr uint32_t kQColX = 256;
+constexpr uint32_t kQColY = 384;
 
 // Instruction descriptor, kind::f16 with A = B = BF16 (format 1 at bits 7-9
 // and 10-12), D = F32 (bits 4-5 = 1), K-major, N >> 3 at 17-22, M >> 4 at 24-28.
@@ -58,25 +80,42 @@ constexpr uint32_t kQIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kQ
 struct __align__(8) QShared {
     uint64_t full[kQStages];
     uint64_t empty[kQStages];
-    uint64_t accfull;
-    uint64_t tmem_empty;
+    uint64_t accfull;     // one arrival per accumulator
+    uint64_t tmem_empty;  // one arrival per epilogue warp
     uint32_t tmem_base;
     int abort;
 };
 
-constexpr size_t kQSmem =
-    1024 + (size_t)kQStages * (kQStageA + kQStageB) + 2 * (size_t)kQTile + sizeof(QShared);
+constexpr size_t kQSmem = 1024 + (size_t)kQStages * (kQStageA + kQStageB) + sizeof(QShared);
 static_assert(kQSmem <= 232448, "shared memory per CTA is limited to 227 KB");
 
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate)
+__device__ __forceinline__ void mma_bf16_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                               uint32_t accumulate)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(kQIdesc), "r"(accumulate)
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %3, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %4, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(kQIdesc)
         : "memory");
+}
+
+__device__ __forceinline__ void commit_elect(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            ptx::smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait by every lane; false in all lanes if any gave up.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *abort, int *err)
+{
+    const bool ok = ptx::mbar_wait(bar, parity, abort, err);
+    return __all_sync(0xFFFFFFFFu, ok);
 }
 
 __device__ __forceinline__ bool qbar_or(bool pred)
@@ -95,6 +134,27 @@ __device__ __forceinline__ bool qbar_or(bool pred)
 
 __device__ __forceinline__ void qbar() { ptx::named_bar(1, kQEpiThreads); }
 
+// Force of 16 replica columns: accumulator 0, plus accumulator 1 when K is
+// split (its chunks are disjoint from those of accumulator 0).
+__device__ __forceinline__ void load_force(uint32_t tcol, bool split, uint32_t (&f)[16])
+{
+    ptx::tmem_ld16(tcol + kQColAcc0, f);
+    if (split) {
+#pragma unroll
+        for (int p8 = 0; p8 < 2; ++p8) {
+            uint32_t f1[8];
+            ptx::tmem_ld8(tcol + kQColAcc1 + p8 * 8, f1);
+            ptx::tmem_ld_wait(f1);
+            ptx::tmem_ld_wait(f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                f[p8 * 8 + j] = __float_as_uint(
+                    __fadd_rn(__uint_as_float(f[p8 * 8 + j]), __uint_as_float(f1[j])));
+        }
+    }
+    ptx::tmem_ld_wait(f);
+}
+
 }  // namespace
 
 template <int FORM>
@@ -102,8 +162,8 @@ __global__ void __launch_bounds__(kQThreads, 1)
 tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                             const __grid_constant__ CUtensorMap tmapB0,
                             const __grid_constant__ CUtensorMap tmapB1,
-                            const __grid_constant__ CUtensorMap tmapSt0,
-                            const __grid_constant__ CUtensorMap tmapSt1, const PersistArgs a)
+                            __nv_bfloat16 *__restrict__ Xc0, __nv_bfloat16 *__restrict__ Xc1,
+                            const PersistArgs a)
 {
     constexpr int kBPlanes = FORM == 0 ? 2 : 1;
     extern __shared__ uint8_t smem_raw[];
@@ -111,8 +171,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = base;
     uint8_t *sB = base + (size_t)kQStages * kQStageA;
-    uint8_t *sT = sB + (size_t)kQStages * kQStageB;  // store tiles: hi, then lo
-    QShared *sh = reinterpret_cast<QShared *>(sT + 2 * (size_t)kQTile);
+    QShared *sh = reinterpret_cast<QShared *>(sB + (size_t)kQStages * kQStageB);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -123,14 +182,17 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
     const int nblk = a.nblk;
     const int nchunks = a.Np / kQKE;  // two per row block
     const int passes = a.nsteps;
+    // K is split when a pass has 3 or more loads: every pass then fills all
+    // three stages, so both accumulators take part in every pass
+    const bool split = nchunks >= 3;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kQStages; ++s) {
             ptx::mbar_init(&sh->full[s], 1);
             ptx::mbar_init(&sh->empty[s], 1);
         }
-        ptx::mbar_init(&sh->accfull, 1);
-        ptx::mbar_init(&sh->tmem_empty, 1);
+        ptx::mbar_init(&sh->accfull, 2);
+        ptx::mbar_init(&sh->tmem_empty, kQEpiWarps);
         sh->abort = 0;
         ptx::mbar_init_fence();
     }
@@ -138,19 +200,18 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
         ptx::prefetch_tmap(&tmapJ);
         ptx::prefetch_tmap(&tmapB0);
         ptx::prefetch_tmap(&tmapB1);
-        ptx::prefetch_tmap(&tmapSt0);
-        ptx::prefetch_tmap(&tmapSt1);
     }
-    if (warp == 1)
+    if (warp == 2)
         ptx::tmem_alloc(&sh->tmem_base, kQTmemCols);
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
 
-    if (warp == 0) {
-        // ---------------------------------------------------------- producer
+    if (warp < 2) {
+        // --------------------------------------------------------- issuers
         if (lane == 0) {
+            const bool isJ = warp == 0;
             uint32_t g = 0;
             bool fail = false;
             for (int kl = 0; kl < passes && !fail; ++kl) {
@@ -160,16 +221,18 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                     int kb = mb + t;  // fixed order: own row block first
                     if (kb >= nblk)
                         kb -= nblk;
-                    // wait until row block kb has published the operand of this pass
-                    while (ptx::ld_acquire_gpu(&a.flags[flag_index(kb, rb, a.nrb)]) < kl) {
+                    // the operand rows of block kb change every pass; J does
+                    // not, so the J issuer only waits for a free stage and
+                    // fetches the first chunks of a pass during the epilogue
+                    unsigned n = 0;
+                    while (!isJ && ptx::ld_acquire_gpu(&a.flags[flag_index(kb, rb, a.nrb)]) < kl) {
                         if (*(volatile int *)&sh->abort ||
-                            ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
+                            ((++n & 15) == 0 && ptx::globaltimer() - t0 > ptx::kWaitBudgetNs)) {
                             *(volatile int *)&sh->abort = 1;
                             atomicExch(a.err, kErrTimeout);
                             fail = true;
                             break;
                         }
-                        __nanosleep(32);
                     }
                     if (fail)
                         break;
@@ -182,71 +245,78 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                             fail = true;
                             break;
                         }
-                        ptx::mbar_expect_tx(&sh->full[s],
-                                            (uint32_t)(kQStageA + kBPlanes * kQPlane));
-                        ptx::tma_load_3d(sA + (size_t)s * kQStageA, &tmapJ, c * kQKE, m0, 0,
-                                         &sh->full[s]);
-                        ptx::tma_load_3d(sB + (size_t)s * kQStageB, mapB, c * kQKE, r0, 0,
-                                         &sh->full[s]);
+                        if (isJ) {
+                            ptx::mbar_expect_tx(&sh->full[s],
+                                                (uint32_t)(kQStageA + kBPlanes * kQPlane));
+                            ptx::tma_load_3d(sA + (size_t)s * kQStageA, &tmapJ, c * kQKE, m0, 0,
+                                             &sh->full[s]);
+                        } else {
+                            ptx::tma_load_3d(sB + (size_t)s * kQStageB, mapB, c * kQKE, r0, 0,
+                                             &sh->full[s]);
+                        }
                         ++g;
                     }
                 }
             }
         }
-    } else if (warp == 1) {
+    } else if (warp < kQFirstEpi) {
         // --------------------------------------------------------------- MMA
-        if (lane == 0) {
-            uint32_t g = 0;
-            for (int kl = 0; kl < passes; ++kl) {
-                if (kl > 0) {
-                    if (!ptx::mbar_wait(&sh->tmem_empty, (uint32_t)(kl - 1) & 1u, &sh->abort,
-                                        a.err))
-                        break;
-                    ptx::tc_fence_after();
-                }
-                bool ok = true;
-                for (int t = 0; t < nchunks; ++t) {
-                    const int s = (int)(g % kQStages);
-                    const uint32_t ph = (g / kQStages) & 1u;
-                    if (!ptx::mbar_wait(&sh->full[s], ph, &sh->abort, a.err)) {
-                        ok = false;
-                        break;
-                    }
-                    ptx::tc_fence_after();
-                    const uint32_t ahi = ptx::smem_u32(sA + (size_t)s * kQStageA);
-                    const uint32_t alo = ahi + kQPlane;
-                    const uint32_t bhi = ptx::smem_u32(sB + (size_t)s * kQStageB);
-                    const uint32_t blo = bhi + kQPlane;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {
-                        const uint32_t off = kk * 32;
-                        mma_bf16(tmem + kQColAcc, ptx::sw128_desc(ahi + off),
-                                 ptx::sw128_desc(bhi + off), (t | kk) != 0 ? 1u : 0u);
-                        mma_bf16(tmem + kQColAcc, ptx::sw128_desc(alo + off),
-                                 ptx::sw128_desc(bhi + off), 1u);
-                        if (FORM == 0)
-                            mma_bf16(tmem + kQColAcc, ptx::sw128_desc(ahi + off),
-                                     ptx::sw128_desc(blo + off), 1u);
-                    }
-                    ptx::mma_commit(&sh->empty[s]);
-                    ++g;
-                }
-                if (!ok)
+        // warp 2 + part issues the loads of its stages (part 1: stage 1)
+        const int part = warp - 2;
+        const uint32_t dcol = tmem + (part ? kQColAcc1 : kQColAcc0);
+        const uint64_t adesc0 = ptx::sw128_desc(ptx::smem_u32(sA));
+        const uint64_t bdesc0 = ptx::sw128_desc(ptx::smem_u32(sB));
+        for (int kl = 0; kl < passes; ++kl) {
+            if (kl > 0) {
+                if (!warp_wait(&sh->tmem_empty, (uint32_t)(kl - 1) & 1u, &sh->abort, a.err))
                     break;
-                ptx::mma_commit(&sh->accfull);
+                ptx::tc_fence_after();
             }
+            bool ok = true;
+            int mine = 0;
+            for (int t = 0; t < nchunks; ++t) {
+                const int g = kl * nchunks + t;
+                const int s = g % kQStages;
+                if ((split && s == 1) != (part == 1))
+                    continue;
+                const uint32_t ph = (uint32_t)(g / kQStages) & 1u;
+                if (!warp_wait(&sh->full[s], ph, &sh->abort, a.err)) {
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                const uint64_t ahi = adesc0 + (uint64_t)((s * kQStageA) >> 4);
+                const uint64_t alo = ahi + (uint64_t)(kQPlane >> 4);
+                const uint64_t bhi = bdesc0 + (uint64_t)((s * kQStageB) >> 4);
+                const uint64_t blo = bhi + (uint64_t)(kQPlane >> 4);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {
+                    const uint64_t off = (uint64_t)((kk * 32) >> 4);
+                    mma_bf16_elect(dcol, ahi + off, bhi + off, (mine | kk) != 0 ? 1u : 0u);
+                    mma_bf16_elect(dcol, alo + off, bhi + off, 1u);
+                    if (FORM == 0)
+                        mma_bf16_elect(dcol, ahi + off, blo + off, 1u);
+                }
+                commit_elect(&sh->empty[s]);
+                ++mine;
+            }
+            if (!ok)
+                break;
+            if (mine > 0)
+                commit_elect(&sh->accfull);
+            else if (lane == 0)
+                ptx::mbar_arrive(&sh->accfull);  // no load of this pass for this accumulator
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const int ew = warp - 2;
+        const int ew = warp - kQFirstEpi;
         const int q = warp & 3;
         const int c0 = (ew >> 2) * 32;
-        const int et = threadIdx.x - 64;
+        const int et = threadIdx.x - 32 * kQFirstEpi;
         const int i = m0 + q * 32 + lane;
         const bool live = i < a.N;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        __nv_bfloat16 *tHi = reinterpret_cast<__nv_bfloat16 *>(sT) + q * 32 + lane;
-        __nv_bfloat16 *tLo = reinterpret_cast<__nv_bfloat16 *>(sT + kQTile) + q * 32 + lane;
+        const size_t row2 = 2 * (size_t)a.Np;  // elements per [hi | lo] row
 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -271,64 +341,100 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
             const uint64_t pk2 = f2_pack(pk, pk);
             if (kl + 1 < passes)
                 pk_next = a.pk[k + 1];
+            __nv_bfloat16 *nxt = (((a.par0 + kl + 1) & 1) ? Xc1 : Xc0) + (size_t)(r0 + c0) * row2 + i;
+
+            // x and y of the first 16 columns: the MMA does not write them
+            uint32_t xpre[16], ypre[16];
+            ptx::tmem_ld16(tmem + lane_off + kQColX + c0, xpre);
+            ptx::tmem_ld16(tmem + lane_off + kQColY + c0, ypre);
             const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
+            ptx::tmem_ld_wait(xpre);
+            ptx::tmem_ld_wait(ypre);
             if (qbar_or(!ok)) {
                 left = true;
                 break;
             }
             ptx::tc_fence_after();
+
+            // ---- phase 1: x' and the next operand, published first
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t col0 = (uint32_t)(c0 + h * 16);
                 uint32_t f[16], xr[16], yr[16];
-                ptx::tmem_ld16(tmem + lane_off + kQColAcc + col0, f);
-                ptx::tmem_ld16(tmem + lane_off + kQColX + col0, xr);
-                ptx::tmem_ld16(tmem + lane_off + kQColY + col0, yr);
-                ptx::tmem_ld_wait();
-                // two replicas per packed binary32 operation
-                float xnv[16];
+                load_force(tmem + lane_off + col0, split, f);
+                if (h == 0) {
 #pragma unroll
-                for (int j = 0; j < 16; j += 2) {
-                    uint64_t yn;
-                    sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
-                               f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xnv[j], xnv[j + 1], yn);
-                    yr[j] = (uint32_t)yn;
-                    yr[j + 1] = (uint32_t)(yn >> 32);
+                    for (int j = 0; j < 16; ++j) {
+                        xr[j] = xpre[j];
+                        yr[j] = ypre[j];
+                    }
+                } else {
+                    ptx::tmem_ld16(tmem + lane_off + kQColX + col0, xr);
+                    ptx::tmem_ld16(tmem + lane_off + kQColY + col0, yr);
+                    ptx::tmem_ld_wait(xr);
+                    ptx::tmem_ld_wait(yr);
                 }
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float xn = xnv[j];
-                    xr[j] = __float_as_uint(xn);
-                    const int col = col0 + j;
-                    if (FORM == 0) {
-                        // x' = hi + lo, hi = bf16(x'), lo = bf16(x' - hi)
-                        const __nv_bfloat16 hi = __float2bfloat16_rn(xn);
-                        const __nv_bfloat16 lo =
-                            __float2bfloat16_rn(__fsub_rn(xn, __bfloat162float(hi)));
-                        tHi[col * kQM] = live ? hi : __float2bfloat16_rn(0.f);
-                        tLo[col * kQM] = live ? lo : __float2bfloat16_rn(0.f);
-                    } else {
-                        tHi[col * kQM] = __float2bfloat16_rn(live ? (xn >= 0.f ? 1.f : -1.f) : 0.f);
+                for (int j = 0; j < 16; j += 2) {
+                    const uint64_t xt =
+                        sb_position2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
+                                     f2_pack_bits(yr[j], yr[j + 1]), pk2, k2);
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        // walls as in sb_update2: x' = clamp(x~, -1, 1)
+                        const float xn = fminf(fmaxf(u ? f2_hi(xt) : f2_lo(xt), -1.f), 1.f);
+                        __nv_bfloat16 *dst = nxt + (size_t)(h * 16 + j + u) * row2;
+                        if (FORM == 0) {
+                            // x' = hi + lo, hi = bf16(x'), lo = bf16(x' - hi)
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(xn);
+                            const __nv_bfloat16 lo =
+                                __float2bfloat16_rn(__fsub_rn(xn, __bfloat162float(hi)));
+                            dst[0] = live ? hi : __float2bfloat16_rn(0.f);
+                            dst[a.Np] = live ? lo : __float2bfloat16_rn(0.f);
+                        } else {
+                            dst[0] = __float2bfloat16_rn(live ? (xn >= 0.f ? 1.f : -1.f) : 0.f);
+                        }
                     }
+                }
+            }
+            qbar();
+            if (et == 0) {
+                // every epilogue thread's operand stores precede the barrier;
+                // the gpu-scope release (cumulative) publishes them
+                ptx::fence_proxy_async_global();
+                ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
+            }
+
+            // ---- phase 2: the full update into tensor memory
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t col0 = (uint32_t)(c0 + h * 16);
+                uint32_t f[16], xr[16], yr[16];
+                ptx::tmem_ld16(tmem + lane_off + kQColX + col0, xr);
+                ptx::tmem_ld16(tmem + lane_off + kQColY + col0, yr);
+                load_force(tmem + lane_off + col0, split, f);
+                ptx::tmem_ld_wait(xr);
+                ptx::tmem_ld_wait(yr);
+                // two replicas per packed binary32 operation
+#pragma unroll
+                for (int j = 0; j < 16; j += 2) {
+                    float xn0, xn1;
+                    uint64_t yn;
+                    sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
+                               f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xn0, xn1, yn);
+                    xr[j] = __float_as_uint(xn0);
+                    xr[j + 1] = __float_as_uint(xn1);
+                    yr[j] = (uint32_t)yn;
+                    yr[j + 1] = (uint32_t)(yn >> 32);
                 }
                 ptx::tmem_st16(tmem + lane_off + kQColX + col0, xr);
                 ptx::tmem_st16(tmem + lane_off + kQColY + col0, yr);
             }
             ptx::tc_fence_before();
             ptx::tmem_st_wait();
-            ptx::fence_proxy_async_smem();
-            qbar();
-            if (et == 0) {
-                ptx::mbar_arrive(&sh->tmem_empty);
-                const CUtensorMap *st = ((a.par0 + kl + 1) & 1) ? &tmapSt1 : &tmapSt0;
-                ptx::tma_store_2d(st, m0, r0, sT);
-                if (FORM == 0)
-                    ptx::tma_store_2d(st, a.Np + m0, r0, sT + kQTile);
-                ptx::bulk_commit();
-                ptx::bulk_wait_all();
-                ptx::fence_proxy_async_global();
-                ptx::st_release_gpu(&a.flags[flag_index(mb, rb, a.nrb)], kl + 1);
-            }
+            __syncwarp();
+            if (lane == 0)
+                ptx::mbar_arrive(&sh->tmem_empty);  // this warp has read the accumulators
         }
         if (!left) {
 #pragma unroll
@@ -350,7 +456,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (warp == 1)
+    if (warp == 2)
         ptx::tmem_dealloc(tmem, kQTmemCols);
 }
 
@@ -390,21 +496,6 @@ bool encode_planes(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t Np, 
     const cuuint32_t estr[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void *>(ptr), dims, strides, box,
               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// 2-D store map over the same array: box 128 spins x 128 replicas, no swizzle.
-bool encode_store(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t Np)
-{
-    EncodeTiledFn fn = encode_fn();
-    if (!fn || (reinterpret_cast<uintptr_t>(ptr) & 15u) != 0)
-        return false;
-    const cuuint64_t dims[2] = {2 * Np, rows};
-    const cuuint64_t strides[1] = {4 * Np};
-    const cuuint32_t box[2] = {128, 128};
-    const cuuint32_t estr[2] = {1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -453,7 +544,7 @@ __global__ void split_state_kernel(const float *__restrict__ X, int N, int Np, i
 struct Bf16Plan {
     CUtensorMap mapJ;
     CUtensorMap mapB[2][2];  // [form][buffer]: 2 planes (ballistic) / 1 plane (discrete)
-    CUtensorMap mapSt[2];
+    void *xcat[2];           // the operand buffers the maps describe
     int Np, Rp;
 };
 
@@ -467,11 +558,12 @@ cudaError_t bf16_plan_create(Bf16Plan **out, const void *Jcat, const void *Xcat0
     p->Np = Np;
     p->Rp = Rp;
     const void *xb[2] = {Xcat0, Xcat1};
+    p->xcat[0] = const_cast<void *>(Xcat0);
+    p->xcat[1] = const_cast<void *>(Xcat1);
     bool ok = encode_planes(&p->mapJ, Jcat, (uint64_t)Np, (uint64_t)Np, 2);
     for (int b = 0; b < 2 && ok; ++b) {
         ok = encode_planes(&p->mapB[0][b], xb[b], (uint64_t)Rp, (uint64_t)Np, 2) &&
-             encode_planes(&p->mapB[1][b], xb[b], (uint64_t)Rp, (uint64_t)Np, 1) &&
-             encode_store(&p->mapSt[b], xb[b], (uint64_t)Rp, (uint64_t)Np);
+             encode_planes(&p->mapB[1][b], xb[b], (uint64_t)Rp, (uint64_t)Np, 1);
     }
     if (!ok) {
         delete p;
@@ -540,7 +632,8 @@ cudaError_t launch_tc_bf16x3_persistent(cudaStream_t st, const Bf16Plan *plan, i
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, kern, plan->mapJ, plan->mapB[form][0], plan->mapB[form][1],
-                              plan->mapSt[0], plan->mapSt[1], a);
+                              static_cast<__nv_bfloat16 *>(plan->xcat[0]),
+                              static_cast<__nv_bfloat16 *>(plan->xcat[1]), a);
 }
 
 }  // namespace hsb
