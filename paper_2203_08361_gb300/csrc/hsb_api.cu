@@ -101,6 +101,7 @@ struct hsb_ctx {
     size_t trace_cap = 0, trace_len = 0;
     double *Ebest = nullptr;
     double *Efinal = nullptr;
+    double *Efpart = nullptr;  // partial sums of the binary64 final energies
     int8_t *Sbest = nullptr;
     int *err = nullptr;
     uint64_t buffers_gen = 0;
@@ -159,6 +160,8 @@ void free_run_buffers(hsb_ctx *h)
     cudaFree(h->Tpart);
     cudaFree(h->Ebest);
     cudaFree(h->Efinal);
+    cudaFree(h->Efpart);
+    h->Efpart = nullptr;
     cudaFree(h->Sbest);
     h->X[0] = h->X[1] = h->Y = nullptr;
     h->S8[0] = h->S8[1] = nullptr;
@@ -197,6 +200,8 @@ hsb_status ensure_buffers(hsb_ctx *h, int Rp, int R)
     CK(cudaMalloc(&h->Tpart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Tpart");
     CK(cudaMalloc(&h->Ebest, (size_t)Rp * sizeof(double)), "cudaMalloc Ebest");
     CK(cudaMalloc(&h->Efinal, (size_t)Rp * sizeof(double)), "cudaMalloc Efinal");
+    CK(cudaMalloc(&h->Efpart, final_energy_part_doubles(Rp) * sizeof(double)),
+       "cudaMalloc Efpart");
     CK(cudaMalloc(&h->Sbest, (size_t)Rp * h->N), "cudaMalloc Sbest");
     h->Rcap = Rp;
     h->buffers_gen++;
@@ -368,7 +373,8 @@ hsb_status enqueue_final(hsb_ctx *h, cudaStream_t st, const RunCfg &c)
            "best kernel");
     }
     if (!h->pm1)
-        CK(launch_final_energy_f64(st, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efinal),
+        CK(launch_final_energy_f64_parts(st, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efpart,
+                                         h->Efinal),
            "final energy kernel");
     return HSB_OK;
 }
@@ -589,9 +595,41 @@ hsb_status enqueue_bf16(hsb_ctx *h, const RunCfg &c, int k_begin, int nsteps, in
     return HSB_OK;
 }
 
+// Energy of s = sgn(x) for every replica on the split-BF16 tensor-core path:
+// one energy-only pass of the discrete kernel over the operand buffer `buf`,
+// which holds [sgn x | 0], writes Epart[nblk][Rp].
+hsb_status enqueue_bf16_energy(hsb_ctx *h, const RunCfg &c, int buf)
+{
+    const int nblk = h->Np / kTileM;
+    const int nrb = c.Rp / kTileR;
+    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * kFlagStride * sizeof(int), h->work),
+       "memset flags");
+    PersistArgs a;
+    memset(&a, 0, sizeof a);
+    a.N = h->N;
+    a.Np = h->Np;
+    a.Rp = c.Rp;
+    a.nblk = nblk;
+    a.nrb = nrb;
+    a.nsteps = 0;
+    a.final_pass = 1;
+    a.steps_total = c.steps;
+    a.par0 = buf;
+    a.pk = h->pk_dev;
+    a.c = c.c;
+    a.X = h->X[0];
+    a.Y = h->Y;
+    a.flags = h->flags;
+    a.Epart = h->Epart;
+    a.err = h->err;
+    CK(launch_tc_bf16x3_persistent(h->work, h->bplan, 1, a), "bf16x3 energy pass");
+    return HSB_OK;
+}
+
 // Whole split-BF16 run: the step loop is cut at the evaluation steps; each
-// evaluation is the plain-FP32 energy pass over sgn(x) (exact for +/-1
-// couplings, binary32 fused multiply-adds otherwise) and a best update.
+// evaluation is an energy-only tensor-core pass over sgn(x) (f = J_hi s +
+// J_lo s, FP32 accumulation: the candidate energies) and a best update; the
+// returned energies are recomputed in binary64 for the chosen spins.
 hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_params *p)
 {
     const int nblk = h->Np / kTileM;
@@ -615,19 +653,29 @@ hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hs
             return s;
         par = (par + (kb - k)) & 1;
         k = kb;
-        // evaluation of s(t_k): at an evaluation step, and at the end
-        CK(launch_simt_step(h->work, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[0], nullptr,
-                            h->Y, 0.f, c.c, h->Epart, nullptr),
-           "energy kernel");
+        // evaluation of s(t_k): at an evaluation step, and at the end.  The
+        // discrete form has just published [sgn x | 0] into buffer par; the
+        // ballistic form writes it into the idle buffer.
+        int ebuf = par;
+        if (c.form == 0) {
+            ebuf = par ^ 1;
+            CK(launch_split_state(h->work, h->X[0], h->N, h->Np, c.Rp, 1, h->Xcat[ebuf]),
+               "sign operand");
+            ++launches;
+        }
+        s = enqueue_bf16_energy(h, c, ebuf);
+        if (s != HSB_OK)
+            return s;
         CK(launch_best_update(h->work, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[0], nullptr,
                               h->Ebest, h->Sbest),
            "best kernel");
         launches += 3;
     }
     if (!h->pm1) {
-        CK(launch_final_energy_f64(h->work, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efinal),
+        CK(launch_final_energy_f64_parts(h->work, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efpart,
+                                         h->Efinal),
            "final energy kernel");
-        launches += 1;
+        launches += 2;
     }
     h->last_R = c.R;
     h->last_x = 0;

@@ -76,6 +76,13 @@ cudaError_t launch_best_update(cudaStream_t st, const float *Epart, int nblk, in
 cudaError_t launch_final_energy_f64(cudaStream_t st, const float *J32, int N, int Np, int R,
                                     const int8_t *Sbest, double *Eout);
 
+// The same energies through partial sums part[16][R] (scratch of
+// final_energy_part_doubles(R) doubles): binary64 additions on the upper
+// triangle only, 32 replicas per warp, fixed summation order.
+size_t final_energy_part_doubles(int R);
+cudaError_t launch_final_energy_f64_parts(cudaStream_t st, const float *J32, int N, int Np, int R,
+                                          const int8_t *Sbest, double *part, double *Eout);
+
 // sgn(X) -> FP8 operand (used when a state is loaded from the host).
 cudaError_t launch_sign_to_fp8(cudaStream_t st, const float *X, int N, int Np, int Rp,
                                uint8_t *S8);

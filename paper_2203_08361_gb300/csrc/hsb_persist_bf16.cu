@@ -41,6 +41,9 @@
 //              hi)], or sgn x') straight from registers and releases the
 //              tile's flag; phase 2 repeats the pinned update in full and
 //              stores x' and y' in tensor memory while the flags travel.
+// An energy-only launch (discrete form, operand sgn x, a.final_pass = 1 and
+// no updates) forms the per-row-block partial sums of s_i f_i of every
+// replica (Eq. (eq_Ising)), with f = J_hi s + J_lo s, into Epart[nblk][Rp].
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -84,6 +87,7 @@ struct __align__(8) QShared {
     uint64_t tmem_empty;  // one arrival per epilogue warp
     uint32_t tmem_base;
     int abort;
+    float red[4][kQN];    // per-quadrant energy partials (energy-only pass)
 };
 
 constexpr size_t kQSmem = 1024 + (size_t)kQStages * (kQStageA + kQStageB) + sizeof(QShared);
@@ -181,7 +185,9 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
     const int r0 = rb * kQN;
     const int nblk = a.nblk;
     const int nchunks = a.Np / kQKE;  // two per row block
-    const int passes = a.nsteps;
+    // a.final_pass: one pass that only evaluates s_i f_i (discrete form,
+    // operand sgn x), no update and no publication
+    const int passes = a.nsteps + a.final_pass;
     // K is split when a pass has 3 or more loads: every pass then fills all
     // three stages, so both accumulators take part in every pass
     const bool split = nchunks >= 3;
@@ -336,10 +342,11 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
         const StepConsts2 k2 = step_consts2(a.c);
         float pk_next = passes > 0 ? a.pk[a.k_begin] : 0.f;
         for (int kl = 0; kl < passes; ++kl) {
+            const bool energy_pass = kl == a.nsteps;
             const int k = a.k_begin + kl;
-            const float pk = pk_next;
+            const float pk = energy_pass ? 0.f : pk_next;
             const uint64_t pk2 = f2_pack(pk, pk);
-            if (kl + 1 < passes)
+            if (kl + 1 < a.nsteps)
                 pk_next = a.pk[k + 1];
             __nv_bfloat16 *nxt = (((a.par0 + kl + 1) & 1) ? Xc1 : Xc0) + (size_t)(r0 + c0) * row2 + i;
 
@@ -358,7 +365,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
 
             // ---- phase 1: x' and the next operand, published first
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < 2 && !energy_pass; ++h) {
                 const uint32_t col0 = (uint32_t)(c0 + h * 16);
                 uint32_t f[16], xr[16], yr[16];
                 load_force(tmem + lane_off + col0, split, f);
@@ -397,8 +404,9 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                     }
                 }
             }
-            qbar();
-            if (et == 0) {
+            if (!energy_pass)
+                qbar();
+            if (et == 0 && !energy_pass) {
                 // every epilogue thread's operand stores precede the barrier;
                 // the gpu-scope release (cumulative) publishes them
                 ptx::fence_proxy_async_global();
@@ -415,6 +423,20 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                 load_force(tmem + lane_off + col0, split, f);
                 ptx::tmem_ld_wait(xr);
                 ptx::tmem_ld_wait(yr);
+                if (energy_pass) {
+                    // s_i f_i summed over the tile's 32 spins of this quadrant
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float fj = __uint_as_float(f[j]);
+                        float term = live ? (__uint_as_float(xr[j]) >= 0.f ? fj : -fj) : 0.f;
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1)
+                            term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
+                        if (lane == 0)
+                            sh->red[q][col0 + j] = term;
+                    }
+                    continue;
+                }
                 // two replicas per packed binary32 operation
 #pragma unroll
                 for (int j = 0; j < 16; j += 2) {
@@ -435,8 +457,14 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
             __syncwarp();
             if (lane == 0)
                 ptx::mbar_arrive(&sh->tmem_empty);  // this warp has read the accumulators
+            if (energy_pass) {
+                qbar();
+                if (et < kQN)
+                    a.Epart[(size_t)mb * a.Rp + r0 + et] =
+                        sh->red[0][et] + sh->red[1][et] + sh->red[2][et] + sh->red[3][et];
+            }
         }
-        if (!left) {
+        if (!left && a.nsteps > 0) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint32_t xr[16], yr[16];
@@ -613,8 +641,10 @@ bool tc_bf16_persistent_fits(int Np, int Rp)
 cudaError_t launch_tc_bf16x3_persistent(cudaStream_t st, const Bf16Plan *plan, int form,
                                         const PersistArgs &a)
 {
-    if (!plan || a.Np != plan->Np || a.Rp > plan->Rp || a.Rp % kQN != 0 || a.nsteps < 1 ||
-        a.final_pass != 0 || (form != 0 && form != 1))
+    // either nsteps >= 1 updates, or (discrete form) one energy-only pass
+    const bool energy_only = a.nsteps == 0 && a.final_pass == 1 && form == 1;
+    if (!plan || a.Np != plan->Np || a.Rp > plan->Rp || a.Rp % kQN != 0 ||
+        (!energy_only && (a.nsteps < 1 || a.final_pass != 0)) || (form != 0 && form != 1))
         return cudaErrorInvalidValue;
     auto kern = form == 0 ? tc_bf16x3_persistent_kernel<0> : tc_bf16x3_persistent_kernel<1>;
     cudaError_t e =

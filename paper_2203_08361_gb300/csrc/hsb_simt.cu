@@ -374,6 +374,96 @@ cudaError_t launch_final_energy_f64(cudaStream_t st, const float *J32, int N, in
     return cudaGetLastError();
 }
 
+// The same energies for many replicas at once, with binary64 additions only
+// on the upper triangle: E = -sum_{i<j} J_ij s_i s_j (J symmetric, zero
+// diagonal).  Block (t, g) takes replicas 32t .. 32t+31 (one per lane) and
+// rows i = 8g + w, 8g + w + 8G, ... (w = warp); a warp converts each J element
+// of its row to binary64 once and broadcasts it with a shuffle, so every
+// element costs one binary64 add per replica (its sign flipped for
+// s_i != s_j).  The row sums of a block are added in a fixed order into
+// part[g][r], and final_energy_sum_kernel adds the groups in order: the
+// result does not depend on timing.
+constexpr int kFeGroups = 16;
+
+__global__ void __launch_bounds__(256)
+final_energy_part_kernel(const float *__restrict__ J, int N, int Np, int R,
+                         const int8_t *__restrict__ Sbest, double *__restrict__ part)
+{
+    extern __shared__ uint8_t neg_sh[];  // [N + 32][32]: 1 where s = -1 (0 past N)
+    __shared__ double red[8][32];
+    const int r0 = blockIdx.x * 32;
+    const int G = gridDim.y;
+    for (int e = threadIdx.x; e < (N + 32) * 32; e += blockDim.x) {
+        const int j = e >> 5, rr = e & 31;
+        const int r = r0 + rr;
+        neg_sh[e] = (j < N && r < R && Sbest[(size_t)r * N + j] < 0) ? 1 : 0;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    double acc = 0.0;
+    for (int i = blockIdx.y * 8 + warp; i < N; i += G * 8) {
+        const uint32_t ni = neg_sh[i * 32 + lane];
+        const float *row = J + (size_t)i * Np;
+        double a = 0.0;
+        for (int j0 = i + 1; j0 < N; j0 += 32) {
+            const int j = j0 + lane;
+            const double vl = j < N ? (double)row[j] : 0.0;
+#pragma unroll 8
+            for (int jj = 0; jj < 32; ++jj) {
+                const double v = __shfl_sync(0xffffffffu, vl, jj);
+                const uint32_t flip = ni ^ neg_sh[(j0 + jj) * 32 + lane];
+                // J_ij s_i s_j: the sign bit of v flipped for s_i != s_j
+                a += __hiloint2double(__double2hiint(v) ^ (int)(flip << 31), __double2loint(v));
+            }
+        }
+        acc += a;
+    }
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && r0 + lane < R) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w)
+            s += red[w][lane];
+        part[(size_t)blockIdx.y * R + r0 + lane] = s;
+    }
+}
+
+__global__ void final_energy_sum_kernel(const double *__restrict__ part, int G, int R,
+                                        double *__restrict__ Eout)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R)
+        return;
+    double s = 0.0;
+    for (int g = 0; g < G; ++g)
+        s += part[(size_t)g * R + r];
+    Eout[r] = -s;
+}
+
+size_t final_energy_part_doubles(int R) { return (size_t)kFeGroups * R; }
+
+cudaError_t launch_final_energy_f64_parts(cudaStream_t st, const float *J32, int N, int Np, int R,
+                                          const int8_t *Sbest, double *part, double *Eout)
+{
+    const dim3 grid((R + 31) / 32, kFeGroups);
+    const size_t smem = (size_t)(N + 32) * 32;
+    if (smem > 200 * 1024)  // N above about 6300: one block per replica instead
+        return launch_final_energy_f64(st, J32, N, Np, R, Sbest, Eout);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(final_energy_part_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess)
+            return e;
+    }
+    final_energy_part_kernel<<<grid, 256, smem, st>>>(J32, N, Np, R, Sbest, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    final_energy_sum_kernel<<<(R + 255) / 256, 256, 0, st>>>(part, kFeGroups, R, Eout);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- conversions ---
 
 __global__ void sign_to_fp8_kernel(const float *__restrict__ X, int N, int Np, size_t total,
