@@ -11,13 +11,20 @@
 //     boundary (the old ones are read by every row block of the step);
 //   - J streams through shared memory two 128-wide K chunks per TMA copy
 //     (3-D box, 32 KB); instances are small enough that J stays in L2;
-//   - for each 128-spin row block one tcgen05.mma chain (M = 128, N = BN)
-//     accumulates F = J S in tensor memory, double-buffered so that the next
-//     block's MMA overlaps the epilogue of this one;
+//   - for each 128-spin row block tcgen05.mma (M = 128, N = BN) accumulates
+//     F = J S in tensor memory, double-buffered so that the next block's MMA
+//     overlaps the epilogue of this one;
 //   - the epilogue (8 warps) applies the pinned update to x, y in global
 //     memory, writes sgn(x') as FP8, and on evaluation steps adds s_i f_i into
 //     per-replica integer sums; after the step the best energy and spins of
 //     each replica are updated in place (exact integers, strict <).
+// Roles: warps 0-1 stream J, one per stage (J does not change, so the next
+// step's first chunks load while the epilogue runs); warps 2-3 issue
+// tcgen05.mma from elected lanes, each consuming one stage into its own
+// accumulator (split K, exact integer partial forces) when BN <= 128 and a
+// row block has two or more loads, warp 2 alone otherwise; warp 2 also loads
+// the resident S of each step; warps 4-11 are the epilogue.  Every stage has one
+// producer and one consumer, so each mbarrier phase is awaited in order.
 // Every wait is bounded; a wait that gives up raises the error word and the
 // CTA stops taking instances.
 #include <cuda.h>
@@ -40,7 +47,8 @@ constexpr int kGStages = 2;
 constexpr int kGStageA = 2 * kTM * 128;  // two K chunks of J, 32 KB
 constexpr int kGEpiWarps = 8;
 constexpr int kGEpiThreads = 32 * kGEpiWarps;
-constexpr int kGThreads = 64 + kGEpiThreads;
+constexpr int kGFirstEpi = 4;            // 2 J producers, 2 MMA warps
+constexpr int kGThreads = 32 * kGFirstEpi + kGEpiThreads;
 
 struct __align__(8) GShared {
     uint64_t full[kGStages];
@@ -75,10 +83,35 @@ __device__ __forceinline__ bool gbar_or(bool pred)
     return r != 0;
 }
 
-__device__ __forceinline__ void mma_fp8_n(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t acc)
+// tcgen05.mma from an elected lane of the converged warp (warp-uniform
+// operands issue faster than from one divergent thread).
+__device__ __forceinline__ void mma_fp8_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                              uint32_t idesc, uint32_t acc)
 {
-    ptx::mma_fp8(tmem_d, adesc, bdesc, idesc, acc);
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void commit_elect(uint64_t *bar)
+{
+    asm volatile(
+        "{\n\t.reg .pred e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}" ::"r"(
+            ptx::smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait by every lane; false in all lanes if any gave up.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *abort, int *err)
+{
+    const bool ok = ptx::mbar_wait(bar, parity, abort, err);
+    return __all_sync(0xFFFFFFFFu, ok);
 }
 
 }  // namespace
@@ -104,13 +137,13 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
         ptx::mbar_init(&sh->s_full, 1);
         ptx::mbar_init(&sh->step_done, 1);
         for (int b = 0; b < 2; ++b) {
-            ptx::mbar_init(&sh->acc_full[b], 1);
+            ptx::mbar_init(&sh->acc_full[b], 2);  // one arrival per MMA warp
             ptx::mbar_init(&sh->acc_empty[b], 1);
         }
         sh->abort = 0;
         ptx::mbar_init_fence();
     }
-    if (warp == 1)
+    if (warp == 2)
         ptx::tmem_alloc(&sh->tmem_base, 512);
     ptx::tc_fence_before();
     __syncthreads();
@@ -136,23 +169,25 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
         const int npairs = (nblk + 1) >> 1;
         const int passes = a.steps + 1;  // updates, then the final evaluation
 
-        if (warp == 0) {
-            // ------------------------------------------------------ producer
+        // K is split over the two MMA warps (each into its own accumulator,
+        // the loads of stage p to warp p) when the accumulators fit and every
+        // row block has at least two loads
+        const bool split = BN <= 128 && npairs >= 2;
+
+        if (warp < 2) {
+            // --------------------------------------------------- J producers
+            // producer p fills stage p (loads g with g % 2 == p); J does not
+            // change, so the next step's first chunks load during the epilogue
             if (lane == 0) {
+                const int pw = warp;
                 ptx::prefetch_tmap(&in.mapA);
                 bool fail = false;
-                for (int k = 0; k < passes && !fail; ++k) {
-                    // the operand of step k is complete once the previous step's
-                    // epilogue (or the initial state) is done
-                    if (!ptx::mbar_wait(&sh->step_done, sdone & 1u, &sh->abort, a.err))
-                        break;
-                    ++sdone;
-                    ptx::fence_proxy_async_global();
-                    ptx::mbar_expect_tx(&sh->s_full, (uint32_t)(BN * Np));
-                    ptx::tma_load_3d(sS, &in.mapS[k & 1], 0, 0, 0, &sh->s_full);
+                for (int k = 0; k < passes && !fail; ++k)
                     for (int mb = 0; mb < nblk && !fail; ++mb)
-                        for (int p = 0; p < npairs; ++p) {
-                            const int s = (int)(g % kGStages);
+                        for (int p = 0; p < npairs; ++p, ++g) {
+                            if ((int)(g & 1u) != pw)
+                                continue;
+                            const int s = pw;
                             const uint32_t ph = (g / kGStages) & 1u;
                             if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err)) {
                                 fail = true;
@@ -161,66 +196,86 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                             ptx::mbar_expect_tx(&sh->full[s], (uint32_t)kGStageA);
                             ptx::tma_load_3d(sA + (size_t)s * kGStageA, &in.mapA, 0, mb * kTM,
                                              2 * p, &sh->full[s]);
-                            ++g;
                         }
-                }
             }
-        } else if (warp == 1) {
+        } else if (warp < kGFirstEpi) {
             // ----------------------------------------------------------- MMA
-            if (lane == 0) {
-                const uint32_t idesc = ptx::idesc_e4m3_f32(kTM, BN);
-                const uint32_t sbase = ptx::smem_u32(sS);
-                bool ok = true;
-                for (int k = 0; k < passes && ok; ++k) {
-                    if (!ptx::mbar_wait(&sh->s_full, sfull & 1u, &sh->abort, a.err))
+            // warp 2 + pw consumes stage pw (with the split) or every stage
+            // (warp 2, without it), always in load order; warp 2 also loads
+            // the resident S of each step (its MMAs cannot start before)
+            const int pw = warp - 2;
+            const uint32_t idesc = ptx::idesc_e4m3_f32(kTM, BN);
+            const uint64_t sdesc0 = ptx::sw128_desc(ptx::smem_u32(sS));
+            const uint64_t adesc0 = ptx::sw128_desc(ptx::smem_u32(sA));
+            bool ok = true;
+            for (int k = 0; k < passes && ok; ++k) {
+                if (pw == 0) {
+                    // the operand of step k is complete once the previous
+                    // step's epilogue (or the initial state) is done
+                    if (!warp_wait(&sh->step_done, sdone & 1u, &sh->abort, a.err))
                         break;
-                    ++sfull;
+                    ++sdone;
+                    if (lane == 0) {
+                        ptx::fence_proxy_async_global();
+                        ptx::mbar_expect_tx(&sh->s_full, (uint32_t)(BN * Np));
+                        ptx::tma_load_3d(sS, &in.mapS[k & 1], 0, 0, 0, &sh->s_full);
+                    }
+                    __syncwarp();
+                }
+                if (!warp_wait(&sh->s_full, sfull & 1u, &sh->abort, a.err))
+                    break;
+                ++sfull;
+                ptx::tc_fence_after();
+                for (int mb = 0; mb < nblk && ok; ++mb) {
+                    const uint32_t buf = tile & 1u;
+                    if (!warp_wait(&sh->acc_empty[buf], ((tile >> 1) & 1u) ^ 1u, &sh->abort,
+                                   a.err)) {
+                        ok = false;
+                        break;
+                    }
                     ptx::tc_fence_after();
-                    for (int mb = 0; mb < nblk && ok; ++mb) {
-                        const uint32_t buf = tile & 1u;
-                        if (!ptx::mbar_wait(&sh->acc_empty[buf], ((tile >> 1) & 1u) ^ 1u,
-                                            &sh->abort, a.err)) {
+                    const uint32_t dcol =
+                        tmem + (split ? buf * 2u + (uint32_t)pw : buf) * (uint32_t)BN;
+                    int mine = 0;
+                    for (int p = 0; p < npairs; ++p, ++g) {
+                        const int s = (int)(g % kGStages);
+                        if (split ? s != pw : pw != 0)
+                            continue;
+                        const uint32_t ph = (g / kGStages) & 1u;
+                        if (!warp_wait(&sh->full[s], ph, &sh->abort, a.err)) {
                             ok = false;
                             break;
                         }
                         ptx::tc_fence_after();
-                        const uint32_t dcol = tmem + buf * (uint32_t)BN;
-                        for (int p = 0; p < npairs; ++p) {
-                            const int s = (int)(g % kGStages);
-                            const uint32_t ph = (g / kGStages) & 1u;
-                            if (!ptx::mbar_wait(&sh->full[s], ph, &sh->abort, a.err)) {
-                                ok = false;
+                        for (int c = 0; c < 2; ++c) {
+                            const int kc = 2 * p + c;
+                            if (kc >= nblk)
                                 break;
-                            }
-                            ptx::tc_fence_after();
-                            for (int c = 0; c < 2; ++c) {
-                                const int kc = 2 * p + c;
-                                if (kc >= nblk)
-                                    break;
-                                const uint32_t a0 =
-                                    ptx::smem_u32(sA + (size_t)s * kGStageA + c * kTM * 128);
-                                const uint32_t b0 = sbase + (uint32_t)(kc * BN * 128);
+                            const uint64_t ad =
+                                adesc0 + (uint64_t)(((size_t)s * kGStageA + c * kTM * 128) >> 4);
+                            const uint64_t bd = sdesc0 + (uint64_t)((kc * BN * 128) >> 4);
 #pragma unroll
-                                for (int kk = 0; kk < 4; ++kk)
-                                    mma_fp8_n(dcol, ptx::sw128_desc(a0 + kk * 32),
-                                              ptx::sw128_desc(b0 + kk * 32), idesc,
-                                              (p | c | kk) != 0 ? 1u : 0u);
-                            }
-                            ptx::mma_commit(&sh->empty[s]);
-                            ++g;
+                            for (int kk = 0; kk < 4; ++kk)
+                                mma_fp8_elect(dcol, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
+                                              idesc, (mine | c | kk) != 0 ? 1u : 0u);
                         }
-                        if (!ok)
-                            break;
-                        ptx::mma_commit(&sh->acc_full[buf]);
-                        ++tile;
+                        commit_elect(&sh->empty[s]);
+                        ++mine;
                     }
+                    if (!ok)
+                        break;
+                    if (mine > 0)
+                        commit_elect(&sh->acc_full[buf]);
+                    else if (lane == 0)
+                        ptx::mbar_arrive(&sh->acc_full[buf]);  // no load of this tile here
+                    ++tile;
                 }
             }
         } else {
             // ------------------------------------------------------ epilogue
-            const int et = threadIdx.x - 64;           // 0..255
-            const int q = warp & 3;                    // lane quadrant
-            const int half = (warp - 2) >> 2;          // column half
+            const int et = threadIdx.x - 32 * kGFirstEpi;  // 0..255
+            const int q = warp & 3;                        // lane quadrant
+            const int half = (warp - kGFirstEpi) >> 2;     // column half
             const int cw = BN / 2;                     // columns per warp (multiple of 16)
             const int cbase = half * cw;
             const uint32_t lane_off = (uint32_t)(q * 32) << 16;
@@ -287,9 +342,12 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     ++tile;
                     ptx::tc_fence_after();
                     for (int cb = 0; cb < cw; cb += 16) {
-                        uint32_t f[16];
-                        ptx::tmem_ld16(tmem + buf * (uint32_t)BN + lane_off + (uint32_t)(cbase + cb),
-                                       f);
+                        uint32_t f[16], f1[16];
+                        const uint32_t acol = tmem + (split ? buf * 2u : buf) * (uint32_t)BN +
+                                              lane_off + (uint32_t)(cbase + cb);
+                        ptx::tmem_ld16(acol, f);
+                        if (split)
+                            ptx::tmem_ld16(acol + (uint32_t)BN, f1);
                         // next chunk's x, y in flight while this chunk computes
                         float xn[16], yn[16];
                         const bool more = cb + 16 < cw;
@@ -300,6 +358,13 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                             yn[j] = more ? in.Y[e] : 0.f;
                         }
                         ptx::tmem_ld_wait();
+                        if (split) {
+                            // partial forces over disjoint K ranges: exact integers
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                f[j] = __float_as_uint(
+                                    __fadd_rn(__uint_as_float(f[j]), __uint_as_float(f1[j])));
+                        }
                         if (ev) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
@@ -353,7 +418,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                         sh->improved[r] = take;
                     }
                     gbar();
-                    const int w = warp - 2;
+                    const int w = warp - kGFirstEpi;
                     for (int r = w; r < R; r += kGEpiWarps)
                         if (sh->improved[r])
                             for (int i = lane; i < N; i += 32)
@@ -378,7 +443,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    if (warp == 1)
+    if (warp == 2)
         ptx::tmem_dealloc(tmem, 512);
 }
 
