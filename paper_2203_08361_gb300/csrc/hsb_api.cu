@@ -12,7 +12,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "hsb.h"
@@ -791,6 +794,98 @@ hsb_status report_error(hsb_status s, const char *msg)
 
 // =================================================================== ABI ===
 
+namespace {
+
+// ---- batch autotuner ---------------------------------------------------
+// The batched kernel runs one instance per CTA.  How many CTAs run at once
+// trades SMs against L2: the FP8 couplings of the instances in flight share
+// the L2, and once they exceed it every step re-reads them from HBM.  Whether
+// K is split over two MMA warps trades tensor issue rate against accumulator
+// room.  Every choice gives the same bits (each instance is computed by one
+// CTA, with exact integer forces), so the choice is made by timing: on the
+// first batch of a shape (device, instance count, replica width, total FP8
+// coupling bytes rounded to a power of two) each candidate runs the whole
+// queue for a short prefix of the steps, and the fastest is kept for the
+// process.
+struct BatchChoice {
+    int ctas = 0;
+    int split = 1;
+};
+
+struct BatchTuneKey {
+    int device, count, BN, log2bytes;
+    bool operator<(const BatchTuneKey &o) const
+    {
+        return std::tie(device, count, BN, log2bytes) <
+               std::tie(o.device, o.count, o.BN, o.log2bytes);
+    }
+};
+
+std::mutex g_tune_mu;
+std::map<BatchTuneKey, BatchChoice> g_tune;
+
+// CTA counts tried: the SM count down to a quarter of it.
+std::vector<int> batch_cta_candidates(int sms, int count)
+{
+    std::vector<int> v;
+    for (int num : {8, 7, 6, 5, 4, 3, 2}) {
+        int c = std::min(count, std::max(1, sms * num / 8));
+        if (std::find(v.begin(), v.end(), c) == v.end())
+            v.push_back(c);
+    }
+    return v;
+}
+
+// Times one launch of the queue (queue counter reset before); returns ms or
+// a negative value on error.
+float time_batch(cudaStream_t st, const BatchInst *d_insts, BatchArgs a, int ctas)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return -1.f;
+    float ms = -1.f;
+    if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st) == cudaSuccess &&
+        cudaEventRecord(e0, st) == cudaSuccess &&
+        launch_tc_fp8_batch(st, d_insts, a, ctas) == cudaSuccess &&
+        cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
+        cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+BatchChoice tune_batch(const BatchTuneKey &key, cudaStream_t st, const BatchInst *d_insts,
+                       const BatchArgs &a, int sms, int count)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end())
+            return it->second;
+    }
+    BatchArgs t = a;
+    t.steps = std::min(a.steps, 64);
+    t.eval_every = 0;
+    BatchChoice best;
+    best.ctas = std::min(count, sms);
+    float best_ms = -1.f;
+    for (int split = 1; split >= 0; --split)
+        for (int ctas : batch_cta_candidates(sms, count)) {
+            t.allow_split = split;
+            const float ms = time_batch(st, d_insts, t, ctas);
+            if (ms > 0.f && (best_ms < 0.f || ms < best_ms)) {
+                best_ms = ms;
+                best.ctas = ctas;
+                best.split = split;
+            }
+        }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+    return best;
+}
+
+}  // namespace
+
 extern "C" {
 
 int hsb_version(void) { return HSB_API_VERSION; }
@@ -1363,7 +1458,18 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
         a.err = hs[0]->err;
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, hs[0]->device);
-        e = launch_tc_fp8_batch(st, d_insts, a, std::min(count, std::max(sms, 1)));
+        sms = std::max(sms, 1);
+        double bytes = 0.0;
+        for (int b = 0; b < count; ++b)
+            bytes += (double)insts[(size_t)b].Np * insts[(size_t)b].Np;
+        const BatchTuneKey key{hs[0]->device, count, round_up(R, 32), (int)ceil(log2(bytes))};
+        const BatchChoice ch = tune_batch(key, st, d_insts, a, sms, count);
+        a.allow_split = ch.split;
+        e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned int), st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(hs[0]->err, 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = launch_tc_fp8_batch(st, d_insts, a, ch.ctas);
     }
     for (int b = 0; b < count && e == cudaSuccess; ++b) {
         hsb_ctx *h = hs[b];

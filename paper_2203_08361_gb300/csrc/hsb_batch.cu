@@ -172,7 +172,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
         // K is split over the two MMA warps (each into its own accumulator,
         // the loads of stage p to warp p) when the accumulators fit and every
         // row block has at least two loads
-        const bool split = BN <= 128 && npairs >= 2;
+        const bool split = a.allow_split && BN <= 128 && npairs >= 2;
 
         if (warp < 2) {
             // --------------------------------------------------- J producers
@@ -280,6 +280,14 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
             const int cbase = half * cw;
             const uint32_t lane_off = (uint32_t)(q * 32) << 16;
             const uint64_t s_inst = splitmix64_out(a.seed, (uint64_t)in.instance + 1u);
+            // the instance's buffers as local restrict pointers: read through
+            // the instance table, they would be reloaded after every store
+            float *__restrict__ X = in.X;
+            float *__restrict__ Y = in.Y;
+            uint8_t *__restrict__ S8a = in.S8a;
+            uint8_t *__restrict__ S8b = in.S8b;
+            double *__restrict__ Ebest = in.Ebest;
+            int8_t *__restrict__ Sbest = in.Sbest;
 
             // initial state: x, y uniform in (-L, L), S = sgn(x), best = +inf
             for (size_t e = et; e < (size_t)BN * Np; e += kGEpiThreads) {
@@ -291,12 +299,12 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     y = init_uniform(s_inst, (uint32_t)r, (uint32_t)i, 1, a.scale);
                     sg = fp8_sign(x);
                 }
-                in.X[e] = x;
-                in.Y[e] = y;
-                in.S8a[e] = sg;
+                X[e] = x;
+                Y[e] = y;
+                S8a[e] = sg;
             }
             for (int r = et; r < R; r += kGEpiThreads)
-                in.Ebest[r] = INFINITY;
+                Ebest[r] = INFINITY;
             for (int r = et; r < kMaxBN; r += kGEpiThreads)
                 sh->esum[r] = 0;
             ptx::fence_proxy_async_global();
@@ -318,8 +326,8 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                                 (a.eval_every > 0 && k > 0 && k % a.eval_every == 0);
                 const float pk = final_pass ? 0.f : a.pk[k];
                 const uint64_t pk2 = f2_pack(pk, pk);
-                const uint8_t *Sold = (k & 1) ? in.S8b : in.S8a;
-                uint8_t *Snew = (k & 1) ? in.S8a : in.S8b;
+                const uint8_t *Sold = (k & 1) ? S8b : S8a;
+                uint8_t *Snew = (k & 1) ? S8a : S8b;
                 for (int mb = 0; mb < nblk; ++mb) {
                     const uint32_t buf = tile & 1u;
                     const int i = mb * kTM + q * 32 + lane;
@@ -330,8 +338,8 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const size_t e = (size_t)(cbase + j) * Np + i;
-                        xr[j] = in.X[e];
-                        yr[j] = in.Y[e];
+                        xr[j] = X[e];
+                        yr[j] = Y[e];
                     }
                     const bool ok = ptx::mbar_wait(&sh->acc_full[buf], (tile >> 1) & 1u,
                                                    &sh->abort, a.err);
@@ -354,8 +362,8 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const size_t e = (size_t)(cbase + cb + 16 + j) * Np + i;
-                            xn[j] = more ? in.X[e] : 0.f;
-                            yn[j] = more ? in.Y[e] : 0.f;
+                            xn[j] = more ? X[e] : 0.f;
+                            yn[j] = more ? Y[e] : 0.f;
                         }
                         ptx::tmem_ld_wait();
                         if (split) {
@@ -387,10 +395,10 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                                 uint64_t yo;
                                 sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack(xr[j], xr[j + 1]),
                                            f2_pack(yr[j], yr[j + 1]), pk2, k2, xo0, xo1, yo);
-                                in.X[e] = xo0;
-                                in.X[e + Np] = xo1;
-                                in.Y[e] = f2_lo(yo);
-                                in.Y[e + Np] = f2_hi(yo);
+                                X[e] = xo0;
+                                X[e + Np] = xo1;
+                                Y[e] = f2_lo(yo);
+                                Y[e + Np] = f2_hi(yo);
                                 Snew[e] = live ? fp8_sign(xo0) : (uint8_t)0;
                                 Snew[e + Np] = live ? fp8_sign(xo1) : (uint8_t)0;
                             }
@@ -412,9 +420,9 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                 if (ev) {
                     for (int r = et; r < R; r += kGEpiThreads) {
                         const double E = -0.5 * (double)sh->esum[r];
-                        const int take = E < in.Ebest[r];
+                        const int take = E < Ebest[r];
                         if (take)
-                            in.Ebest[r] = E;
+                            Ebest[r] = E;
                         sh->improved[r] = take;
                     }
                     gbar();
@@ -422,7 +430,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     for (int r = w; r < R; r += kGEpiWarps)
                         if (sh->improved[r])
                             for (int i = lane; i < N; i += 32)
-                                in.Sbest[(size_t)r * N + i] =
+                                Sbest[(size_t)r * N + i] =
                                     Sold[(size_t)r * Np + i] == kFp8PlusOne ? (int8_t)1 : (int8_t)-1;
                     for (int r = et; r < kMaxBN; r += kGEpiThreads)
                         sh->esum[r] = 0;

@@ -186,6 +186,7 @@ struct BatchArgs {
     float scale;           // fl32(L * 2^-24) of the initial distribution
     uint64_t seed;
     int *err;
+    int allow_split;       // K may be split over the two MMA warps
 };
 
 bool batch_shape_ok(int Np, int R);
