@@ -138,6 +138,15 @@ HSB_API hsb_status hsb_set_stream(hsb_handle h, void *cuda_stream);
 /* Number of spins N and whether J is in {-1, 0, +1} (the FP8 path applies). */
 HSB_API hsb_status hsb_info(hsb_handle h, int *N, int *is_pm1);
 
+/* MAX-CUT front end (Results, Eq. (eq_Cut)): a MAX-CUT problem with weights
+ * w_ij = w_ji is the Ising problem with J_ij = -w_ij, and a spin vector with
+ * Ising energy E cuts C = -E/2 - (1/4) sum_ij J_ij.  Writes cut[r] for the
+ * energies best_energy[r], r = 0..R-1 (e.g. the output of hsb_run); both are
+ * caller-owned HOST arrays of R doubles.  sum_ij J_ij is summed row by row in
+ * binary64 when the couplings are set, so for integer weights the cut values
+ * are exact.  Errors: HSB_E_INVAL for a NULL argument or R < 1. */
+HSB_API hsb_status hsb_cut_values(hsb_handle h, int R, const double *best_energy, double *cut);
+
 /* Runs `steps` >= 1 heated SB steps for replicas r = 0..R-1 (R >= 1) from the
  * seeded initial state and returns, per replica, the best evaluated energy
  * best_energy[r] (float64) and its spins best_spins[r*N + i] (+1 / -1).

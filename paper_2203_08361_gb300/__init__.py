@@ -31,7 +31,8 @@ SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2, "resident": 3}
 EXPORTS = ["hsb_params_default", "hsb_version", "hsb_create", "hsb_destroy", "hsb_set_stream",
            "hsb_info", "hsb_run", "hsb_run_device", "hsb_get_state", "hsb_advance",
            "hsb_advance_device", "hsb_set_couplings", "hsb_run_stats", "hsb_synchronize",
-           "hsb_run_fp32_noalloc", "hsb_get_trace", "hsb_run_batch", "hsb_last_error"]
+           "hsb_run_fp32_noalloc", "hsb_get_trace", "hsb_run_batch", "hsb_cut_values",
+           "hsb_last_error"]
 
 
 class HsbError(RuntimeError):
@@ -88,6 +89,8 @@ def load():
         lib.hsb_set_stream.argtypes = [H, P]
         lib.hsb_info.restype = I
         lib.hsb_info.argtypes = [H, C.POINTER(I), C.POINTER(I)]
+        lib.hsb_cut_values.restype = I
+        lib.hsb_cut_values.argtypes = [H, I, P, P]
         lib.hsb_run.restype = I
         lib.hsb_run.argtypes = [H, C.POINTER(Params), I, I, C.c_uint64, P, P]
         lib.hsb_run_device.restype = I
@@ -165,6 +168,14 @@ def info(h: int):
     n, pm1 = C.c_int(), C.c_int()
     _check(load().hsb_info(C.c_void_p(h), C.byref(n), C.byref(pm1)))
     return n.value, bool(pm1.value)
+
+
+def cut_values(h: int, best_energy: np.ndarray) -> np.ndarray:
+    """hsb_cut_values: MAX-CUT values (weights w = -J) of the given energies."""
+    e = np.ascontiguousarray(best_energy, dtype=np.float64)
+    cut = np.empty_like(e)
+    _check(load().hsb_cut_values(C.c_void_p(h), int(e.shape[0]), _ptr(e), _ptr(cut)))
+    return cut
 
 
 def run(h: int, p: Params, R: int, steps: int, seed: int):
@@ -276,6 +287,9 @@ class Solver:
 
     def get_state(self, R: int):
         return get_state(self.h, R)
+
+    def cut_values(self, best_energy):
+        return cut_values(self.h, best_energy)
 
     def advance(self, p, steps, k_begin, k_end, x, y):
         return advance(self.h, p, steps, k_begin, k_end, x, y)

@@ -89,6 +89,7 @@ struct RunCfg {
 struct hsb_ctx {
     int N = 0, Np = 0, device = 0, pm1 = 0;
     double sigma = 0.0;
+    double sumJ = 0.0;  // sum_ij J_ij in binary64, row by row (cut values, Eq. (eq_Cut))
     cudaStream_t work = nullptr;     // where work is queued (user's or own)
     cudaStream_t own = nullptr;      // private stream (default work stream, capture stream)
     float *J32 = nullptr;            // [Np][Np]
@@ -922,7 +923,7 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
         return set_error(HSB_E_INVAL, "N must be in [2, 2^20] (got %d)", N);
     // Eq. (eq_Ising): J_ij = J_ji and J_ii = 0.
     int pm1 = 1;
-    double sum2 = 0.0;
+    double sum2 = 0.0, sumJ = 0.0;
     for (int i = 0; i < N; ++i) {
         if (J[(size_t)i * N + i] != 0.0f)
             return set_error(HSB_E_DIAG, "J[%d][%d] = %g is not zero", i, i,
@@ -936,6 +937,7 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
             // sigma_J^2 = sum_ij J_ij^2 / (N(N-1)), summed row by row in binary64
             const double d = (double)v;
             sum2 += d * d;
+            sumJ += d;
         }
     }
     if (!(sum2 > 0.0))
@@ -951,6 +953,7 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
     h->Np = round_up(N, kTileM);
     h->pm1 = pm1;
     h->sigma = sqrt(sum2 / ((double)N * (double)(N - 1)));
+    h->sumJ = sumJ;
     hsb_status s = HSB_OK;
     do {
         cudaError_t e = cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking);
@@ -1030,6 +1033,18 @@ hsb_status hsb_info(hsb_handle h, int *N, int *is_pm1)
         *N = h->N;
     if (is_pm1)
         *is_pm1 = h->pm1;
+    return HSB_OK;
+}
+
+hsb_status hsb_cut_values(hsb_handle h, int R, const double *best_energy, double *cut)
+{
+    if (!h || !best_energy || !cut)
+        return set_error(HSB_E_INVAL, "hsb_cut_values: null argument");
+    if (R < 1)
+        return set_error(HSB_E_INVAL, "R must be >= 1 (got %d)", R);
+    // Eq. (eq_Cut) with w_ij = -J_ij: C = -E/2 - (1/4) sum_ij J_ij
+    for (int r = 0; r < R; ++r)
+        cut[r] = -0.5 * best_energy[r] - 0.25 * h->sumJ;
     return HSB_OK;
 }
 
@@ -1275,7 +1290,7 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
         return set_error(HSB_E_INVAL, "J is NULL");
     const int N = h->N;
     int pm1 = 1;
-    double sum2 = 0.0;
+    double sum2 = 0.0, sumJ = 0.0;
     for (int i = 0; i < N; ++i) {
         if (J[(size_t)i * N + i] != 0.0f)
             return set_error(HSB_E_DIAG, "J[%d][%d] = %g is not zero", i, i,
@@ -1288,6 +1303,7 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
                 pm1 = 0;
             const double d = (double)v;
             sum2 += d * d;
+            sumJ += d;
         }
     }
     if (!(sum2 > 0.0))
@@ -1301,6 +1317,7 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
        "copy J");
     h->pm1 = pm1;
     h->sigma = sqrt(sum2 / ((double)N * (double)(N - 1)));
+    h->sumJ = sumJ;
     if (h->J8) {
         if (pm1) {
             CK(launch_j_to_fp8(h->work, h->J32, h->Np, h->J8), "j_to_fp8");

@@ -1,0 +1,37 @@
+"""Trial statistics of the evaluation harness (Results: P and step-to-solution
+S = N_s log(0.01) / log(1 - P)), checked against closed forms."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2203_08361_gb300 import evaluation as ev
+
+
+def test_step_to_solution_closed_forms():
+    # log(0.01) / log(0.1) = 2 and log(0.01) / log(0.5) = log2(100)
+    assert ev.step_to_solution(0.9, 100) == pytest.approx(200.0, rel=1e-15)
+    assert ev.step_to_solution(0.5, 100) == pytest.approx(100 * math.log2(100.0), rel=1e-14)
+    # one run succeeds with probability >= 0.99: S = N_s; continuous at 0.99
+    assert ev.step_to_solution(0.99, 700) == 700.0
+    assert ev.step_to_solution(1.0, 700) == 700.0
+    assert ev.step_to_solution(0.98999999, 700) == pytest.approx(700.0, rel=1e-5)
+    assert ev.step_to_solution(0.0, 50) == math.inf
+    # fewer successes need more steps
+    ps = np.linspace(0.01, 0.98, 50)
+    s = [ev.step_to_solution(float(p), 100) for p in ps]
+    assert all(a > b for a, b in zip(s, s[1:]))
+    with pytest.raises(ValueError):
+        ev.step_to_solution(1.5, 10)
+    with pytest.raises(ValueError):
+        ev.step_to_solution(0.5, 0)
+
+
+def test_success_probability_counts_trials_at_or_below_target():
+    e = np.array([-10.0, -12.0, -12.0, -11.0, -9.0])
+    assert ev.success_probability(e, -12.0) == pytest.approx(0.4)
+    assert ev.success_probability(e, -11.0) == pytest.approx(0.6)
+    assert ev.success_probability(e, -13.0) == 0.0
+    assert ev.success_probability(e, -11.5, tol=0.6) == pytest.approx(0.6)
+    with pytest.raises(ValueError):
+        ev.success_probability([], 0.0)
