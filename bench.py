@@ -382,6 +382,163 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------- the other configurations ---
+# The same measurement for the other workloads of the library's configuration
+# list (not the headline line): the Gaussian-coupling BF16x3 run, the batch of
+# uneven instances, and the large streamed instance.  `--workload NAME`.
+
+OTHER = {
+    "gauss2000": dict(name="HbSB Gaussian SK N=2000 R=1024 5000 steps BF16x3", kind="single",
+                      N=2000, J="gauss", J_seed=2, R=1024, sb_steps=5000, form="ballistic",
+                      prec="bf16x3", c1=0.9, dt=1.1, gamma=0.5, eval_every=100, trace_every=0,
+                      peak="bf16", dtype="bf16x3"),
+    "sk16384": dict(name="HdSB SK +/-1 N=16384 R=4096 10000 steps FP8 with per-step trace",
+                    kind="single", N=16384, J="pm1", J_seed=3, R=4096, sb_steps=10000,
+                    form="discrete", prec="fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
+                    trace_every=1, peak="fp8", dtype="fp8"),
+    "batch256": dict(name="HdSB 256 SK +/-1 instances, N uniform in [100, 2000], R=64, 2000 "
+                          "steps, FP8, one batched launch", kind="batch", count=256, sizes_seed=4,
+                     R=64, sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1,
+                     gamma=0.06, eval_every=100, trace_every=0, peak="fp8", dtype="fp8"),
+}
+
+
+def _other_couplings(w):
+    import synth
+    if w["kind"] == "batch":
+        sizes = [int(v) for v in synth.batch_sizes(w["count"], w["sizes_seed"])]
+        return [synth.sk_pm1(n, 500 + b) for b, n in enumerate(sizes)]
+    gen = synth.sk_gauss if w["J"] == "gauss" else synth.sk_pm1
+    return [gen(w["N"], w["J_seed"])]
+
+
+def _other_cpu_baseline(w, Js, target_s=10.0):
+    """The binary32 oracle on a bounded sample: the first instance, one
+    replica per thread, steps calibrated to about target_s seconds."""
+    import oracle
+    cores = os.cpu_count() or 1
+    J = Js[0]
+    op = oracle.make_params(0 if w["form"] == "ballistic" else 1,
+                            oracle.c0_from_c1(J, w["c1"]), w["dt"], w["gamma"],
+                            eval_every=w["eval_every"])
+    t0 = time.perf_counter()
+    oracle.run(J, op, 4, 1, range(cores), "f32", nthreads=cores)
+    rate = J.shape[0] * cores * 4 / (time.perf_counter() - t0)
+    steps = int(max(4, min(w["sb_steps"], target_s * rate / (J.shape[0] * cores))))
+    t0 = time.perf_counter()
+    oracle.run(J, op, steps, 1, range(cores), "f32", nthreads=cores)
+    t = time.perf_counter() - t0
+    return {"value": J.shape[0] * cores * steps / t, "unit": UNIT, "cores": cores,
+            "kind": "oracle",
+            "sample": f"{cores} replicas x {steps} steps of instance 0 (N={J.shape[0]}), "
+                      f"binary32 oracle, {cores} threads, {t:.1f} s"}
+
+
+def run_other(args, w):
+    import torch
+    import paper_2203_08361_gb300 as hsb
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    world, rank, local = _dist_env()
+    torch.cuda.set_device(local)
+    R, S = w["R"], w["sb_steps"]
+    Js = _other_couplings(w)
+    p = hsb.params(w["form"], w["prec"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
+                   eval_every=w["eval_every"], trace_every=w["trace_every"])
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    units = sum(J.shape[0] for J in Js) * R * S            # replica-spin-steps per run
+    flops = sum(2.0 * J.shape[0] ** 2 for J in Js) * R * S  # algorithmic
+    seed = 1000 + rank
+    clocks = ClockSampler(torch.cuda.current_device())
+    if w["kind"] == "batch":
+        solvers = [hsb.Solver(J) for J in Js]
+        hs = [s.h for s in solvers]
+        for _ in range(max(args.warmup, 3)):
+            hsb.run_batch(hs, p, R, S, seed)  # the first call also tunes the launch
+        times = []
+        clocks.start()
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hsb.run_batch(hs, p, R, S, seed)  # host outputs: the whole call
+            times.append(time.perf_counter() - t0)
+        clock_rec = clocks.stop()
+        t_run = sum(times) / len(times)
+        e2e_t, launches = t_run, 1
+        for s in solvers:
+            s.close()
+        timing = "host wall clock around hsb_run_batch (one launch plus output copies)"
+    else:
+        stream = torch.cuda.Stream()
+        solver = hsb.Solver(Js[0])
+        solver.set_stream(stream.cuda_stream)
+        N = Js[0].shape[0]
+        spins = torch.empty((R, N), dtype=torch.int8, device="cuda")
+        energy = torch.empty(R, dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            for _ in range(max(args.warmup, 3)):
+                solver.run_device(p, R, S, seed, spins.data_ptr(), energy.data_ptr())
+            solver.synchronize()
+            launches = solver.run_stats()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            clocks.start()
+            for i in range(args.steps):
+                flush.fill_(i & 0xFF)
+                ev[i][0].record(stream)
+                solver.run_device(p, R, S, seed, spins.data_ptr(), energy.data_ptr())
+                ev[i][1].record(stream)
+            solver.synchronize()
+            torch.cuda.synchronize()
+            clock_rec = clocks.stop()
+        t_run = sum(a.elapsed_time(b) for a, b in ev) / args.steps / 1000.0
+        pin_J = torch.from_numpy(Js[0]).pin_memory()
+        import ctypes as C
+        lib = hsb.load()
+        out_s = torch.empty((R, N), dtype=torch.int8).pin_memory()
+        out_e = torch.empty(R, dtype=torch.float64).pin_memory()
+        t0 = time.perf_counter()
+        st = lib.hsb_set_couplings(C.c_void_p(solver.h), C.c_void_p(pin_J.data_ptr()))
+        if st == 0:
+            st = lib.hsb_run(C.c_void_p(solver.h), C.byref(p), R, S, C.c_uint64(seed),
+                             C.c_void_p(out_s.data_ptr()), C.c_void_p(out_e.data_ptr()))
+        if st != 0:
+            raise hsb.HsbError(st, lib.hsb_last_error().decode())
+        e2e_t = time.perf_counter() - t0
+        solver.close()
+        timing = "CUDA events on the solver's stream around each whole run"
+    mp, src = _peaks()
+    bf16 = float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops")))
+    peak = 2.0 * bf16 if w["peak"] == "fp8" else bf16
+    achieved = flops / t_run / 1e12
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": (f"{'FP8 dense = 2 x ' if w['peak'] == 'fp8' else ''}bf16 "
+                                f"sustained of {src} peaks"),
+                "scope": "whole run (force, update, evaluations, final energies); "
+                         "algorithmic 2 N^2 R per step"}
+    if w["prec"] == "bf16x3":
+        roofline["executed_tflops"] = 3.0 * achieved
+    line = {"metric": f"replica-spin-steps/s ({w['name']})", "value": units / t_run,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": 1000.0 * t_run, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
+            "config": {"workload": w["name"], "R": R, "sb_steps": S,
+                       "l2": "256 MiB buffer written between timed runs", "timing": timing},
+            "roofline": roofline, "clocks": clock_rec,
+            "e2e": {"value": units / e2e_t, "unit": UNIT,
+                    "h2d_bytes_per_step": 0 if w["kind"] == "batch" else int(Js[0].size * 4),
+                    "d2h_bytes_per_step": int(sum(J.shape[0] for J in Js) * R + 8 * R * len(Js))},
+            "gpu_launches": int(launches * args.steps)}
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _other_cpu_baseline(w, Js)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -391,6 +548,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-baseline", action="store_true",
                     help="skip the plain FP32 GPU comparison (e.g. for launch-list captures)")
+    ap.add_argument("--workload", choices=["sk2000"] + sorted(OTHER), default="sk2000",
+                    help="sk2000 (default): the headline line; the others measure the "
+                         "remaining configurations the same way")
     ap.add_argument("--sb-steps", type=int, default=None,
                     help="override the SB steps per run (profiling of small cases only; "
                          "the headline workload is 2000)")
@@ -402,6 +562,11 @@ def main():
         WORKLOAD["name"] = WORKLOAD["name"].replace("2000 steps", f"{args.sb_steps} steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "sk2000":
+        w = dict(OTHER[args.workload])
+        if args.sb_steps:
+            w["sb_steps"] = int(args.sb_steps)
+        return run_other(args, w)
     return run_gpu(args)
 
 

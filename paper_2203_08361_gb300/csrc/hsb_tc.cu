@@ -274,36 +274,59 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                     fetch(col0);
                 ptx::tmem_ld_wait();
 #pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    const int col = col0 + jj;
-                    const int r = r0 + col;
-                    const float fj = __uint_as_float(fr[jj]);
-                    float term = 0.f, t2 = 0.f;
-                    if (r < Rp) {
-                        const size_t e = (size_t)r * Np + i;
-                        const float x0 = xv[jj];
-                        if (energy || energy_only)
-                            term = live ? (x0 >= 0.f ? fj : -fj) : 0.f;
-                        if (!energy_only) {
-                            const float y0 = yv[jj];
-                            if (Tpart)
-                                t2 = __fmul_rn(y0, y0);  // y_i(t_k)^2 (Eq. eq_TInst)
-                            float xn, yn;
-                            sb_update(fj, x0, y0, pk, c, xn, yn);
-                            X[e] = xn;
-                            Y[e] = yn;
-                            S8next[e] = live ? fp8_sign(xn) : (uint8_t)0;
+                for (int hh = 0; hh < 2; ++hh) {
+                    // partial sums over this warp's 32 spins of 16 columns:
+                    // s_i f_i (evaluations) and y_i(t_k)^2 (trace)
+                    float tv[16], t2v[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int jj = hh * 16 + u;
+                        const int r = r0 + col0 + jj;
+                        const float fj = __uint_as_float(fr[jj]);
+                        float term = 0.f, t2 = 0.f;
+                        if (r < Rp) {
+                            const size_t e = (size_t)r * Np + i;
+                            const float x0 = xv[jj];
+                            if (energy || energy_only)
+                                term = live ? (x0 >= 0.f ? fj : -fj) : 0.f;
+                            if (!energy_only) {
+                                const float y0 = yv[jj];
+                                if (Tpart)
+                                    t2 = __fmul_rn(y0, y0);  // y_i(t_k)^2 (Eq. eq_TInst)
+                                float xn, yn;
+                                sb_update(fj, x0, y0, pk, c, xn, yn);
+                                X[e] = xn;
+                                Y[e] = yn;
+                                S8next[e] = live ? fp8_sign(xn) : (uint8_t)0;
+                            }
                         }
+                        tv[u] = term;
+                        t2v[u] = t2;
                     }
                     if (reduce) {
+                        // transposed butterfly: after the exchanges over lane
+                        // bits 4..1 (8 + 4 + 2 + 1 shuffles per quantity) and
+                        // one over bit 0, lane l holds the sum over all 32
+                        // lanes of column (l >> 1) & 15
 #pragma unroll
-                        for (int off = 16; off > 0; off >>= 1) {
-                            term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
-                            t2 += __shfl_xor_sync(0xFFFFFFFFu, t2, off);
+                        for (int m = 16, n = 8; m >= 2; m >>= 1, n >>= 1) {
+                            const bool up = (lane & m) != 0;
+#pragma unroll
+                            for (int k = 0; k < n; ++k) {
+                                const float sa = up ? tv[k] : tv[k + n];
+                                const float sb = up ? t2v[k] : t2v[k + n];
+                                const float ra = __shfl_xor_sync(0xFFFFFFFFu, sa, m);
+                                const float rb = __shfl_xor_sync(0xFFFFFFFFu, sb, m);
+                                tv[k] = (up ? tv[k + n] : tv[k]) + ra;
+                                t2v[k] = (up ? t2v[k + n] : t2v[k]) + rb;
+                            }
                         }
-                        if (lane == 0) {
-                            sh->red[q][col] = term;
-                            sh->tred[q][col] = t2;
+                        const float ta = tv[0] + __shfl_xor_sync(0xFFFFFFFFu, tv[0], 1);
+                        const float tb = t2v[0] + __shfl_xor_sync(0xFFFFFFFFu, t2v[0], 1);
+                        if ((lane & 1) == 0) {
+                            const int col = col0 + hh * 16 + ((lane >> 1) & 15);
+                            sh->red[q][col] = ta;
+                            sh->tred[q][col] = tb;
                         }
                     }
                 }
