@@ -15,6 +15,10 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
                       reduction to plain bSB/dSB, wall invariants, conserved
                       quadratic form per eigenmode, linear heating map, N = 2
                       normal modes, replica independence, determinism
+  run, Nose-Hoover -- large-M reduction to constant heating gamma = -xi0,
+                      the conserved quantity M xi^2 + S - N T ln S of the
+                      force-free thermostat, time average of T_inst equal to
+                      T, the heating / cooling direction of xi
 """
 from __future__ import annotations
 
@@ -62,6 +66,10 @@ class Params(C.Structure):
         ("instance", C.c_uint32),
         ("force_plain_sum", C.c_int),
         ("trace_every", C.c_int),
+        ("thermostat", C.c_int),
+        ("nh_T", C.c_double),
+        ("nh_M", C.c_double),
+        ("nh_xi0", C.c_double),
     ]
 
 
@@ -102,7 +110,7 @@ def _load():
             rn = getattr(lib, f"oracle_run_{sfx}")
             rn.restype = C.c_int
             rn.argtypes = [P, C.c_int, C.POINTER(Params), C.c_int, C.c_uint64, C.c_int, P, P, P,
-                           P, P, P, P, P, C.c_int]
+                           P, P, P, P, P, P, C.c_int]
         _lib = lib
         return lib
 
@@ -226,11 +234,17 @@ def step(J, x, y, form: int, pk: float, c0: float, dt: float, q: float, g: float
 
 def make_params(form: int, c0: float, dt: float, gamma: float, a0: float = 1.0,
                 init_half_width: float = 1.0, eval_every: int = 100, instance: int = 0,
-                force_plain_sum: bool = False, trace_every: int = 0) -> Params:
+                force_plain_sum: bool = False, trace_every: int = 0,
+                nose_hoover: bool = False, nh_T: float = 0.0, nh_M: float = 1.0,
+                nh_xi0: float = 0.0) -> Params:
+    """Run parameters; nose_hoover=True replaces the constant heating gamma by
+    the dynamic xi of Eqs. (eq_NH1), (eq_NH) with temperature nh_T, mass nh_M
+    and xi(t_0) = nh_xi0."""
     return Params(form=int(form), eval_every=int(eval_every), a0=float(a0), c0=float(c0),
                   dt=float(dt), gamma=float(gamma), init_half_width=float(init_half_width),
                   instance=int(instance), force_plain_sum=int(bool(force_plain_sum)),
-                  trace_every=int(trace_every))
+                  trace_every=int(trace_every), thermostat=1 if nose_hoover else 0,
+                  nh_T=float(nh_T), nh_M=float(nh_M), nh_xi0=float(nh_xi0))
 
 
 def num_traced(steps: int, trace_every: int) -> int:
@@ -242,7 +256,9 @@ def run(J, params: Params, steps: int, seed: int, reps, precision: str = "f64",
     """Whole run for the replica indices `reps`.
 
     Returns dict(best_e [nrep] float64, best_s [nrep, N] int8, x, y [nrep, N]
-    in the working precision, e_trace [nrep, n_evals] or None).
+    in the working precision, e_trace [nrep, n_evals] or None, trace_e /
+    trace_t [nrep, n_traced] or None, xi [nrep] float64: the Nose-Hoover
+    variable after the last step).
     """
     J = _coupling(J)
     real = _real(precision)
@@ -258,13 +274,14 @@ def run(J, params: Params, steps: int, seed: int, reps, precision: str = "f64",
     nt = num_traced(steps, params.trace_every)
     tr_e = np.zeros((nrep, nt), np.float64) if nt else None
     tr_t = np.zeros((nrep, nt), np.float64) if nt else None
+    xi = np.zeros(nrep, np.float64)
     fn = getattr(_load(), f"oracle_run_{precision}")
     rc = fn(_ptr(J), n, C.byref(params), int(steps), C.c_uint64(seed & (2**64 - 1)), nrep,
             _ptr(reps), _ptr(best_s), _ptr(best_e), _ptr(x), _ptr(y),
             _ptr(trace) if trace is not None else None,
             _ptr(tr_e) if tr_e is not None else None,
-            _ptr(tr_t) if tr_t is not None else None, int(nthreads))
+            _ptr(tr_t) if tr_t is not None else None, _ptr(xi), int(nthreads))
     if rc != 0:
         raise RuntimeError(f"oracle_run failed ({rc})")
     return {"best_e": best_e, "best_s": best_s, "x": x, "y": y, "e_trace": trace,
-            "trace_e": tr_e, "trace_t": tr_t}
+            "trace_e": tr_e, "trace_t": tr_t, "xi": xi}

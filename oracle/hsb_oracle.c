@@ -43,6 +43,14 @@
  *   - evaluation steps are t_k for k = m*eval_every (m >= 1, k < Ns) and
  *     k = Ns; eval_every = 0 evaluates the final step only.  A new best needs
  *     a strictly lower energy, so the earliest step wins ties.
+ *   - Nose-Hoover SB (Eqs. eq_NH1, eq_NH; the paper gives no discretisation):
+ *     the friction term -xi y_i takes the place of the heating term, so step k
+ *     uses g_k = -xi_k dt (binary64, rounded once to the working precision)
+ *     in the same update; xi is kept per replica in binary64 and advanced
+ *     after the momenta, from the updated ones (the ordering of the
+ *     symplectic Euler method applied to (y, xi)):
+ *       S = sum_i y_i(t_{k+1})^2           (binary64, i ascending)
+ *       xi_{k+1} = xi_k + (dt/M) (S - N T)  (h = dt/M and N T in binary64)
  *
  * Precision: every routine exists twice, in binary64 ("_f64", the reference
  * for tolerance checks) and in binary32 ("_f32", the paper's own single
@@ -202,6 +210,11 @@ typedef struct {
     uint32_t instance;      /* RNG stream of the instance */
     int force_plain_sum;    /* 1: never take the int32 force shortcut */
     int trace_every;        /* > 0: record E(t_k) and T_inst(t_k) for k = m*trace_every < Ns */
+    int thermostat;         /* 0: constant heating gamma, Eq. (eq_MomHeat);
+                               1: Nose-Hoover xi per replica, Eqs. (eq_NH1), (eq_NH) */
+    double nh_T;            /* Nose-Hoover temperature T */
+    double nh_M;            /* Nose-Hoover mass M */
+    double nh_xi0;          /* xi(t_0) */
 } oracle_params;
 
 /* Number of traced times of a run: t_k for k = m*trace_every < Ns. */

@@ -137,11 +137,13 @@ int SFX(oracle_step)(const float *J, int N, int nrep, REAL *x, REAL *y, int form
  * e_trace (energy at every evaluation step, [nrep][oracle_num_evals], may be
  * NULL), trace_e / trace_t (Ising energy, Eq. (eq_Ising), and instantaneous
  * temperature T_inst = (1/N) sum_i y_i^2, Eq. (eq_TInst), at the traced times
- * t_k, k = m*trace_every < Ns, [nrep][oracle_num_traced]; may be NULL). */
+ * t_k, k = m*trace_every < Ns, [nrep][oracle_num_traced]; may be NULL),
+ * xi_out (Nose-Hoover xi(t_Ns) per replica, [nrep], may be NULL; xi0 when the
+ * heating is constant). */
 int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, uint64_t seed,
                     int nrep, const int32_t *rep_ids, int8_t *best_s, double *best_e,
                     REAL *x_out, REAL *y_out, double *e_trace, double *trace_e,
-                    double *trace_t, int nthreads)
+                    double *trace_t, double *xi_out, int nthreads)
 {
     if (N < 1 || steps < 1 || nrep < 0 || p->eval_every < 0)
         return -1;
@@ -165,6 +167,10 @@ int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, ui
     const REAL dt = (REAL)p->dt;
     const REAL q = (REAL)(p->a0 * p->dt);
     const REAL g = (REAL)(p->gamma * p->dt);
+    /* Nose-Hoover (Eqs. eq_NH1, eq_NH): h = dt/M and N T, binary64 */
+    const int nose_hoover = p->thermostat == 1;
+    const double nh_h = p->dt / p->nh_M;
+    const double nh_NT = (double)N * p->nh_T;
     for (int k = 0; k < steps; ++k)
         pk[k] = (REAL)oracle_pump_factor(p->a0, k, steps);
     const int n_evals = (p->eval_every > 0 ? (steps - 1) / p->eval_every : 0) + 1;
@@ -192,6 +198,7 @@ int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, ui
                 y[i] = (REAL)oracle_init_value(seed, p->instance, r, (uint32_t)i, 1, p->init_half_width);
             }
             double best = INFINITY;
+            double xi = p->nh_xi0;
             int ev = 0;
             for (int k = 0; k <= steps; ++k) {
                 int is_eval = (k == steps) || (p->eval_every > 0 && k > 0 && k % p->eval_every == 0);
@@ -222,9 +229,22 @@ int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, ui
                         trace_t[at] = t2 / (double)N;
                 }
                 SFX(force)(Jr, Jint, N, p->form, x, f, stmp);
-                SFX(update)(N, x, y, f, c0, pk[k], dt, q, g);
+                if (nose_hoover) {
+                    /* friction -xi_k y in place of the heating term */
+                    const REAL gk = (REAL)(-xi * p->dt);
+                    SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);
+                    /* xi_{k+1} from the updated momenta, Eq. (eq_NH) */
+                    double s2 = 0.0;
+                    for (int i = 0; i < N; ++i)
+                        s2 += (double)y[i] * (double)y[i];
+                    xi = xi + nh_h * (s2 - nh_NT);
+                } else {
+                    SFX(update)(N, x, y, f, c0, pk[k], dt, q, g);
+                }
             }
             best_e[t] = best;
+            if (xi_out)
+                xi_out[t] = xi;
             if (x_out)
                 memcpy(x_out + (size_t)t * N, x, sizeof(REAL) * (size_t)N);
             if (y_out)

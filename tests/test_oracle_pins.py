@@ -421,3 +421,79 @@ def test_trace_energy_and_instantaneous_temperature():
         assert out["trace_e"][r, 0] == oracle.ising_energy(J, s0)
     # evaluations at t = 30, 60, 90 are traced at indices 3, 6, 9
     np.testing.assert_array_equal(out["trace_e"][:, [3, 6, 9]], out["e_trace"][:, :3])
+
+
+# ------------------------------------------------------- Nose-Hoover SB ----
+# Eqs. (eq_NH1), (eq_NH): the friction -xi y_i replaces the heating term and
+# xi follows (sum_i y_i^2 - N T) / M.
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_nose_hoover_large_mass_is_constant_heating(form, prec):
+    # The paper: large M makes xi nearly constant, and xi = -gamma is heated
+    # SB.  With M = 1e300 the xi increments vanish below binary64 resolution,
+    # so the run equals the constant-gamma run bit for bit and xi stays xi0.
+    J = synth.sk_pm1(48, 3)
+    c0 = oracle.c0_from_c1(J, 0.7)
+    gamma = 0.06
+    heat = oracle.make_params(form, c0, 1.1, gamma, eval_every=20)
+    nh = oracle.make_params(form, c0, 1.1, 0.0, eval_every=20, nose_hoover=True, nh_T=0.3,
+                            nh_M=1e300, nh_xi0=-gamma)
+    a = oracle.run(J, heat, 150, 5, range(4), prec)
+    b = oracle.run(J, nh, 150, 5, range(4), prec)
+    for key in ("best_e", "best_s", "x", "y"):
+        np.testing.assert_array_equal(a[key], b[key])
+    np.testing.assert_array_equal(b["xi"], np.full(4, -gamma))
+
+
+def _thermostat_only(n, T, M, xi0, dt, steps, seed=11, trace=False):
+    # J = 0 and a0 = 0: no force, no pump and x fixed, so only y and xi move:
+    # y' = (1 - xi dt) y, the discrete form of y' = -xi y.
+    J = np.zeros((n, n), np.float32)
+    prm = oracle.make_params(0, 1.0, dt, 0.0, a0=0.0, eval_every=0, nose_hoover=True,
+                             nh_T=T, nh_M=M, nh_xi0=xi0, trace_every=1 if trace else 0)
+    return oracle.run(J, prm, steps, seed, [0], "f64", want_trace=trace)
+
+
+def test_nose_hoover_heats_below_and_cools_above_the_temperature():
+    # T_inst < T drives xi negative and T_inst up (heating); T_inst > T drives
+    # xi positive and T_inst down (cooling).  The initial T_inst of U(-1, 1)
+    # momenta is about 1/3.
+    n = 64
+    for T, sign in ((1.0, -1.0), (0.05, 1.0)):
+        out = _thermostat_only(n, T, 2.0, 0.0, 0.05, 40, trace=True)
+        xi1 = _thermostat_only(n, T, 2.0, 0.0, 0.05, 1)["xi"][0]
+        assert np.sign(xi1) == sign
+        t_inst = out["trace_t"][0]
+        # step 0 runs with xi_0 = 0: no friction yet, T_inst(t_1) = T_inst(t_0)
+        assert t_inst[1] == t_inst[0]
+        if sign < 0:
+            assert t_inst[10] > t_inst[2] > t_inst[1]
+        else:
+            assert t_inst[10] < t_inst[2] < t_inst[1]
+
+
+def test_nose_hoover_force_free_invariant_and_mean_temperature():
+    # Without force, S = sum_i y_i^2 and xi obey dS/dt = -2 xi S and
+    # dxi/dt = (S - N T) / M, which conserve H = M xi^2 + S - N T ln S (dH/dt
+    # = 2 M xi xi' + S' - N T S'/S = 2 xi (S - N T) - 2 xi (S - N T) = 0), and
+    # the time average of xi' vanishes over a bounded orbit, so the mean of
+    # T_inst is T.  The discrete map conserves H up to O(dt).  A wrong sign
+    # of the friction or of the xi equation turns the orbit into growth or
+    # decay of H.
+    n, T, M, dt = 6, 0.5, 5.0, 0.01
+    steps = 1200   # about two periods (2 pi / sqrt(2 N T / M) = 5.7 time units)
+    ks = list(range(0, steps, 40))
+    tr = _thermostat_only(n, T, M, 0.0, dt, steps, trace=True)["trace_t"][0]
+    S = n * tr[ks]
+    xi = np.array([0.0] + [_thermostat_only(n, T, M, 0.0, dt, k)["xi"][0] for k in ks[1:]])
+    H = M * xi ** 2 + S - n * T * np.log(S)
+    h_min = n * T - n * T * math.log(n * T)          # at S = N T, xi = 0
+    swing = H[0] - h_min
+    assert swing > 0.05                                # a real orbit
+    assert np.max(np.abs(H - H[0])) < 0.02 * swing
+    assert xi.min() < -0.5 * math.sqrt(swing / M)      # xi swings both ways
+    assert xi.max() > 0.5 * math.sqrt(swing / M)
+    # mean of T_inst over the run: sum_k (S_k - N T) = M (xi_K - xi_0) / dt
+    long = _thermostat_only(n, T, M, 0.0, dt, 20000, trace=True)
+    assert abs(long["trace_t"][0].mean() - T) < 0.01 * T
