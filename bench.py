@@ -396,6 +396,11 @@ OTHER = {
                     kind="single", N=16384, J="pm1", J_seed=3, R=4096, sb_steps=10000,
                     form="discrete", prec="fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
                     trace_every=1, peak="fp8", dtype="fp8"),
+    "nh2000": dict(name="Nose-Hoover dSB SK +/-1 N=2000 R=1024 2000 steps FP8 per-step "
+                        "(T=0.3, M=40000, xi0=-0.05)", kind="single", N=2000, J="pm1", J_seed=1,
+                   R=1024, sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1,
+                   gamma=0.0, eval_every=100, trace_every=0, peak="fp8", dtype="fp8",
+                   nh=dict(thermostat="nose_hoover", nh_T=0.3, nh_M=40000.0, nh_xi0=-0.05)),
     "batch256": dict(name="HdSB 256 SK +/-1 instances, N uniform in [100, 2000], R=64, 2000 "
                           "steps, FP8, one batched launch", kind="batch", count=256, sizes_seed=4,
                      R=64, sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1,
@@ -418,9 +423,11 @@ def _other_cpu_baseline(w, Js, target_s=10.0):
     import oracle
     cores = os.cpu_count() or 1
     J = Js[0]
+    nh = w.get("nh")
     op = oracle.make_params(0 if w["form"] == "ballistic" else 1,
                             oracle.c0_from_c1(J, w["c1"]), w["dt"], w["gamma"],
-                            eval_every=w["eval_every"])
+                            eval_every=w["eval_every"], nose_hoover=nh is not None,
+                            **({k: v for k, v in nh.items() if k != "thermostat"} if nh else {}))
     t0 = time.perf_counter()
     oracle.run(J, op, 4, 1, range(cores), "f32", nthreads=cores)
     rate = J.shape[0] * cores * 4 / (time.perf_counter() - t0)
@@ -445,7 +452,7 @@ def run_other(args, w):
     R, S = w["R"], w["sb_steps"]
     Js = _other_couplings(w)
     p = hsb.params(w["form"], w["prec"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
-                   eval_every=w["eval_every"], trace_every=w["trace_every"])
+                   eval_every=w["eval_every"], trace_every=w["trace_every"], **w.get("nh", {}))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     units = sum(J.shape[0] for J in Js) * R * S            # replica-spin-steps per run
     flops = sum(2.0 * J.shape[0] ** 2 for J in Js) * R * S  # algorithmic

@@ -45,7 +45,7 @@
 extern "C" {
 #endif
 
-#define HSB_API_VERSION 1
+#define HSB_API_VERSION 2
 
 #if defined(__GNUC__)
 #define HSB_API __attribute__((visibility("default")))
@@ -109,8 +109,31 @@ typedef struct {
                                kernel with the CTA's rows of J held on chip for
                                the whole run (N <= 2048, else
                                HSB_E_UNSUPPORTED) */
-    uint32_t reserved[6];   /* must be zero */
+    int thermostat;         /* HSB_HEAT_CONSTANT: the constant heating rate gamma of
+                               Eq. (eq_MomHeat) (HbSB / HdSB); HSB_HEAT_NOSE_HOOVER:
+                               the dynamic xi of Eqs. (eq_NH1), (eq_NH), one per
+                               replica, in place of -gamma (gamma is then unused).
+                               Nose-Hoover runs on FP32 or on FP8 with one launch per
+                               step (AUTO never picks BF16X3 for it); schedules 1 and
+                               3, hsb_advance* and hsb_run_batch return
+                               HSB_E_UNSUPPORTED.  A momentum |y| >= 2^19 (an
+                               unstable setting: M much below N) makes the run
+                               return HSB_E_INVAL.  See hsb_get_xi. */
+    int reserved0;          /* must be zero */
+    double nh_T;            /* Nose-Hoover temperature T >= 0 */
+    double nh_M;            /* Nose-Hoover mass M > 0 */
+    double nh_xi0;          /* xi(t_0), finite; negative values heat from the start */
+    uint32_t reserved[2];   /* must be zero */
 } hsb_params;
+
+typedef enum {
+    HSB_HEAT_CONSTANT = 0,
+    /* Per step, in binary64 with each operation rounded once: the update uses
+       the friction factor g_r = fl32(-xi_r dt) where HbSB uses fl32(gamma dt)
+       (the friction -xi y(t_k) in place of the heating term); then
+       S_r = sum_i y_i(t_{k+1})^2, xi_r += (dt / M) (S_r - N T). */
+    HSB_HEAT_NOSE_HOOVER = 1
+} hsb_thermostat;
 
 /* Fills *p with the paper's tuned HdSB settings (Fig. 1 caption): discrete
  * form, AUTO precision, a0 = 1, c1 = 0.7, dt = 1.1, gamma = 0.06, L = 1,
@@ -205,6 +228,12 @@ HSB_API hsb_status hsb_advance_device(hsb_handle h, const hsb_params *p, int R, 
  * buf (host, 3 doubles each) and the trace length to *entries (may be NULL).
  * Blocks. */
 HSB_API hsb_status hsb_get_trace(hsb_handle h, double *buf, size_t max_entries, size_t *entries);
+
+/* Copies xi_r(t_Ns) of the last run's R replicas (binary64, host buffer of R
+ * doubles) after a run with thermostat = HSB_HEAT_NOSE_HOOVER (Eq. (eq_NH)).
+ * HSB_E_INVAL when the last run had no Nose-Hoover thermostat or R differs
+ * from its replica count.  Blocks. */
+HSB_API hsb_status hsb_get_xi(hsb_handle h, int R, double *xi);
 
 /* Replaces the couplings of the handle by a new instance of the same N (host,
  * float32, N x N, row-major; validated as in hsb_create).  Device buffers and

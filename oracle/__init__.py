@@ -15,6 +15,7 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
                       reduction to plain bSB/dSB, wall invariants, conserved
                       quadratic form per eigenmode, linear heating map, N = 2
                       normal modes, replica independence, determinism
+  kinetic_sum      -- exact rational arithmetic (Python fractions)
   run, Nose-Hoover -- large-M reduction to constant heating gamma = -xi0,
                       the conserved quantity M xi^2 + S - N T ln S of the
                       force-free thermostat, time average of T_inst equal to
@@ -103,6 +104,10 @@ def _load():
         lib.oracle_num_traced.argtypes = [C.c_int, C.c_int]
         lib.oracle_is_pm1.restype = C.c_int
         lib.oracle_is_pm1.argtypes = [P, C.c_int]
+        for sfx in ("f64", "f32"):
+            ks = getattr(lib, f"oracle_kinetic_sum_{sfx}")
+            ks.restype = C.c_double
+            ks.argtypes = [P, C.c_int]
         for sfx, real in (("f64", C.c_double), ("f32", C.c_float)):
             st = getattr(lib, f"oracle_step_{sfx}")
             st.restype = C.c_int
@@ -199,6 +204,15 @@ def pump_factor(a0: float, k: int, steps: int) -> float:
 
 def num_evals(steps: int, eval_every: int) -> int:
     return int(_load().oracle_num_evals(steps, eval_every))
+
+
+def kinetic_sum(y, precision: str = "f32") -> float:
+    """S = sum_i y_i^2 of Eq. (eq_NH) as the Nose-Hoover update forms it (each
+    y_i^2 rounded to a multiple of 2^-64, exact 128-bit sum, one rounding)."""
+    real = _real(precision)
+    y = np.ascontiguousarray(y, dtype=real).ravel()
+    fn = getattr(_load(), f"oracle_kinetic_sum_{precision}")
+    return float(fn(_ptr(y), int(y.shape[0])))
 
 
 def is_pm1(J) -> bool:

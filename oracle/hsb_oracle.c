@@ -49,8 +49,13 @@
  *     in the same update; xi is kept per replica in binary64 and advanced
  *     after the momenta, from the updated ones (the ordering of the
  *     symplectic Euler method applied to (y, xi)):
- *       S = sum_i y_i(t_{k+1})^2           (binary64, i ascending)
- *       xi_{k+1} = xi_k + (dt/M) (S - N T)  (h = dt/M and N T in binary64)
+ *       S = sum_i y_i(t_{k+1})^2
+ *       xi_{k+1} = xi_k + (dt/M) (S - N T)  (h = dt/M and N T in binary64,
+ *                                            each operation rounded once)
+ *     S is formed in fixed point so that it does not depend on the order of
+ *     summation: each y_i^2 is rounded to the nearest multiple of 2^-64 (ties
+ *     to even), the multiples are added exactly as 128-bit integers, and the
+ *     total is rounded once to binary64 (oracle_kinetic_sum).
  *
  * Precision: every routine exists twice, in binary64 ("_f64", the reference
  * for tolerance checks) and in binary32 ("_f32", the paper's own single

@@ -89,6 +89,22 @@ static void SFX(update)(int N, REAL *x, REAL *y, const REAL *f, REAL c0, REAL pk
     }
 }
 
+/* S = sum_i y_i^2 of the Nose-Hoover equation (eq_NH) in fixed point: each
+ * y_i^2 (exact in binary64 when y is binary32) is scaled by 2^64 (exact),
+ * rounded to the nearest integer, ties to even (nearbyint in the default
+ * rounding mode), added exactly to a 128-bit unsigned integer, and the total
+ * is converted once to binary64 (correctly rounded) and scaled back by 2^-64.
+ * The result is independent of the order of the terms.  sum_i y_i^2 < 2^63. */
+double SFX(oracle_kinetic_sum)(const REAL *y, int N)
+{
+    unsigned __int128 acc = 0;
+    for (int i = 0; i < N; ++i) {
+        const double v = (double)y[i] * (double)y[i];
+        acc += (unsigned __int128)nearbyint(v * 0x1p64);
+    }
+    return (double)acc * 0x1p-64;
+}
+
 static REAL *SFX(widen)(const float *J, int N)
 {
     REAL *Jr = (REAL *)malloc(sizeof(REAL) * (size_t)N * (size_t)N);
@@ -234,9 +250,7 @@ int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, ui
                     const REAL gk = (REAL)(-xi * p->dt);
                     SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);
                     /* xi_{k+1} from the updated momenta, Eq. (eq_NH) */
-                    double s2 = 0.0;
-                    for (int i = 0; i < N; ++i)
-                        s2 += (double)y[i] * (double)y[i];
+                    const double s2 = SFX(oracle_kinetic_sum)(y, N);
                     xi = xi + nh_h * (s2 - nh_NT);
                 } else {
                     SFX(update)(N, x, y, f, c0, pk[k], dt, q, g);

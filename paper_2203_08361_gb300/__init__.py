@@ -20,19 +20,22 @@ LIB_PATH = os.path.join(_PKG, "libhsb.so")
 
 HSB_BALLISTIC, HSB_DISCRETE = 0, 1
 HSB_PREC_AUTO, HSB_PREC_FP32, HSB_PREC_FP8, HSB_PREC_BF16X3 = 0, 1, 2, 3
+HSB_E_INVAL, HSB_E_UNSUPPORTED = 1, 7
+HSB_HEAT_CONSTANT, HSB_HEAT_NOSE_HOOVER = 0, 1
 STATUS = {0: "HSB_OK", 1: "HSB_E_INVAL", 2: "HSB_E_ASYM", 3: "HSB_E_DIAG", 4: "HSB_E_NOMEM",
           5: "HSB_E_CUDA", 6: "HSB_E_TIMEOUT", 7: "HSB_E_UNSUPPORTED", 8: "HSB_E_NODEVICE"}
 PREC = {"auto": HSB_PREC_AUTO, "fp32": HSB_PREC_FP32, "fp8": HSB_PREC_FP8,
         "bf16x3": HSB_PREC_BF16X3}
 FORM = {"ballistic": HSB_BALLISTIC, "discrete": HSB_DISCRETE}
 SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2, "resident": 3}
+THERMOSTAT = {"constant": HSB_HEAT_CONSTANT, "nose_hoover": HSB_HEAT_NOSE_HOOVER}
 
 # Every symbol include/hsb.h declares.
 EXPORTS = ["hsb_params_default", "hsb_version", "hsb_create", "hsb_destroy", "hsb_set_stream",
            "hsb_info", "hsb_run", "hsb_run_device", "hsb_get_state", "hsb_advance",
            "hsb_advance_device", "hsb_set_couplings", "hsb_run_stats", "hsb_synchronize",
            "hsb_run_fp32_noalloc", "hsb_get_trace", "hsb_run_batch", "hsb_cut_values",
-           "hsb_last_error"]
+           "hsb_get_xi", "hsb_last_error"]
 
 
 class HsbError(RuntimeError):
@@ -56,7 +59,12 @@ class Params(C.Structure):
         ("trace_every", C.c_int),
         ("instance", C.c_uint32),
         ("schedule", C.c_int),
-        ("reserved", C.c_uint32 * 6),
+        ("thermostat", C.c_int),
+        ("reserved0", C.c_int),
+        ("nh_T", C.c_double),
+        ("nh_M", C.c_double),
+        ("nh_xi0", C.c_double),
+        ("reserved", C.c_uint32 * 2),
     ]
 
 
@@ -111,6 +119,8 @@ def load():
         lib.hsb_run_batch.argtypes = [P, I, C.POINTER(Params), I, I, C.c_uint64, P, P]
         lib.hsb_get_trace.restype = I
         lib.hsb_get_trace.argtypes = [H, P, C.c_size_t, C.POINTER(C.c_size_t)]
+        lib.hsb_get_xi.restype = I
+        lib.hsb_get_xi.argtypes = [H, I, P]
         lib.hsb_run_fp32_noalloc.restype = I
         lib.hsb_run_fp32_noalloc.argtypes = [P, I, C.POINTER(Params), I, I, C.c_uint64, P, P, P]
         _lib = lib
@@ -139,6 +149,8 @@ def params(form="discrete", prec="auto", **kw) -> Params:
     p.prec = PREC[prec] if isinstance(prec, str) else int(prec)
     if isinstance(kw.get("schedule"), str):
         kw["schedule"] = SCHEDULE[kw["schedule"]]
+    if isinstance(kw.get("thermostat"), str):
+        kw["thermostat"] = THERMOSTAT[kw["thermostat"]]
     for k, v in kw.items():
         if not hasattr(p, k):
             raise AttributeError(f"hsb_params has no field {k!r}")
@@ -252,6 +264,13 @@ def get_trace(h: int):
     return buf
 
 
+def get_xi(h: int, R: int):
+    """hsb_get_xi: float64 [R], the Nose-Hoover xi of each replica after the last run."""
+    xi = np.zeros(int(R), np.float64)
+    _check(load().hsb_get_xi(C.c_void_p(h), int(R), _ptr(xi)))
+    return xi
+
+
 def run_stats(h: int) -> int:
     """Kernels queued by the last run on the handle."""
     n = C.c_longlong()
@@ -305,6 +324,9 @@ class Solver:
 
     def get_trace(self):
         return get_trace(self.h)
+
+    def get_xi(self, R: int):
+        return get_xi(self.h, R)
 
     def set_stream(self, stream_ptr):
         set_stream(self.h, stream_ptr)

@@ -6,6 +6,8 @@
 // is captured once into a CUDA graph per run shape and replayed.
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <cmath>
 #include <stdarg.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -70,9 +72,9 @@ struct DeviceGuard {
 
 // Everything that determines the captured step loop.
 struct GraphKey {
-    int prec, form, R, Rp, steps, eval_every, trace_every, pm1;
+    int prec, form, R, Rp, steps, eval_every, trace_every, pm1, thermo;
     float c0, dt, q, g;
-    double a0;
+    double a0, nh_h, nh_NT, dt64;
     uint64_t buffers_gen;
     bool operator==(const GraphKey &o) const { return memcmp(this, &o, sizeof *this) == 0; }
 };
@@ -80,6 +82,9 @@ struct GraphKey {
 struct RunCfg {
     int prec, form, R, Rp, steps, eval_every, trace_every, schedule;
     double a0;
+    // Nose-Hoover thermostat: h = dt / M, N T and dt in binary64, xi(t_0)
+    int thermo;
+    double nh_h, nh_NT, nh_xi0, dt64;
     StepConsts c;
     std::vector<float> pk;  // p_k = a0 - a(t_k), k = 0..steps-1, rounded once
 };
@@ -105,7 +110,11 @@ struct hsb_ctx {
     size_t trace_cap = 0, trace_len = 0;
     double *Ebest = nullptr;
     double *Efinal = nullptr;
-    double *Efpart = nullptr;  // partial sums of the binary64 final energies
+    double *Efpart = nullptr;  // partial sums of the binary64 final energies (and trace)
+    unsigned *trace_ticket = nullptr;  // block ticket of the trace reduction, kept at zero
+    double *xi = nullptr;    // [Rp] Nose-Hoover xi per replica
+    float *gvec = nullptr;   // [Rp] friction factor fl32(-xi dt) of the next step
+    bool have_xi = false;    // the last run used the Nose-Hoover thermostat
     int8_t *Sbest = nullptr;
     int *err = nullptr;
     uint64_t buffers_gen = 0;
@@ -166,6 +175,13 @@ void free_run_buffers(hsb_ctx *h)
     cudaFree(h->Efinal);
     cudaFree(h->Efpart);
     h->Efpart = nullptr;
+    cudaFree(h->trace_ticket);
+    h->trace_ticket = nullptr;
+    cudaFree(h->xi);
+    cudaFree(h->gvec);
+    h->xi = nullptr;
+    h->gvec = nullptr;
+    h->have_xi = false;
     cudaFree(h->Sbest);
     h->X[0] = h->X[1] = h->Y = nullptr;
     h->S8[0] = h->S8[1] = nullptr;
@@ -206,6 +222,10 @@ hsb_status ensure_buffers(hsb_ctx *h, int Rp, int R)
     CK(cudaMalloc(&h->Efinal, (size_t)Rp * sizeof(double)), "cudaMalloc Efinal");
     CK(cudaMalloc(&h->Efpart, final_energy_part_doubles(Rp) * sizeof(double)),
        "cudaMalloc Efpart");
+    CK(cudaMalloc(&h->trace_ticket, sizeof(unsigned)), "cudaMalloc trace ticket");
+    CK(cudaMemset(h->trace_ticket, 0, sizeof(unsigned)), "cudaMemset trace ticket");
+    CK(cudaMalloc(&h->xi, (size_t)Rp * sizeof(double)), "cudaMalloc xi");
+    CK(cudaMalloc(&h->gvec, (size_t)Rp * sizeof(float)), "cudaMalloc gvec");
     CK(cudaMalloc(&h->Sbest, (size_t)Rp * h->N), "cudaMalloc Sbest");
     h->Rcap = Rp;
     h->buffers_gen++;
@@ -262,6 +282,13 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_INVAL, "eval_every and trace_every must be >= 0");
     if (p->schedule < 0 || p->schedule > 3)
         return set_error(HSB_E_INVAL, "schedule must be 0, 1, 2 or 3");
+    if (p->thermostat != HSB_HEAT_CONSTANT && p->thermostat != HSB_HEAT_NOSE_HOOVER)
+        return set_error(HSB_E_INVAL, "thermostat must be HSB_HEAT_CONSTANT or "
+                                      "HSB_HEAT_NOSE_HOOVER");
+    const bool nose_hoover = p->thermostat == HSB_HEAT_NOSE_HOOVER;
+    if (nose_hoover && (!(p->nh_M > 0.0) || !(p->nh_T >= 0.0) || !std::isfinite(p->nh_M) ||
+                        !std::isfinite(p->nh_T) || !std::isfinite(p->nh_xi0)))
+        return set_error(HSB_E_INVAL, "Nose-Hoover needs finite nh_M > 0, nh_T >= 0 and nh_xi0");
     if ((long long)R * h->N > (1LL << 40))
         return set_error(HSB_E_INVAL, "R*N too large");
     int prec = p->prec;
@@ -270,7 +297,8 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         if (p->form == HSB_DISCRETE && h->pm1)
             prec = HSB_PREC_FP8;
         else
-            prec = tc_bf16_persistent_fits(h->Np, Rp_) ? HSB_PREC_BF16X3 : HSB_PREC_FP32;
+            prec = !nose_hoover && tc_bf16_persistent_fits(h->Np, Rp_) ? HSB_PREC_BF16X3
+                                                                       : HSB_PREC_FP32;
     }
     if (prec == HSB_PREC_FP8 && !(p->form == HSB_DISCRETE && h->pm1))
         return set_error(HSB_E_UNSUPPORTED,
@@ -285,6 +313,11 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_UNSUPPORTED, "the trace needs the FP32 or FP8 precision");
     if (p->trace_every > 0 && prec == HSB_PREC_FP8 && (p->schedule == 1 || p->schedule == 3))
         return set_error(HSB_E_UNSUPPORTED, "the trace runs on the one-launch-per-step schedule");
+    if (nose_hoover && prec == HSB_PREC_BF16X3)
+        return set_error(HSB_E_UNSUPPORTED, "the Nose-Hoover thermostat needs FP32 or FP8");
+    if (nose_hoover && prec == HSB_PREC_FP8 && (p->schedule == 1 || p->schedule == 3))
+        return set_error(HSB_E_UNSUPPORTED,
+                         "the Nose-Hoover thermostat runs on the one-launch-per-step schedule");
     cfg->prec = prec;
     cfg->form = p->form;
     cfg->R = R;
@@ -294,6 +327,11 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
     cfg->trace_every = p->trace_every;
     cfg->schedule = p->schedule;
     cfg->a0 = p->a0;
+    cfg->thermo = nose_hoover ? 1 : 0;
+    cfg->nh_h = nose_hoover ? p->dt / p->nh_M : 0.0;
+    cfg->nh_NT = nose_hoover ? (double)h->N * p->nh_T : 0.0;
+    cfg->nh_xi0 = nose_hoover ? p->nh_xi0 : 0.0;
+    cfg->dt64 = p->dt;
     // c0 = c1 / (sqrt(N) sigma_J) (Results; sigma_J = 1 for +/-1 couplings)
     const double c0 = p->c0 > 0.0 ? p->c0 : p->c1 / (sqrt((double)h->N) * h->sigma);
     cfg->c.c0 = (float)c0;
@@ -328,13 +366,15 @@ hsb_status enqueue_step(hsb_ctx *h, cudaStream_t st, const RunCfg &c, int k, int
     const bool en = ev || tr;
     float *tpart = tr ? h->Tpart : nullptr;
     const int nblk = h->Np / kTileM;
+    const float *gv = c.thermo ? h->gvec : nullptr;  // Nose-Hoover friction per replica
     if (c.prec == HSB_PREC_FP32) {
         if (en && c.form == HSB_BALLISTIC)
             CK(launch_simt_step(st, 1, true, true, h->J32, h->N, h->Np, c.Rp, h->X[cur], nullptr,
                                 h->Y, 0.f, c.c, h->Epart, nullptr),
                "energy kernel");
         CK(launch_simt_step(st, c.form, false, en && c.form == HSB_DISCRETE, h->J32, h->N, h->Np,
-                            c.Rp, h->X[cur], h->X[cur ^ 1], h->Y, c.pk[k], c.c, h->Epart, tpart),
+                            c.Rp, h->X[cur], h->X[cur ^ 1], h->Y, c.pk[k], c.c, h->Epart, tpart,
+                            gv),
            "fp32 step kernel");
         if (ev)
             CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[cur], nullptr,
@@ -342,7 +382,7 @@ hsb_status enqueue_step(hsb_ctx *h, cudaStream_t st, const RunCfg &c, int k, int
                "best kernel");
     } else {  // FP8: S8[cur] -> S8[cur^1], X and Y in place
         CK(launch_tc_fp8_step(st, h->plan, cur, en, false, h->N, c.Rp, h->X[0], h->Y, c.pk[k],
-                              c.c, h->Epart, tpart, h->S8[cur ^ 1], h->err),
+                              c.c, h->Epart, tpart, h->S8[cur ^ 1], h->err, gv),
            "fp8 step kernel");
         if (ev)
             CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, h->S8[cur],
@@ -351,8 +391,13 @@ hsb_status enqueue_step(hsb_ctx *h, cudaStream_t st, const RunCfg &c, int k, int
     }
     if (tr)
         CK(launch_trace_reduce(st, h->Epart, h->Tpart, nblk, h->N, c.R, c.Rp,
+                               h->Efpart, h->trace_ticket,
                                h->trace + 3 * (size_t)(k / c.trace_every)),
            "trace kernel");
+    if (c.thermo)  // xi_{k+1} from y(t_{k+1}), Eq. (eq_NH)
+        CK(launch_nh_update(st, h->Y, h->N, h->Np, c.R, c.nh_h, c.nh_NT, c.dt64, h->xi, h->gvec,
+                            h->err),
+           "Nose-Hoover kernel");
     return HSB_OK;
 }
 
@@ -400,6 +445,8 @@ long long count_launches(const hsb_ctx *h, const RunCfg &c)
     }
     if (!h->pm1)
         n += 1;
+    if (c.thermo)
+        n += 1 + c.steps;  // xi init, one xi update per step
     return n;
 }
 
@@ -463,7 +510,7 @@ int num_evals(const RunCfg &c)
 hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
 {
     *out = false;
-    if (c.prec != HSB_PREC_FP8 || c.schedule == 2 || c.trace_every > 0)
+    if (c.prec != HSB_PREC_FP8 || c.schedule == 2 || c.trace_every > 0 || c.thermo)
         return HSB_OK;
     const bool fits = c.schedule == 3 ? tc_resident_fits(h->Np, c.Rp)
                                       : tc_persistent_fits(h->Np, c.Rp);
@@ -685,6 +732,7 @@ hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hs
     h->last_x = 0;
     h->state_par = par;
     h->have_state = true;
+    h->have_xi = false;
     h->launches = launches;
     h->trace_len = 0;
     return HSB_OK;
@@ -716,6 +764,7 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
         h->have_state = true;
         h->launches = 3;
         h->trace_len = 0;
+        h->have_xi = false;
         return HSB_OK;
     }
     if (c.trace_every > 0) {
@@ -742,6 +791,9 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
     CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R, c.Rp,
                    h->X[0], h->Y, c.prec == HSB_PREC_FP8 ? h->S8[0] : nullptr, h->Ebest),
        "init kernel");
+    if (c.thermo)
+        CK(launch_nh_init(h->work, c.R, c.Rp, c.nh_xi0, c.dt64, h->xi, h->gvec), "xi init");
+    h->have_xi = c.thermo != 0;
     CK(cudaGraphLaunch(h->gexec, h->work), "graph launch");
     h->last_R = c.R;
     h->last_x = c.prec == HSB_PREC_FP32 ? (c.steps & 1) : 0;
@@ -768,6 +820,10 @@ GraphKey make_key(const hsb_ctx *h, const RunCfg &c)
     key.q = c.c.q;
     key.g = c.c.g;
     key.a0 = c.a0;
+    key.thermo = c.thermo;
+    key.nh_h = c.nh_h;
+    key.nh_NT = c.nh_NT;
+    key.dt64 = c.dt64;
     key.buffers_gen = h->buffers_gen;
     return key;
 }
@@ -779,6 +835,8 @@ hsb_status check_device_error(hsb_ctx *h)
     CK(cudaStreamSynchronize(h->work), "synchronize");
     if (e == kErrTimeout)
         return set_error(HSB_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (e == kErrRange)
+        return set_error(HSB_E_INVAL, "a momentum reached |y| >= 2^19 in the Nose-Hoover sum");
     if (e != 0)
         return set_error(HSB_E_CUDA, "device error code %d", e);
     return HSB_OK;
@@ -909,6 +967,10 @@ hsb_status hsb_params_default(hsb_params *p)
     p->eval_every = 100;
     p->trace_every = 0;
     p->instance = 0;
+    p->thermostat = HSB_HEAT_CONSTANT;
+    p->nh_T = 0.0;
+    p->nh_M = 1.0;
+    p->nh_xi0 = 0.0;
     return HSB_OK;
 }
 
@@ -1126,6 +1188,8 @@ hsb_status hsb_advance(hsb_handle h, const hsb_params *p, int R, int steps, int 
         return set_error(HSB_E_INVAL, "handle is NULL");
     if (!x || !y)
         return set_error(HSB_E_INVAL, "state pointer is NULL");
+    if (p && p->thermostat == HSB_HEAT_NOSE_HOOVER)
+        return set_error(HSB_E_UNSUPPORTED, "hsb_advance keeps no Nose-Hoover xi");
     if (k_begin < 0 || k_end < k_begin || k_end > steps)
         return set_error(HSB_E_INVAL, "need 0 <= k_begin <= k_end <= steps");
     DeviceGuard g(h->device);
@@ -1203,6 +1267,9 @@ hsb_status hsb_advance_device(hsb_handle h, const hsb_params *p, int R, int step
 {
     if (!h)
         return set_error(HSB_E_INVAL, "handle is NULL");
+    if (p && p->thermostat == HSB_HEAT_NOSE_HOOVER)
+        return set_error(HSB_E_UNSUPPORTED, "hsb_advance_device keeps no Nose-Hoover xi");
+    h->have_xi = false;
     if (k_begin < 0 || k_end < k_begin || k_end > steps)
         return set_error(HSB_E_INVAL, "need 0 <= k_begin <= k_end <= steps");
     DeviceGuard g(h->device);
@@ -1354,6 +1421,22 @@ hsb_status hsb_get_trace(hsb_handle h, double *buf, size_t max_entries, size_t *
     return HSB_OK;
 }
 
+hsb_status hsb_get_xi(hsb_handle h, int R, double *xi)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (!xi)
+        return set_error(HSB_E_INVAL, "xi is NULL");
+    if (!h->have_xi || !h->have_state || R != h->last_R)
+        return set_error(HSB_E_INVAL, "the last run had no Nose-Hoover thermostat or %d replicas",
+                         R);
+    DeviceGuard g(h->device);
+    CK(cudaMemcpyAsync(xi, h->xi, (size_t)R * sizeof(double), cudaMemcpyDeviceToHost, h->work),
+       "copy xi");
+    CK(cudaStreamSynchronize(h->work), "synchronize");
+    return HSB_OK;
+}
+
 hsb_status hsb_run_stats(hsb_handle h, long long *kernel_launches)
 {
     if (!h)
@@ -1379,7 +1462,8 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
     // The batched kernel applies to the discrete form with +/-1 couplings in
     // FP8; any other case runs the instances one after another.
     bool batched = p->form == HSB_DISCRETE &&
-                   (p->prec == HSB_PREC_AUTO || p->prec == HSB_PREC_FP8) && p->trace_every == 0;
+                   (p->prec == HSB_PREC_AUTO || p->prec == HSB_PREC_FP8) && p->trace_every == 0 &&
+                   p->thermostat == HSB_HEAT_CONSTANT;
     for (int b = 0; b < count && batched; ++b)
         batched = hs[b]->pm1 && batch_shape_ok(hs[b]->Np, R);
     if (!batched) {

@@ -42,7 +42,7 @@ __host__ __device__ constexpr int flag_index(int mb, int rb, int nrb)
 }
 
 // Error word written by kernels whose bounded waits gave up.
-enum : int { kErrNone = 0, kErrTimeout = 1, kErrBadLaunch = 2 };
+enum : int { kErrNone = 0, kErrTimeout = 1, kErrBadLaunch = 2, kErrRange = 3 };
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
@@ -60,11 +60,28 @@ cudaError_t launch_init(cudaStream_t st, uint64_t seed, uint32_t instance, float
 cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool energy,
                              const float *J32, int N, int Np, int Rp, const float *Xcur,
                              float *Xnext, float *Y, float pk, StepConsts c, float *Epart,
-                             float *Tpart);
+                             float *Tpart, const float *gvec = nullptr);
+
+// Nose-Hoover thermostat (Eqs. eq_NH1, eq_NH), one variable xi_r per replica
+// (binary64) and the friction factor g_r = fl32(-xi_r dt) that replaces the
+// constant heating factor gamma dt in the next step (gvec of the step kernels).
+// init: xi_r = xi0, g_r = fl32(-xi0 dt) for r < R; xi_r = g_r = 0 up to Rp.
+cudaError_t launch_nh_init(cudaStream_t st, int R, int Rp, double xi0, double dt, double *xi,
+                           float *gvec);
+// update after a step: S_r = sum_{i<N} y_i^2 (each term rounded to a multiple
+// of 2^-64, exact 128-bit sum, one rounding to binary64), xi_r += h (S_r - NT)
+// with h = dt / M and NT = N T given in binary64, then g_r = fl32(-xi_r dt).
+// A momentum with |y| >= 2^19 (or not finite) sets *err = kErrRange.
+cudaError_t launch_nh_update(cudaStream_t st, const float *Y, int N, int Np, int R, double h,
+                             double NT, double dt, double *xi, float *gvec, int *err);
 
 // Trace entry {min_r E_r, mean_r E_r, mean_r T_inst,r} from Epart / Tpart.
+// One trace entry {min E, mean E, mean T_inst} into out.  scratch (3 ceil(R / 32)
+// doubles) and ticket (one unsigned, zero before the first call; the kernel
+// leaves it zero) select the many-block reduction; NULL selects one block.
 cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,
-                                int N, int R, int Rp, double *out);
+                                int N, int R, int Rp, double *scratch, unsigned *ticket,
+                                double *out);
 
 // Best tracking after an evaluation: E_r = -1/2 sum_blocks Epart; if E_r <
 // Ebest[r] store it with the spins sgn(x) read from X (fp32) or S8 (fp8).
@@ -112,7 +129,7 @@ void tc_plan_destroy(TcPlan *p);
 cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
                                bool energy_only, int N, int Rp, float *X, float *Y, float pk,
                                StepConsts c, float *Epart, float *Tpart, uint8_t *S8next,
-                               int *err);
+                               int *err, const float *gvec = nullptr);
 
 // ---- hsb_persist.cu --------------------------------------------------------
 // Arguments of the persistent FP8 kernel: `nsteps` updates starting at global

@@ -108,6 +108,9 @@ extern "C" HSB_API hsb_status hsb_run_fp32_noalloc(const float *J, int N, const 
         return report_error(HSB_E_INVAL,
                     "hsb_run_fp32_noalloc: needs steps >= 1, a valid form, a0 > 0, dt > 0, "
                     "gamma >= 0, init_half_width > 0, eval_every >= 0 and an explicit c0 > 0");
+    if (p->thermostat != HSB_HEAT_CONSTANT)
+        return report_error(HSB_E_UNSUPPORTED,
+                    "hsb_run_fp32_noalloc: constant heating only (no Nose-Hoover thermostat)");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(256, 1)
 simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
                  const float *__restrict__ Xcur, float *__restrict__ Xnext,
                  float *__restrict__ Y, float pk, StepConsts c, int energy,
-                 float *__restrict__ Epart, float *__restrict__ Tpart)
+                 float *__restrict__ Epart, float *__restrict__ Tpart,
+                 const float *__restrict__ gvec)
 {
     constexpr bool kSign = (FORM == 1) || ENERGY_ONLY;
     __shared__ __align__(16) float As[2][8][128];
@@ -153,6 +154,10 @@ simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
     for (int b = 0; b < 8; ++b) {
         const int col = (b < 4 ? tx * 4 + b : 64 + tx * 4 + (b - 4));
         const size_t rowbase = (size_t)(r0 + col) * Np + m0;
+        // per-replica friction factor of the Nose-Hoover thermostat
+        StepConsts cr = c;
+        if (gvec)
+            cr.g = gvec[r0 + col];
         float e = 0.f, t2 = 0.f;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -178,7 +183,7 @@ simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
                 float xo[4], yo[4];
 #pragma unroll
                 for (int a = 0; a < 4; ++a)
-                    sb_update(acc[h * 4 + a][b], xv[a], yv[a], pk, c, xo[a], yo[a]);
+                    sb_update(acc[h * 4 + a][b], xv[a], yv[a], pk, cr, xo[a], yo[a]);
                 *reinterpret_cast<float4 *>(Xnext + rowbase + ibase) =
                     make_float4(xo[0], xo[1], xo[2], xo[3]);
                 *reinterpret_cast<float4 *>(Y + rowbase + ibase) =
@@ -223,18 +228,152 @@ simt_step_kernel(const float *__restrict__ J, int N, int Np, int Rp,
 cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool energy,
                              const float *J32, int N, int Np, int Rp, const float *Xcur,
                              float *Xnext, float *Y, float pk, StepConsts c, float *Epart,
-                             float *Tpart)
+                             float *Tpart, const float *gvec)
 {
     dim3 grid(Np / 128, Rp / 128);
     if (energy_only)
         simt_step_kernel<1, true><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
-                                                         1, Epart, nullptr);
+                                                         1, Epart, nullptr, nullptr);
     else if (form == 1)
         simt_step_kernel<1, false><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
-                                                          energy ? 1 : 0, Epart, Tpart);
+                                                          energy ? 1 : 0, Epart, Tpart, gvec);
     else
         simt_step_kernel<0, false><<<grid, 256, 0, st>>>(J32, N, Np, Rp, Xcur, Xnext, Y, pk, c,
-                                                          0, Epart, Tpart);
+                                                          0, Epart, Tpart, gvec);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------- Nose-Hoover thermostat ---
+// Eqs. (eq_NH1), (eq_NH): the friction -xi_r y_i takes the heating term's
+// place in the update (factor g_r = -xi_r dt), and xi_r advances after the
+// momenta from the updated ones.  Arithmetic in binary64 with the operations
+// rounded one by one (no contraction), the factor rounded once to binary32.
+// S_r = sum_i y_i^2 is formed in fixed point so that it does not depend on the
+// order of summation: each y_i^2 is rounded to the nearest multiple of 2^-64,
+// the multiples are added exactly as 128-bit integers, and the total is
+// rounded once to binary64.
+
+__global__ void nh_init_kernel(int R, int Rp, double xi0, double dt, double *__restrict__ xi,
+                               float *__restrict__ gvec)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Rp)
+        return;
+    const bool live = r < R;
+    xi[r] = live ? xi0 : 0.0;
+    gvec[r] = live ? __double2float_rn(__dmul_rn(-xi0, dt)) : 0.f;
+}
+
+namespace {
+
+// y^2 in units of 2^-64, rounded to the nearest integer, as (hi, lo).  With
+// y = m 2^ex (m < 2^24), y^2 2^64 = m^2 2^s, s = 2 ex + 64 (even).  A tie
+// would need m^2 = 2^(k-1) mod 2^k for k = -s > 0, impossible for a square
+// (even 2-adic valuation), so rounding up on "remainder above half" is exact
+// round-to-nearest.  |y| >= 2^19 (s > 54) or a non-finite y sets *bad.
+__device__ __forceinline__ void square_q64(float y, uint64_t &hi, uint64_t &lo, bool &bad)
+{
+    const uint32_t b = __float_as_uint(y) & 0x7FFFFFFFu;
+    const uint32_t e = b >> 23;
+    hi = 0;
+    lo = 0;
+    if (e == 255u) {
+        bad = true;
+        return;
+    }
+    const uint64_t m = e ? (uint64_t)((b & 0x7FFFFFu) | 0x800000u) : (uint64_t)b;
+    const int ex = e ? (int)e - 150 : -149;
+    const uint64_t m2 = m * m;  // < 2^48
+    const int s = 2 * ex + 64;
+    if (m2 == 0)
+        return;
+    if (s >= 0) {
+        if (s > 54) {
+            bad = true;
+            return;
+        }
+        lo = m2 << s;
+        hi = s ? m2 >> (64 - s) : 0;
+    } else {
+        const int k = -s;
+        if (k >= 49)  // m2 2^-k < 2^48 2^-49: below one half
+            return;
+        const uint64_t q = m2 >> k;
+        const uint64_t rem = m2 & ((1ull << k) - 1ull);
+        lo = q + (rem > (1ull << (k - 1)) ? 1ull : 0ull);
+    }
+}
+
+__device__ __forceinline__ void add_u128(uint64_t &hi, uint64_t &lo, uint64_t bh, uint64_t bl)
+{
+    const uint64_t l = lo + bl;
+    hi += bh + (l < lo ? 1ull : 0ull);
+    lo = l;
+}
+
+// (hi 2^64 + lo) 2^-64 rounded once to binary64: the top 64 significant bits
+// with the bits below them folded into a sticky bit 0 round to 53 bits as the
+// full value does (the rounding position is bit 11 of the 64); the scaling
+// by a power of two is exact.
+__device__ __forceinline__ double u128_scaled_to_double(uint64_t hi, uint64_t lo)
+{
+    if (hi == 0)
+        return __dmul_rn(__ull2double_rn(lo), 0x1p-64);
+    const int lz = __clzll((long long)hi);
+    uint64_t t = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+    if (lo << lz)
+        t |= 1ull;
+    const double scale = __longlong_as_double((long long)(1023 - lz) << 52);  // 2^-lz
+    return __dmul_rn(__ull2double_rn(t), scale);
+}
+
+}  // namespace
+
+// One warp per replica: lane l accumulates i = l, l + 32, ...; integer sums
+// are exact, so the lane split and the xor tree do not change S.
+__global__ void __launch_bounds__(256)
+nh_update_kernel(const float *__restrict__ Y, int N, int Np, int R, double h, double NT, double dt,
+                 double *__restrict__ xi, float *__restrict__ gvec, int *__restrict__ err)
+{
+    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= R)
+        return;
+    const float *yr = Y + (size_t)r * Np;
+    uint64_t hi = 0, lo = 0;
+    bool bad = false;
+#pragma unroll 4
+    for (int i = lane; i < N; i += 32) {
+        uint64_t th, tl;
+        square_q64(yr[i], th, tl, bad);
+        add_u128(hi, lo, th, tl);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t oh = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
+        const uint64_t ol = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
+        add_u128(hi, lo, oh, ol);
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0)
+        atomicExch(err, kErrRange);
+    if (lane == 0) {
+        const double S = u128_scaled_to_double(hi, lo);
+        const double x = __dadd_rn(xi[r], __dmul_rn(h, __dsub_rn(S, NT)));
+        xi[r] = x;
+        gvec[r] = __double2float_rn(__dmul_rn(-x, dt));
+    }
+}
+
+cudaError_t launch_nh_init(cudaStream_t st, int R, int Rp, double xi0, double dt, double *xi,
+                           float *gvec)
+{
+    nh_init_kernel<<<(Rp + 255) / 256, 256, 0, st>>>(R, Rp, xi0, dt, xi, gvec);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nh_update(cudaStream_t st, const float *Y, int N, int Np, int R, double h,
+                             double NT, double dt, double *xi, float *gvec, int *err)
+{
+    nh_update_kernel<<<(R + 7) / 8, 256, 0, st>>>(Y, N, Np, R, h, NT, dt, xi, gvec, err);
     return cudaGetLastError();
 }
 
@@ -277,10 +416,99 @@ trace_reduce_kernel(const float *__restrict__ Epart, const float *__restrict__ T
     }
 }
 
-cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,
-                                int N, int R, int Rp, double *out)
+// The same trace entry from many blocks.  Block b takes replicas 32 b ..
+// 32 b + 31 (lane) and splits the row blocks over its 8 warps (warp w sums
+// blocks w, w + 8, ... in order); warp 0 adds the 8 slices in order, reduces
+// its 32 replicas with a fixed shuffle tree and writes part[3 b .. 3 b + 2] =
+// {minimum E, sum E, sum T_inst}.  The last block to finish (ticket counter,
+// reset by that block) combines the parts in a fixed order into out, so the
+// result does not depend on the order in which blocks run.
+__global__ void __launch_bounds__(256)
+trace_parts_kernel(const float *__restrict__ Epart, const float *__restrict__ Tpart, int nblk,
+                   int N, int R, int Rp, double *__restrict__ part, unsigned *__restrict__ ticket,
+                   double *__restrict__ out)
 {
-    trace_reduce_kernel<<<1, 1024, 0, st>>>(Epart, Tpart, nblk, N, R, Rp, out);
+    __shared__ double se_sh[8][32], st_sh[8][32];
+    __shared__ double fmin_sh[256], fsum_sh[256], ftt_sh[256];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r = blockIdx.x * 32 + lane;
+    double e = 0.0, t = 0.0;
+    if (r < R) {
+#pragma unroll 4
+        for (int b = w; b < nblk; b += 8) {
+            e += (double)Epart[(size_t)b * Rp + r];
+            t += (double)Tpart[(size_t)b * Rp + r];
+        }
+    }
+    se_sh[w][lane] = e;
+    st_sh[w][lane] = t;
+    __syncthreads();
+    if (w == 0) {
+        double es = 0.0, ts = 0.0;
+        for (int v = 0; v < 8; ++v) {
+            es += se_sh[v][lane];
+            ts += st_sh[v][lane];
+        }
+        double mn = INFINITY, sm = 0.0, tt = 0.0;
+        if (r < R) {
+            mn = -0.5 * es;
+            sm = -0.5 * es;
+            tt = ts / (double)N;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = fmin(mn, __shfl_down_sync(0xffffffffu, mn, o));
+            sm += __shfl_down_sync(0xffffffffu, sm, o);
+            tt += __shfl_down_sync(0xffffffffu, tt, o);
+        }
+        if (lane == 0) {
+            part[3 * (size_t)blockIdx.x] = mn;
+            part[3 * (size_t)blockIdx.x + 1] = sm;
+            part[3 * (size_t)blockIdx.x + 2] = tt;
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        }
+    }
+    __syncthreads();
+    if (!last)
+        return;
+    __threadfence();
+    double mn = INFINITY, sm = 0.0, tt = 0.0;
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += 256) {
+        mn = fmin(mn, __ldcg(part + 3 * (size_t)q));
+        sm += __ldcg(part + 3 * (size_t)q + 1);
+        tt += __ldcg(part + 3 * (size_t)q + 2);
+    }
+    fmin_sh[threadIdx.x] = mn;
+    fsum_sh[threadIdx.x] = sm;
+    ftt_sh[threadIdx.x] = tt;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            fmin_sh[threadIdx.x] = fmin(fmin_sh[threadIdx.x], fmin_sh[threadIdx.x + h]);
+            fsum_sh[threadIdx.x] += fsum_sh[threadIdx.x + h];
+            ftt_sh[threadIdx.x] += ftt_sh[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[0] = fmin_sh[0];
+        out[1] = fsum_sh[0] / (double)R;
+        out[2] = ftt_sh[0] / (double)R;
+        *ticket = 0u;
+    }
+}
+
+cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,
+                                int N, int R, int Rp, double *scratch, unsigned *ticket,
+                                double *out)
+{
+    if (!scratch || !ticket) {
+        trace_reduce_kernel<<<1, 1024, 0, st>>>(Epart, Tpart, nblk, N, R, Rp, out);
+        return cudaGetLastError();
+    }
+    trace_parts_kernel<<<(R + 31) / 32, 256, 0, st>>>(Epart, Tpart, nblk, N, R, Rp, scratch, ticket,
+                                                      out);
     return cudaGetLastError();
 }
 

@@ -130,7 +130,7 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                    int ntiles, float *__restrict__ X, float *__restrict__ Y,
                    uint8_t *__restrict__ S8next, float pk, StepConsts c, int energy,
                    int energy_only, float *__restrict__ Epart, float *__restrict__ Tpart,
-                   int *__restrict__ err)
+                   int *__restrict__ err, const float *__restrict__ gvec)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -293,8 +293,12 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                                 const float y0 = yv[jj];
                                 if (Tpart)
                                     t2 = __fmul_rn(y0, y0);  // y_i(t_k)^2 (Eq. eq_TInst)
+                                // per-replica friction of the Nose-Hoover thermostat
+                                StepConsts cr = c;
+                                if (gvec)
+                                    cr.g = __ldg(gvec + r);
                                 float xn, yn;
-                                sb_update(fj, x0, y0, pk, c, xn, yn);
+                                sb_update(fj, x0, y0, pk, cr, xn, yn);
                                 X[e] = xn;
                                 Y[e] = yn;
                                 S8next[e] = live ? fp8_sign(xn) : (uint8_t)0;
@@ -464,7 +468,7 @@ void tc_plan_destroy(TcPlan *p) { delete p; }
 cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
                                bool energy_only, int N, int Rp, float *X, float *Y, float pk,
                                StepConsts c, float *Epart, float *Tpart, uint8_t *S8next,
-                               int *err)
+                               int *err, const float *gvec)
 {
     // Rp (this run's padded replica count) may be below the capacity the
     // tensor maps were encoded for; Epart rows are Rp long.  A last tile that
@@ -482,7 +486,7 @@ cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, 
     const int grid = ntiles < sms ? ntiles : sms;
     tc_fp8_step_kernel<<<grid, kThreads, kSmemBytes, st>>>(
         plan->mapA, plan->mapBw[parity & 1], N, plan->Np, Rp, nrb, ntiles, X, Y, S8next, pk, c,
-        energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err);
+        energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err, gvec);
     return cudaGetLastError();
 }
 

@@ -28,13 +28,16 @@ def test_every_declared_symbol_is_exported():
 
 
 def test_version_and_defaults():
-    assert hsb.version() == 1
+    assert hsb.version() == 2
     p = hsb.params()
     assert (p.form, p.prec) == (hsb.HSB_DISCRETE, hsb.HSB_PREC_AUTO)
     # the paper's tuned HdSB settings (Fig. 1 caption), a0 = 1 (Results)
     assert (p.a0, p.c1, p.dt, p.gamma, p.init_half_width, p.eval_every) == \
         (1.0, 0.7, 1.1, 0.06, 1.0, 100)
-    assert C.sizeof(hsb.Params) == 96
+    # constant heating by default; Nose-Hoover fields at their documented offsets
+    assert (p.thermostat, p.nh_T, p.nh_M, p.nh_xi0) == (0, 0.0, 1.0, 0.0)
+    assert (hsb.Params.thermostat.offset, hsb.Params.nh_T.offset) == (72, 80)
+    assert C.sizeof(hsb.Params) == 112
 
 
 def test_create_validates_couplings_on_the_host():

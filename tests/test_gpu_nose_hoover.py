@@ -1,0 +1,131 @@
+"""GPU parity of Nose-Hoover SB (Eqs. eq_NH1, eq_NH) against the CPU oracle.
+
+The friction -xi_r y replaces the constant heating term; xi_r advances after
+each step from S_r = sum_i y_i^2, which both sides form in exact fixed point
+(each term rounded to a multiple of 2^-64, exact 128-bit sum, one rounding),
+so the result does not depend on summation order and trajectories, xi and
+best spins equal the binary32 oracle bit for bit.  Runs on plain FP32 (any
+couplings) and on the one-launch-per-step FP8 kernel (+/-1 couplings), with
+ragged spin and replica tails.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2203_08361_gb300 as hsb
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+
+def _nh(n):
+    # M of order 20 N: the increments dt (S - N T) / M stay of order
+    # dt (T_inst - T) / 20, so xi settles instead of driving |1 - xi dt| past 1
+    return dict(nh_T=0.3, nh_M=20.0 * n, nh_xi0=-0.05)
+
+
+def _nh_oracle(J, form, c1, dt, eval_every, trace_every=0, **nh):
+    c0 = oracle.c0_from_c1(J, c1)
+    return oracle.make_params(form, c0, dt, 0.0, eval_every=eval_every, trace_every=trace_every,
+                              nose_hoover=True, **nh)
+
+
+@pytest.mark.parametrize("kind,form,prec,n,R", [
+    ("pm1", "discrete", "fp8", 1000, 300),
+    ("pm1", "discrete", "fp8", 257, 130),
+    ("pm1", "discrete", "fp32", 300, 130),
+    ("gauss", "ballistic", "fp32", 300, 130),
+    ("gauss", "discrete", "fp32", 200, 40),
+])
+def test_nose_hoover_bit_exact(kind, form, prec, n, R):
+    J = synth.sk_pm1(n, 40 + n) if kind == "pm1" else synth.sk_gauss(n, 40 + n)
+    fcode = 0 if form == "ballistic" else 1
+    c1 = 0.7 if form == "discrete" else 0.9
+    steps, seed, ev, te = 200, 12, 50, 10
+    NH = _nh(n)
+    p = hsb.params(form, prec, c1=c1, dt=1.1, eval_every=ev, trace_every=te,
+                   thermostat="nose_hoover", **NH)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, steps, seed)
+        x, y = s.get_state(R)
+        xi = s.get_xi(R)
+        tr = s.get_trace()
+    ref = oracle.run(J, _nh_oracle(J, fcode, c1, 1.1, ev, te, **NH), steps, seed, range(R),
+                     "f32", want_trace=True)
+    np.testing.assert_array_equal(xi, ref["xi"])
+    np.testing.assert_array_equal(x, ref["x"])
+    np.testing.assert_array_equal(y, ref["y"])
+    np.testing.assert_array_equal(spins, ref["best_s"])
+    if kind == "pm1":
+        np.testing.assert_array_equal(energy, ref["best_e"])
+    else:
+        np.testing.assert_allclose(energy, ref["best_e"], rtol=1e-12, atol=1e-9)
+    # the thermostat acts: xi moved away from xi0 in every replica
+    assert np.all(xi != NH["nh_xi0"])
+    # trace: minimum / mean energy and mean T_inst at t_k, k = 0, 10, ...;
+    # exact integers for +/-1 couplings, binary32 force sums otherwise
+    rt = 0.0 if kind == "pm1" else 1e-5
+    np.testing.assert_allclose(tr[:, 0], ref["trace_e"].min(axis=0), rtol=rt, atol=1e-9)
+    np.testing.assert_allclose(tr[:, 1], ref["trace_e"].mean(axis=0), rtol=max(rt, 1e-12),
+                               atol=1e-9)
+    np.testing.assert_allclose(tr[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6)
+
+
+@pytest.mark.parametrize("prec", ["fp8", "fp32"])
+def test_nose_hoover_large_mass_equals_constant_heating(prec):
+    # With M = 1e300 the xi increments vanish below binary64 resolution, so a
+    # run with xi0 = -gamma is the constant-gamma run, bit for bit.
+    J = synth.sk_pm1(500, 5)
+    R, steps, seed = 200, 150, 3
+    heat = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=30,
+                      schedule="per_step")
+    nh = hsb.params("discrete", prec, c1=0.7, dt=1.1, eval_every=30, schedule="per_step",
+                    thermostat="nose_hoover", nh_T=0.3, nh_M=1e300, nh_xi0=-0.06)
+    with hsb.Solver(J) as s:
+        sa, ea = s.run(heat, R, steps, seed)
+        xa, ya = s.get_state(R)
+        sb, eb = s.run(nh, R, steps, seed)
+        xb, yb = s.get_state(R)
+        xi = s.get_xi(R)
+    np.testing.assert_array_equal(sa, sb)
+    np.testing.assert_array_equal(ea, eb)
+    np.testing.assert_array_equal(xa, xb)
+    np.testing.assert_array_equal(ya, yb)
+    np.testing.assert_array_equal(xi, np.full(R, -0.06))
+
+
+def test_nose_hoover_argument_checks():
+    J = synth.sk_pm1(256, 1)
+    G = synth.sk_gauss(256, 1)
+    nh = dict(thermostat="nose_hoover", **_nh(256))
+    with hsb.Solver(J) as s:
+        for bad in (dict(schedule="persistent"), dict(schedule="resident")):
+            with pytest.raises(hsb.HsbError) as e:
+                s.run(hsb.params("discrete", "fp8", **nh, **bad), 128, 10, 0)
+            assert e.value.status == hsb.HSB_E_UNSUPPORTED
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("discrete", "fp8", thermostat="nose_hoover", nh_M=0.0), 128, 10, 0)
+        assert e.value.status == hsb.HSB_E_INVAL
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("discrete", "fp8", thermostat=2), 128, 10, 0)
+        assert e.value.status == hsb.HSB_E_INVAL
+        x0 = np.zeros((4, 256), np.float32)
+        with pytest.raises(hsb.HsbError) as e:
+            s.advance(hsb.params("discrete", "fp32", **nh), 10, 0, 5, x0, x0)
+        assert e.value.status == hsb.HSB_E_UNSUPPORTED
+        # xi exists only after a Nose-Hoover run, for its replica count
+        s.run(hsb.params("discrete", "fp8", gamma=0.06), 128, 10, 0)
+        with pytest.raises(hsb.HsbError):
+            s.get_xi(128)
+        s.run(hsb.params("discrete", "fp8", **nh), 128, 10, 0)
+        assert s.get_xi(128).shape == (128,)
+        with pytest.raises(hsb.HsbError):
+            s.get_xi(64)
+    with hsb.Solver(G) as s:
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("ballistic", "bf16x3", **nh), 128, 10, 0)
+        assert e.value.status == hsb.HSB_E_UNSUPPORTED
+        # AUTO picks plain FP32 for general couplings under the thermostat
+        s.run(hsb.params("ballistic", "auto", **nh), 128, 10, 0)
+        assert s.get_xi(128).shape == (128,)
