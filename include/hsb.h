@@ -116,7 +116,7 @@ typedef struct {
                                Nose-Hoover runs on FP32 or on FP8 with one launch per
                                step (AUTO never picks BF16X3 for it); schedules 1 and
                                3, hsb_advance* and hsb_run_batch return
-                               HSB_E_UNSUPPORTED.  A momentum |y| >= 2^19 (an
+                               HSB_E_UNSUPPORTED.  A momentum |y| >= 256 (an
                                unstable setting: M much below N) makes the run
                                return HSB_E_INVAL.  See hsb_get_xi. */
     int reserved0;          /* must be zero */
@@ -131,7 +131,9 @@ typedef enum {
     /* Per step, in binary64 with each operation rounded once: the update uses
        the friction factor g_r = fl32(-xi_r dt) where HbSB uses fl32(gamma dt)
        (the friction -xi y(t_k) in place of the heating term); then
-       S_r = sum_i y_i(t_{k+1})^2, xi_r += (dt / M) (S_r - N T). */
+       S_r = sum_i y_i(t_{k+1})^2, xi_r += (dt / M) (S_r - N T).  S_r is
+       exact fixed point, independent of summation order: each y_i rounded
+       to a multiple of 2^-24, the squares summed as integers, one rounding. */
     HSB_HEAT_NOSE_HOOVER = 1
 } hsb_thermostat;
 

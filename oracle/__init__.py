@@ -208,7 +208,7 @@ def num_evals(steps: int, eval_every: int) -> int:
 
 def kinetic_sum(y, precision: str = "f32") -> float:
     """S = sum_i y_i^2 of Eq. (eq_NH) as the Nose-Hoover update forms it (each
-    y_i^2 rounded to a multiple of 2^-64, exact 128-bit sum, one rounding)."""
+    y_i rounded to a multiple of 2^-24, squares summed exactly, one rounding)."""
     real = _real(precision)
     y = np.ascontiguousarray(y, dtype=real).ravel()
     fn = getattr(_load(), f"oracle_kinetic_sum_{precision}")

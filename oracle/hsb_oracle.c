@@ -53,9 +53,11 @@
  *       xi_{k+1} = xi_k + (dt/M) (S - N T)  (h = dt/M and N T in binary64,
  *                                            each operation rounded once)
  *     S is formed in fixed point so that it does not depend on the order of
- *     summation: each y_i^2 is rounded to the nearest multiple of 2^-64 (ties
- *     to even), the multiples are added exactly as 128-bit integers, and the
- *     total is rounded once to binary64 (oracle_kinetic_sum).
+ *     summation: each y_i is rounded to the nearest multiple of 2^-24 (ties to
+ *     even; exact for |y_i| >= 1/2 in binary32), q_i = 2^24 y_i is squared
+ *     exactly as an integer, the squares are added exactly as 128-bit
+ *     integers, and 2^-48 times the total is rounded once to binary64
+ *     (oracle_kinetic_sum).  |y_i| < 256.
  *
  * Precision: every routine exists twice, in binary64 ("_f64", the reference
  * for tolerance checks) and in binary32 ("_f32", the paper's own single

@@ -90,19 +90,19 @@ static void SFX(update)(int N, REAL *x, REAL *y, const REAL *f, REAL c0, REAL pk
 }
 
 /* S = sum_i y_i^2 of the Nose-Hoover equation (eq_NH) in fixed point: each
- * y_i^2 (exact in binary64 when y is binary32) is scaled by 2^64 (exact),
- * rounded to the nearest integer, ties to even (nearbyint in the default
- * rounding mode), added exactly to a 128-bit unsigned integer, and the total
- * is converted once to binary64 (correctly rounded) and scaled back by 2^-64.
- * The result is independent of the order of the terms.  sum_i y_i^2 < 2^63. */
+ * y_i is scaled by 2^24 (exact) and rounded to the nearest integer q_i, ties
+ * to even (nearbyint in the default rounding mode); the squares q_i^2 (exact
+ * in 64 bits for |y_i| < 256) are added exactly to a 128-bit unsigned integer,
+ * and 2^-48 times the total is converted once to binary64 (correctly
+ * rounded).  The result is independent of the order of the terms. */
 double SFX(oracle_kinetic_sum)(const REAL *y, int N)
 {
     unsigned __int128 acc = 0;
     for (int i = 0; i < N; ++i) {
-        const double v = (double)y[i] * (double)y[i];
-        acc += (unsigned __int128)nearbyint(v * 0x1p64);
+        const uint64_t q = (uint64_t)fabs(nearbyint((double)y[i] * 0x1p24));
+        acc += (unsigned __int128)q * q;
     }
-    return (double)acc * 0x1p-64;
+    return (double)acc * 0x1p-48;
 }
 
 static REAL *SFX(widen)(const float *J, int N)

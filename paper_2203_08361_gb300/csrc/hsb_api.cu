@@ -836,7 +836,7 @@ hsb_status check_device_error(hsb_ctx *h)
     if (e == kErrTimeout)
         return set_error(HSB_E_TIMEOUT, "a bounded device-side wait gave up");
     if (e == kErrRange)
-        return set_error(HSB_E_INVAL, "a momentum reached |y| >= 2^19 in the Nose-Hoover sum");
+        return set_error(HSB_E_INVAL, "a momentum reached |y| >= 256 in the Nose-Hoover sum");
     if (e != 0)
         return set_error(HSB_E_CUDA, "device error code %d", e);
     return HSB_OK;

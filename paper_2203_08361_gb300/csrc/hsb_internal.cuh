@@ -68,10 +68,10 @@ cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool e
 // init: xi_r = xi0, g_r = fl32(-xi0 dt) for r < R; xi_r = g_r = 0 up to Rp.
 cudaError_t launch_nh_init(cudaStream_t st, int R, int Rp, double xi0, double dt, double *xi,
                            float *gvec);
-// update after a step: S_r = sum_{i<N} y_i^2 (each term rounded to a multiple
-// of 2^-64, exact 128-bit sum, one rounding to binary64), xi_r += h (S_r - NT)
-// with h = dt / M and NT = N T given in binary64, then g_r = fl32(-xi_r dt).
-// A momentum with |y| >= 2^19 (or not finite) sets *err = kErrRange.
+// update after a step: S_r = sum_{i<N} y_i^2 (y_i rounded to a multiple of
+// 2^-24, squares summed exactly, one rounding to binary64), xi_r += h (S_r -
+// NT) with h = dt / M and NT = N T given in binary64, then g_r = fl32(-xi_r
+// dt).  A momentum with |y| >= 256 (or not finite) sets *err = kErrRange.
 cudaError_t launch_nh_update(cudaStream_t st, const float *Y, int N, int Np, int R, double h,
                              double NT, double dt, double *xi, float *gvec, int *err);
 

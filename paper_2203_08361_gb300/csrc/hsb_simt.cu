@@ -249,9 +249,10 @@ cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool e
 // momenta from the updated ones.  Arithmetic in binary64 with the operations
 // rounded one by one (no contraction), the factor rounded once to binary32.
 // S_r = sum_i y_i^2 is formed in fixed point so that it does not depend on the
-// order of summation: each y_i^2 is rounded to the nearest multiple of 2^-64,
-// the multiples are added exactly as 128-bit integers, and the total is
-// rounded once to binary64.
+// order of summation: y_i is rounded to the nearest multiple of 2^-24 (exact
+// for |y_i| >= 1/2), q_i = 2^24 y_i is squared as a 64-bit integer, the
+// squares are added exactly in 128 bits, and 2^-48 times the total is rounded
+// once to binary64.
 
 __global__ void nh_init_kernel(int R, int Rp, double xi0, double dt, double *__restrict__ xi,
                                float *__restrict__ gvec)
@@ -266,43 +267,8 @@ __global__ void nh_init_kernel(int R, int Rp, double xi0, double dt, double *__r
 
 namespace {
 
-// y^2 in units of 2^-64, rounded to the nearest integer, as (hi, lo).  With
-// y = m 2^ex (m < 2^24), y^2 2^64 = m^2 2^s, s = 2 ex + 64 (even).  A tie
-// would need m^2 = 2^(k-1) mod 2^k for k = -s > 0, impossible for a square
-// (even 2-adic valuation), so rounding up on "remainder above half" is exact
-// round-to-nearest.  |y| >= 2^19 (s > 54) or a non-finite y sets *bad.
-__device__ __forceinline__ void square_q64(float y, uint64_t &hi, uint64_t &lo, bool &bad)
-{
-    const uint32_t b = __float_as_uint(y) & 0x7FFFFFFFu;
-    const uint32_t e = b >> 23;
-    hi = 0;
-    lo = 0;
-    if (e == 255u) {
-        bad = true;
-        return;
-    }
-    const uint64_t m = e ? (uint64_t)((b & 0x7FFFFFu) | 0x800000u) : (uint64_t)b;
-    const int ex = e ? (int)e - 150 : -149;
-    const uint64_t m2 = m * m;  // < 2^48
-    const int s = 2 * ex + 64;
-    if (m2 == 0)
-        return;
-    if (s >= 0) {
-        if (s > 54) {
-            bad = true;
-            return;
-        }
-        lo = m2 << s;
-        hi = s ? m2 >> (64 - s) : 0;
-    } else {
-        const int k = -s;
-        if (k >= 49)  // m2 2^-k < 2^48 2^-49: below one half
-            return;
-        const uint64_t q = m2 >> k;
-        const uint64_t rem = m2 & ((1ull << k) - 1ull);
-        lo = q + (rem > (1ull << (k - 1)) ? 1ull : 0ull);
-    }
-}
+constexpr int kNhThreads = 128;  // one block per replica
+constexpr int kNhBatch = 8;      // loads in flight per thread
 
 __device__ __forceinline__ void add_u128(uint64_t &hi, uint64_t &lo, uint64_t bh, uint64_t bl)
 {
@@ -311,52 +277,85 @@ __device__ __forceinline__ void add_u128(uint64_t &hi, uint64_t &lo, uint64_t bh
     lo = l;
 }
 
-// (hi 2^64 + lo) 2^-64 rounded once to binary64: the top 64 significant bits
+// q^2 for q = round(2^24 y) (scaling exact, rounding to nearest even); |y|
+// must stay below 256 (so |q| < 2^32), else *bad (also for NaN).
+__device__ __forceinline__ void add_square_q24(float y, uint64_t &hi, uint64_t &lo, bool &bad)
+{
+    const float s = y * 16777216.0f;
+    if (!(fabsf(s) < 4294967296.0f)) {
+        bad = true;
+        return;
+    }
+    const long long q = __float2ll_rn(s);
+    const uint32_t a = (uint32_t)(q < 0 ? -q : q);
+    add_u128(hi, lo, 0ull, (uint64_t)a * a);
+}
+
+// 2^-48 (hi 2^64 + lo) rounded once to binary64: the top 64 significant bits
 // with the bits below them folded into a sticky bit 0 round to 53 bits as the
 // full value does (the rounding position is bit 11 of the 64); the scaling
 // by a power of two is exact.
-__device__ __forceinline__ double u128_scaled_to_double(uint64_t hi, uint64_t lo)
+__device__ __forceinline__ double u128_q48_to_double(uint64_t hi, uint64_t lo)
 {
     if (hi == 0)
-        return __dmul_rn(__ull2double_rn(lo), 0x1p-64);
+        return __dmul_rn(__ull2double_rn(lo), 0x1p-48);
     const int lz = __clzll((long long)hi);
     uint64_t t = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
     if (lo << lz)
         t |= 1ull;
-    const double scale = __longlong_as_double((long long)(1023 - lz) << 52);  // 2^-lz
+    const double scale = __longlong_as_double((long long)(1023 + 16 - lz) << 52);  // 2^(16-lz)
     return __dmul_rn(__ull2double_rn(t), scale);
 }
 
 }  // namespace
 
-// One warp per replica: lane l accumulates i = l, l + 32, ...; integer sums
-// are exact, so the lane split and the xor tree do not change S.
-__global__ void __launch_bounds__(256)
-nh_update_kernel(const float *__restrict__ Y, int N, int Np, int R, double h, double NT, double dt,
+// One block per replica; thread t takes i = t + 128 m, eight loads in flight
+// at a time.  Integer sums are exact, so the split over threads, the xor tree
+// and the combination of the warps do not change S.
+__global__ void __launch_bounds__(kNhThreads)
+nh_update_kernel(const float *__restrict__ Y, int N, int Np, double h, double NT, double dt,
                  double *__restrict__ xi, float *__restrict__ gvec, int *__restrict__ err)
 {
-    const int r = blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= R)
-        return;
+    __shared__ uint64_t part[kNhThreads / 32][2];
+    __shared__ int any_bad;
+    const int r = blockIdx.x;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0)
+        any_bad = 0;
     const float *yr = Y + (size_t)r * Np;
     uint64_t hi = 0, lo = 0;
     bool bad = false;
-#pragma unroll 4
-    for (int i = lane; i < N; i += 32) {
-        uint64_t th, tl;
-        square_q64(yr[i], th, tl, bad);
-        add_u128(hi, lo, th, tl);
+    for (int i0 = threadIdx.x; i0 < N; i0 += kNhThreads * kNhBatch) {
+        float v[kNhBatch];
+#pragma unroll
+        for (int u = 0; u < kNhBatch; ++u) {
+            const int i = i0 + u * kNhThreads;
+            v[u] = i < N ? yr[i] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kNhBatch; ++u)
+            add_square_q24(v[u], hi, lo, bad);
     }
     for (int o = 16; o > 0; o >>= 1) {
         const uint64_t oh = __shfl_xor_sync(0xFFFFFFFFu, hi, o);
         const uint64_t ol = __shfl_xor_sync(0xFFFFFFFFu, lo, o);
         add_u128(hi, lo, oh, ol);
     }
-    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0)
-        atomicExch(err, kErrRange);
+    __syncthreads();  // any_bad is initialised
+    if (bad)
+        any_bad = 1;
     if (lane == 0) {
-        const double S = u128_scaled_to_double(hi, lo);
+        part[w][0] = hi;
+        part[w][1] = lo;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t sh = 0, sl = 0;
+        for (int q = 0; q < kNhThreads / 32; ++q)
+            add_u128(sh, sl, part[q][0], part[q][1]);
+        if (any_bad)
+            atomicExch(err, kErrRange);
+        const double S = u128_q48_to_double(sh, sl);
         const double x = __dadd_rn(xi[r], __dmul_rn(h, __dsub_rn(S, NT)));
         xi[r] = x;
         gvec[r] = __double2float_rn(__dmul_rn(-x, dt));
@@ -373,7 +372,7 @@ cudaError_t launch_nh_init(cudaStream_t st, int R, int Rp, double xi0, double dt
 cudaError_t launch_nh_update(cudaStream_t st, const float *Y, int N, int Np, int R, double h,
                              double NT, double dt, double *xi, float *gvec, int *err)
 {
-    nh_update_kernel<<<(R + 7) / 8, 256, 0, st>>>(Y, N, Np, R, h, NT, dt, xi, gvec, err);
+    nh_update_kernel<<<R, kNhThreads, 0, st>>>(Y, N, Np, h, NT, dt, xi, gvec, err);
     return cudaGetLastError();
 }
 

@@ -500,24 +500,28 @@ def test_nose_hoover_force_free_invariant_and_mean_temperature():
 
 
 def test_nose_hoover_kinetic_sum_is_the_exact_fixed_point_sum():
-    # S of Eq. (eq_NH) as formed by the update: each y_i^2 rounded to the
-    # nearest multiple of 2^-64, summed exactly, rounded once.  Reference:
-    # Python's exact rationals (round() to nearest, float() correctly rounded).
+    # S of Eq. (eq_NH) as formed by the update: each y_i rounded to the
+    # nearest multiple of 2^-24, the squares summed exactly, 2^-48 times the
+    # total rounded once.  Reference: Python's exact rationals (round() to
+    # nearest even, float() correctly rounded).
     from fractions import Fraction
     rng = np.random.default_rng(4)
     cases = [
         rng.uniform(-1, 1, 1000).astype(np.float32),
-        np.float32([2.0**-32, 3 * 2.0**-33, 1e-12, 7e-10, -2.0**-40, 0.0, -0.0]),
-        np.concatenate([rng.uniform(-1, 1, 300), rng.uniform(-1e-9, 1e-9, 300),
-                        rng.uniform(-300, 300, 40)]).astype(np.float32),
-        np.float32([1.0] * 5000),     # the 128-bit sum carries past 2^64 units
+        np.float32([2.0**-24, 3 * 2.0**-26, 2.0**-25, 3 * 2.0**-25, 1e-12, 7e-8, -2.0**-40,
+                    0.0, -0.0, 255.9]),
+        np.concatenate([rng.uniform(-1, 1, 300), rng.uniform(-1e-6, 1e-6, 300),
+                        rng.uniform(-200, 200, 40)]).astype(np.float32),
+        np.float32([1.0] * 70000),    # the 128-bit sum carries past 2^64
     ]
     for y in cases:
-        units = sum(round(Fraction(float(v)) ** 2 * 2**64) for v in y)
-        want = float(Fraction(units, 2**64))
+        units = sum(round(Fraction(float(v)) * 2**24) ** 2 for v in y)
+        want = float(Fraction(units, 2**48))
         assert oracle.kinetic_sum(y) == want
         # order does not matter
         assert oracle.kinetic_sum(y[::-1].copy()) == want
-        # and it is the plain sum of squares up to the 2^-64 quantisation
+        # and it is the plain sum of squares up to the 2^-24 quantisation of y
         exact = sum(Fraction(float(v)) ** 2 for v in y)
-        assert abs(Fraction(want) - exact) <= Fraction(len(y) + 1, 2**65) + abs(exact) * 2.0**-53
+        bound = sum(abs(Fraction(float(v))) for v in y) * Fraction(1, 2**24) \
+            + Fraction(len(y), 2**50) + abs(exact) * Fraction(1, 2**53)
+        assert abs(Fraction(want) - exact) <= bound
