@@ -526,6 +526,21 @@ def run_other(args, w):
                                 f"sustained of {src} peaks"),
                 "scope": "whole run (force, update, evaluations, final energies); "
                          "algorithmic 2 N^2 R per step"}
+    if w["kind"] == "batch":
+        # The batch streams every instance's FP8 couplings each step (their sum
+        # exceeds L2) and keeps x, y in global memory: per step and instance
+        # N^2 bytes of J, 16 N R bytes of x, y read and written, 2 N R bytes
+        # of the sign operand written and read back.  That traffic, not the
+        # tensor rate, bounds it.
+        nbytes = sum(J.shape[0] ** 2 + 18 * J.shape[0] * R for J in Js) * S
+        hbm = float(mp.get("hbm_gbs", 6800.0))
+        gbs = nbytes / t_run / 1e9
+        roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                    "frac": gbs / hbm, "traffic": None,
+                    "peak_source": f"hbm_gbs of {src} peaks",
+                    "scope": "whole batched launch; algorithmic bytes per step and instance "
+                             "N^2 (J, FP8) + 18 N R (x, y read and written, sign operand)",
+                    "tensor_frac": achieved / peak}
     if w["prec"] == "bf16x3":
         roofline["executed_tflops"] = 3.0 * achieved
     line = {"metric": f"replica-spin-steps/s ({w['name']})", "value": units / t_run,

@@ -23,6 +23,10 @@ NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
     "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+    # host arithmetic (sigma_J, p_k, c0, the Nose-Hoover constants) rounds
+    # every operation, as the oracle does: no contraction into fused
+    # multiply-add (arm64 gcc contracts by default)
+    "-Xcompiler", "-ffp-contract=off",
     "-I", INCLUDE, "-I", CSRC,
 ]
 

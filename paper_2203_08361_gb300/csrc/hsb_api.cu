@@ -17,6 +17,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <vector>
 
@@ -499,6 +500,115 @@ hsb_status prepare(hsb_ctx *h, const RunCfg &c)
     return HSB_OK;
 }
 
+// Eq. (eq_Ising): J_ij = J_ji and J_ii = 0 (host, row-major N x N).  Also
+// reports whether every entry is -1, 0 or +1, and sum_ij J_ij^2 and
+// sum_ij J_ij (sigma_J and the cut offset) as the binary64 sums taken row by
+// row with j ascending.  Symmetry is checked in 64 x 64 block pairs over the
+// upper triangle; for +/-1 couplings every partial sum is an integer below
+// 2^53, so integer counts give the same binary64 values.  Row blocks are
+// split over a few host threads (interleaved, for balance); every result is
+// a boolean or an exact integer, so the split does not change it.  General
+// couplings take the sequential binary64 sums afterwards.
+struct CouplingScan {
+    long long nonzero = 0, signed_sum = 0;
+    bool other = false;           // an entry outside {-1, 0, +1}
+    int ai = -1, aj = -1;         // first asymmetric pair found (i < j)
+};
+
+void scan_row_blocks(const float *J, int N, int first, int stride, CouplingScan *out)
+{
+    constexpr int kB = 64;
+    const size_t n = (size_t)N;
+    CouplingScan r;
+    for (int ib = first * kB; ib < N && r.ai < 0; ib += stride * kB) {
+        const int ie = std::min(ib + kB, N);
+        for (int jb = ib; jb < N && r.ai < 0; jb += kB) {
+            const int je = std::min(jb + kB, N);
+            for (int i = ib; i < ie && r.ai < 0; ++i)
+                for (int j = std::max(jb, i + 1); j < je; ++j)
+                    if (!(J[(size_t)i * n + j] == J[(size_t)j * n + i])) {
+                        r.ai = i;
+                        r.aj = j;
+                        break;
+                    }
+        }
+        for (int i = ib; i < ie; ++i) {
+            // branch-free (random signs would defeat branch prediction)
+            const float *row = J + (size_t)i * n;
+            int nz = 0, sg = 0, other = 0;
+            for (int jj = 0; jj < N; ++jj) {
+                const float v = row[jj];
+                const int p = v == 1.0f, m = v == -1.0f, z = v == 0.0f;
+                nz += p + m;
+                sg += p - m;
+                other |= (p | m | z) ^ 1;
+            }
+            r.nonzero += nz;
+            r.signed_sum += sg;
+            r.other = r.other || other != 0;
+        }
+    }
+    *out = r;
+}
+
+hsb_status validate_couplings(const float *J, int N, int *pm1_out, double *sum2_out,
+                              double *sumJ_out)
+{
+    const size_t n = (size_t)N;
+    for (int i = 0; i < N; ++i)
+        if (J[(size_t)i * n + i] != 0.0f)
+            return set_error(HSB_E_DIAG, "J[%d][%d] = %g is not zero", i, i,
+                             (double)J[(size_t)i * n + i]);
+    const unsigned hw = std::thread::hardware_concurrency();
+    int nt = N >= 1024 ? (int)std::min(8u, hw ? hw : 1u) : 1;
+    std::vector<CouplingScan> part((size_t)nt);
+    std::vector<std::thread> pool;
+    try {
+        for (int t = 1; t < nt; ++t)
+            pool.emplace_back(scan_row_blocks, J, N, t, nt, &part[(size_t)t]);
+    } catch (...) {
+        // no threads to be had: scan the remaining row blocks here
+        for (size_t t = pool.size() + 1; t < (size_t)nt; ++t)
+            scan_row_blocks(J, N, (int)t, nt, &part[t]);
+    }
+    scan_row_blocks(J, N, 0, nt, &part[0]);
+    for (std::thread &th : pool)
+        th.join();
+    long long nonzero = 0, signed_sum = 0;
+    bool pm1 = true;
+    int ai = -1, aj = -1;
+    for (const CouplingScan &r : part) {
+        nonzero += r.nonzero;
+        signed_sum += r.signed_sum;
+        pm1 = pm1 && !r.other;
+        if (r.ai >= 0 && (ai < 0 || r.ai < ai || (r.ai == ai && r.aj < aj))) {
+            ai = r.ai;
+            aj = r.aj;
+        }
+    }
+    if (ai >= 0)
+        return set_error(HSB_E_ASYM, "J[%d][%d] != J[%d][%d]", ai, aj, aj, ai);
+    double sum2 = 0.0, sumJ = 0.0;
+    if (pm1) {
+        sum2 = (double)nonzero;
+        sumJ = (double)signed_sum;
+    } else {
+        // sigma_J^2 = sum_ij J_ij^2 / (N(N-1)), summed row by row in binary64
+        for (size_t e = 0; e < n * n; ++e) {
+            const double d = (double)J[e];
+            sum2 += d * d;
+            sumJ += d;
+        }
+    }
+    if (!(sum2 > 0.0))
+        return set_error(HSB_E_INVAL, "J is all zero");
+    *pm1_out = pm1 ? 1 : 0;
+    *sum2_out = sum2;
+    *sumJ_out = sumJ;
+    return HSB_OK;
+}
+
+GraphKey make_key(const hsb_ctx *h, const RunCfg &c);
 GraphKey make_key(const hsb_ctx *h, const RunCfg &c);
 
 int num_evals(const RunCfg &c)
@@ -983,27 +1093,11 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
         return set_error(HSB_E_INVAL, "J is NULL");
     if (N < 2 || N > (1 << 20))
         return set_error(HSB_E_INVAL, "N must be in [2, 2^20] (got %d)", N);
-    // Eq. (eq_Ising): J_ij = J_ji and J_ii = 0.
     int pm1 = 1;
     double sum2 = 0.0, sumJ = 0.0;
-    for (int i = 0; i < N; ++i) {
-        if (J[(size_t)i * N + i] != 0.0f)
-            return set_error(HSB_E_DIAG, "J[%d][%d] = %g is not zero", i, i,
-                             (double)J[(size_t)i * N + i]);
-        for (int j = 0; j < N; ++j) {
-            const float v = J[(size_t)i * N + j];
-            if (!(v == J[(size_t)j * N + i]))
-                return set_error(HSB_E_ASYM, "J[%d][%d] != J[%d][%d]", i, j, j, i);
-            if (!(v == 1.0f || v == -1.0f || v == 0.0f))
-                pm1 = 0;
-            // sigma_J^2 = sum_ij J_ij^2 / (N(N-1)), summed row by row in binary64
-            const double d = (double)v;
-            sum2 += d * d;
-            sumJ += d;
-        }
-    }
-    if (!(sum2 > 0.0))
-        return set_error(HSB_E_INVAL, "J is all zero");
+    hsb_status vs = validate_couplings(J, N, &pm1, &sum2, &sumJ);
+    if (vs != HSB_OK)
+        return vs;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
         cudaGetLastError();
@@ -1358,23 +1452,9 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
     const int N = h->N;
     int pm1 = 1;
     double sum2 = 0.0, sumJ = 0.0;
-    for (int i = 0; i < N; ++i) {
-        if (J[(size_t)i * N + i] != 0.0f)
-            return set_error(HSB_E_DIAG, "J[%d][%d] = %g is not zero", i, i,
-                             (double)J[(size_t)i * N + i]);
-        for (int j = 0; j < N; ++j) {
-            const float v = J[(size_t)i * N + j];
-            if (!(v == J[(size_t)j * N + i]))
-                return set_error(HSB_E_ASYM, "J[%d][%d] != J[%d][%d]", i, j, j, i);
-            if (!(v == 1.0f || v == -1.0f || v == 0.0f))
-                pm1 = 0;
-            const double d = (double)v;
-            sum2 += d * d;
-            sumJ += d;
-        }
-    }
-    if (!(sum2 > 0.0))
-        return set_error(HSB_E_INVAL, "J is all zero");
+    hsb_status vs = validate_couplings(J, N, &pm1, &sum2, &sumJ);
+    if (vs != HSB_OK)
+        return vs;
     DeviceGuard g(h->device);
     if (!g.ok)
         return set_error(HSB_E_NODEVICE, "cannot select the handle's device");

@@ -55,6 +55,36 @@ def test_create_validates_couplings_on_the_host():
     with pytest.raises(hsb.HsbError) as e:
         hsb.create(np.zeros((1, 1), np.float32))
     assert e.value.status == 1  # HSB_E_INVAL
+    with pytest.raises(hsb.HsbError) as e:
+        hsb.create(np.zeros((5, 5), np.float32))
+    assert e.value.status == 1  # all zero
+
+
+@pytest.mark.parametrize("n", [63, 64, 65, 200, 301])
+def test_symmetry_check_covers_every_pair(n):
+    # the host check walks 64 x 64 block pairs of the upper triangle: a single
+    # broken pair anywhere (inside a block, across block edges, last row and
+    # column, or a NaN) is found and named
+    rng = np.random.default_rng(n)
+    J = synth.sk_gauss(n, 1)
+    pairs = [(0, 1), (0, n - 1), (n - 2, n - 1), (62 % (n - 1), 63 % n)]
+    pairs += [tuple(sorted(rng.choice(n, 2, replace=False))) for _ in range(20)]
+    for i, j in pairs:
+        if i == j:
+            continue
+        for lower in (False, True):
+            bad = J.copy()
+            a, b = (j, i) if lower else (i, j)
+            bad[a, b] = np.nextafter(bad[a, b], np.float32(np.inf))
+            with pytest.raises(hsb.HsbError) as e:
+                hsb.create(bad)
+            assert e.value.status == 2, (i, j, lower)
+            assert f"J[{min(i, j)}][{max(i, j)}]" in str(e.value)
+    bad = J.copy()
+    bad[n // 2, n // 3] = bad[n // 3, n // 2] = np.nan
+    with pytest.raises(hsb.HsbError) as e:
+        hsb.create(bad)
+    assert e.value.status == 2
 
 
 def test_no_cpu_fallback_without_a_device():
