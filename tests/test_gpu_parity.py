@@ -250,3 +250,49 @@ def test_best_energy_bounded_by_ground_state():
     assert energy.min() == e0
     for r in range(0, 256, 37):
         assert oracle.ising_energy(J, spins[r]) == energy[r]
+
+
+def _dilute_pm1(n, seed, p_zero=0.5):
+    # +/-1 couplings with about half of the pairs removed (J_ij = 0): still
+    # the FP8 path (0 is exact in e4m3), exact integer forces
+    J = synth.sk_pm1(n, seed)
+    rng = np.random.default_rng(seed + 99)
+    keep = np.triu(rng.random((n, n)) >= p_zero, 1)
+    keep = keep | keep.T
+    return np.where(keep, J, np.float32(0.0)).astype(np.float32)
+
+
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
+                                           ("fp32", "auto")])
+@pytest.mark.parametrize("n,R,steps,ev", [
+    (129, 1, 1, 0),       # one replica, one step, final evaluation only
+    (129, 1, 37, 0),      # final evaluation only (the 700-spin protocol)
+    (200, 5, 30, 100),    # evaluation cadence longer than the run
+    (256, 129, 64, 1),    # evaluation at every step
+])
+def test_edge_cases_bit_exact(prec, schedule, n, R, steps, ev):
+    J = synth.sk_pm1(n, 500 + n)
+    seed = 21
+    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=ev,
+                   schedule=schedule)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, steps, seed)
+        x, y = s.get_state(R)
+    ref = oracle.run(J, _oparams(J, 1, 0.7, 1.1, 0.06, ev), steps, seed, range(R), "f32")
+    _assert_same(x, y, spins, energy, ref)
+
+
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
+                                           ("fp32", "auto")])
+def test_diluted_couplings_bit_exact(prec, schedule):
+    n, R, steps, seed, ev = 500, 70, 120, 4, 30
+    J = _dilute_pm1(n, 8)
+    assert 0.4 < np.mean(J == 0) < 0.6
+    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=ev,
+                   schedule=schedule)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, steps, seed)
+        x, y = s.get_state(R)
+    # c0 = c1 / (sqrt(N) sigma_J), sigma_J < 1 for diluted couplings
+    ref = oracle.run(J, _oparams(J, 1, 0.7, 1.1, 0.06, ev), steps, seed, range(R), "f32")
+    _assert_same(x, y, spins, energy, ref)
