@@ -122,8 +122,10 @@ struct hsb_ctx {
     TcPlan *plan = nullptr;
     // persistent FP8 schedule: flags, p_k table, per-evaluation partials and
     // spin snapshots
-    int *flags = nullptr;
+    int *flags = nullptr;  // [2][nblk][nrb] strided: sign tiles, Nose-Hoover sums
     size_t flags_cap = 0;
+    unsigned long long *nhpart = nullptr;  // [3][nblk][Rp][2] Nose-Hoover tile sums
+    size_t nhpart_cap = 0;
     float *pk_dev = nullptr;
     int pk_cap = 0, pk_steps = -1;
     double pk_a0 = 0.0;
@@ -316,9 +318,9 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_UNSUPPORTED, "the trace runs on the one-launch-per-step schedule");
     if (nose_hoover && prec == HSB_PREC_BF16X3)
         return set_error(HSB_E_UNSUPPORTED, "the Nose-Hoover thermostat needs FP32 or FP8");
-    if (nose_hoover && prec == HSB_PREC_FP8 && (p->schedule == 1 || p->schedule == 3))
+    if (nose_hoover && prec == HSB_PREC_FP8 && p->schedule == 3)
         return set_error(HSB_E_UNSUPPORTED,
-                         "the Nose-Hoover thermostat runs on the one-launch-per-step schedule");
+                         "the Nose-Hoover thermostat does not run on the resident-J schedule");
     cfg->prec = prec;
     cfg->form = p->form;
     cfg->R = R;
@@ -620,7 +622,7 @@ int num_evals(const RunCfg &c)
 hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
 {
     *out = false;
-    if (c.prec != HSB_PREC_FP8 || c.schedule == 2 || c.trace_every > 0 || c.thermo)
+    if (c.prec != HSB_PREC_FP8 || c.schedule == 2 || c.trace_every > 0)
         return HSB_OK;
     const bool fits = c.schedule == 3 ? tc_resident_fits(h->Np, c.Rp)
                                       : tc_persistent_fits(h->Np, c.Rp);
@@ -675,15 +677,18 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     const int nrb = c.Rp / kTileR;
     const int ne = evaluate ? num_evals(c) : 0;
     hsb_status s = ensure_pk(h, c);
+    const size_t nflags = (size_t)nblk * nrb * kFlagStride;
     if (s == HSB_OK)
-        s = grow(&h->flags, &h->flags_cap, (size_t)nblk * nrb * kFlagStride, "cudaMalloc flags");
+        s = grow(&h->flags, &h->flags_cap, 2 * nflags, "cudaMalloc flags");
+    if (s == HSB_OK && c.thermo)
+        s = grow(&h->nhpart, &h->nhpart_cap, (size_t)3 * nblk * c.Rp * 2, "cudaMalloc nhpart");
     if (s == HSB_OK && evaluate)
         s = grow(&h->Eeval, &h->eeval_cap, (size_t)ne * nblk * c.Rp, "cudaMalloc Eeval");
     if (s == HSB_OK && evaluate)
         s = grow(&h->Snap, &h->snap_cap, (size_t)ne * c.Rp * h->Np, "cudaMalloc snapshots");
     if (s != HSB_OK)
         return s;
-    CK(cudaMemsetAsync(h->flags, 0, (size_t)nblk * nrb * kFlagStride * sizeof(int), h->work),
+    CK(cudaMemsetAsync(h->flags, 0, (c.thermo ? 2 : 1) * nflags * sizeof(int), h->work),
        "memset flags");
     PersistArgs a;
     memset(&a, 0, sizeof a);
@@ -709,6 +714,16 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     a.Epart = h->Eeval;
     a.Snap = h->Snap;
     a.err = h->err;
+    if (c.thermo) {
+        // Nose-Hoover: xi (set by launch_nh_init) in and out, tile sums, flags
+        a.nh = 1;
+        a.nh_h = c.nh_h;
+        a.nh_NT = c.nh_NT;
+        a.dt64 = c.dt64;
+        a.xi = h->xi;
+        a.nhpart = h->nhpart;
+        a.nhflags = h->flags + nflags;
+    }
     // schedule 3: J resident on chip; otherwise J streamed every step
     if (c.schedule == 3)
         CK(launch_tc_fp8_resident(h->work, h->plan, h->J8, a), "resident fp8 kernel");
@@ -865,6 +880,8 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
         CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R,
                        c.Rp, h->X[0], h->Y, h->S8[0], h->Ebest),
            "init kernel");
+        if (c.thermo)
+            CK(launch_nh_init(h->work, c.R, c.Rp, c.nh_xi0, c.dt64, h->xi, h->gvec), "xi init");
         s = enqueue_persistent(h, c, 0, c.steps, true, 0);
         if (s != HSB_OK)
             return s;
@@ -872,9 +889,9 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
         h->last_x = 0;
         h->state_par = c.steps & 1;
         h->have_state = true;
-        h->launches = 3;
+        h->launches = c.thermo ? 4 : 3;
         h->trace_len = 0;
-        h->have_xi = false;
+        h->have_xi = c.thermo != 0;
         return HSB_OK;
     }
     if (c.trace_every > 0) {
@@ -1164,6 +1181,7 @@ void hsb_destroy(hsb_handle h)
     cudaFree(h->Jcat);
     cudaFree(h->trace);
     cudaFree(h->err);
+    cudaFree(h->nhpart);
     cudaFree(h->flags);
     cudaFree(h->pk_dev);
     cudaFree(h->Eeval);

@@ -148,6 +148,17 @@ struct PersistArgs {
     float *Epart;
     uint8_t *Snap;
     int *err;
+    // Nose-Hoover thermostat (Eqs. eq_NH1, eq_NH; persistent kernel only):
+    // nh != 0 selects it; h = dt / M, NT = N T and dt in binary64; xi [Rp]
+    // holds xi(t_k_begin) on entry and xi after the last update on exit;
+    // nhpart [3][nblk][Rp][2] the exact per-tile sums of q^2 (q = 2^24 y,
+    // rounded) as (hi, lo) words; nhflags like flags, tile (mb, rb) stores
+    // pass + 1 once its sums of that pass are written.
+    int nh;
+    double nh_h, nh_NT, dt64;
+    double *xi;
+    unsigned long long *nhpart;
+    int *nhflags;
 };
 
 // Resident-J variant (hsb_persist_ar.cu): N <= 2048, same arguments.

@@ -41,6 +41,19 @@
 // A final pass after the last update evaluates E(t_Ns).  The best evaluation
 // per replica is chosen afterwards by select_best_kernel.
 //
+// With the Nose-Hoover thermostat (kNH; Eqs. eq_NH1, eq_NH) the friction
+// factor fl32(-xi_r dt) of each replica replaces the heating factor in phase
+// 2.  Phase 2 also forms S_r = sum_i y_i'^2 of the tile's rows exactly (q_i =
+// 2^24 y_i rounded, q_i^2 split into 22-bit chunks summed over the warp with
+// redux and over the quadrants with shared-memory atomics), writes the tile's
+// sums to a three-slot buffer and releases a second flag.  Phase 2 of the next
+// pass waits for the row blocks' flags of its replica block, adds their sums
+// (exact integers) and advances xi before its update.  Phase 1 needs no xi
+// (the friction does not move x~), so the wait stays off the critical path.
+// Three slots: a tile writes slot p % 3 in pass p only after every tile of its
+// replica block has published pass p - 1's signs, hence finished reading
+// slot (p - 3) % 3 in pass p - 2.
+//
 // All CTAs must be co-resident (cooperative launch).  Every wait is bounded:
 // mbarrier, ring and flag waits give up after a wall-clock budget, raise the
 // CTA's abort flag and the error word; epilogue warps decide to leave through
@@ -93,6 +106,11 @@ struct __align__(8) PShared {
     uint64_t ring[kOrder];  // slot g % kOrder named: one arrival per use
     int order[kOrder];    // pair of load g at order[g % kOrder]
     float red[4][kPN];    // per-quadrant energy partials
+    // Nose-Hoover (kNH): xi of the tile's replicas, the friction factor of
+    // the current pass, and 22-bit chunk sums of q^2 over the tile's rows
+    double xi[kPN];
+    float gnh[kPN];
+    unsigned nhacc[3][kPN];
 };
 
 constexpr size_t kPSmem =
@@ -117,6 +135,21 @@ __device__ __forceinline__ bool epi_bar_or(bool pred)
 }
 
 __device__ __forceinline__ void epi_bar() { ptx::named_bar(1, kEpiThreads); }
+
+// The same OR-barrier over the first four epilogue warps (Nose-Hoover xi).
+__device__ __forceinline__ bool nh_bar_or(bool pred)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 2, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)pred)
+        : "memory");
+    return r != 0;
+}
 
 // Bounded wait by every lane of a warp; false in all lanes if any gave up.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *abort, int *err)
@@ -173,8 +206,46 @@ __device__ __forceinline__ void load_force(uint32_t tcol, bool two_acc, uint32_t
     ptx::tmem_ld_wait(f);
 }
 
+// q^2 for q = round(2^24 y) (exact scaling, round to nearest even), |y| < 256
+// (else *bad), split into 22-bit chunks; each chunk summed over the warp's 32
+// rows stays below 2^27.  Lane `owner` keeps the three sums of this column.
+__device__ __forceinline__ void nh_sum_square(float y, bool owner, unsigned &s0, unsigned &s1,
+                                              unsigned &s2, bool &bad)
+{
+    const float s = fabsf(y * 16777216.0f);
+    uint64_t v = 0;
+    if (s < 4294967296.0f) {
+        const uint32_t m = __float2uint_rn(s);  // |round(2^24 y)|, ties to even
+        v = (uint64_t)m * m;
+    } else {
+        bad = true;  // also NaN
+    }
+    const unsigned c0 = __reduce_add_sync(0xFFFFFFFFu, (unsigned)(v & 0x3FFFFFu));
+    const unsigned c1 = __reduce_add_sync(0xFFFFFFFFu, (unsigned)((v >> 22) & 0x3FFFFFu));
+    const unsigned c2 = __reduce_add_sync(0xFFFFFFFFu, (unsigned)(v >> 44));
+    if (owner) {
+        s0 = c0;
+        s1 = c1;
+        s2 = c2;
+    }
+}
+
+// (hi 2^64 + lo) 2^-48 rounded once to binary64 (see nh_update_kernel).
+__device__ __forceinline__ double nh_u128_q48_to_double(uint64_t hi, uint64_t lo)
+{
+    if (hi == 0)
+        return __dmul_rn(__ull2double_rn(lo), 0x1p-48);
+    const int lz = __clzll((long long)hi);
+    uint64_t t = lz ? (hi << lz) | (lo >> (64 - lz)) : hi;
+    if (lo << lz)
+        t |= 1ull;
+    return __dmul_rn(__ull2double_rn(t),
+                     __longlong_as_double((long long)(1023 + 16 - lz) << 52));
+}
+
 }  // namespace
 
+template <bool kNH>
 __global__ void __launch_bounds__(kPThreads, 1)
 tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                          const __grid_constant__ CUtensorMap tmapB0,
@@ -396,6 +467,15 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             ptx::tmem_st16(tmem + lane_off + kColY + c0 + h * 16, yr);
         }
         ptx::tmem_st_wait();
+        if (kNH && et < kPN) {
+            // xi(t_k_begin) of this tile's replicas and its friction factor;
+            // the epilogue barrier of the first pass orders these stores
+            const double x0 = a.xi[r0 + et];
+            sh->xi[et] = x0;
+            sh->gnh[et] = __double2float_rn(__dmul_rn(-x0, a.dt64));
+            sh->nhacc[0][et] = sh->nhacc[1][et] = sh->nhacc[2][et] = 0u;
+        }
+        bool nh_bad = false;
 
         bool left = false;
         // this spin's byte in row `col` of the sign tile
@@ -415,11 +495,62 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             if (kl + 1 < a.nsteps)
                 pk_next = a.pk[k + 1];  // p_k of the next pass, off the critical path
 
+            // Nose-Hoover: xi_k = xi_{k-1} + (dt/M)(S - N T), S = sum_i
+            // y_i(t_k)^2 from every row block's sums of the previous pass (Eq.
+            // eq_NH).  Warps 0-3 (one thread per replica column) do it while
+            // the MMA runs; phase 2 reads the factor after the phase-1 barrier.
+            bool ok_nh = true;
+            if (kNH && kl > 0 && ew < 4) {
+                if (ew == 0) {
+                    bool mine = lane >= nblk;
+                    const unsigned long long t0 = ptx::globaltimer();
+                    int idle = 0;
+                    while (!__all_sync(0xFFFFFFFFu, mine)) {
+                        if (!mine)
+                            mine = ptx::ld_acquire_gpu(
+                                       &a.nhflags[flag_index(lane, rb, a.nrb)]) >= kl;
+                        int give_up = 0;
+                        if (lane == 0) {
+                            if (*(volatile int *)&sh->abort) {
+                                give_up = 1;
+                            } else if ((++idle & 15) == 0 &&
+                                       ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
+                                *(volatile int *)&sh->abort = 1;
+                                atomicExch(a.err, kErrTimeout);
+                                give_up = 1;
+                            }
+                        }
+                        if (__shfl_sync(0xFFFFFFFFu, give_up, 0)) {
+                            ok_nh = false;
+                            break;
+                        }
+                    }
+                }
+                ok_nh = !nh_bar_or(!ok_nh);
+                if (ok_nh) {
+                    const unsigned long long *src =
+                        a.nhpart + ((size_t)((kl - 1) % 3) * nblk * a.Rp + r0 + et) * 2;
+                    uint64_t hi = 0, lo = 0;
+                    for (int b = 0; b < nblk; ++b) {
+                        const uint64_t bh = __ldcg(src + (size_t)b * a.Rp * 2);
+                        const uint64_t bl = __ldcg(src + (size_t)b * a.Rp * 2 + 1);
+                        const uint64_t l = lo + bl;
+                        hi += bh + (l < lo ? 1ull : 0ull);
+                        lo = l;
+                    }
+                    const double S = nh_u128_q48_to_double(hi, lo);
+                    const double x =
+                        __dadd_rn(sh->xi[et], __dmul_rn(a.nh_h, __dsub_rn(S, a.nh_NT)));
+                    sh->xi[et] = x;
+                    sh->gnh[et] = __double2float_rn(__dmul_rn(-x, a.dt64));
+                }
+            }
             // x and y of the first 16 columns: the MMA does not write them
             uint32_t xpre[16], ypre[16];
             ptx::tmem_ld16(tmem + lane_off + kColX + c0, xpre);
             ptx::tmem_ld16(tmem + lane_off + kColY + c0, ypre);
-            const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
+            const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err) &&
+                            ok_nh;
             ptx::tmem_ld_wait(xpre);
             ptx::tmem_ld_wait(ypre);
             if (epi_bar_or(!ok)) {
@@ -512,8 +643,18 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                     for (int j = 0; j < 16; j += 2) {
                         float xn0, xn1;
                         uint64_t yn;
-                        sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
-                                   f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xn0, xn1, yn);
+                        if (kNH) {
+                            // per-replica friction factor in place of gamma dt
+                            StepConsts2 kn = k2;
+                            kn.g = f2_pack(sh->gnh[col0 + j], sh->gnh[col0 + j + 1]);
+                            sb_update2(f2_pack_bits(f[j], f[j + 1]),
+                                       f2_pack_bits(xr[j], xr[j + 1]),
+                                       f2_pack_bits(yr[j], yr[j + 1]), pk2, kn, xn0, xn1, yn);
+                        } else {
+                            sb_update2(f2_pack_bits(f[j], f[j + 1]),
+                                       f2_pack_bits(xr[j], xr[j + 1]),
+                                       f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xn0, xn1, yn);
+                        }
                         xr[j] = __float_as_uint(xn0);
                         xr[j + 1] = __float_as_uint(xn1);
                         yr[j] = (uint32_t)yn;
@@ -536,7 +677,47 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                     a.Epart[((size_t)e * nblk + mb) * a.Rp + r0 + et] = s;
                 }
             }
+            if (kNH && !final_pass) {
+                // this tile's sums of q^2 of y(t_{k+1}) (in tensor memory; the
+                // accumulator is already released): slot kl % 3, then the flag
+                // lane l ends with the sums of column c0 + l; one warp-wide
+                // atomic per chunk adds them to the tile's sums
+                unsigned s0 = 0u, s1 = 0u, s2 = 0u;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t yr[16];
+                    ptx::tmem_ld16(tmem + lane_off + kColY + (uint32_t)(c0 + h * 16), yr);
+                    ptx::tmem_ld_wait(yr);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        nh_sum_square(__uint_as_float(yr[j]), lane == h * 16 + j, s0, s1, s2,
+                                      nh_bad);
+                }
+                atomicAdd(&sh->nhacc[0][c0 + lane], s0);
+                atomicAdd(&sh->nhacc[1][c0 + lane], s1);
+                atomicAdd(&sh->nhacc[2][c0 + lane], s2);
+                epi_bar();  // every warp's atomics are in
+                if (et < kPN) {
+                    const uint64_t c0 = sh->nhacc[0][et], c1 = sh->nhacc[1][et],
+                                   c2 = sh->nhacc[2][et];
+                    sh->nhacc[0][et] = sh->nhacc[1][et] = sh->nhacc[2][et] = 0u;
+                    const uint64_t lo0 = c0 + (c1 << 22);
+                    const uint64_t lo = lo0 + (c2 << 44);
+                    const uint64_t hi = (c2 >> 20) + (lo < lo0 ? 1ull : 0ull);
+                    unsigned long long *dst =
+                        a.nhpart + ((size_t)(kl % 3) * nblk * a.Rp + (size_t)mb * a.Rp + r0 + et) * 2;
+                    dst[0] = hi;
+                    dst[1] = lo;
+                }
+                epi_bar();
+                if (et == 0)
+                    ptx::st_release_gpu(&a.nhflags[flag_index(mb, rb, a.nrb)], kl + 1);
+                if (nh_bad)
+                    atomicExch(a.err, kErrRange);
+            }
         }
+        if (kNH && !left && mb == 0 && et < kPN)
+            a.xi[r0 + et] = sh->xi[et];  // xi after the last update (final pass)
 
         // final state back to global memory
         if (!left) {
@@ -606,10 +787,11 @@ bool tc_persistent_fits(int Np, int Rp)
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return false;
-    if (cudaFuncSetAttribute(tc_fp8_persistent_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kPSmem) != cudaSuccess)
+    // both instantiations have the same block size and shared memory
+    if (cudaFuncSetAttribute(tc_fp8_persistent_kernel<false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem) != cudaSuccess)
         return false;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_fp8_persistent_kernel,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_fp8_persistent_kernel<false>,
                                                       kPThreads, kPSmem) != cudaSuccess)
         return false;
     return (long long)nblk * nrb <= (long long)per_sm * sms;
@@ -619,8 +801,10 @@ cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const 
 {
     if (!plan || a.Np != plan->Np || a.Rp > plan->Rp || a.Rp % kPN != 0 || a.nblk > 32)
         return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(tc_fp8_persistent_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (a.nh && (!a.xi || !a.nhpart || !a.nhflags || !a.final_pass))
+        return cudaErrorInvalidValue;
+    auto kern = a.nh ? tc_fp8_persistent_kernel<true> : tc_fp8_persistent_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kPSmem);
     if (e != cudaSuccess)
         return e;
@@ -634,7 +818,7 @@ cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const 
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, tc_fp8_persistent_kernel, plan->mapA3, plan->mapB3[0],
+    return cudaLaunchKernelEx(&cfg, kern, plan->mapA3, plan->mapB3[0],
                               plan->mapB3[1], a);
 }
 

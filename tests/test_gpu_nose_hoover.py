@@ -5,7 +5,9 @@ each step from S_r = sum_i y_i^2, which both sides form in exact fixed point
 (each term rounded to a multiple of 2^-64, exact 128-bit sum, one rounding),
 so the result does not depend on summation order and trajectories, xi and
 best spins equal the binary32 oracle bit for bit.  Runs on plain FP32 (any
-couplings) and on the one-launch-per-step FP8 kernel (+/-1 couplings), with
+couplings) and on both FP8 schedules (+/-1 couplings): the persistent kernel,
+whose tiles exchange their sums of q^2 through a second set of flags each
+step, and the one-launch-per-step kernel with a separate xi update, with
 ragged spin and replica tails.
 """
 import numpy as np
@@ -31,28 +33,36 @@ def _nh_oracle(J, form, c1, dt, eval_every, trace_every=0, **nh):
                               nose_hoover=True, **nh)
 
 
-@pytest.mark.parametrize("kind,form,prec,n,R", [
-    ("pm1", "discrete", "fp8", 1000, 300),
-    ("pm1", "discrete", "fp8", 257, 130),
-    ("pm1", "discrete", "fp32", 300, 130),
-    ("gauss", "ballistic", "fp32", 300, 130),
-    ("gauss", "discrete", "fp32", 200, 40),
+@pytest.mark.parametrize("kind,form,prec,schedule,n,R", [
+    ("pm1", "discrete", "fp8", "persistent", 1000, 300),
+    ("pm1", "discrete", "fp8", "persistent", 257, 130),
+    ("pm1", "discrete", "fp8", "persistent", 4000, 256),
+    ("pm1", "discrete", "fp8", "per_step", 1000, 300),
+    ("pm1", "discrete", "fp8", "per_step", 257, 130),
+    ("pm1", "discrete", "fp32", "auto", 300, 130),
+    ("gauss", "ballistic", "fp32", "auto", 300, 130),
+    ("gauss", "discrete", "fp32", "auto", 200, 40),
 ])
-def test_nose_hoover_bit_exact(kind, form, prec, n, R):
+def test_nose_hoover_bit_exact(kind, form, prec, schedule, n, R):
     J = synth.sk_pm1(n, 40 + n) if kind == "pm1" else synth.sk_gauss(n, 40 + n)
     fcode = 0 if form == "ballistic" else 1
     c1 = 0.7 if form == "discrete" else 0.9
     steps, seed, ev, te = 200, 12, 50, 10
     NH = _nh(n)
+    # the trace runs on the per-step schedule only
+    te = te if schedule != "persistent" else 0
     p = hsb.params(form, prec, c1=c1, dt=1.1, eval_every=ev, trace_every=te,
-                   thermostat="nose_hoover", **NH)
+                   schedule=schedule, thermostat="nose_hoover", **NH)
     with hsb.Solver(J) as s:
         spins, energy = s.run(p, R, steps, seed)
         x, y = s.get_state(R)
         xi = s.get_xi(R)
         tr = s.get_trace()
+        launches = s.run_stats()
+    if schedule == "persistent":
+        assert launches == 4  # init, xi init, the step loop, best selection
     ref = oracle.run(J, _nh_oracle(J, fcode, c1, 1.1, ev, te, **NH), steps, seed, range(R),
-                     "f32", want_trace=True)
+                     "f32", want_trace=te > 0)
     np.testing.assert_array_equal(xi, ref["xi"])
     np.testing.assert_array_equal(x, ref["x"])
     np.testing.assert_array_equal(y, ref["y"])
@@ -63,6 +73,8 @@ def test_nose_hoover_bit_exact(kind, form, prec, n, R):
         np.testing.assert_allclose(energy, ref["best_e"], rtol=1e-12, atol=1e-9)
     # the thermostat acts: xi moved away from xi0 in every replica
     assert np.all(xi != NH["nh_xi0"])
+    if te == 0:
+        return
     # trace: minimum / mean energy and mean T_inst at t_k, k = 0, 10, ...;
     # exact integers for +/-1 couplings, binary32 force sums otherwise
     rt = 0.0 if kind == "pm1" else 1e-5
@@ -72,15 +84,16 @@ def test_nose_hoover_bit_exact(kind, form, prec, n, R):
     np.testing.assert_allclose(tr[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6)
 
 
-@pytest.mark.parametrize("prec", ["fp8", "fp32"])
-def test_nose_hoover_large_mass_equals_constant_heating(prec):
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
+                                           ("fp32", "per_step")])
+def test_nose_hoover_large_mass_equals_constant_heating(prec, schedule):
     # With M = 1e300 the xi increments vanish below binary64 resolution, so a
     # run with xi0 = -gamma is the constant-gamma run, bit for bit.
     J = synth.sk_pm1(500, 5)
     R, steps, seed = 200, 150, 3
     heat = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=30,
-                      schedule="per_step")
-    nh = hsb.params("discrete", prec, c1=0.7, dt=1.1, eval_every=30, schedule="per_step",
+                      schedule=schedule)
+    nh = hsb.params("discrete", prec, c1=0.7, dt=1.1, eval_every=30, schedule=schedule,
                     thermostat="nose_hoover", nh_T=0.3, nh_M=1e300, nh_xi0=-0.06)
     with hsb.Solver(J) as s:
         sa, ea = s.run(heat, R, steps, seed)
@@ -100,10 +113,9 @@ def test_nose_hoover_argument_checks():
     G = synth.sk_gauss(256, 1)
     nh = dict(thermostat="nose_hoover", **_nh(256))
     with hsb.Solver(J) as s:
-        for bad in (dict(schedule="persistent"), dict(schedule="resident")):
-            with pytest.raises(hsb.HsbError) as e:
-                s.run(hsb.params("discrete", "fp8", **nh, **bad), 128, 10, 0)
-            assert e.value.status == hsb.HSB_E_UNSUPPORTED
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("discrete", "fp8", schedule="resident", **nh), 128, 10, 0)
+        assert e.value.status == hsb.HSB_E_UNSUPPORTED
         with pytest.raises(hsb.HsbError) as e:
             s.run(hsb.params("discrete", "fp8", thermostat="nose_hoover", nh_M=0.0), 128, 10, 0)
         assert e.value.status == hsb.HSB_E_INVAL
