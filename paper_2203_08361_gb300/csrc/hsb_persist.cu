@@ -530,13 +530,24 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 if (ok_nh) {
                     const unsigned long long *src =
                         a.nhpart + ((size_t)((kl - 1) % 3) * nblk * a.Rp + r0 + et) * 2;
+                    // eight row blocks' sums in flight at a time (one L2 round
+                    // trip per eight, not per block)
                     uint64_t hi = 0, lo = 0;
-                    for (int b = 0; b < nblk; ++b) {
-                        const uint64_t bh = __ldcg(src + (size_t)b * a.Rp * 2);
-                        const uint64_t bl = __ldcg(src + (size_t)b * a.Rp * 2 + 1);
-                        const uint64_t l = lo + bl;
-                        hi += bh + (l < lo ? 1ull : 0ull);
-                        lo = l;
+                    for (int b0 = 0; b0 < nblk; b0 += 8) {
+                        uint64_t bh[8], bl[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const bool in = b0 + u < nblk;
+                            const unsigned long long *pb = src + (size_t)(b0 + u) * a.Rp * 2;
+                            bh[u] = in ? __ldcg(pb) : 0ull;
+                            bl[u] = in ? __ldcg(pb + 1) : 0ull;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const uint64_t l = lo + bl[u];
+                            hi += bh[u] + (l < lo ? 1ull : 0ull);
+                            lo = l;
+                        }
                     }
                     const double S = nh_u128_q48_to_double(hi, lo);
                     const double x =
