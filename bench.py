@@ -396,7 +396,7 @@ OTHER = {
                     kind="single", N=16384, J="pm1", J_seed=3, R=4096, sb_steps=10000,
                     form="discrete", prec="fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
                     trace_every=1, peak="fp8", dtype="fp8"),
-    "nh2000": dict(name="Nose-Hoover dSB SK +/-1 N=2000 R=1024 2000 steps FP8 per-step "
+    "nh2000": dict(name="Nose-Hoover dSB SK +/-1 N=2000 R=1024 2000 steps FP8 "
                         "(T=0.3, M=40000, xi0=-0.05)", kind="single", N=2000, J="pm1", J_seed=1,
                    R=1024, sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1,
                    gamma=0.0, eval_every=100, trace_every=0, peak="fp8", dtype="fp8",
@@ -452,7 +452,8 @@ def run_other(args, w):
     R, S = w["R"], w["sb_steps"]
     Js = _other_couplings(w)
     p = hsb.params(w["form"], w["prec"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
-                   eval_every=w["eval_every"], trace_every=w["trace_every"], **w.get("nh", {}))
+                   eval_every=w["eval_every"], trace_every=w["trace_every"],
+                   schedule=args.schedule, **w.get("nh", {}))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     units = sum(J.shape[0] for J in Js) * R * S            # replica-spin-steps per run
     flops = sum(2.0 * J.shape[0] ** 2 for J in Js) * R * S  # algorithmic
@@ -573,6 +574,9 @@ def main():
     ap.add_argument("--workload", choices=["sk2000"] + sorted(OTHER), default="sk2000",
                     help="sk2000 (default): the headline line; the others measure the "
                          "remaining configurations the same way")
+    ap.add_argument("--schedule", choices=["auto", "persistent", "per_step"], default="auto",
+                    help="FP8 step loop of the --workload runs (profiling of the "
+                         "one-launch-per-step path)")
     ap.add_argument("--sb-steps", type=int, default=None,
                     help="override the SB steps per run (profiling of small cases only; "
                          "the headline workload is 2000)")
@@ -588,6 +592,8 @@ def main():
         w = dict(OTHER[args.workload])
         if args.sb_steps:
             w["sb_steps"] = int(args.sb_steps)
+        if args.schedule != "auto":
+            w["name"] += f", {args.schedule.replace('_', '-')} schedule"
         return run_other(args, w)
     return run_gpu(args)
 

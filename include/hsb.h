@@ -113,10 +113,10 @@ typedef struct {
                                Eq. (eq_MomHeat) (HbSB / HdSB); HSB_HEAT_NOSE_HOOVER:
                                the dynamic xi of Eqs. (eq_NH1), (eq_NH), one per
                                replica, in place of -gamma (gamma is then unused).
-                               Nose-Hoover runs on FP32 or on FP8 with one launch per
-                               step (AUTO never picks BF16X3 for it); schedules 1 and
-                               3, hsb_advance* and hsb_run_batch return
-                               HSB_E_UNSUPPORTED.  A momentum |y| >= 256 (an
+                               Nose-Hoover runs on FP32 and on FP8 (persistent or one
+                               launch per step; AUTO never picks BF16X3 for it);
+                               schedule 3 and hsb_advance* return HSB_E_UNSUPPORTED,
+                               hsb_run_batch runs the instances one after another.  A momentum |y| >= 256 (an
                                unstable setting: M much below N) makes the run
                                return HSB_E_INVAL.  See hsb_get_xi. */
     int reserved0;          /* must be zero */
