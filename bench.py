@@ -49,6 +49,31 @@ def _dist_env():
     return world, rank, local
 
 
+# ---- one process per GPU, replicas only: no data-path collective.  Each rank
+# runs R independent replicas of its own seed; the host-side collectives are
+# the barriers around the timed region and the max of the ranks' times.
+
+def rank_seed(rank: int) -> int:
+    """Seed of a rank's replicas (distinct per rank: independent trials)."""
+    return 1000 + rank
+
+
+def max_over_ranks(value: float, world: int, device: str = "cpu") -> float:
+    """The largest of the ranks' values (the job's time is its slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units all ranks processed per second of the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _config(extra=None):
     w = WORKLOAD
     cfg = {"workload": w["name"], "N": w["N"], "R": w["R"], "sb_steps": w["sb_steps"],
@@ -223,7 +248,7 @@ def run_gpu(args):
     J = synth.sk_pm1(N, w["J_seed"])
     p = hsb.params(w["form"], w["prec"], a0=w["a0"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
                    init_half_width=w["init_half_width"], eval_every=w["eval_every"])
-    seed = 1000 + rank  # independent replicas on every rank
+    seed = rank_seed(rank)  # independent replicas on every rank
     stream = torch.cuda.Stream()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     spins = torch.empty((R, N), dtype=torch.int8, device="cuda")
@@ -305,12 +330,8 @@ def run_gpu(args):
 
     fp32_ms, identical = (None, None) if args.no_fp32_baseline else fp32_comparison()
 
-    t_max = elapsed_ms
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * N * R * S * args.steps / (t_max / 1000.0)
+    t_max = max_over_ranks(elapsed_ms, world, "cuda")
+    value = whole_job_rate(world, N * R * S * args.steps, t_max / 1000.0)
 
     # ---- end to end through the C ABI with host buffers (rank-local)
     pin_J = torch.from_numpy(J).pin_memory()
@@ -334,7 +355,7 @@ def run_gpu(args):
     for _ in range(e2e_iters):
         e2e_step()
     e2e_s = (time.perf_counter() - t0) / e2e_iters
-    e2e_value = N * R * S / e2e_s * world
+    e2e_value = whole_job_rate(world, N * R * S, max_over_ranks(e2e_s, world, "cuda"))
     solver.close()
 
     if rank != 0:
@@ -449,6 +470,9 @@ def run_other(args, w):
         raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
     world, rank, local = _dist_env()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
     R, S = w["R"], w["sb_steps"]
     Js = _other_couplings(w)
     p = hsb.params(w["form"], w["prec"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
@@ -457,7 +481,7 @@ def run_other(args, w):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     units = sum(J.shape[0] for J in Js) * R * S            # replica-spin-steps per run
     flops = sum(2.0 * J.shape[0] ** 2 for J in Js) * R * S  # algorithmic
-    seed = 1000 + rank
+    seed = rank_seed(rank)
     clocks = ClockSampler(torch.cuda.current_device())
     if w["kind"] == "batch":
         solvers = [hsb.Solver(J) for J in Js]
@@ -465,6 +489,8 @@ def run_other(args, w):
         for _ in range(max(args.warmup, 3)):
             hsb.run_batch(hs, p, R, S, seed)  # the first call also tunes the launch
         times = []
+        if world > 1:
+            dist.barrier()
         clocks.start()
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
@@ -492,6 +518,9 @@ def run_other(args, w):
             launches = solver.run_stats()
             ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                   for _ in range(args.steps)]
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
             clocks.start()
             for i in range(args.steps):
                 flush.fill_(i & 0xFF)
@@ -517,10 +546,16 @@ def run_other(args, w):
         e2e_t = time.perf_counter() - t0
         solver.close()
         timing = "CUDA events on the solver's stream around each whole run"
+    if world > 1:
+        dist.barrier()
+    # the job's time is its slowest rank's; every rank ran `units` of its own
+    t_run = max_over_ranks(t_run, world, "cuda")
+    e2e_t = max_over_ranks(e2e_t, world, "cuda")
+    units_job = world * units
     mp, src = _peaks()
     bf16 = float(mp.get("bf16_tflops_sustained", mp.get("bf16_tflops")))
     peak = 2.0 * bf16 if w["peak"] == "fp8" else bf16
-    achieved = flops / t_run / 1e12
+    achieved = world * flops / t_run / 1e12
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None,
                 "peak_source": (f"{'FP8 dense = 2 x ' if w['peak'] == 'fp8' else ''}bf16 "
@@ -533,7 +568,7 @@ def run_other(args, w):
         # N^2 bytes of J, 16 N R bytes of x, y read and written, 2 N R bytes
         # of the sign operand written and read back.  That traffic, not the
         # tensor rate, bounds it.
-        nbytes = sum(J.shape[0] ** 2 + 18 * J.shape[0] * R for J in Js) * S
+        nbytes = world * sum(J.shape[0] ** 2 + 18 * J.shape[0] * R for J in Js) * S
         hbm = float(mp.get("hbm_gbs", 6800.0))
         gbs = nbytes / t_run / 1e9
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
@@ -544,21 +579,23 @@ def run_other(args, w):
                     "tensor_frac": achieved / peak}
     if w["prec"] == "bf16x3":
         roofline["executed_tflops"] = 3.0 * achieved
-    line = {"metric": f"replica-spin-steps/s ({w['name']})", "value": units / t_run,
+    line = {"metric": f"replica-spin-steps/s ({w['name']})", "value": units_job / t_run,
             "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": 1000.0 * t_run, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
             "config": {"workload": w["name"], "R": R, "sb_steps": S,
                        "l2": "256 MiB buffer written between timed runs", "timing": timing},
             "roofline": roofline, "clocks": clock_rec,
-            "e2e": {"value": units / e2e_t, "unit": UNIT,
+            "e2e": {"value": units_job / e2e_t, "unit": UNIT,
                     "h2d_bytes_per_step": 0 if w["kind"] == "batch" else int(Js[0].size * 4),
                     "d2h_bytes_per_step": int(sum(J.shape[0] for J in Js) * R + 8 * R * len(Js))},
             "gpu_launches": int(launches * args.steps)}
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _other_cpu_baseline(w, Js)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
