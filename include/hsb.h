@@ -237,6 +237,15 @@ HSB_API hsb_status hsb_get_trace(hsb_handle h, double *buf, size_t max_entries, 
  * from its replica count.  Blocks. */
 HSB_API hsb_status hsb_get_xi(hsb_handle h, int R, double *xi);
 
+/* Failure-detection test hook.  The next FP8 run on the persistent schedule
+ * (streamed J) of this handle skips the publication of one tile's sign
+ * operand (row block `row_block`, first replica block), so that the bounded
+ * device waits of the other tiles expire: the run returns HSB_E_TIMEOUT after
+ * the wait budget (about 2 s), the kernel frees its tensor memory, and the
+ * handle stays usable (the following run is unaffected).  0 <= row_block <
+ * ceil(N / 128), else HSB_E_INVAL. */
+HSB_API hsb_status hsb_debug_drop_publication(hsb_handle h, int row_block);
+
 /* Replaces the couplings of the handle by a new instance of the same N (host,
  * float32, N x N, row-major; validated as in hsb_create).  Device buffers and
  * captured step loops are kept, so solving many instances of one size pays

@@ -116,6 +116,7 @@ struct hsb_ctx {
     double *xi = nullptr;    // [Rp] Nose-Hoover xi per replica
     float *gvec = nullptr;   // [Rp] friction factor fl32(-xi dt) of the next step
     bool have_xi = false;    // the last run used the Nose-Hoover thermostat
+    int debug_drop_mb = -1;  // failure-detection test hook, consumed by the next launch
     int8_t *Sbest = nullptr;
     int *err = nullptr;
     uint64_t buffers_gen = 0;
@@ -714,6 +715,11 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     a.Epart = h->Eeval;
     a.Snap = h->Snap;
     a.err = h->err;
+    a.drop_mb = -1;
+    if (c.schedule != 3) {
+        a.drop_mb = h->debug_drop_mb;
+        h->debug_drop_mb = -1;
+    }
     if (c.thermo) {
         // Nose-Hoover: xi (set by launch_nh_init) in and out, tile sums, flags
         a.nh = 1;
@@ -1532,6 +1538,16 @@ hsb_status hsb_get_xi(hsb_handle h, int R, double *xi)
     CK(cudaMemcpyAsync(xi, h->xi, (size_t)R * sizeof(double), cudaMemcpyDeviceToHost, h->work),
        "copy xi");
     CK(cudaStreamSynchronize(h->work), "synchronize");
+    return HSB_OK;
+}
+
+hsb_status hsb_debug_drop_publication(hsb_handle h, int row_block)
+{
+    if (!h)
+        return set_error(HSB_E_INVAL, "handle is NULL");
+    if (row_block < 0 || row_block >= h->Np / kTileM)
+        return set_error(HSB_E_INVAL, "row_block must be in [0, %d)", h->Np / kTileM);
+    h->debug_drop_mb = row_block;
     return HSB_OK;
 }
 

@@ -159,6 +159,9 @@ struct PersistArgs {
     double *xi;
     unsigned long long *nhpart;
     int *nhflags;
+    // failure-detection test: tile (drop_mb, 0) never publishes its signs, so
+    // the bounded waits of the launch expire (-1: off)
+    int drop_mb;
 };
 
 // Resident-J variant (hsb_persist_ar.cu): N <= 2048, same arguments.

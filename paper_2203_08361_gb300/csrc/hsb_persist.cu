@@ -612,7 +612,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                     *reinterpret_cast<uint4 *>(dst + (size_t)row * a.Np + off) = val;
                 }
                 epi_bar();
-                if (et == 0) {
+                if (et == 0 && !(mb == a.drop_mb && rb == 0)) {
                     // every epilogue thread's S stores precede the barrier; the
                     // gpu-scope release (cumulative) publishes them with the flag
                     ptx::fence_proxy_async_global();
