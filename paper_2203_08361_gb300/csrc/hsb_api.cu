@@ -96,6 +96,7 @@ struct hsb_ctx {
     int N = 0, Np = 0, device = 0, pm1 = 0;
     double sigma = 0.0;
     double sumJ = 0.0;  // sum_ij J_ij in binary64, row by row (cut values, Eq. (eq_Cut))
+    int jscale = 0;     // fixed-point exponent of the final energies: max |J| 2^jscale < 2^40
     cudaStream_t work = nullptr;     // where work is queued (user's or own)
     cudaStream_t own = nullptr;      // private stream (default work stream, capture stream)
     float *J32 = nullptr;            // [Np][Np]
@@ -426,8 +427,8 @@ hsb_status enqueue_final(hsb_ctx *h, cudaStream_t st, const RunCfg &c)
            "best kernel");
     }
     if (!h->pm1)
-        CK(launch_final_energy_f64_parts(st, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efpart,
-                                         h->Efinal),
+        CK(launch_final_energy_f64_parts(st, h->J32, h->N, h->Np, c.R, h->Sbest, h->jscale,
+                                         h->Efpart, h->Efinal),
            "final energy kernel");
     return HSB_OK;
 }
@@ -555,7 +556,7 @@ void scan_row_blocks(const float *J, int N, int first, int stride, CouplingScan 
 }
 
 hsb_status validate_couplings(const float *J, int N, int *pm1_out, double *sum2_out,
-                              double *sumJ_out)
+                              double *sumJ_out, double *maxabs_out)
 {
     const size_t n = (size_t)N;
     for (int i = 0; i < N; ++i)
@@ -591,16 +592,18 @@ hsb_status validate_couplings(const float *J, int N, int *pm1_out, double *sum2_
     }
     if (ai >= 0)
         return set_error(HSB_E_ASYM, "J[%d][%d] != J[%d][%d]", ai, aj, aj, ai);
-    double sum2 = 0.0, sumJ = 0.0;
+    double sum2 = 0.0, sumJ = 0.0, maxabs = 1.0;
     if (pm1) {
         sum2 = (double)nonzero;
         sumJ = (double)signed_sum;
     } else {
         // sigma_J^2 = sum_ij J_ij^2 / (N(N-1)), summed row by row in binary64
+        maxabs = 0.0;
         for (size_t e = 0; e < n * n; ++e) {
             const double d = (double)J[e];
             sum2 += d * d;
             sumJ += d;
+            maxabs = std::max(maxabs, std::fabs(d));
         }
     }
     if (!(sum2 > 0.0))
@@ -608,7 +611,16 @@ hsb_status validate_couplings(const float *J, int N, int *pm1_out, double *sum2_
     *pm1_out = pm1 ? 1 : 0;
     *sum2_out = sum2;
     *sumJ_out = sumJ;
+    *maxabs_out = maxabs;
     return HSB_OK;
+}
+
+// Exponent s of the fixed-point final energies: max |J| 2^s < 2^40.
+int energy_scale_exp(double maxabs)
+{
+    int e = 0;
+    std::frexp(maxabs, &e);  // maxabs = m 2^e, m in [0.5, 1): maxabs < 2^e
+    return 40 - e;
 }
 
 GraphKey make_key(const hsb_ctx *h, const RunCfg &c);
@@ -854,8 +866,8 @@ hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hs
         launches += 3;
     }
     if (!h->pm1) {
-        CK(launch_final_energy_f64_parts(h->work, h->J32, h->N, h->Np, c.R, h->Sbest, h->Efpart,
-                                         h->Efinal),
+        CK(launch_final_energy_f64_parts(h->work, h->J32, h->N, h->Np, c.R, h->Sbest,
+                                         h->jscale, h->Efpart, h->Efinal),
            "final energy kernel");
         launches += 2;
     }
@@ -1118,7 +1130,8 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
         return set_error(HSB_E_INVAL, "N must be in [2, 2^20] (got %d)", N);
     int pm1 = 1;
     double sum2 = 0.0, sumJ = 0.0;
-    hsb_status vs = validate_couplings(J, N, &pm1, &sum2, &sumJ);
+    double maxabs = 1.0;
+    hsb_status vs = validate_couplings(J, N, &pm1, &sum2, &sumJ, &maxabs);
     if (vs != HSB_OK)
         return vs;
     int ndev = 0;
@@ -1132,6 +1145,7 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
     h->Np = round_up(N, kTileM);
     h->pm1 = pm1;
     h->sigma = sqrt(sum2 / ((double)N * (double)(N - 1)));
+    h->jscale = energy_scale_exp(maxabs);
     h->sumJ = sumJ;
     hsb_status s = HSB_OK;
     do {
@@ -1476,7 +1490,8 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
     const int N = h->N;
     int pm1 = 1;
     double sum2 = 0.0, sumJ = 0.0;
-    hsb_status vs = validate_couplings(J, N, &pm1, &sum2, &sumJ);
+    double maxabs = 1.0;
+    hsb_status vs = validate_couplings(J, N, &pm1, &sum2, &sumJ, &maxabs);
     if (vs != HSB_OK)
         return vs;
     DeviceGuard g(h->device);
@@ -1488,6 +1503,7 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
        "copy J");
     h->pm1 = pm1;
     h->sigma = sqrt(sum2 / ((double)N * (double)(N - 1)));
+    h->jscale = energy_scale_exp(maxabs);
     h->sumJ = sumJ;
     if (h->J8) {
         if (pm1) {

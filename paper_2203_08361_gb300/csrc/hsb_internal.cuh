@@ -94,11 +94,16 @@ cudaError_t launch_final_energy_f64(cudaStream_t st, const float *J32, int N, in
                                     const int8_t *Sbest, double *Eout);
 
 // The same energies through partial sums part[16][R] (scratch of
-// final_energy_part_doubles(R) doubles): binary64 additions on the upper
-// triangle only, 32 replicas per warp, fixed summation order.
+// final_energy_part_doubles(R) 8-byte words) in exact fixed point: every
+// J_ij is rounded to a multiple of 2^-scale_exp (scale_exp = 40 - e with
+// max |J| < 2^e, so |J_ij| 2^scale_exp < 2^40), the upper-triangle sum
+// -sum_{i<j} J_ij s_i s_j is formed exactly in 64-bit integers, and the total
+// is rounded once to binary64; it does not depend on the summation order.
+// N above about 6300 falls back to launch_final_energy_f64.
 size_t final_energy_part_doubles(int R);
 cudaError_t launch_final_energy_f64_parts(cudaStream_t st, const float *J32, int N, int Np, int R,
-                                          const int8_t *Sbest, double *part, double *Eout);
+                                          const int8_t *Sbest, int scale_exp, double *part,
+                                          double *Eout);
 
 // sgn(X) -> FP8 operand (used when a state is loaded from the host).
 cudaError_t launch_sign_to_fp8(cudaStream_t st, const float *X, int N, int Np, int Rp,

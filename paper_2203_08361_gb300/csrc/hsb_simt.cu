@@ -601,23 +601,24 @@ cudaError_t launch_final_energy_f64(cudaStream_t st, const float *J32, int N, in
     return cudaGetLastError();
 }
 
-// The same energies for many replicas at once, with binary64 additions only
-// on the upper triangle: E = -sum_{i<j} J_ij s_i s_j (J symmetric, zero
-// diagonal).  Block (t, g) takes replicas 32t .. 32t+31 (one per lane) and
-// rows i = 8g + w, 8g + w + 8G, ... (w = warp); a warp converts each J element
-// of its row to binary64 once and broadcasts it with a shuffle, so every
-// element costs one binary64 add per replica (its sign flipped for
-// s_i != s_j).  The row sums of a block are added in a fixed order into
-// part[g][r], and final_energy_sum_kernel adds the groups in order: the
-// result does not depend on timing.
+// The same energies for many replicas at once, in exact fixed point on the
+// upper triangle: E = -sum_{i<j} J_ij s_i s_j (J symmetric, zero diagonal),
+// with q_ij = round(J_ij 2^scale_exp) (|q_ij| < 2^40; exact unless J_ij has
+// bits below 2^-scale_exp).  Block (t, g) takes replicas 32t .. 32t+31 (one
+// per lane) and rows i = 8g + w, 8g + w + 8G, ... (w = warp); a warp converts
+// each element of its row once and broadcasts it with a shuffle, so every
+// element costs one 64-bit integer add per replica (negated for s_i != s_j).
+// Bounds (N <= 6300): a row sum < 2^53, a thread's rows < 2^59, a block
+// < 2^62; final_energy_sum_kernel adds the G groups exactly and rounds once.
 constexpr int kFeGroups = 16;
 
 __global__ void __launch_bounds__(256)
 final_energy_part_kernel(const float *__restrict__ J, int N, int Np, int R,
-                         const int8_t *__restrict__ Sbest, double *__restrict__ part)
+                         const int8_t *__restrict__ Sbest, double scale,
+                         long long *__restrict__ part)
 {
     extern __shared__ uint8_t neg_sh[];  // [N + 32][32]: 1 where s = -1 (0 past N)
-    __shared__ double red[8][32];
+    __shared__ long long red[8][32];
     const int r0 = blockIdx.x * 32;
     const int G = gridDim.y;
     for (int e = threadIdx.x; e < (N + 32) * 32; e += blockDim.x) {
@@ -628,20 +629,20 @@ final_energy_part_kernel(const float *__restrict__ J, int N, int Np, int R,
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    double acc = 0.0;
+    long long acc = 0;
     for (int i = blockIdx.y * 8 + warp; i < N; i += G * 8) {
         const uint32_t ni = neg_sh[i * 32 + lane];
         const float *row = J + (size_t)i * Np;
-        double a = 0.0;
+        long long a = 0;
         for (int j0 = i + 1; j0 < N; j0 += 32) {
             const int j = j0 + lane;
-            const double vl = j < N ? (double)row[j] : 0.0;
+            // the power-of-two scaling is exact in binary64; one rounding to an integer
+            const long long ql = j < N ? __double2ll_rn(__dmul_rn((double)row[j], scale)) : 0ll;
 #pragma unroll 8
             for (int jj = 0; jj < 32; ++jj) {
-                const double v = __shfl_sync(0xffffffffu, vl, jj);
+                const long long q = __shfl_sync(0xffffffffu, ql, jj);
                 const uint32_t flip = ni ^ neg_sh[(j0 + jj) * 32 + lane];
-                // J_ij s_i s_j: the sign bit of v flipped for s_i != s_j
-                a += __hiloint2double(__double2hiint(v) ^ (int)(flip << 31), __double2loint(v));
+                a += flip ? -q : q;  // q_ij s_i s_j
             }
         }
         acc += a;
@@ -649,29 +650,37 @@ final_energy_part_kernel(const float *__restrict__ J, int N, int Np, int R,
     red[warp][lane] = acc;
     __syncthreads();
     if (warp == 0 && r0 + lane < R) {
-        double s = 0.0;
+        long long s = 0;
         for (int w = 0; w < 8; ++w)
             s += red[w][lane];
         part[(size_t)blockIdx.y * R + r0 + lane] = s;
     }
 }
 
-__global__ void final_energy_sum_kernel(const double *__restrict__ part, int G, int R,
-                                        double *__restrict__ Eout)
+// E_r = -2^-scale_exp sum_g part[g][r]: each part (< 2^62 in magnitude) is
+// split at bit 31, the halves summed exactly in 64 bits, and the total
+// hi 2^31 + lo (two exact binary64 values) rounded once by their addition.
+__global__ void final_energy_sum_kernel(const long long *__restrict__ part, int G, int R,
+                                        double inv_scale, double *__restrict__ Eout)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R)
         return;
-    double s = 0.0;
-    for (int g = 0; g < G; ++g)
-        s += part[(size_t)g * R + r];
-    Eout[r] = -s;
+    long long hi = 0, lo = 0;
+    for (int g = 0; g < G; ++g) {
+        const long long v = part[(size_t)g * R + r];
+        hi += v >> 31;  // floor division: v = (v >> 31) 2^31 + (v & (2^31 - 1))
+        lo += v & 0x7FFFFFFFll;
+    }
+    const double t = __dadd_rn(__dmul_rn((double)hi, 2147483648.0), (double)lo);
+    Eout[r] = -__dmul_rn(t, inv_scale);
 }
 
 size_t final_energy_part_doubles(int R) { return (size_t)kFeGroups * R; }
 
 cudaError_t launch_final_energy_f64_parts(cudaStream_t st, const float *J32, int N, int Np, int R,
-                                          const int8_t *Sbest, double *part, double *Eout)
+                                          const int8_t *Sbest, int scale_exp, double *part,
+                                          double *Eout)
 {
     const dim3 grid((R + 31) / 32, kFeGroups);
     const size_t smem = (size_t)(N + 32) * 32;
@@ -683,11 +692,14 @@ cudaError_t launch_final_energy_f64_parts(cudaStream_t st, const float *J32, int
         if (e != cudaSuccess)
             return e;
     }
-    final_energy_part_kernel<<<grid, 256, smem, st>>>(J32, N, Np, R, Sbest, part);
+    long long *ipart = reinterpret_cast<long long *>(part);
+    final_energy_part_kernel<<<grid, 256, smem, st>>>(J32, N, Np, R, Sbest,
+                                                      ldexp(1.0, scale_exp), ipart);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
         return e;
-    final_energy_sum_kernel<<<(R + 255) / 256, 256, 0, st>>>(part, kFeGroups, R, Eout);
+    final_energy_sum_kernel<<<(R + 255) / 256, 256, 0, st>>>(ipart, kFeGroups, R,
+                                                             ldexp(1.0, -scale_exp), Eout);
     return cudaGetLastError();
 }
 

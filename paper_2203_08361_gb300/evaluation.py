@@ -9,6 +9,7 @@ it is not part of the step path (every step runs in the CUDA kernels).
 """
 from __future__ import annotations
 
+import itertools
 import math
 from dataclasses import dataclass
 
@@ -66,4 +67,42 @@ def evaluate(J, form: str, steps_list, trials: int, seed: int, target_energy: fl
             prob = success_probability(energy, target_energy, tol)
             out.append(TrialStats(int(steps), trials, float(cut.mean()), float(cut.max()),
                                   float(energy.min()), prob, step_to_solution(prob, int(steps))))
+    return out
+
+
+def grid_points(grid: dict) -> list:
+    """Every combination of the parameter values in `grid` (name -> list of
+    values), the last name varying fastest, as dicts."""
+    names = list(grid)
+    for n in names:
+        if len(grid[n]) == 0:
+            raise ValueError(f"no values for {n!r}")
+    return [dict(zip(names, combo)) for combo in itertools.product(*(grid[n] for n in names))]
+
+
+@dataclass
+class SweepPoint:
+    params: dict
+    stats: TrialStats
+
+
+def sweep(J, form: str, grid: dict, steps: int, trials: int, seed: int, target_energy: float,
+          tol: float = 0.0, **fixed) -> list:
+    """The paper's parameter scans (Fig. 1: P and S over gamma and dt at fixed
+    N_s; c1 likewise): `trials` replicas per point of `grid` (e.g. {"dt":
+    [...], "gamma": [...], "c1": [...]}), every point on the same seed, with
+    the remaining parameters from `fixed`.  Returns one SweepPoint per grid
+    point in grid_points order."""
+    out = []
+    with Solver(J) as s:
+        for point in grid_points(grid):
+            kw = dict(fixed)
+            kw.update(point)
+            p = make_params(form, **kw)
+            _, energy = s.run(p, trials, int(steps), seed)
+            cut = s.cut_values(energy)
+            prob = success_probability(energy, target_energy, tol)
+            out.append(SweepPoint(dict(point), TrialStats(
+                int(steps), trials, float(cut.mean()), float(cut.max()), float(energy.min()),
+                prob, step_to_solution(prob, int(steps)))))
     return out

@@ -35,3 +35,14 @@ def test_success_probability_counts_trials_at_or_below_target():
     assert ev.success_probability(e, -11.5, tol=0.6) == pytest.approx(0.6)
     with pytest.raises(ValueError):
         ev.success_probability([], 0.0)
+
+
+def test_grid_points_cover_the_product_last_name_fastest():
+    g = {"dt": [0.5, 1.1], "gamma": [0.0, 0.06, 0.1]}
+    pts = ev.grid_points(g)
+    assert len(pts) == 6
+    assert pts[0] == {"dt": 0.5, "gamma": 0.0} and pts[1] == {"dt": 0.5, "gamma": 0.06}
+    assert pts[-1] == {"dt": 1.1, "gamma": 0.1}
+    assert ev.grid_points({"c1": [0.7]}) == [{"c1": 0.7}]
+    with pytest.raises(ValueError):
+        ev.grid_points({"dt": []})

@@ -50,3 +50,21 @@ def test_harness_statistics_match_oracle_trials():
         assert st.step_to_solution == ev.step_to_solution(p_ref, st.steps)
         assert st.min_energy == float(np.min(ref["best_e"])) >= e0
     assert stats[-1].p > 0.0  # the ground state is found within 80 steps
+
+
+def test_parameter_sweep_matches_oracle_trials():
+    # the paper's gamma / dt scan at fixed N_s on a 16-spin instance: every
+    # grid point's P equals that of oracle trials with the same parameters
+    J = synth.sk_pm1(16, 8)
+    e0 = float(oracle.brute_force(J)[0])
+    trials, seed, steps = 48, 3, 40
+    grid = {"dt": [0.5, 1.1], "gamma": [0.0, 0.06]}
+    pts = ev.sweep(J, "discrete", grid, steps, trials, seed, e0, prec="fp32", c1=0.7,
+                   eval_every=20)
+    assert [pt.params for pt in pts] == ev.grid_points(grid)
+    c0 = oracle.c0_from_c1(J, 0.7)
+    for pt in pts:
+        op = oracle.make_params(1, c0, pt.params["dt"], pt.params["gamma"], eval_every=20)
+        ref = oracle.run(J, op, steps, seed, range(trials), "f32")
+        assert pt.stats.p == ev.success_probability(ref["best_e"], e0)
+        assert pt.stats.min_energy == float(np.min(ref["best_e"]))
