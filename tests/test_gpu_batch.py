@@ -54,3 +54,29 @@ def test_batch_uneven_workload_full_size():
     # 100: one batched launch against 256 separate runs.
     sizes = synth.batch_sizes(256, 4)
     _batch_vs_single(sizes, 64, 2000, 100, 9, check_oracle=(sizes.index(min(sizes)),))
+
+
+@pytest.mark.parametrize("kind", ["gauss", "nose_hoover"])
+def test_batch_of_other_instances_runs_them_one_after_another(kind):
+    # instances the batched FP8 kernel does not take (general couplings, the
+    # Nose-Hoover thermostat) run one after another with instance = b: the
+    # same results as separate runs
+    sizes = [150, 300, 77]
+    R, steps, seed = 40, 60, 9
+    if kind == "gauss":
+        Js = [synth.sk_gauss(n, 600 + b) for b, n in enumerate(sizes)]
+        kw = dict(form="ballistic", prec="auto", c1=0.9, dt=1.1, gamma=0.5, eval_every=20)
+    else:
+        Js = [synth.sk_pm1(n, 600 + b) for b, n in enumerate(sizes)]
+        kw = dict(form="discrete", prec="auto", c1=0.7, dt=1.1, eval_every=20,
+                  thermostat="nose_hoover", nh_T=0.3, nh_M=20.0 * max(sizes), nh_xi0=-0.05)
+    solvers = [hsb.Solver(J) for J in Js]
+    try:
+        out = hsb.run_batch([s.h for s in solvers], hsb.params(**kw), R, steps, seed)
+        for b, s in enumerate(solvers):
+            spins, energy = s.run(hsb.params(instance=b, **kw), R, steps, seed)
+            np.testing.assert_array_equal(out[b][0], spins)
+            np.testing.assert_array_equal(out[b][1], energy)
+    finally:
+        for s in solvers:
+            s.close()

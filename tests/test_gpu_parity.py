@@ -296,3 +296,17 @@ def test_diluted_couplings_bit_exact(prec, schedule):
     # c0 = c1 / (sqrt(N) sigma_J), sigma_J < 1 for diluted couplings
     ref = oracle.run(J, _oparams(J, 1, 0.7, 1.1, 0.06, ev), steps, seed, range(R), "f32")
     _assert_same(x, y, spins, energy, ref)
+
+
+@pytest.mark.parametrize("n", [6000, 6500])
+def test_general_couplings_final_energy_fixed_point_and_large_n(n):
+    # the final binary64 energies of general couplings: fixed point up to
+    # N of about 6300, one block per replica beyond; both within 1e-12 of the
+    # oracle's binary64 sum of the returned spins
+    J = synth.sk_gauss(n, 31)
+    R, steps, seed = 32, 3, 2
+    p = hsb.params("ballistic", "fp32", c1=0.9, dt=1.1, gamma=0.5, eval_every=0)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, steps, seed)
+    for r in (0, 17, 31):
+        assert energy[r] == pytest.approx(oracle.ising_energy(J, spins[r]), rel=1e-12)
