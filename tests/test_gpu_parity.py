@@ -310,3 +310,28 @@ def test_general_couplings_final_energy_fixed_point_and_large_n(n):
         spins, energy = s.run(p, R, steps, seed)
     for r in (0, 17, 31):
         assert energy[r] == pytest.approx(oracle.ising_energy(J, spins[r]), rel=1e-12)
+
+
+def test_auto_schedule_falls_back_when_the_persistent_grid_does_not_fit():
+    # N = 1024, R = 4096: 8 x 32 = 256 tiles of 128 x 128, more than the
+    # co-resident grid of one CTA per SM, so AUTO runs one launch per step;
+    # sampled replicas equal the oracle bit for bit and the run equals the
+    # explicit per-step schedule
+    n, R, steps, seed, ev = 1024, 4096, 30, 13, 10
+    J = synth.sk_pm1(n, 77)
+    p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=ev)
+    ps = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=ev,
+                    schedule="per_step")
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, steps, seed)
+        assert s.run_stats() > steps  # one launch per step at least
+        x, y = s.get_state(R)
+        spins2, energy2 = s.run(ps, R, steps, seed)
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("discrete", "fp8", schedule="persistent"), R, steps, seed)
+        assert e.value.status == hsb.HSB_E_UNSUPPORTED
+    np.testing.assert_array_equal(spins, spins2)
+    np.testing.assert_array_equal(energy, energy2)
+    rows = [0, 1, 2047, 4095]
+    ref = oracle.run(J, _oparams(J, 1, 0.7, 1.1, 0.06, ev), steps, seed, rows, "f32")
+    _assert_same(x, y, spins, energy, ref, rows=rows)
