@@ -266,6 +266,18 @@ def get_trace(h: int):
     return buf
 
 
+def trace_cut(h: int):
+    """The trace as cut values (the paper's instantaneous C and T_inst at every
+    traced step): float64 [n, 3] = (max C, mean C, mean T_inst).  C = -E/2 -
+    1/4 sum_ij J_ij (Eq. eq_Cut, w = -J) is affine in E with a negative slope,
+    so the maximum cut is the cut of the minimum energy and the mean cut the
+    cut of the mean energy."""
+    tr = get_trace(h)
+    if tr.shape[0] == 0:
+        return tr
+    return np.stack([cut_values(h, tr[:, 0]), cut_values(h, tr[:, 1]), tr[:, 2]], axis=1)
+
+
 def get_xi(h: int, R: int):
     """hsb_get_xi: float64 [R], the Nose-Hoover xi of each replica after the last run."""
     xi = np.zeros(int(R), np.float64)
@@ -335,6 +347,9 @@ class Solver:
 
     def get_xi(self, R: int):
         return get_xi(self.h, R)
+
+    def trace_cut(self):
+        return trace_cut(self.h)
 
     def set_stream(self, stream_ptr):
         set_stream(self.h, stream_ptr)

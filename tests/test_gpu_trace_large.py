@@ -35,9 +35,17 @@ def test_trace_matches_oracle(prec):
     with hsb.Solver(J) as s:
         spins, energy = s.run(p, R, steps, 6)
         tr = s.get_trace()
+        tc = s.trace_cut()
         x, y = s.get_state(R)
     ref = _oracle_trace(J, 0.7, steps, 6, range(R), te, eval_every=25)
     assert tr.shape == (steps // te, 3)
+    # instantaneous cut values (Eq. eq_Cut, w = -J): C_r = -E_r/2 - sum(J)/4
+    # per replica, so the trace's maximum and mean cut follow from the
+    # oracle's per-replica energies
+    c_ref = -0.5 * ref["trace_e"] - 0.25 * float(J.astype(np.float64).sum())
+    np.testing.assert_allclose(tc[:, 0], c_ref.max(axis=0), rtol=1e-15)
+    np.testing.assert_allclose(tc[:, 1], c_ref.mean(axis=0), rtol=1e-12)
+    np.testing.assert_array_equal(tc[:, 2], tr[:, 2])
     np.testing.assert_array_equal(tr[:, 0], ref["trace_e"].min(axis=0))
     np.testing.assert_array_equal(tr[:, 1], ref["trace_e"].mean(axis=0))
     np.testing.assert_allclose(tr[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6)
