@@ -1,7 +1,10 @@
 """hsb_run_fp32_noalloc, the entry point that allocates nothing (it works in a
 fixed scratch array the library holds), against hsb_run on the plain FP32
 path: two calls in a row, each on a different instance, must give the same
-best spins and energies.  This file is collected last on purpose."""
+best spins and energies (exact integers for +/-1 couplings; for general
+couplings the no-alloc path sums the final energies in binary64 and hsb_run
+in exact fixed point, so they agree to 1e-12 relative).  This file is
+collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -38,7 +41,8 @@ def test_no_alloc_run_matches_hsb_run_on_two_calls_in_a_row():
             want_s, want_e = s.run(p, R, steps, 9)
         got_s, got_e = _noalloc(torch, J, p, R, steps, 9, stream)
         np.testing.assert_array_equal(got_s, want_s)
-        np.testing.assert_allclose(got_e, want_e, rtol=0, atol=0)
+        exact = bool(np.all(np.isin(J, (-1.0, 0.0, 1.0))))
+        np.testing.assert_allclose(got_e, want_e, rtol=0 if exact else 1e-12, atol=0)
 
 
 def test_no_alloc_rejects_sizes_beyond_its_scratch():
