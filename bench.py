@@ -38,7 +38,9 @@ WORKLOAD = dict(name="HdSB SK +/-1 N=2000 R=1024 2000 steps FP8", N=2000, J_seed
                 sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1, gamma=0.06,
                 init_half_width=1.0, eval_every=100, a0=1.0)
 L2_FLUSH_BYTES = 256 << 20
-TC_SOURCE = os.path.join(ROOT, "paper_2203_08361_gb300", "csrc", "hsb_persist.cu")
+# every source compiled into the loop kernel (its DRAM record is void once any changes)
+TC_SOURCES = [os.path.join(ROOT, "paper_2203_08361_gb300", "csrc", f)
+              for f in ("hsb_persist.cu", "hsb_ptx.cuh", "hsb_device.cuh", "hsb_internal.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -211,8 +213,11 @@ def _traffic_for_current_kernel():
     try:
         with open(TRAFFIC_FILE) as fh:
             rec = json.load(fh)
-        with open(TC_SOURCE, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for f in TC_SOURCES:
+            with open(f, "rb") as fh:
+                h.update(fh.read())
+        sha = h.hexdigest()[:16]
         if rec.get("source_sha256_16") == sha:
             return rec.get("dram_bytes_per_launch")
     except (OSError, ValueError):
