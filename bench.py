@@ -422,6 +422,11 @@ OTHER = {
                     kind="single", N=16384, J="pm1", J_seed=3, R=4096, sb_steps=10000,
                     form="discrete", prec="fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
                     trace_every=1, peak="fp8", dtype="fp8"),
+    "trace2000": dict(name="HdSB SK +/-1 N=2000 R=1024 2000 steps FP8 with per-step trace "
+                           "(min / mean E, mean T_inst)", kind="single", N=2000, J="pm1",
+                      J_seed=1, R=1024, sb_steps=2000, form="discrete", prec="fp8", c1=0.7,
+                      dt=1.1, gamma=0.06, eval_every=100, trace_every=1, peak="fp8",
+                      dtype="fp8"),
     "nh2000": dict(name="Nose-Hoover dSB SK +/-1 N=2000 R=1024 2000 steps FP8 "
                         "(T=0.3, M=40000, xi0=-0.05)", kind="single", N=2000, J="pm1", J_seed=1,
                    R=1024, sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1,

@@ -128,6 +128,14 @@ struct hsb_ctx {
     size_t flags_cap = 0;
     unsigned long long *nhpart = nullptr;  // [3][nblk][Rp][2] Nose-Hoover tile sums
     size_t nhpart_cap = 0;
+    // per-step trace on the persistent kernel: row-block sums of every traced
+    // step, the batched reduction's scratch and its tickets (kept at zero)
+    float *trE = nullptr, *trT = nullptr;
+    size_t trE_cap = 0, trT_cap = 0;
+    double *tr_scratch = nullptr;
+    size_t tr_scratch_cap = 0;
+    unsigned *tr_tickets = nullptr;
+    size_t tr_tickets_cap = 0;
     float *pk_dev = nullptr;
     int pk_cap = 0, pk_steps = -1;
     double pk_a0 = 0.0;
@@ -316,8 +324,8 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_INVAL, "unknown precision %d", p->prec);
     if (p->trace_every > 0 && prec == HSB_PREC_BF16X3)
         return set_error(HSB_E_UNSUPPORTED, "the trace needs the FP32 or FP8 precision");
-    if (p->trace_every > 0 && prec == HSB_PREC_FP8 && (p->schedule == 1 || p->schedule == 3))
-        return set_error(HSB_E_UNSUPPORTED, "the trace runs on the one-launch-per-step schedule");
+    if (p->trace_every > 0 && prec == HSB_PREC_FP8 && p->schedule == 3)
+        return set_error(HSB_E_UNSUPPORTED, "the trace does not run on the resident-J schedule");
     if (nose_hoover && prec == HSB_PREC_BF16X3)
         return set_error(HSB_E_UNSUPPORTED, "the Nose-Hoover thermostat needs FP32 or FP8");
     if (nose_hoover && prec == HSB_PREC_FP8 && p->schedule == 3)
@@ -635,7 +643,7 @@ int num_evals(const RunCfg &c)
 hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
 {
     *out = false;
-    if (c.prec != HSB_PREC_FP8 || c.schedule == 2 || c.trace_every > 0)
+    if (c.prec != HSB_PREC_FP8 || c.schedule == 2)
         return HSB_OK;
     const bool fits = c.schedule == 3 ? tc_resident_fits(h->Np, c.Rp)
                                       : tc_persistent_fits(h->Np, c.Rp);
@@ -695,6 +703,22 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
         s = grow(&h->flags, &h->flags_cap, 2 * nflags, "cudaMalloc flags");
     if (s == HSB_OK && c.thermo)
         s = grow(&h->nhpart, &h->nhpart_cap, (size_t)3 * nblk * c.Rp * 2, "cudaMalloc nhpart");
+    const bool traced = evaluate && c.trace_every > 0;
+    const int ntr = traced ? (c.steps - 1) / c.trace_every + 1 : 0;
+    const int nparts = (c.R + 31) / 32;
+    if (s == HSB_OK && traced)
+        s = grow(&h->trE, &h->trE_cap, (size_t)ntr * nblk * c.Rp, "cudaMalloc trace sums");
+    if (s == HSB_OK && traced)
+        s = grow(&h->trT, &h->trT_cap, (size_t)ntr * nblk * c.Rp, "cudaMalloc trace sums");
+    if (s == HSB_OK && traced)
+        s = grow(&h->tr_scratch, &h->tr_scratch_cap, (size_t)3 * nparts * ntr,
+                 "cudaMalloc trace scratch");
+    if (s == HSB_OK && traced && h->tr_tickets_cap < (size_t)ntr) {
+        s = grow(&h->tr_tickets, &h->tr_tickets_cap, (size_t)ntr, "cudaMalloc trace tickets");
+        if (s == HSB_OK)
+            CK(cudaMemsetAsync(h->tr_tickets, 0, h->tr_tickets_cap * sizeof(unsigned), h->work),
+               "memset trace tickets");
+    }
     if (s == HSB_OK && evaluate)
         s = grow(&h->Eeval, &h->eeval_cap, (size_t)ne * nblk * c.Rp, "cudaMalloc Eeval");
     if (s == HSB_OK && evaluate)
@@ -727,6 +751,11 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     a.Epart = h->Eeval;
     a.Snap = h->Snap;
     a.err = h->err;
+    if (traced) {
+        a.trace_every = c.trace_every;
+        a.trE = h->trE;
+        a.trT = h->trT;
+    }
     a.drop_mb = -1;
     if (c.schedule != 3) {
         a.drop_mb = h->debug_drop_mb;
@@ -751,6 +780,10 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
         CK(launch_select_best(h->work, h->Eeval, h->Snap, ne, nblk, h->N, h->Np, c.R, c.Rp,
                               h->Ebest, h->Sbest),
            "select best kernel");
+    if (traced)
+        CK(launch_trace_reduce_many(h->work, h->trE, h->trT, nblk, h->N, c.R, c.Rp, ntr,
+                                    h->tr_scratch, h->tr_tickets, h->trace),
+           "trace kernel");
     return HSB_OK;
 }
 
@@ -882,6 +915,27 @@ hsb_status enqueue_run_bf16(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hs
 }
 
 // Queues a whole run (init, graph of the step loop) on the work stream.
+// The trace buffer of a run: 3 doubles per traced time t_k, k = m trace_every
+// < steps (sets trace_len; 0 without a trace).
+hsb_status ensure_trace(hsb_ctx *h, const RunCfg &c)
+{
+    if (c.trace_every <= 0) {
+        h->trace_len = 0;
+        return HSB_OK;
+    }
+    const size_t need = 3 * (size_t)((c.steps - 1) / c.trace_every + 1);
+    if (h->trace_cap < need) {
+        cudaFree(h->trace);
+        h->trace = nullptr;
+        h->trace_cap = 0;
+        CK(cudaMalloc(&h->trace, need * sizeof(double)), "cudaMalloc trace");
+        h->trace_cap = need;
+        h->graph_valid = false;  // the captured loop holds the trace pointer
+    }
+    h->trace_len = need / 3;
+    return HSB_OK;
+}
+
 hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_params *p)
 {
     hsb_status s = prepare(h, c);
@@ -894,6 +948,9 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
     if (s != HSB_OK)
         return s;
     if (persistent) {
+        s = ensure_trace(h, c);
+        if (s != HSB_OK)
+            return s;
         CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->work), "memset err");
         CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R,
                        c.Rp, h->X[0], h->Y, h->S8[0], h->Ebest),
@@ -907,25 +964,13 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
         h->last_x = 0;
         h->state_par = c.steps & 1;
         h->have_state = true;
-        h->launches = c.thermo ? 4 : 3;
-        h->trace_len = 0;
+        h->launches = 3 + (c.thermo ? 1 : 0) + (c.trace_every > 0 ? 1 : 0);
         h->have_xi = c.thermo != 0;
         return HSB_OK;
     }
-    if (c.trace_every > 0) {
-        const size_t need = 3 * (size_t)((c.steps - 1) / c.trace_every + 1);
-        if (h->trace_cap < need) {
-            cudaFree(h->trace);
-            h->trace = nullptr;
-            h->trace_cap = 0;
-            CK(cudaMalloc(&h->trace, need * sizeof(double)), "cudaMalloc trace");
-            h->trace_cap = need;
-            h->graph_valid = false;  // the captured loop holds the trace pointer
-        }
-        h->trace_len = need / 3;
-    } else {
-        h->trace_len = 0;
-    }
+    s = ensure_trace(h, c);
+    if (s != HSB_OK)
+        return s;
     const GraphKey key = make_key(h, c);
     if (!h->graph_valid || !(h->gkey == key)) {
         s = build_graph(h, c, key);
@@ -1201,6 +1246,10 @@ void hsb_destroy(hsb_handle h)
     cudaFree(h->Jcat);
     cudaFree(h->trace);
     cudaFree(h->err);
+    cudaFree(h->trE);
+    cudaFree(h->trT);
+    cudaFree(h->tr_scratch);
+    cudaFree(h->tr_tickets);
     cudaFree(h->nhpart);
     cudaFree(h->flags);
     cudaFree(h->pk_dev);

@@ -82,6 +82,12 @@ cudaError_t launch_nh_update(cudaStream_t st, const float *Y, int N, int Np, int
 cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,
                                 int N, int R, int Rp, double *scratch, unsigned *ticket,
                                 double *out);
+// `entries` trace entries at once: entry m reads Epart / Tpart + m nblk Rp,
+// uses scratch + m 3 ceil(R / 32) and ticket m (zero before, left zero), and
+// writes out[3 m .. 3 m + 2].
+cudaError_t launch_trace_reduce_many(cudaStream_t st, const float *Epart, const float *Tpart,
+                                     int nblk, int N, int R, int Rp, int entries, double *scratch,
+                                     unsigned *tickets, double *out);
 
 // Best tracking after an evaluation: E_r = -1/2 sum_blocks Epart; if E_r <
 // Ebest[r] store it with the spins sgn(x) read from X (fp32) or S8 (fp8).
@@ -167,6 +173,11 @@ struct PersistArgs {
     // failure-detection test: tile (drop_mb, 0) never publishes its signs, so
     // the bounded waits of the launch expire (-1: off)
     int drop_mb;
+    // per-step trace (persistent kernel): at t_k, k = m trace_every < steps,
+    // each tile stores its row block's sums of s_i f_i and y_i^2 per replica
+    // in trE / trT [m][nblk][Rp] (binary32)
+    int trace_every;
+    float *trE, *trT;
 };
 
 // Resident-J variant (hsb_persist_ar.cu): N <= 2048, same arguments.

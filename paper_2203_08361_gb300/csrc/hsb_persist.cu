@@ -111,6 +111,9 @@ struct __align__(8) PShared {
     double xi[kPN];
     float gnh[kPN];
     unsigned nhacc[3][kPN];
+    // per-step trace: per-quadrant sums of s_i f_i and y_i^2 (traced passes)
+    int tre[4][kPN];
+    float trt[4][kPN];
 };
 
 constexpr size_t kPSmem =
@@ -490,6 +493,11 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 e = a.n_evals - 1;
             else if (a.eval_every > 0 && k > 0 && k < a.steps_total && k % a.eval_every == 0)
                 e = k / a.eval_every - 1;
+            // traced time t_k (per-step trace): energy and T_inst of the state
+            // before this pass's update
+            const int tm = (!final_pass && a.trace_every > 0 && k % a.trace_every == 0)
+                               ? k / a.trace_every
+                               : -1;
             const float pk = final_pass ? 0.f : pk_next;
             const uint64_t pk2 = f2_pack(pk, pk);
             if (kl + 1 < a.nsteps)
@@ -632,6 +640,39 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 load_force(tmem + lane_off + col0, two_acc, f);
                 ptx::tmem_ld_wait(xr);
                 ptx::tmem_ld_wait(yr);
+                if (tm >= 0) {
+                    // s_i f_i is an exact integer: one redux per column (lane j
+                    // keeps column col0 + j); y_i^2 through the transposed
+                    // butterfly (lane l ends with column (l >> 1) & 15)
+                    int emine = 0;
+                    float tv[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float fj = __uint_as_float(f[j]);
+                        const float x0 = __uint_as_float(xr[j]);
+                        const int term = live ? (x0 >= 0.f ? (int)fj : -(int)fj) : 0;
+                        const int sum = __reduce_add_sync(0xFFFFFFFFu, term);
+                        if (lane == j)
+                            emine = sum;
+                        const float y0 = __uint_as_float(yr[j]);
+                        tv[j] = __fmul_rn(y0, y0);  // y_i(t_k)^2 (Eq. eq_TInst)
+                    }
+#pragma unroll
+                    for (int m = 16, n = 8; m >= 2; m >>= 1, n >>= 1) {
+                        const bool up = (lane & m) != 0;
+#pragma unroll
+                        for (int kk = 0; kk < n; ++kk) {
+                            const float sa = up ? tv[kk] : tv[kk + n];
+                            const float ra = __shfl_xor_sync(0xFFFFFFFFu, sa, m);
+                            tv[kk] = (up ? tv[kk + n] : tv[kk]) + ra;
+                        }
+                    }
+                    const float tsum = tv[0] + __shfl_xor_sync(0xFFFFFFFFu, tv[0], 1);
+                    if (lane < 16)
+                        sh->tre[q][col0 + lane] = emine;
+                    if ((lane & 1) == 0)
+                        sh->trt[q][col0 + ((lane >> 1) & 15)] = tsum;
+                }
                 if (e >= 0) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -681,11 +722,17 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             __syncwarp();
             if (lane == 0)
                 ptx::mbar_arrive(&sh->tmem_empty);  // this warp has read the accumulator
-            if (e >= 0) {
+            if (e >= 0 || tm >= 0) {
                 epi_bar();
-                if (et < kPN) {
+                if (et < kPN && e >= 0) {
                     const float s = sh->red[0][et] + sh->red[1][et] + sh->red[2][et] + sh->red[3][et];
                     a.Epart[((size_t)e * nblk + mb) * a.Rp + r0 + et] = s;
+                }
+                if (et < kPN && tm >= 0) {
+                    const size_t o = ((size_t)tm * nblk + mb) * a.Rp + r0 + et;
+                    a.trE[o] = (float)(sh->tre[0][et] + sh->tre[1][et] + sh->tre[2][et] +
+                                       sh->tre[3][et]);
+                    a.trT[o] = sh->trt[0][et] + sh->trt[1][et] + sh->trt[2][et] + sh->trt[3][et];
                 }
             }
             if (kNH && !final_pass) {

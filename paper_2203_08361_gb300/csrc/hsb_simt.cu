@@ -427,6 +427,15 @@ trace_parts_kernel(const float *__restrict__ Epart, const float *__restrict__ Tp
                    int N, int R, int Rp, double *__restrict__ part, unsigned *__restrict__ ticket,
                    double *__restrict__ out)
 {
+    // entry blockIdx.y of a batch (one entry when gridDim.y == 1)
+    {
+        const size_t m = blockIdx.y;
+        Epart += m * (size_t)nblk * Rp;
+        Tpart += m * (size_t)nblk * Rp;
+        part += m * 3 * (size_t)gridDim.x;
+        ticket += m;
+        out += 3 * m;
+    }
     __shared__ double se_sh[8][32], st_sh[8][32];
     __shared__ double fmin_sh[256], fsum_sh[256], ftt_sh[256];
     __shared__ bool last;
@@ -496,6 +505,17 @@ trace_parts_kernel(const float *__restrict__ Epart, const float *__restrict__ Tp
         out[2] = ftt_sh[0] / (double)R;
         *ticket = 0u;
     }
+}
+
+cudaError_t launch_trace_reduce_many(cudaStream_t st, const float *Epart, const float *Tpart,
+                                     int nblk, int N, int R, int Rp, int entries, double *scratch,
+                                     unsigned *tickets, double *out)
+{
+    if (entries < 1)
+        return cudaSuccess;
+    const dim3 grid((R + 31) / 32, entries);
+    trace_parts_kernel<<<grid, 256, 0, st>>>(Epart, Tpart, nblk, N, R, Rp, scratch, tickets, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,

@@ -49,8 +49,6 @@ def test_nose_hoover_bit_exact(kind, form, prec, schedule, n, R):
     c1 = 0.7 if form == "discrete" else 0.9
     steps, seed, ev, te = 200, 12, 50, 10
     NH = _nh(n)
-    # the trace runs on the per-step schedule only
-    te = te if schedule != "persistent" else 0
     p = hsb.params(form, prec, c1=c1, dt=1.1, eval_every=ev, trace_every=te,
                    schedule=schedule, thermostat="nose_hoover", **NH)
     with hsb.Solver(J) as s:
@@ -60,7 +58,7 @@ def test_nose_hoover_bit_exact(kind, form, prec, schedule, n, R):
         tr = s.get_trace()
         launches = s.run_stats()
     if schedule == "persistent":
-        assert launches == 4  # init, xi init, the step loop, best selection
+        assert launches == 5  # init, xi init, the step loop, best selection, trace
     ref = oracle.run(J, _nh_oracle(J, fcode, c1, 1.1, ev, te, **NH), steps, seed, range(R),
                      "f32", want_trace=te > 0)
     np.testing.assert_array_equal(xi, ref["xi"])

@@ -228,11 +228,11 @@ def test_unsupported_precision_and_argument_errors():
         with pytest.raises(hsb.HsbError) as e:
             s.run(hsb.params("ballistic", "fp8"), 4, 10, 0)
         assert e.value.status == 7
-        # the per-step trace runs on the one-launch-per-step schedule only
-        for sched in ("persistent", "resident"):
-            with pytest.raises(hsb.HsbError) as e:
-                s.run(hsb.params("discrete", "fp8", trace_every=1, schedule=sched), 4, 10, 0)
-            assert e.value.status == 7
+        # the per-step trace runs on the persistent and per-step schedules,
+        # not on the resident-J one
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("discrete", "fp8", trace_every=1, schedule="resident"), 4, 10, 0)
+        assert e.value.status == 7
     # J held on chip needs N <= 2048
     with hsb.Solver(synth.sk_pm1(2100, 0)) as s:
         with pytest.raises(hsb.HsbError) as e:

@@ -27,16 +27,20 @@ def _oracle_trace(J, c1, steps, seed, reps, trace_every, eval_every=0):
     return oracle.run(J, op, steps, seed, reps, "f32", nthreads=0)
 
 
-@pytest.mark.parametrize("prec", ["fp8", "fp32"])
-def test_trace_matches_oracle(prec):
+@pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
+                                           ("fp32", "auto")])
+def test_trace_matches_oracle(prec, schedule):
     n, R, steps, te = 300, 40, 100, 10
     J = synth.sk_pm1(n, 17)
-    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=25, trace_every=te)
+    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=25, trace_every=te,
+                   schedule=schedule)
     with hsb.Solver(J) as s:
         spins, energy = s.run(p, R, steps, 6)
         tr = s.get_trace()
         tc = s.trace_cut()
         x, y = s.get_state(R)
+        if schedule == "persistent":
+            assert s.run_stats() == 4  # init, step loop, best selection, trace entries
     ref = _oracle_trace(J, 0.7, steps, 6, range(R), te, eval_every=25)
     assert tr.shape == (steps // te, 3)
     # instantaneous cut values (Eq. eq_Cut, w = -J): C_r = -E_r/2 - sum(J)/4
@@ -81,3 +85,26 @@ def test_large_instance_fp8_sampled_replicas_and_trace():
     assert np.all(tr_all[:, 0] == np.round(tr_all[:, 0]))
     assert np.all(tr_all[:, 0] <= tr_all[:, 1])
     assert abs(tr_all[0, 2] - 1.0 / 3.0) < 1e-3
+
+
+def test_persistent_trace_every_step_full_size_sampled():
+    # the paper's per-step trace (Fig. 2) at N = 2000, R = 1024 on the
+    # persistent kernel: the trace entries of two replicas' runs equal the
+    # oracle's, and the full trace is that of the per-step schedule
+    n, R, steps, seed = 2000, 1024, 60, 4
+    J = synth.sk_pm1(n, 1)
+    kw = dict(c1=0.7, dt=1.1, gamma=0.06, eval_every=20, trace_every=1)
+    with hsb.Solver(J) as s:
+        s.run(hsb.params("discrete", "fp8", schedule="persistent", **kw), R, steps, seed)
+        tr_p = s.get_trace()
+        s.run(hsb.params("discrete", "fp8", schedule="per_step", **kw), R, steps, seed)
+        tr_s = s.get_trace()
+        s.run(hsb.params("discrete", "fp8", schedule="persistent", **kw), 2, steps, seed)
+        tr2 = s.get_trace()
+    assert tr_p.shape == (steps, 3)
+    np.testing.assert_array_equal(tr_p[:, :2], tr_s[:, :2])   # exact integer energies
+    np.testing.assert_allclose(tr_p[:, 2], tr_s[:, 2], rtol=1e-6)
+    ref = _oracle_trace(J, 0.7, steps, seed, [0, 1], 1, eval_every=20)
+    np.testing.assert_array_equal(tr2[:, 0], ref["trace_e"].min(axis=0))
+    np.testing.assert_array_equal(tr2[:, 1], ref["trace_e"].mean(axis=0))
+    np.testing.assert_allclose(tr2[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6)
