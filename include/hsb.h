@@ -100,7 +100,8 @@ typedef struct {
                                the minimum and mean Ising energy over replicas and
                                the mean instantaneous temperature (1/N) sum y^2
                                (Eq. (eq_TInst)); see hsb_get_trace.  FP32 and FP8
-                               (one launch per step) only */
+                               (persistent or one launch per step; not schedule 3);
+                               BF16X3 returns HSB_E_UNSUPPORTED */
     uint32_t instance;      /* random stream of the instance (x0, y0) */
     int schedule;           /* FP8 step loop: 0 = automatic (persistent kernel
                                when its grid fits on the device), 1 = persistent
