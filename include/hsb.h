@@ -117,9 +117,10 @@ typedef struct {
                                Nose-Hoover runs on FP32 and on FP8 (persistent or one
                                launch per step; AUTO never picks BF16X3 for it);
                                schedule 3 and hsb_advance* return HSB_E_UNSUPPORTED,
-                               hsb_run_batch runs the instances one after another.  A momentum |y| >= 256 (an
-                               unstable setting: M much below N) makes the run
-                               return HSB_E_INVAL.  See hsb_get_xi. */
+                               hsb_run_batch runs the instances one after another.
+                               A momentum |y| >= 256 (an unstable setting: M much
+                               below N) makes the run return HSB_E_INVAL.  See
+                               hsb_get_xi. */
     int reserved0;          /* must be zero */
     double nh_T;            /* Nose-Hoover temperature T >= 0 */
     double nh_M;            /* Nose-Hoover mass M > 0 */
