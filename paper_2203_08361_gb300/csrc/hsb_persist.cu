@@ -8,8 +8,9 @@
 // Each CTA owns one tile of 128 spins x 128 replicas for the whole run.  The
 // tile's positions x and momenta y stay in tensor memory next to the FP32
 // accumulator (columns 0-127 accumulator, 128-255 x, 256-383 y; lane = spin),
-// so a step moves only J and the FP8 spin operand S = sgn(x) through L2.  One step of a tile is a dependency chain (the force needs the
-// sign tiles of every row block), so the roles are arranged to shorten it:
+// so a step moves only J and the FP8 spin operand S = sgn(x) through L2.  One
+// step of a tile is a dependency chain (the force needs the sign tiles of
+// every row block), so the roles are arranged to shorten it:
 //   warp 0      poller: reads the per-tile "published" flags of the step's
 //               operand (one flag per 128-spin chunk, all lanes at once) and
 //               appends the K-chunk pairs, in the order they become ready, to
