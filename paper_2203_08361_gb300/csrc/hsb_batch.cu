@@ -10,7 +10,7 @@
 //     other global buffer and are fetched back with one TMA copy at the step
 //     boundary (the old ones are read by every row block of the step);
 //   - J streams through shared memory two 128-wide K chunks per TMA copy
-//     (3-D box, 32 KB); instances are small enough that J stays in L2;
+//     (3-D box, 32 KB), three copies in flight;
 //   - for each 128-spin row block tcgen05.mma (M = 128, N = BN) accumulates
 //     F = J S in tensor memory, double-buffered so that the next block's MMA
 //     overlaps the epilogue of this one;
@@ -18,11 +18,12 @@
 //     memory, writes sgn(x') as FP8, and on evaluation steps adds s_i f_i into
 //     per-replica integer sums; after the step the best energy and spins of
 //     each replica are updated in place (exact integers, strict <).
-// Roles: warps 0-1 stream J, one per stage (J does not change, so the next
-// step's first chunks load while the epilogue runs); warps 2-3 issue
-// tcgen05.mma from elected lanes, each consuming one stage into its own
-// accumulator (split K, exact integer partial forces) when BN <= 128 and a
-// row block has two or more loads, warp 2 alone otherwise; warp 2 also loads
+// Roles: warps 0-1 stream J through three stages, warp p filling the stages
+// s with s % 2 == p (J does not change, so the next step's first chunks load
+// while the epilogue runs); warps 2-3 issue tcgen05.mma from elected lanes,
+// warp 2 + (s % 2) consuming stage s into its own accumulator (split K, exact
+// integer partial forces) when BN <= 128 and a row block has three or more
+// loads, warp 2 alone otherwise; warp 2 also loads
 // the resident S of each step; warps 4-11 are the epilogue.  Every stage has one
 // producer and one consumer, so each mbarrier phase is awaited in order.
 // Every wait is bounded; a wait that gives up raises the error word and the
@@ -43,7 +44,7 @@ namespace {
 constexpr int kTM = 128;                 // spins per row block
 constexpr int kMaxBN = 256;              // replica columns per instance
 constexpr int kMaxS = 128 * 1024;        // resident spin operand bytes (BN * Np)
-constexpr int kGStages = 2;
+constexpr int kGStages = 3;             // stage s is filled by producer s % 2
 constexpr int kGStageA = 2 * kTM * 128;  // two K chunks of J, 32 KB
 constexpr int kGEpiWarps = 8;
 constexpr int kGEpiThreads = 32 * kGEpiWarps;
@@ -61,7 +62,7 @@ struct __align__(8) GShared {
     int abort;
     int inst;               // current instance index (-1: none left)
     int esum[kMaxBN];       // per-replica sum of s_i f_i of the step (exact)
-    int improved[kMaxBN];
+    uint8_t improved[kMaxBN];
 };
 
 constexpr size_t kGSmem = 1024 + (size_t)kMaxS + (size_t)kGStages * kGStageA + sizeof(GShared);
@@ -172,7 +173,9 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
         // K is split over the two MMA warps (each into its own accumulator,
         // the loads of stage p to warp p) when the accumulators fit and every
         // row block has at least two loads
-        const bool split = a.allow_split && BN <= 128 && npairs >= 2;
+        // (every kGStages consecutive loads include stages of both parities,
+        // so each MMA warp gets at least one load of every row block)
+        const bool split = a.allow_split && BN <= 128 && npairs >= kGStages;
 
         if (warp < 2) {
             // --------------------------------------------------- J producers
@@ -185,9 +188,9 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                 for (int k = 0; k < passes && !fail; ++k)
                     for (int mb = 0; mb < nblk && !fail; ++mb)
                         for (int p = 0; p < npairs; ++p, ++g) {
-                            if ((int)(g & 1u) != pw)
+                            const int s = (int)(g % kGStages);
+                            if ((s & 1) != pw)
                                 continue;
-                            const int s = pw;
                             const uint32_t ph = (g / kGStages) & 1u;
                             if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err)) {
                                 fail = true;
@@ -239,7 +242,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     int mine = 0;
                     for (int p = 0; p < npairs; ++p, ++g) {
                         const int s = (int)(g % kGStages);
-                        if (split ? s != pw : pw != 0)
+                        if (split ? (s & 1) != pw : pw != 0)
                             continue;
                         const uint32_t ph = (g / kGStages) & 1u;
                         if (!warp_wait(&sh->full[s], ph, &sh->abort, a.err)) {
