@@ -94,3 +94,25 @@ def test_no_cpu_fallback_without_a_device():
     with pytest.raises(hsb.HsbError) as e:
         hsb.create(synth.sk_pm1(8, 0))
     assert e.value.status == 8  # HSB_E_NODEVICE
+
+
+def test_header_is_plain_c_and_matches_the_binding_layout(tmp_path):
+    # include/hsb.h is a C ABI: it compiles as strict C11, and its parameter struct
+    # has the size and offsets the ctypes mirror uses
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    checks = [f"_Static_assert(sizeof(hsb_params) == {C.sizeof(hsb.Params)}, \"size\");"]
+    for name, _ in hsb.Params._fields_:
+        off = getattr(hsb.Params, name).offset
+        checks.append(f"_Static_assert(offsetof(hsb_params, {name}) == {off}, \"{name}\");")
+    src = tmp_path / "abi_check.c"
+    src.write_text("#include <stddef.h>\n#include \"hsb.h\"\n" + "\n".join(checks) +
+                   "\nint main(void) { return 0; }\n")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-pedantic", "-I", inc, "-c",
+                        str(src), "-o", str(tmp_path / "abi_check.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
