@@ -139,3 +139,26 @@ def test_nose_hoover_argument_checks():
         # AUTO picks plain FP32 for general couplings under the thermostat
         s.run(hsb.params("ballistic", "auto", **nh), 128, 10, 0)
         assert s.get_xi(128).shape == (128,)
+
+
+def test_nose_hoover_full_size_workload_sampled_replicas():
+    # the benchmarked Nose-Hoover workload (N = 2000, R = 1024, 2000 steps,
+    # T = 0.3, M = 40000, xi0 = -0.05, persistent FP8) in its launch
+    # configuration: replicas 0 and 1023 equal the oracle bit for bit,
+    # spins, best energy, final state and xi
+    J = synth.sk_pm1(2000, 1)
+    R, steps, seed = 1024, 2000, 1000
+    nh = dict(nh_T=0.3, nh_M=40000.0, nh_xi0=-0.05)
+    p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, eval_every=100,
+                   thermostat="nose_hoover", **nh)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, steps, seed)
+        x, y = s.get_state(R)
+        xi = s.get_xi(R)
+    rows = [0, 1023]
+    ref = oracle.run(J, _nh_oracle(J, 1, 0.7, 1.1, 100, **nh), steps, seed, rows, "f32")
+    np.testing.assert_array_equal(spins[rows], ref["best_s"])
+    np.testing.assert_array_equal(energy[rows], ref["best_e"])
+    np.testing.assert_array_equal(x[rows], ref["x"])
+    np.testing.assert_array_equal(y[rows], ref["y"])
+    np.testing.assert_array_equal(xi[rows], ref["xi"])
