@@ -335,3 +335,30 @@ def test_auto_schedule_falls_back_when_the_persistent_grid_does_not_fit():
     rows = [0, 1, 2047, 4095]
     ref = oracle.run(J, _oparams(J, 1, 0.7, 1.1, 0.06, ev), steps, seed, rows, "f32")
     _assert_same(x, y, spins, energy, ref, rows=rows)
+
+
+def test_set_couplings_across_coupling_classes():
+    # one handle serving instances of different kinds: +/-1 (FP8), Gaussian
+    # (BF16x3 and FP32, exact fixed-point final energies), +/-1 again; every
+    # run equals a run on a fresh handle of the same instance
+    n, R, steps, seed = 256, 128, 60, 3
+    Ja, Jg, Jb = synth.sk_pm1(n, 4), synth.sk_gauss(n, 4), synth.sk_pm1(n, 5)
+    pd = hsb.params("discrete", "auto", c1=0.7, dt=1.1, gamma=0.06, eval_every=20)
+    pb = hsb.params("ballistic", "auto", c1=0.9, dt=1.1, gamma=0.5, eval_every=20)
+    pf = hsb.params("ballistic", "fp32", c1=0.9, dt=1.1, gamma=0.5, eval_every=20)
+    seq = [(Ja, pd), (Jg, pb), (Jg, pf), (Jb, pd), (Ja, pd)]
+    got = []
+    with hsb.Solver(Ja) as s:
+        for J, p in seq:
+            s.set_couplings(J)
+            got.append(s.run(p, R, steps, seed))
+    for (J, p), (sp, en) in zip(seq, got):
+        with hsb.Solver(J) as t:
+            sp2, en2 = t.run(p, R, steps, seed)
+        np.testing.assert_array_equal(sp, sp2)
+        np.testing.assert_array_equal(en, en2)
+    # the cut values follow the current instance's sum of couplings
+    with hsb.Solver(Ja) as s:
+        s.set_couplings(Jg)
+        c = s.cut_values(np.array([-10.0]))
+    assert c[0] == pytest.approx(5.0 - 0.25 * float(Jg.astype(np.float64).sum()), rel=1e-15)
