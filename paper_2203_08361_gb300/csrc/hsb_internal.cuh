@@ -65,7 +65,7 @@ cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool e
 // Nose-Hoover thermostat (Eqs. eq_NH1, eq_NH), one variable xi_r per replica
 // (binary64) and the friction factor g_r = fl32(-xi_r dt) that replaces the
 // constant heating factor gamma dt in the next step (gvec of the step kernels).
-// init: xi_r = xi0, g_r = fl32(-xi0 dt) for r < R; xi_r = g_r = 0 up to Rp.
+// init: xi_r = xi0, g_r = fl32(-xi0 dt) for every r < Rp (padding included).
 cudaError_t launch_nh_init(cudaStream_t st, int R, int Rp, double xi0, double dt, double *xi,
                            float *gvec);
 // update after a step: S_r = sum_{i<N} y_i^2 (y_i rounded to a multiple of

@@ -254,15 +254,18 @@ cudaError_t launch_simt_step(cudaStream_t st, int form, bool energy_only, bool e
 // squares are added exactly in 128 bits, and 2^-48 times the total is rounded
 // once to binary64.
 
+// Padded replicas (R <= r < Rp) start from xi0 too: they carry real initial
+// states, and on the persistent kernel they run the same thermostat, so they
+// stay as stable as the reported replicas.
 __global__ void nh_init_kernel(int R, int Rp, double xi0, double dt, double *__restrict__ xi,
                                float *__restrict__ gvec)
 {
+    (void)R;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= Rp)
         return;
-    const bool live = r < R;
-    xi[r] = live ? xi0 : 0.0;
-    gvec[r] = live ? __double2float_rn(__dmul_rn(-xi0, dt)) : 0.f;
+    xi[r] = xi0;
+    gvec[r] = __double2float_rn(__dmul_rn(-xi0, dt));
 }
 
 namespace {
