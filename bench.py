@@ -114,9 +114,16 @@ def cpu_baseline(target_s: float = 20.0):
     want = target_s * rate / (WORKLOAD["N"] * steps)
     reps = int(min(WORKLOAD["R"], max(cores, round(want / cores) * cores)))
     rate, t = oracle_sample(reps, steps, cores)
+    # the same oracle on one thread (one replica, steps for about 3 s): the
+    # per-core rate, beside the all-cores figure
+    r1, _ = oracle_sample(1, 10, 1)
+    s1 = int(max(10, min(steps, 3.0 * r1 / WORKLOAD["N"])))
+    r1, t1 = oracle_sample(1, s1, 1)
     return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} replicas x {steps} of the {WORKLOAD['sb_steps']} steps "
-                      f"(N={WORKLOAD['N']}), binary32 oracle, {cores} threads, {t:.1f} s"}
+                      f"(N={WORKLOAD['N']}), binary32 oracle, {cores} threads, {t:.1f} s",
+            "single_thread": {"value": r1, "unit": UNIT, "cores": 1,
+                              "sample": f"1 replica x {s1} steps, {t1:.1f} s"}}
 
 
 def run_reference(args):
