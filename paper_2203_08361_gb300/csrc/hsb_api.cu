@@ -964,7 +964,10 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
         h->last_x = 0;
         h->state_par = c.steps & 1;
         h->have_state = true;
-        h->launches = 3 + (c.thermo ? 1 : 0) + (c.trace_every > 0 ? 1 : 0);
+        // init, (xi init), the step loop, best selection, trace entries in
+        // launches of at most 65535
+        const long long ntr = c.trace_every > 0 ? (c.steps - 1) / c.trace_every + 1 : 0;
+        h->launches = 3 + (c.thermo ? 1 : 0) + (ntr + 65534) / 65535;
         h->have_xi = c.thermo != 0;
         return HSB_OK;
     }

@@ -514,11 +514,19 @@ cudaError_t launch_trace_reduce_many(cudaStream_t st, const float *Epart, const 
                                      int nblk, int N, int R, int Rp, int entries, double *scratch,
                                      unsigned *tickets, double *out)
 {
-    if (entries < 1)
-        return cudaSuccess;
-    const dim3 grid((R + 31) / 32, entries);
-    trace_parts_kernel<<<grid, 256, 0, st>>>(Epart, Tpart, nblk, N, R, Rp, scratch, tickets, out);
-    return cudaGetLastError();
+    // at most 65535 entries per launch (the grid's y extent)
+    const int nparts = (R + 31) / 32;
+    for (int m0 = 0; m0 < entries; m0 += 65535) {
+        const int cnt = entries - m0 < 65535 ? entries - m0 : 65535;
+        const size_t off = (size_t)m0 * nblk * Rp;
+        trace_parts_kernel<<<dim3(nparts, cnt), 256, 0, st>>>(
+            Epart + off, Tpart + off, nblk, N, R, Rp, scratch + (size_t)m0 * 3 * nparts,
+            tickets + m0, out + (size_t)m0 * 3);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float *Tpart, int nblk,
