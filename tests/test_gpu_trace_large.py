@@ -108,3 +108,23 @@ def test_persistent_trace_every_step_full_size_sampled():
     np.testing.assert_array_equal(tr2[:, 0], ref["trace_e"].min(axis=0))
     np.testing.assert_array_equal(tr2[:, 1], ref["trace_e"].mean(axis=0))
     np.testing.assert_allclose(tr2[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6)
+
+
+def test_persistent_trace_beyond_one_launch_of_entries():
+    # more traced steps than one launch of the batched reduction takes
+    # (65535 entries): N = 128, two replicas, 70000 steps, trace every step
+    n, R, steps, seed = 128, 2, 70000, 8
+    J = synth.sk_pm1(n, 9)
+    p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=0, trace_every=1,
+                   schedule="persistent")
+    with hsb.Solver(J) as s:
+        s.run(p, R, steps, seed)
+        tr = s.get_trace()
+        assert s.run_stats() == 3 + 2
+    ref = _oracle_trace(J, 0.7, steps, seed, range(R), 1, eval_every=0)
+    assert tr.shape == (steps, 3)
+    np.testing.assert_array_equal(tr[:, 0], ref["trace_e"].min(axis=0))
+    np.testing.assert_array_equal(tr[:, 1], ref["trace_e"].mean(axis=0))
+    # late in this long run the momenta decay below 2^-63, where their binary32
+    # squares underflow (the oracle squares in binary64): an absolute floor
+    np.testing.assert_allclose(tr[:, 2], ref["trace_t"].mean(axis=0), rtol=1e-6, atol=1e-30)
