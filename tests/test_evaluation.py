@@ -46,3 +46,53 @@ def test_grid_points_cover_the_product_last_name_fastest():
     assert ev.grid_points({"c1": [0.7]}) == [{"c1": 0.7}]
     with pytest.raises(ValueError):
         ev.grid_points({"dt": []})
+
+
+class _OracleSolver:
+    """Test double of hsb.Solver for the harness's host logic: runs the
+    binary32 oracle (only tests may) and the cut identity of Eq. (eq_Cut)."""
+
+    def __init__(self, J):
+        import oracle
+        self.oracle = oracle
+        self.J = np.asarray(J, np.float32)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+    def run(self, p, R, steps, seed):
+        c0 = self.oracle.c0_from_c1(self.J, p.c1)
+        op = self.oracle.make_params(p.form, c0, p.dt, p.gamma, eval_every=p.eval_every)
+        out = self.oracle.run(self.J, op, steps, seed, range(R), "f32")
+        return out["best_s"], out["best_e"]
+
+    def cut_values(self, energy):
+        return -0.5 * np.asarray(energy) - 0.25 * float(self.J.astype(np.float64).sum())
+
+
+def test_evaluate_and_sweep_statistics_on_the_host(monkeypatch):
+    import oracle
+    import synth
+    monkeypatch.setattr(ev, "Solver", _OracleSolver)
+    J = synth.sk_pm1(12, 3)
+    e0, s0 = oracle.brute_force(J)
+    stats = ev.evaluate(J, "discrete", [10, 40], 24, 5, e0, prec="fp32", c1=0.7, dt=1.1,
+                        gamma=0.06, eval_every=10)
+    for st in stats:
+        c0 = oracle.c0_from_c1(J, 0.7)
+        ref = oracle.run(J, oracle.make_params(1, c0, 1.1, 0.06, eval_every=10), st.steps, 5,
+                         range(24), "f32")
+        cuts = np.array([oracle.cut_value(J, s) for s in ref["best_s"]])
+        assert st.trials == 24
+        assert st.mean_cut == pytest.approx(cuts.mean(), rel=1e-12)
+        assert st.max_cut == pytest.approx(cuts.max(), rel=1e-12)
+        assert st.min_energy == ref["best_e"].min()
+        assert st.p == ev.success_probability(ref["best_e"], e0)
+        assert st.step_to_solution == ev.step_to_solution(st.p, st.steps)
+    pts = ev.sweep(J, "discrete", {"gamma": [0.0, 0.06], "dt": [0.9]}, 20, 16, 2, e0,
+                   prec="fp32", c1=0.7, eval_every=10)
+    assert [pt.params for pt in pts] == [{"gamma": 0.0, "dt": 0.9}, {"gamma": 0.06, "dt": 0.9}]
+    assert all(0.0 <= pt.stats.p <= 1.0 for pt in pts)
