@@ -2,8 +2,11 @@
 //
 // Host side of the heated SB run (Kanao & Goto, arXiv 2203.08361): argument
 // validation, coupling conversion, device buffers, the per-run constants
-// (Methods; Results "SB with thermal fluctuation"), and the step loop, which
-// is captured once into a CUDA graph per run shape and replayed.
+// (Methods; Results "SB with thermal fluctuation"), and the step loop: one
+// persistent launch when its grid fits (FP8, split BF16), otherwise one launch
+// per step captured once into a CUDA graph per run shape and replayed; the
+// batch of instances with its autotuner; the Nose-Hoover thermostat and the
+// per-step trace around either form.
 #include <cuda_runtime.h>
 #include <math.h>
 

@@ -1,10 +1,13 @@
 // hsb_simt.cu -- CUDA-core kernels of libhsb: seeded initial state, the plain
 // FP32 step (the comparison form), energy evaluation, best tracking, the
-// binary64 final energy and operand conversions.
+// Nose-Hoover xi update, the per-step trace reductions, the final energies of
+// general couplings (exact fixed point, and binary64 for large N) and operand
+// conversions.
 //
 // Paper: Kanao & Goto, arXiv 2203.08361.  Methods, Eqs. (eq_SyEuY),
 // (eq_SyEuX), (eq_WallX), (eq_WallY), (eq_EuHeat); forces Eqs. (eq_fb),
-// (eq_fd); energy Eq. (eq_Ising).
+// (eq_fd); energy Eq. (eq_Ising); instantaneous temperature Eq. (eq_TInst);
+// Nose-Hoover Eqs. (eq_NH1), (eq_NH).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
