@@ -1,6 +1,7 @@
 // hsb_tc.cu -- one-step tensor-core (tcgen05) kernel of libhsb for sm_103a,
 // used when the persistent step loop does not fit (large N, many tiles) and
-// for per-step traces.
+// on the one-launch-per-step schedule (with the per-step trace and the
+// Nose-Hoover friction factor per replica where asked).
 //
 // Discrete heated SB with couplings in {-1, 0, +1} (HdSB; Kanao & Goto,
 // arXiv 2203.08361, Eq. (eq_fd) and Methods): the force F = J sgn(X) of all
