@@ -46,3 +46,21 @@ def test_dram_record_is_used_only_for_the_sources_it_was_taken_from(tmp_path, mo
     assert bench._traffic_for_current_kernel() is None
     monkeypatch.setattr(bench, "TRAFFIC_FILE", str(tmp_path / "missing.json"))
     assert bench._traffic_for_current_kernel() is None
+
+
+def test_every_workload_definition_builds_valid_parameters():
+    import paper_2203_08361_gb300 as hsb
+    need = {"name", "kind", "R", "sb_steps", "form", "prec", "c1", "dt", "gamma",
+            "eval_every", "trace_every", "peak", "dtype"}
+    for key, w in bench.OTHER.items():
+        assert need <= set(w), key
+        assert w["peak"] in ("fp8", "bf16") and w["kind"] in ("single", "batch")
+        p = hsb.params(w["form"], w["prec"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
+                       eval_every=w["eval_every"], trace_every=w["trace_every"],
+                       **w.get("nh", {}))
+        assert p.form == hsb.FORM[w["form"]] and p.prec == hsb.PREC[w["prec"]]
+        if "nh" in w:
+            assert p.thermostat == hsb.HSB_HEAT_NOSE_HOOVER and p.nh_M > 0
+    # the headline workload is the one named by the metric
+    assert bench.WORKLOAD["N"] == 2000 and bench.WORKLOAD["R"] == 1024
+    assert bench.WORKLOAD["sb_steps"] == 2000 and bench.WORKLOAD["prec"] == "fp8"
