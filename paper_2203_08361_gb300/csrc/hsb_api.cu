@@ -617,6 +617,8 @@ hsb_status validate_couplings(const float *J, int N, int *pm1_out, double *sum2_
             maxabs = std::max(maxabs, std::fabs(d));
         }
     }
+    if (!std::isfinite(sum2))
+        return set_error(HSB_E_INVAL, "J has an infinite entry");
     if (!(sum2 > 0.0))
         return set_error(HSB_E_INVAL, "J is all zero");
     *pm1_out = pm1 ? 1 : 0;

@@ -58,6 +58,11 @@ def test_create_validates_couplings_on_the_host():
     with pytest.raises(hsb.HsbError) as e:
         hsb.create(np.zeros((5, 5), np.float32))
     assert e.value.status == 1  # all zero
+    bad = synth.sk_gauss(8, 0)
+    bad[2, 5] = bad[5, 2] = np.inf  # symmetric, but not a finite coupling
+    with pytest.raises(hsb.HsbError) as e:
+        hsb.create(bad)
+    assert e.value.status == 1 and "infinite" in str(e.value)
 
 
 @pytest.mark.parametrize("n", [63, 64, 65, 200, 301])
