@@ -149,7 +149,9 @@ HSB_API int hsb_version(void);
 
 /* Creates a handle for the couplings J (host, float32, N x N, row-major),
  * copying them to the current CUDA device.  J must be exactly symmetric with a
- * zero diagonal (Eq. (eq_Ising)); otherwise HSB_E_ASYM / HSB_E_DIAG.  N >= 2.
+ * zero diagonal (Eq. (eq_Ising)); otherwise HSB_E_ASYM / HSB_E_DIAG (a NaN
+ * entry fails the symmetry test).  An infinite entry or an all-zero J gives
+ * HSB_E_INVAL.  N >= 2.
  * Work is queued on a private stream of the handle until hsb_set_stream(). */
 HSB_API hsb_status hsb_create(const float *J, int N, hsb_handle *out);
 
