@@ -79,7 +79,9 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        # HSB_ORACLE_LIB names another compiled copy of this source to load
+        # instead (the planted-mistake test runs the pins against such copies).
+        lib = C.CDLL(os.environ.get("HSB_ORACLE_LIB") or build())
         P = C.c_void_p
         lib.oracle_splitmix64.restype = C.c_uint64
         lib.oracle_splitmix64.argtypes = [C.c_uint64, C.c_uint64]

@@ -378,6 +378,25 @@ def test_best_tracking_and_eval_cadence():
     np.testing.assert_array_equal(last["best_e"], tr[:, -1])
 
 
+def test_best_state_ties_keep_the_earliest_evaluation():
+    # J = 0: every evaluation has E = 0 while the spins keep turning (the
+    # pumped oscillator of each x_i), so a new best needing a strictly lower
+    # energy keeps the spins of the first evaluation step t = eval_every.
+    n, steps, ev, a0, dt, c0 = 16, 300, 50, 1.0, 0.5, 0.3
+    J = np.zeros((n, n), np.float32)
+    out = oracle.run(J, oracle.make_params(1, c0, dt, 0.0, a0=a0, eval_every=ev), steps, 5,
+                     range(4), "f64")
+    x, y = oracle.init_values(5, 0, range(4), n, 1.0)
+    for k in range(ev):
+        x, y, _ = oracle.step(J, x, y, 1, oracle.pump_factor(a0, k, steps), c0, dt, a0 * dt,
+                              0.0, "f64")
+    s_first = np.where(x >= 0, 1, -1).astype(np.int8)
+    s_last = np.where(out["x"] >= 0, 1, -1).astype(np.int8)
+    assert np.any(s_first != s_last)
+    np.testing.assert_array_equal(out["best_e"], 0.0)
+    np.testing.assert_array_equal(out["best_s"], s_first)
+
+
 @pytest.mark.parametrize("form,gamma", [(1, 0.06), (0, 0.5)])
 def test_small_instances_reach_brute_force_ground_state(form, gamma):
     n = 14
