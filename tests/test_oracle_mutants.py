@@ -81,6 +81,9 @@ MUTANTS = [
      "xi = xi + nh_h * (s2 - nh_NT);", "xi = xi - nh_h * (s2 - nh_NT);"),
     ("friction with the wrong sign", IMPL,
      "const REAL gk = (REAL)(-xi * p->dt);", "const REAL gk = (REAL)(xi * p->dt);"),
+    ("xi reads the momenta before the update", IMPL,
+     "SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);\n                    /* xi_{k+1} from the updated momenta, Eq. (eq_NH) */\n                    const double s2 = SFX(oracle_kinetic_sum)(y, N);",
+     "const double s2 = SFX(oracle_kinetic_sum)(y, N);\n                    SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);"),
     ("N dropped from N T", IMPL,
      "const double nh_NT = (double)N * p->nh_T;", "const double nh_NT = p->nh_T;"),
     # ---- trace, Eq. (eq_TInst), and the best-state bookkeeping

@@ -518,6 +518,27 @@ def test_nose_hoover_force_free_invariant_and_mean_temperature():
     assert abs(long["trace_t"][0].mean() - T) < 0.01 * T
 
 
+@pytest.mark.parametrize("xi0", [0.25, -0.25])
+def test_nose_hoover_xi_reads_the_updated_momenta(xi0):
+    # Discrete Eq. (eq_NH): xi_{k+1} takes S = sum_i y_i^2 at t_{k+1}, after
+    # the momentum update.  Force-free and unpumped (J = 0, a0 = 0), one step
+    # only scales y by 1 - xi0 dt.  With N T = S(t_0), a xi read from the old
+    # momenta would not move; read from the new ones it moves against xi0 by
+    # (dt / M) ((1 - xi0 dt)^2 - 1) S(t_0), up to the 2^-24 quantisation of S.
+    n, dt, M = 64, 0.5, 8.0
+    J = np.zeros((n, n), np.float32)
+    x0, y0 = oracle.init_values(11, 0, [0], n, 1.0)
+    S0 = oracle.kinetic_sum(y0[0], "f64")
+    prm = oracle.make_params(0, 0.0, dt, 0.0, a0=0.0, eval_every=0, nose_hoover=True,
+                             nh_T=S0 / n, nh_M=M, nh_xi0=xi0)
+    out = oracle.run(J, prm, 1, 11, [0], "f64")
+    np.testing.assert_array_equal(out["x"][0], x0[0])
+    np.testing.assert_array_equal(out["y"][0], y0[0].astype(np.float64) * (1.0 - xi0 * dt))
+    want = xi0 + dt / M * ((1.0 - xi0 * dt) ** 2 - 1.0) * S0
+    assert abs(want - xi0) > 0.1
+    assert out["xi"][0] == pytest.approx(want, abs=1e-6)
+
+
 def test_nose_hoover_kinetic_sum_is_the_exact_fixed_point_sum():
     # S of Eq. (eq_NH) as formed by the update: each y_i rounded to the
     # nearest multiple of 2^-24, the squares summed exactly, 2^-48 times the
