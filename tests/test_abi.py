@@ -114,6 +114,13 @@ def test_header_is_plain_c_and_matches_the_binding_layout(tmp_path):
     for name, _ in hsb.Params._fields_:
         off = getattr(hsb.Params, name).offset
         checks.append(f"_Static_assert(offsetof(hsb_params, {name}) == {off}, \"{name}\");")
+    # and its enumerators have the values the binding passes and decodes
+    consts = {name: code for code, name in hsb.STATUS.items()}
+    consts.update({n: getattr(hsb, n) for n in (
+        "HSB_BALLISTIC", "HSB_DISCRETE", "HSB_PREC_AUTO", "HSB_PREC_FP32", "HSB_PREC_FP8",
+        "HSB_PREC_BF16X3", "HSB_HEAT_CONSTANT", "HSB_HEAT_NOSE_HOOVER")})
+    for name, v in consts.items():
+        checks.append(f"_Static_assert({name} == {v}, \"{name}\");")
     src = tmp_path / "abi_check.c"
     src.write_text("#include <stddef.h>\n#include \"hsb.h\"\n" + "\n".join(checks) +
                    "\nint main(void) { return 0; }\n")
