@@ -128,3 +128,54 @@ def test_header_is_plain_c_and_matches_the_binding_layout(tmp_path):
                         str(src), "-o", str(tmp_path / "abi_check.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_a_c_program_links_and_calls_the_library(tmp_path):
+    # A plain C11 client, linked against libhsb.so with nothing else: the
+    # defaults, the host validation with its message, and hsb_create on valid
+    # couplings (HSB_E_NODEVICE without a device, a handle otherwise).
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    hsb.load()
+    libdir = os.path.dirname(hsb.LIB_PATH)
+    src = tmp_path / "client.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "hsb.h"
+int main(void)
+{
+    hsb_params p;
+    if (hsb_version() != HSB_API_VERSION || hsb_params_default(&p) != HSB_OK)
+        return 10;
+    if (p.form != HSB_DISCRETE || p.prec != HSB_PREC_AUTO || p.dt != 1.1)
+        return 11;
+    float bad[9] = {0, 1, -1, 1, 0, 1, -1, 2, 0}; /* J[1][2] = 1, J[2][1] = 2 */
+    hsb_handle h = (hsb_handle)&p;
+    if (hsb_create(bad, 3, &h) != HSB_E_ASYM || h != NULL)
+        return 12;
+    printf("asym: %s\n", hsb_last_error());
+    if (hsb_create(bad, 1, &h) != HSB_E_INVAL)
+        return 13;
+    float J[9] = {0, 1, -1, 1, 0, 1, -1, 1, 0};
+    hsb_status s = hsb_create(J, 3, &h);
+    printf("create: %d\n", (int)s);
+    if (s == HSB_OK)
+        hsb_destroy(h);
+    return 0;
+}
+""")
+    exe = tmp_path / "client"
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-pedantic", "-I", inc, str(src),
+                        "-L", libdir, "-lhsb", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert "J[1][2]" in r.stdout
+    torch = pytest.importorskip("torch")
+    want = 0 if torch.cuda.is_available() else 8  # HSB_OK or HSB_E_NODEVICE
+    assert f"create: {want}" in r.stdout
