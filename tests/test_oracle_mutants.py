@@ -48,6 +48,10 @@ MUTANTS = [
     ("ballistic force takes the sign", IMPL,
      "REAL b = form == 1 ? SFX(sgn)(x[j]) : x[j];",
      "REAL b = SFX(sgn)(x[j]);"),
+    ("binary64 force term without the state", IMPL,
+     "REAL t = jv * b;", "REAL t = jv;"),
+    ("integer couplings copied with the wrong sign", IMPL,
+     "Jint[e] = (int8_t)J[e];", "Jint[e] = (int8_t)-J[e];"),
     # ---- symplectic Euler step, Eqs. (eq_SyEuY), (eq_SyEuX)
     ("c0 dropped from the force term", IMPL,
      "REAL u = c0 * f[i];", "REAL u = f[i];"),
@@ -86,9 +90,15 @@ MUTANTS = [
      "const double s2 = SFX(oracle_kinetic_sum)(y, N);\n                    SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);"),
     ("N dropped from N T", IMPL,
      "const double nh_NT = (double)N * p->nh_T;", "const double nh_NT = p->nh_T;"),
+    ("thermostat step M / dt in place of dt / M", IMPL,
+     "const double nh_h = p->dt / p->nh_M;", "const double nh_h = p->nh_M / p->dt;"),
     # ---- trace, Eq. (eq_TInst), and the best-state bookkeeping
     ("instantaneous temperature not divided by N", IMPL,
      "trace_t[at] = t2 / (double)N;", "trace_t[at] = t2;"),
+    ("instantaneous temperature from the positions", IMPL,
+     "t2 += (double)y[i] * (double)y[i];", "t2 += (double)x[i] * (double)x[i];"),
+    ("final step not evaluated", IMPL,
+     "int is_eval = (k == steps) || (", "int is_eval = ("),
     ("best state is the last of equal energies", IMPL,
      "if (e < best) {", "if (e <= best) {"),
     ("evaluation cadence shifted by one step", IMPL,
@@ -112,6 +122,9 @@ MUTANTS = [
      "return a0 - t;", "return t;"),
     ("pump schedule over Ns - 1 steps", MAIN,
      "t = t / (double)steps;", "t = t / (double)(steps - 1);"),
+    ("traced count off by one", MAIN,
+     "return trace_every > 0 ? (steps - 1) / trace_every + 1 : 0;",
+     "return trace_every > 0 ? steps / trace_every : 0;"),
     ("evaluation count off by one", MAIN,
      "return (eval_every > 0 ? (steps - 1) / eval_every : 0) + 1;",
      "return (eval_every > 0 ? steps / eval_every : 0) + 1;"),
@@ -120,6 +133,8 @@ MUTANTS = [
      "z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBULL;"),
     ("x and y streams overlap", MAIN,
      "2u * (uint64_t)i + (uint64_t)(comp & 1)", "(uint64_t)i + (uint64_t)(comp & 1)"),
+    ("initial values over twice the width", MAIN,
+     "(float)(half_width / 16777216.0)", "(float)(half_width / 8388608.0)"),
     ("initial values on the closed interval", MAIN,
      "(float)(2.0 * (double)m + 1.0 - 16777216.0)", "(float)(2.0 * (double)m - 16777216.0)"),
 ]

@@ -440,6 +440,14 @@ def test_trace_energy_and_instantaneous_temperature():
         assert out["trace_e"][r, 0] == oracle.ising_energy(J, s0)
     # evaluations at t = 30, 60, 90 are traced at indices 3, 6, 9
     np.testing.assert_array_equal(out["trace_e"][:, [3, 6, 9]], out["e_trace"][:, :3])
+    # a period that does not divide N_s: the traced times are k = 0, 10, ..., 120 < 125
+    # (the count is checked first: the trace buffers are sized by it)
+    assert oracle.num_traced(125, 10) == len(range(0, 125, 10)) == 13
+    assert oracle.num_traced(120, 10) == 12 and oracle.num_traced(5, 1) == 5
+    prm = oracle.make_params(1, c0, 1.1, 0.06, eval_every=120, trace_every=10)
+    out = oracle.run(J, prm, 125, 4, range(3), "f64", want_trace=True)
+    assert out["trace_e"].shape == (3, 13)
+    np.testing.assert_array_equal(out["trace_e"][:, 12], out["e_trace"][:, 0])
 
 
 # ------------------------------------------------------- Nose-Hoover SB ----
