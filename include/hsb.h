@@ -250,6 +250,15 @@ HSB_API hsb_status hsb_get_xi(hsb_handle h, int R, double *xi);
  * ceil(N / 128), else HSB_E_INVAL. */
 HSB_API hsb_status hsb_debug_drop_publication(hsb_handle h, int row_block);
 
+/* Allocation-failure test hook, process-wide.  From this call on, every device
+ * allocation the library makes of more than `bytes` bytes fails as the
+ * device's allocator does when memory runs out: the call that needed it
+ * returns HSB_E_NOMEM and its handle stays usable (what that call allocated
+ * before the failure is freed by the next run or by hsb_destroy; a failed
+ * hsb_create frees it at once).  0 removes the cap.  Buffers allocated earlier are kept.  Not
+ * thread-safe with respect to calls in flight on other threads. */
+HSB_API hsb_status hsb_debug_alloc_cap(size_t bytes);
+
 /* Replaces the couplings of the handle by a new instance of the same N (host,
  * float32, N x N, row-major; validated as in hsb_create).  Device buffers and
  * captured step loops are kept, so solving many instances of one size pays

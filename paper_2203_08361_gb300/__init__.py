@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libhsb.so")
 
 HSB_BALLISTIC, HSB_DISCRETE = 0, 1
 HSB_PREC_AUTO, HSB_PREC_FP32, HSB_PREC_FP8, HSB_PREC_BF16X3 = 0, 1, 2, 3
-HSB_E_INVAL, HSB_E_TIMEOUT, HSB_E_UNSUPPORTED = 1, 6, 7
+HSB_E_INVAL, HSB_E_NOMEM, HSB_E_TIMEOUT, HSB_E_UNSUPPORTED = 1, 4, 6, 7
 HSB_HEAT_CONSTANT, HSB_HEAT_NOSE_HOOVER = 0, 1
 STATUS = {0: "HSB_OK", 1: "HSB_E_INVAL", 2: "HSB_E_ASYM", 3: "HSB_E_DIAG", 4: "HSB_E_NOMEM",
           5: "HSB_E_CUDA", 6: "HSB_E_TIMEOUT", 7: "HSB_E_UNSUPPORTED", 8: "HSB_E_NODEVICE"}
@@ -35,7 +35,8 @@ EXPORTS = ["hsb_params_default", "hsb_version", "hsb_create", "hsb_destroy", "hs
            "hsb_info", "hsb_run", "hsb_run_device", "hsb_get_state", "hsb_advance",
            "hsb_advance_device", "hsb_set_couplings", "hsb_run_stats", "hsb_synchronize",
            "hsb_run_fp32_noalloc", "hsb_get_trace", "hsb_run_batch", "hsb_cut_values",
-           "hsb_get_xi", "hsb_debug_drop_publication", "hsb_last_error"]
+           "hsb_get_xi", "hsb_debug_drop_publication", "hsb_debug_alloc_cap",
+           "hsb_last_error"]
 
 
 class HsbError(RuntimeError):
@@ -123,6 +124,8 @@ def load():
         lib.hsb_get_xi.argtypes = [H, I, P]
         lib.hsb_debug_drop_publication.restype = I
         lib.hsb_debug_drop_publication.argtypes = [H, I]
+        lib.hsb_debug_alloc_cap.restype = I
+        lib.hsb_debug_alloc_cap.argtypes = [C.c_size_t]
         lib.hsb_run_fp32_noalloc.restype = I
         lib.hsb_run_fp32_noalloc.argtypes = [P, I, C.POINTER(Params), I, I, C.c_uint64, P, P, P]
         _lib = lib
@@ -289,6 +292,12 @@ def debug_drop_publication(h: int, row_block: int) -> None:
     """hsb_debug_drop_publication: the next persistent FP8 run drops one tile's
     publication, so its bounded device waits expire (failure-detection tests)."""
     _check(load().hsb_debug_drop_publication(C.c_void_p(h), int(row_block)))
+
+
+def debug_alloc_cap(nbytes: int) -> None:
+    """hsb_debug_alloc_cap: device allocations of more than nbytes bytes fail
+    with HSB_E_NOMEM from now on (process-wide; 0 removes the cap)."""
+    _check(load().hsb_debug_alloc_cap(int(nbytes)))
 
 
 def run_stats(h: int) -> int:

@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <map>
 #include <mutex>
 #include <string>
@@ -49,6 +50,28 @@ hsb_status cuda_error(cudaError_t e, const char *what)
     if (e == cudaErrorMemoryAllocation)
         return set_error(HSB_E_NOMEM, "%s: %s", what, cudaGetErrorString(e));
     return set_error(HSB_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Allocation-failure test hook (hsb_debug_alloc_cap): a device allocation of
+// more than this many bytes fails as the device's own allocator does when it
+// is out of memory; 0 = no cap.  Every device allocation of the library goes
+// through dev_alloc.
+std::atomic<size_t> g_alloc_cap{0};
+
+cudaError_t dev_alloc(void **ptr, size_t bytes)
+{
+    const size_t cap = g_alloc_cap.load(std::memory_order_relaxed);
+    if (cap != 0 && bytes > cap) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+
+template <typename T>
+cudaError_t dev_alloc(T **ptr, size_t bytes)
+{
+    return dev_alloc(reinterpret_cast<void **>(ptr), bytes);
 }
 
 #define CK(call, what)                                   \
@@ -227,22 +250,22 @@ hsb_status ensure_buffers(hsb_ctx *h, int Rp, int R)
         return HSB_OK;
     free_run_buffers(h);
     const size_t elems = (size_t)Rp * h->Np;
-    CK(cudaMalloc(&h->X[0], elems * sizeof(float)), "cudaMalloc X");
-    CK(cudaMalloc(&h->X[1], elems * sizeof(float)), "cudaMalloc X");
-    CK(cudaMalloc(&h->Y, elems * sizeof(float)), "cudaMalloc Y");
-    CK(cudaMalloc(&h->S8[0], elems), "cudaMalloc S8");
-    CK(cudaMalloc(&h->S8[1], elems), "cudaMalloc S8");
-    CK(cudaMalloc(&h->Epart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Epart");
-    CK(cudaMalloc(&h->Tpart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Tpart");
-    CK(cudaMalloc(&h->Ebest, (size_t)Rp * sizeof(double)), "cudaMalloc Ebest");
-    CK(cudaMalloc(&h->Efinal, (size_t)Rp * sizeof(double)), "cudaMalloc Efinal");
-    CK(cudaMalloc(&h->Efpart, final_energy_part_doubles(Rp) * sizeof(double)),
+    CK(dev_alloc(&h->X[0], elems * sizeof(float)), "cudaMalloc X");
+    CK(dev_alloc(&h->X[1], elems * sizeof(float)), "cudaMalloc X");
+    CK(dev_alloc(&h->Y, elems * sizeof(float)), "cudaMalloc Y");
+    CK(dev_alloc(&h->S8[0], elems), "cudaMalloc S8");
+    CK(dev_alloc(&h->S8[1], elems), "cudaMalloc S8");
+    CK(dev_alloc(&h->Epart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Epart");
+    CK(dev_alloc(&h->Tpart, (size_t)(h->Np / kTileM) * Rp * sizeof(float)), "cudaMalloc Tpart");
+    CK(dev_alloc(&h->Ebest, (size_t)Rp * sizeof(double)), "cudaMalloc Ebest");
+    CK(dev_alloc(&h->Efinal, (size_t)Rp * sizeof(double)), "cudaMalloc Efinal");
+    CK(dev_alloc(&h->Efpart, final_energy_part_doubles(Rp) * sizeof(double)),
        "cudaMalloc Efpart");
-    CK(cudaMalloc(&h->trace_ticket, sizeof(unsigned)), "cudaMalloc trace ticket");
+    CK(dev_alloc(&h->trace_ticket, sizeof(unsigned)), "cudaMalloc trace ticket");
     CK(cudaMemset(h->trace_ticket, 0, sizeof(unsigned)), "cudaMemset trace ticket");
-    CK(cudaMalloc(&h->xi, (size_t)Rp * sizeof(double)), "cudaMalloc xi");
-    CK(cudaMalloc(&h->gvec, (size_t)Rp * sizeof(float)), "cudaMalloc gvec");
-    CK(cudaMalloc(&h->Sbest, (size_t)Rp * h->N), "cudaMalloc Sbest");
+    CK(dev_alloc(&h->xi, (size_t)Rp * sizeof(double)), "cudaMalloc xi");
+    CK(dev_alloc(&h->gvec, (size_t)Rp * sizeof(float)), "cudaMalloc gvec");
+    CK(dev_alloc(&h->Sbest, (size_t)Rp * h->N), "cudaMalloc Sbest");
     h->Rcap = Rp;
     h->buffers_gen++;
     return HSB_OK;
@@ -251,7 +274,7 @@ hsb_status ensure_buffers(hsb_ctx *h, int Rp, int R)
 hsb_status ensure_fp8(hsb_ctx *h)
 {
     if (!h->J8) {
-        CK(cudaMalloc(&h->J8, (size_t)h->Np * h->Np), "cudaMalloc J8");
+        CK(dev_alloc(&h->J8, (size_t)h->Np * h->Np), "cudaMalloc J8");
         CK(launch_j_to_fp8(h->work, h->J32, h->Np, h->J8), "j_to_fp8");
     }
     if (!h->plan) {
@@ -265,12 +288,12 @@ hsb_status ensure_bf16(hsb_ctx *h)
 {
     const size_t np = (size_t)h->Np;
     if (!h->Jcat) {
-        CK(cudaMalloc(&h->Jcat, np * 2 * np * 2), "cudaMalloc Jcat");
+        CK(dev_alloc(&h->Jcat, np * 2 * np * 2), "cudaMalloc Jcat");
         CK(launch_split_couplings(h->work, h->J32, h->Np, h->Jcat), "split couplings");
     }
     for (int b = 0; b < 2; ++b)
         if (!h->Xcat[b]) {
-            CK(cudaMalloc(&h->Xcat[b], (size_t)h->Rcap * 2 * np * 2), "cudaMalloc Xcat");
+            CK(dev_alloc(&h->Xcat[b], (size_t)h->Rcap * 2 * np * 2), "cudaMalloc Xcat");
             CK(cudaMemsetAsync(h->Xcat[b], 0, (size_t)h->Rcap * 2 * np * 2, h->work),
                "memset Xcat");
         }
@@ -668,7 +691,7 @@ hsb_status grow(T **ptr, size_t *cap, size_t n, const char *what)
     cudaFree(*ptr);
     *ptr = nullptr;
     *cap = 0;
-    CK(cudaMalloc(ptr, n * sizeof(T)), what);
+    CK(dev_alloc(ptr, n * sizeof(T)), what);
     *cap = n;
     return HSB_OK;
 }
@@ -682,7 +705,7 @@ hsb_status ensure_pk(hsb_ctx *h, const RunCfg &c)
         cudaFree(h->pk_dev);
         h->pk_dev = nullptr;
         h->pk_cap = 0;
-        CK(cudaMalloc(&h->pk_dev, (size_t)c.steps * sizeof(float)), "cudaMalloc pk");
+        CK(dev_alloc(&h->pk_dev, (size_t)c.steps * sizeof(float)), "cudaMalloc pk");
         h->pk_cap = c.steps;
     }
     CK(cudaMemcpyAsync(h->pk_dev, c.pk.data(), (size_t)c.steps * sizeof(float),
@@ -933,7 +956,7 @@ hsb_status ensure_trace(hsb_ctx *h, const RunCfg &c)
         cudaFree(h->trace);
         h->trace = nullptr;
         h->trace_cap = 0;
-        CK(cudaMalloc(&h->trace, need * sizeof(double)), "cudaMalloc trace");
+        CK(dev_alloc(&h->trace, need * sizeof(double)), "cudaMalloc trace");
         h->trace_cap = need;
         h->graph_valid = false;  // the captured loop holds the trace pointer
     }
@@ -1208,7 +1231,7 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
             break;
         }
         h->work = h->own;
-        e = cudaMalloc(&h->err, sizeof(int));
+        e = dev_alloc(&h->err, sizeof(int));
         if (e == cudaSuccess)
             e = cudaMemsetAsync(h->err, 0, sizeof(int), h->work);
         if (e != cudaSuccess) {
@@ -1216,7 +1239,7 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
             break;
         }
         const size_t np = (size_t)h->Np;
-        e = cudaMalloc(&h->J32, np * np * sizeof(float));
+        e = dev_alloc(&h->J32, np * np * sizeof(float));
         if (e != cudaSuccess) {
             s = cuda_error(e, "cudaMalloc J");
             break;
@@ -1624,6 +1647,12 @@ hsb_status hsb_debug_drop_publication(hsb_handle h, int row_block)
     return HSB_OK;
 }
 
+hsb_status hsb_debug_alloc_cap(size_t bytes)
+{
+    g_alloc_cap.store(bytes, std::memory_order_relaxed);
+    return HSB_OK;
+}
+
 hsb_status hsb_run_stats(hsb_handle h, long long *kernel_launches)
 {
     if (!h)
@@ -1714,11 +1743,11 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
     float *d_pk = nullptr;
     cudaStream_t st = hs[0]->work;
     hsb_status status = HSB_OK;
-    cudaError_t e = cudaMalloc(&d_insts, sizeof(BatchInst) * (size_t)count);
+    cudaError_t e = dev_alloc(&d_insts, sizeof(BatchInst) * (size_t)count);
     if (e == cudaSuccess)
-        e = cudaMalloc(&d_queue, sizeof(unsigned int));
+        e = dev_alloc(&d_queue, sizeof(unsigned int));
     if (e == cudaSuccess)
-        e = cudaMalloc(&d_pk, sizeof(float) * (size_t)steps);
+        e = dev_alloc(&d_pk, sizeof(float) * (size_t)steps);
     if (e == cudaSuccess)
         e = cudaMemcpy(d_insts, sorted.data(), sizeof(BatchInst) * (size_t)count,
                        cudaMemcpyHostToDevice);

@@ -6,6 +6,8 @@ and the error word, frees tensor memory and returns.  The test hook makes one
 tile skip the publication of its sign operand: the other tiles' waits run
 out, the run returns HSB_E_TIMEOUT, and the handle and the context stay
 usable: the next run on the same handle equals a run before the failure.
+Allocation failure is injected on the host (a cap on one device allocation):
+the call returns HSB_E_NOMEM and the handle recovers once the cap is lifted.
 """
 import time
 
@@ -42,3 +44,29 @@ def test_dropped_publication_times_out_and_the_handle_stays_usable():
     with hsb.Solver(J) as s:
         s3, e3 = s.run(p, R, steps, seed)
     np.testing.assert_array_equal(s1, s3)
+
+
+def test_allocation_failure_is_reported_and_the_handle_recovers():
+    # Host-side fault injection: a cap on one device allocation makes the
+    # library's allocations fail as they do on a full device.
+    J = synth.sk_pm1(256, 5)
+    p = hsb.params("discrete", "fp8", eval_every=10)
+    with hsb.Solver(J) as s:
+        s_ref, e_ref = s.run(p, 128, 50, 3)
+        try:
+            hsb.debug_alloc_cap(1 << 20)
+            with pytest.raises(hsb.HsbError) as e:
+                s.run(p, 4096, 50, 3)                  # x alone takes 4 MiB
+            assert e.value.status == hsb.HSB_E_NOMEM
+            with pytest.raises(hsb.HsbError) as e:
+                hsb.create(synth.sk_pm1(1024, 1))      # J takes 4 MiB
+            assert e.value.status == hsb.HSB_E_NOMEM
+        finally:
+            hsb.debug_alloc_cap(0)
+        s1, e1 = s.run(p, 128, 50, 3)
+        s2, e2 = s.run(p, 4096, 50, 3)
+    np.testing.assert_array_equal(s1, s_ref)
+    np.testing.assert_array_equal(e1, e_ref)
+    # replica r depends on (seed, r) only: the first 128 of the larger run agree
+    np.testing.assert_array_equal(s2[:128], s_ref)
+    np.testing.assert_array_equal(e2[:128], e_ref)
