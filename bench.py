@@ -30,8 +30,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-import numpy as np  # noqa: E402
-
 METRIC = "replica-spin-steps/s and % of dense tensor roofline at N=2000, R=1024 vs plain FP32 GPU"
 UNIT = "replica-spin-steps/s"
 WORKLOAD = dict(name="HdSB SK +/-1 N=2000 R=1024 2000 steps FP8", N=2000, J_seed=1, R=1024,
