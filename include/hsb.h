@@ -179,9 +179,16 @@ HSB_API hsb_status hsb_cut_values(hsb_handle h, int R, const double *best_energy
 /* Runs `steps` >= 1 heated SB steps for replicas r = 0..R-1 (R >= 1) from the
  * seeded initial state and returns, per replica, the best evaluated energy
  * best_energy[r] (float64) and its spins best_spins[r*N + i] (+1 / -1).
+ * One step is the Methods update, Eqs. (eq_SyEuY), (eq_SyEuX), (eq_WallX),
+ * (eq_WallY), (eq_EuHeat), with the force of Eq. (eq_fb) or (eq_fd); the
+ * energy of Eq. (eq_Ising) is evaluated every p->eval_every steps and after
+ * the last one, and the first strictly lowest is kept.
  * Both outputs are caller-owned HOST buffers; the call blocks until they are
  * written.  Replica r's result depends only on (J, params, steps, seed, r),
- * not on R. */
+ * not on R.  Errors: HSB_E_INVAL (NULL argument, R, steps or a parameter out
+ * of range), HSB_E_UNSUPPORTED (a precision, schedule or thermostat the
+ * couplings or form do not allow), HSB_E_NOMEM, HSB_E_CUDA, HSB_E_TIMEOUT (a
+ * bounded device wait gave up; the handle stays usable). */
 HSB_API hsb_status hsb_run(hsb_handle h, const hsb_params *p, int R, int steps, uint64_t seed,
                    int8_t *best_spins, double *best_energy);
 
