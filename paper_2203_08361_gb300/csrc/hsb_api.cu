@@ -280,6 +280,10 @@ hsb_status ensure_fp8(hsb_ctx *h)
     if (!h->plan) {
         CK(tc_fp8_plan_create(&h->plan, h->J8, h->S8[0], h->S8[1], h->Np, h->Rcap),
            "tc_fp8_plan_create");
+        // A captured step loop holds the old plan's tensor maps, which may name
+        // a J8 that hsb_set_couplings has freed since: such a graph must not
+        // be replayed, and the generation is part of its key.
+        h->buffers_gen++;
     }
     return HSB_OK;
 }
