@@ -262,7 +262,9 @@ hsb_status ensure_buffers(hsb_ctx *h, int Rp, int R)
     CK(dev_alloc(&h->Efpart, final_energy_part_doubles(Rp) * sizeof(double)),
        "cudaMalloc Efpart");
     CK(dev_alloc(&h->trace_ticket, sizeof(unsigned)), "cudaMalloc trace ticket");
-    CK(cudaMemset(h->trace_ticket, 0, sizeof(unsigned)), "cudaMemset trace ticket");
+    // on the work stream: the kernels that read it run there (a non-blocking
+    // stream is not ordered after the legacy default stream)
+    CK(cudaMemsetAsync(h->trace_ticket, 0, sizeof(unsigned), h->work), "cudaMemset trace ticket");
     CK(dev_alloc(&h->xi, (size_t)Rp * sizeof(double)), "cudaMalloc xi");
     CK(dev_alloc(&h->gvec, (size_t)Rp * sizeof(float)), "cudaMalloc gvec");
     CK(dev_alloc(&h->Sbest, (size_t)Rp * h->N), "cudaMalloc Sbest");
@@ -1752,14 +1754,18 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
         e = dev_alloc(&d_queue, sizeof(unsigned int));
     if (e == cudaSuccess)
         e = dev_alloc(&d_pk, sizeof(float) * (size_t)steps);
+    // The set-up is ordered on the stream of the launch: the handles' streams
+    // are non-blocking, so they are not ordered after the legacy default
+    // stream, and a pageable cudaMemcpy may return before its DMA lands.  The
+    // host vectors live until the stream synchronize at the end of the call.
     if (e == cudaSuccess)
-        e = cudaMemcpy(d_insts, sorted.data(), sizeof(BatchInst) * (size_t)count,
-                       cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(d_insts, sorted.data(), sizeof(BatchInst) * (size_t)count,
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpy(d_pk, c0cfg.pk.data(), sizeof(float) * (size_t)steps,
-                       cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(d_pk, c0cfg.pk.data(), sizeof(float) * (size_t)steps,
+                            cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemset(d_queue, 0, sizeof(unsigned int));
+        e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(hs[0]->err, 0, sizeof(int), st);
     if (e == cudaSuccess) {
