@@ -161,7 +161,12 @@ HSB_API void hsb_destroy(hsb_handle h);
 
 /* Sets the CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream())
  * on which the handle queues its work; NULL selects the handle's private
- * stream again. */
+ * stream again.  Work the handle queued on the previous stream is ordered
+ * before anything it queues on the new one (the new stream waits on an event;
+ * the host does not block), unless the new stream is being captured into a
+ * CUDA graph, where the capturing caller orders the two.  Errors: HSB_E_INVAL for a NULL handle,
+ * HSB_E_CUDA when the event cannot be recorded or waited on (the handle then
+ * keeps its previous stream). */
 HSB_API hsb_status hsb_set_stream(hsb_handle h, void *cuda_stream);
 
 /* Number of spins N and whether J is in {-1, 0, +1} (the FP8 path applies). */

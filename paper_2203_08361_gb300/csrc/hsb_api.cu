@@ -1301,7 +1301,31 @@ hsb_status hsb_set_stream(hsb_handle h, void *cuda_stream)
 {
     if (!h)
         return set_error(HSB_E_INVAL, "handle is NULL");
-    h->work = cuda_stream ? (cudaStream_t)cuda_stream : h->own;
+    const cudaStream_t next = cuda_stream ? (cudaStream_t)cuda_stream : h->own;
+    if (next == h->work)
+        return HSB_OK;
+    DeviceGuard g(h->device);
+    if (!g.ok)
+        return set_error(HSB_E_NODEVICE, "cannot select the handle's device");
+    // Work already queued on the old stream uses the handle's buffers: the new
+    // stream waits for it (without blocking the host).  The event may be
+    // destroyed at once; the wait holds and its resources go when it completes.
+    // A stream being captured cannot wait on an event recorded outside its
+    // capture; the caller that captures orders the two streams itself.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(next, &cap), "stream capture status");
+    if (cap != cudaStreamCaptureStatusNone) {
+        h->work = next;
+        return HSB_OK;
+    }
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event create");
+    cudaError_t e = cudaEventRecord(ev, h->work);
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(next, ev, 0);
+    cudaEventDestroy(ev);
+    CK(e, "order the new stream after the old one");
+    h->work = next;
     return HSB_OK;
 }
 
