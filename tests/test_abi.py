@@ -128,6 +128,16 @@ def test_header_is_plain_c_and_matches_the_binding_layout(tmp_path):
                         str(src), "-o", str(tmp_path / "abi_check.o")],
                        capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+    # and C++ clients include it as is (extern "C" linkage, no C-only syntax)
+    gxx = shutil.which("g++")
+    if gxx is not None:
+        cxx = tmp_path / "abi_check.cpp"
+        cxx.write_text("#include \"hsb.h\"\nint main() { hsb_params p; "
+                       "return hsb_params_default(&p) == HSB_OK ? 0 : 1; }\n")
+        r = subprocess.run([gxx, "-std=c++17", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I",
+                            inc, "-c", str(cxx), "-o", str(tmp_path / "abi_check_cxx.o")],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
 
 
 def test_a_c_program_links_and_calls_the_library(tmp_path):
