@@ -14,12 +14,20 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   step / run       -- hand-derived worked steps (tests/golden), gamma = 0
                       reduction to plain bSB/dSB, wall invariants, conserved
                       quadratic form per eigenmode, linear heating map, N = 2
-                      normal modes, replica independence, determinism
+                      normal modes, replica independence, determinism,
+                      ties keep the earliest evaluation (J = 0), the traced
+                      times k = m*trace_every < Ns (ragged count)
   kinetic_sum      -- exact rational arithmetic (Python fractions)
   run, Nose-Hoover -- large-M reduction to constant heating gamma = -xi0,
                       the conserved quantity M xi^2 + S - N T ln S of the
                       force-free thermostat, time average of T_inst equal to
-                      T, the heating / cooling direction of xi
+                      T, the heating / cooling direction of xi, xi read
+                      from the momenta after the update (one force-free step)
+
+The pins are themselves checked: tests/test_oracle_mutants.py plants one
+plausible mistake at a time in a copy of the C source (a dropped term, a wrong
+sign or index, an operand at the wrong time, an off-by-one) and every such
+copy fails at least one pin.
 """
 from __future__ import annotations
 
