@@ -111,6 +111,8 @@ MUTANTS = [
      "acc += (double)J[(size_t)i * N + j] * (double)s[i] * (double)s[i];"),
     ("cut with w = J instead of -J", MAIN,
      "acc += -(double)J[(size_t)i * N + j]", "acc += (double)J[(size_t)i * N + j]"),
+    ("cut value counted from both ends", MAIN,
+     "return 0.5 * acc;", "return acc;"),
     ("brute force reads one bit for every spin", MAIN,
      "s[i] = ((b >> i) & 1u) ? -1 : 1;", "s[i] = ((b >> 0) & 1u) ? -1 : 1;"),
     # ---- scale and pumping schedule
@@ -120,6 +122,8 @@ MUTANTS = [
      "c1 / (sqrt((double)N) * oracle_sigma_j(J, N))", "c1 / ((double)N * oracle_sigma_j(J, N))"),
     ("pump factor a(t) in place of a0 - a(t)", MAIN,
      "return a0 - t;", "return t;"),
+    ("pump a(t) without the factor a0", MAIN,
+     "double t = a0 * (double)k;", "double t = (double)k;"),
     ("pump schedule over Ns - 1 steps", MAIN,
      "t = t / (double)steps;", "t = t / (double)(steps - 1);"),
     ("traced count off by one", MAIN,
