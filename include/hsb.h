@@ -163,7 +163,7 @@ HSB_API void hsb_destroy(hsb_handle h);
  * on which the handle queues its work; NULL selects the handle's private
  * stream again.  Work the handle queued on the previous stream is ordered
  * before anything it queues on the new one (the new stream waits on an event;
- * the host does not block), unless the new stream is being captured into a
+ * the host does not block), unless either stream is being captured into a
  * CUDA graph, where the capturing caller orders the two.  Errors: HSB_E_INVAL for a NULL handle,
  * HSB_E_CUDA when the event cannot be recorded or waited on (the handle then
  * keeps its previous stream). */

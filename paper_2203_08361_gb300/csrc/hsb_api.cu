@@ -1310,11 +1310,14 @@ hsb_status hsb_set_stream(hsb_handle h, void *cuda_stream)
     // Work already queued on the old stream uses the handle's buffers: the new
     // stream waits for it (without blocking the host).  The event may be
     // destroyed at once; the wait holds and its resources go when it completes.
-    // A stream being captured cannot wait on an event recorded outside its
-    // capture; the caller that captures orders the two streams itself.
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    CK(cudaStreamIsCapturing(next, &cap), "stream capture status");
-    if (cap != cudaStreamCaptureStatusNone) {
+    // While either stream is being captured into a graph, an event between
+    // them would fail (the new stream) or pull the new stream into the capture
+    // (the old one); the caller that captures orders the two streams itself.
+    cudaStreamCaptureStatus cap_new = cudaStreamCaptureStatusNone;
+    cudaStreamCaptureStatus cap_old = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(next, &cap_new), "stream capture status");
+    CK(cudaStreamIsCapturing(h->work, &cap_old), "stream capture status");
+    if (cap_new != cudaStreamCaptureStatusNone || cap_old != cudaStreamCaptureStatusNone) {
         h->work = next;
         return HSB_OK;
     }
