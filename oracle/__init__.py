@@ -11,7 +11,9 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
                       single-flip identity, brute force
   brute_force      -- independent Python enumeration, hand-derived fixtures
   init_values      -- published SplitMix64 output vectors, range/uniformity
-  step / run       -- hand-derived worked steps (tests/golden), gamma = 0
+  step / run       -- hand-derived worked steps (tests/golden), the binary32
+                      force as a chain of correctly rounded fused multiply-adds
+                      (exact rational arithmetic), gamma = 0
                       reduction to plain bSB/dSB, wall invariants, conserved
                       quadratic form per eigenmode, linear heating map, N = 2
                       normal modes, replica independence, determinism,

@@ -39,6 +39,9 @@ MUTANTS = [
      "return acc + t;", "return acc - t;"),
     ("binary32 force fma operands swapped", IMPL,
      "fmaf((float)jv, (float)b, (float)acc)", "fmaf((float)jv, (float)acc, (float)b)"),
+    ("binary32 force term rounded twice", IMPL,
+     "return (REAL)fmaf((float)jv, (float)b, (float)acc);",
+     "return (REAL)((float)acc + (float)jv * (float)b);"),
     ("integer force uses the row's own spin", IMPL,
      "acc += (int32_t)row[j] * (int32_t)stmp[j];",
      "acc += (int32_t)row[j] * (int32_t)stmp[i];"),

@@ -137,6 +137,36 @@ def test_worked_steps(precision):
         np.testing.assert_allclose(y1[0], case["y_next"], rtol=0, atol=tol, err_msg=case["name"])
 
 
+def _round_f32(q):
+    """The binary32 value nearest to the rational q, ties to even."""
+    from fractions import Fraction
+    x = np.float32(float(q))  # within one binary32 ulp of q
+    cands = [np.nextafter(x, np.float32(-np.inf)), x, np.nextafter(x, np.float32(np.inf))]
+    return min(cands, key=lambda c: (abs(Fraction(float(c)) - q),
+                                     int(np.array(c, np.float32).view(np.uint32)) & 1))
+
+
+def test_binary32_force_is_one_rounding_per_term_j_ascending():
+    # The binary32 reading of f_i = sum_j J_ij b_j (Eq. eq_fb): acc <- the
+    # binary32 value nearest to J_ij b_j + acc (a fused multiply-add), j
+    # ascending.  Checked against exact rational arithmetic.
+    from fractions import Fraction as F
+    n, R = 24, 2
+    J = synth.sk_gauss(n, 7)
+    x = np.random.default_rng(7).uniform(-1, 1, (R, n)).astype(np.float32)
+    _, _, f = oracle.step(J, x, np.zeros_like(x), 0, 0.0, 1.0, 1.0, 0.0, 0.0, "f32")
+    differs = False
+    for r in range(R):
+        for i in range(n):
+            acc = two = np.float32(0)
+            for j in range(n):
+                acc = _round_f32(F(float(J[i, j])) * F(float(x[r, j])) + F(float(acc)))
+                two = np.float32(two + np.float32(J[i, j] * x[r, j]))  # two roundings
+            assert f[r, i] == acc, (r, i)
+            differs |= bool(two != acc)
+    assert differs  # the two readings are told apart on this input
+
+
 # ------------------------------------------------------- dynamics pins ----
 
 def _modes(J):
