@@ -13,7 +13,8 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
   init_values      -- published SplitMix64 output vectors, range/uniformity
   step / run       -- hand-derived worked steps (tests/golden), the binary32
                       force as a chain of correctly rounded fused multiply-adds
-                      (exact rational arithmetic), gamma = 0
+                      and the binary32 update as one rounding per operation in
+                      the stated order (exact rational arithmetic), gamma = 0
                       reduction to plain bSB/dSB, wall invariants, conserved
                       quadratic form per eigenmode, linear heating map, N = 2
                       normal modes, replica independence, determinism,

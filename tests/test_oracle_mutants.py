@@ -64,6 +64,8 @@ MUTANTS = [
      "REAL w = u - v;", "REAL w = u + v;"),
     ("dt dropped from the momentum update", IMPL,
      "REAL wd = w * dt;", "REAL wd = w;"),
+    ("momentum step as u dt - v dt", IMPL,
+     "REAL wd = w * dt;", "REAL wd = u * dt - v * dt;"),
     ("position advanced with the old momentum", IMPL,
      "REAL qy = q * yt;", "REAL qy = q * y0;"),
     # ---- inelastic walls, Eqs. (eq_WallX), (eq_WallY)

@@ -167,6 +167,44 @@ def test_binary32_force_is_one_rounding_per_term_j_ascending():
     assert differs  # the two readings are told apart on this input
 
 
+def test_binary32_update_rounds_each_operation_in_the_stated_order():
+    # The binary32 reading of one update (Methods, Eqs. eq_SyEuY, eq_SyEuX,
+    # eq_WallX, eq_WallY, eq_EuHeat): u = c0 f, v = p x, w = u - v,
+    # y~ = y + w dt, x~ = x + q y~, the walls, y' = y~~ + g y, every operation
+    # rounded once to binary32.  Checked against exact rational arithmetic.
+    from fractions import Fraction as F
+
+    def r32(v):
+        return F(float(_round_f32(v)))
+
+    n, R = 16, 4
+    J = synth.sk_gauss(n, 9)
+    rng = np.random.default_rng(9)
+    x = rng.uniform(-0.9, 0.9, (R, n)).astype(np.float32)
+    y = rng.uniform(-0.5, 0.5, (R, n)).astype(np.float32)
+    pk, c0, dt, q, g = 0.7, 0.37, 0.45, 0.45, 0.03
+    x1, y1, f = oracle.step(J, x, y, 0, pk, c0, dt, q, g, "f32")
+    P, C0, DT, Q, G = (F(float(np.float32(v))) for v in (pk, c0, dt, q, g))
+    differs, walls = False, 0
+    for r in range(R):
+        for i in range(n):
+            x0, y0, fi = F(float(x[r, i])), F(float(y[r, i])), F(float(f[r, i]))
+            u, v = r32(C0 * fi), r32(P * x0)
+            w = r32(u - v)
+            yt = r32(y0 + r32(w * DT))
+            xt = r32(x0 + r32(Q * yt))
+            if abs(xt) > 1:
+                xn, ytt = F(1 if xt > 0 else -1), F(0)
+                walls += 1
+            else:
+                xn, ytt = xt, yt
+            yn = r32(ytt + r32(G * y0))
+            assert (F(float(x1[r, i])), F(float(y1[r, i]))) == (xn, yn), (r, i)
+            # an algebraically equal order, u dt - v dt, rounds differently
+            differs |= r32(y0 + r32(r32(u * DT) - r32(v * DT))) != yt
+    assert differs and walls > 0
+
+
 # ------------------------------------------------------- dynamics pins ----
 
 def _modes(J):
