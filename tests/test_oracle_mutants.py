@@ -88,6 +88,8 @@ MUTANTS = [
      "return (double)acc * 0x1p-48;", "return (double)acc * 0x1p-24;"),
     ("thermostat variable moves the wrong way", IMPL,
      "xi = xi + nh_h * (s2 - nh_NT);", "xi = xi - nh_h * (s2 - nh_NT);"),
+    ("thermostat step as h S - h N T", IMPL,
+     "xi = xi + nh_h * (s2 - nh_NT);", "xi = xi + (nh_h * s2 - nh_h * nh_NT);"),
     ("friction with the wrong sign", IMPL,
      "const REAL gk = (REAL)(-xi * p->dt);", "const REAL gk = (REAL)(xi * p->dt);"),
     ("xi reads the momenta before the update", IMPL,

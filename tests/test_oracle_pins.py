@@ -601,7 +601,7 @@ def test_nose_hoover_xi_reads_the_updated_momenta(xi0):
     # only scales y by 1 - xi0 dt.  With N T = S(t_0), a xi read from the old
     # momenta would not move; read from the new ones it moves against xi0 by
     # (dt / M) ((1 - xi0 dt)^2 - 1) S(t_0), up to the 2^-24 quantisation of S.
-    n, dt, M = 64, 0.5, 8.0
+    n, dt, M = 64, 0.5, 7.0  # dt / M not a power of two: its products round
     J = np.zeros((n, n), np.float32)
     x0, y0 = oracle.init_values(11, 0, [0], n, 1.0)
     S0 = oracle.kinetic_sum(y0[0], "f64")
@@ -613,6 +613,9 @@ def test_nose_hoover_xi_reads_the_updated_momenta(xi0):
     want = xi0 + dt / M * ((1.0 - xi0 * dt) ** 2 - 1.0) * S0
     assert abs(want - xi0) > 0.1
     assert out["xi"][0] == pytest.approx(want, abs=1e-6)
+    # and in binary64 exactly xi0 + (dt / M) (S(t_1) - N T), rounded in that order
+    S1 = oracle.kinetic_sum(out["y"][0], "f64")
+    assert out["xi"][0] == xi0 + (dt / M) * (S1 - n * (S0 / n))
 
 
 def test_nose_hoover_kinetic_sum_is_the_exact_fixed_point_sum():
