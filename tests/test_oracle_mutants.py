@@ -66,6 +66,12 @@ MUTANTS = [
      "REAL wd = w * dt;", "REAL wd = w;"),
     ("momentum step as u dt - v dt", IMPL,
      "REAL wd = w * dt;", "REAL wd = u * dt - v * dt;"),
+    ("a0 dt rounded twice", IMPL,
+     "const REAL q = (REAL)(p->a0 * p->dt);", "const REAL q = (REAL)p->a0 * (REAL)p->dt;"),
+    ("gamma dt rounded twice", IMPL,
+     "const REAL g = (REAL)(p->gamma * p->dt);", "const REAL g = (REAL)p->gamma * (REAL)p->dt;"),
+    ("xi dt rounded twice", IMPL,
+     "const REAL gk = (REAL)(-xi * p->dt);", "const REAL gk = -(REAL)xi * (REAL)p->dt;"),
     ("position advanced with the old momentum", IMPL,
      "REAL qy = q * yt;", "REAL qy = q * y0;"),
     # ---- inelastic walls, Eqs. (eq_WallX), (eq_WallY)

@@ -329,14 +329,18 @@ def _plain_sb_f32(J, x, y, steps, c0, dt, a0, form):
     return x, y
 
 
-def test_gamma_zero_reduces_to_plain_dsb_bit_exact():
-    n, steps, reps = 40, 150, [0, 3, 9]
+@pytest.mark.parametrize("a0,steps", [(1.0, 150), (0.73, 5)])
+def test_gamma_zero_reduces_to_plain_dsb_bit_exact(a0, steps):
+    # a0 != 1 also fixes q = a0 dt and p_k as binary64 values rounded once
+    # (with a0 = 0.73 and dt = 1.1, rounding a0 and dt first gives another q;
+    # after 5 steps most spins are still inside the walls, which erase it)
+    n, reps = 40, [0, 3, 9]
     J = synth.sk_pm1(n, 12)
     c0 = oracle.c0_from_c1(J, 0.6)
-    prm = oracle.make_params(1, c0, 1.1, 0.0, eval_every=0)
+    prm = oracle.make_params(1, c0, 1.1, 0.0, a0=a0, eval_every=0)
     out = oracle.run(J, prm, steps, 77, reps, "f32")
     x0, y0 = oracle.init_values(77, 0, reps, n, 1.0)
-    xp, yp = _plain_sb_f32(J, x0, y0, steps, c0, 1.1, 1.0, 1)
+    xp, yp = _plain_sb_f32(J, x0, y0, steps, c0, 1.1, a0, 1)
     np.testing.assert_array_equal(out["x"], xp)
     np.testing.assert_array_equal(out["y"], yp)
 
@@ -530,7 +534,9 @@ def test_nose_hoover_large_mass_is_constant_heating(form, prec):
     # so the run equals the constant-gamma run bit for bit and xi stays xi0.
     J = synth.sk_pm1(48, 3)
     c0 = oracle.c0_from_c1(J, 0.7)
-    gamma = 0.06
+    # with gamma = 0.05 and dt = 1.1, rounding gamma and dt before their
+    # product gives another binary32 g: both runs must take fl32(gamma dt)
+    gamma = 0.05
     heat = oracle.make_params(form, c0, 1.1, gamma, eval_every=20)
     nh = oracle.make_params(form, c0, 1.1, 0.0, eval_every=20, nose_hoover=True, nh_T=0.3,
                             nh_M=1e300, nh_xi0=-gamma)
