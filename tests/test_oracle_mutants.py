@@ -72,6 +72,9 @@ MUTANTS = [
      "const REAL g = (REAL)(p->gamma * p->dt);", "const REAL g = (REAL)p->gamma * (REAL)p->dt;"),
     ("xi dt rounded twice", IMPL,
      "const REAL gk = (REAL)(-xi * p->dt);", "const REAL gk = -(REAL)xi * (REAL)p->dt;"),
+    ("p_k formed in binary32", IMPL,
+     "pk[k] = (REAL)oracle_pump_factor(p->a0, k, steps);",
+     "pk[k] = (REAL)p->a0 - (REAL)p->a0 * (REAL)k / (REAL)steps;"),
     ("position advanced with the old momentum", IMPL,
      "REAL qy = q * yt;", "REAL qy = q * y0;"),
     # ---- inelastic walls, Eqs. (eq_WallX), (eq_WallY)
