@@ -109,7 +109,12 @@ typedef struct {
                                2 = one kernel launch per step, 3 = persistent
                                kernel with the CTA's rows of J held on chip for
                                the whole run (N <= 2048, else
-                               HSB_E_UNSUPPORTED) */
+                               HSB_E_UNSUPPORTED), 4 = persistent kernel run by
+                               CTA pairs, F^T = S^T J (constant heating, no
+                               trace, N <= 4096, R rounded up to 128 a multiple
+                               of 256 and a grid that fits, else
+                               HSB_E_UNSUPPORTED).  Automatic takes 1
+                               where its grid fits, then 4, then 2. */
     int thermostat;         /* HSB_HEAT_CONSTANT: the constant heating rate gamma of
                                Eq. (eq_MomHeat) (HbSB / HdSB); HSB_HEAT_NOSE_HOOVER:
                                the dynamic xi of Eqs. (eq_NH1), (eq_NH), one per

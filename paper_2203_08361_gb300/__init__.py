@@ -27,7 +27,7 @@ STATUS = {0: "HSB_OK", 1: "HSB_E_INVAL", 2: "HSB_E_ASYM", 3: "HSB_E_DIAG", 4: "H
 PREC = {"auto": HSB_PREC_AUTO, "fp32": HSB_PREC_FP32, "fp8": HSB_PREC_FP8,
         "bf16x3": HSB_PREC_BF16X3}
 FORM = {"ballistic": HSB_BALLISTIC, "discrete": HSB_DISCRETE}
-SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2, "resident": 3}
+SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2, "resident": 3, "pair": 4}
 THERMOSTAT = {"constant": HSB_HEAT_CONSTANT, "nose_hoover": HSB_HEAT_NOSE_HOOVER}
 
 # Every symbol include/hsb.h declares.

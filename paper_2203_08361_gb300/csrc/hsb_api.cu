@@ -325,8 +325,8 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
         return set_error(HSB_E_INVAL, "need c0 > 0 or c1 > 0");
     if (p->eval_every < 0 || p->trace_every < 0)
         return set_error(HSB_E_INVAL, "eval_every and trace_every must be >= 0");
-    if (p->schedule < 0 || p->schedule > 3)
-        return set_error(HSB_E_INVAL, "schedule must be 0, 1, 2 or 3");
+    if (p->schedule < 0 || p->schedule > 4)
+        return set_error(HSB_E_INVAL, "schedule must be 0, 1, 2, 3 or 4");
     if (p->thermostat != HSB_HEAT_CONSTANT && p->thermostat != HSB_HEAT_NOSE_HOOVER)
         return set_error(HSB_E_INVAL, "thermostat must be HSB_HEAT_CONSTANT or "
                                       "HSB_HEAT_NOSE_HOOVER");
@@ -673,12 +673,38 @@ int num_evals(const RunCfg &c)
     return (c.eval_every > 0 ? (c.steps - 1) / c.eval_every : 0) + 1;
 }
 
+// Whether the FP8 step loop runs on the CTA-pair kernel: schedule 4, or the
+// automatic choice when the one-CTA persistent grid does not fit.  It needs
+// constant heating, no per-step trace, N <= 4096, an even number of
+// 128-replica blocks and a grid that fits.
+bool use_pair(const hsb_ctx *h, const RunCfg &c)
+{
+    if (c.prec != HSB_PREC_FP8 || (c.schedule != 0 && c.schedule != 4) || c.thermo ||
+        c.trace_every > 0)
+        return false;
+    if (c.schedule == 0 && tc_persistent_fits(h->Np, c.Rp))
+        return false;
+    return tc_pair_fits(h->Np, c.Rp);
+}
+
 // Whether the FP8 step loop runs as one persistent kernel.
 hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
 {
     *out = false;
     if (c.prec != HSB_PREC_FP8 || c.schedule == 2)
         return HSB_OK;
+    if (c.schedule == 4) {
+        if (!use_pair(h, c))
+            return set_error(HSB_E_UNSUPPORTED,
+                             "the CTA-pair schedule needs constant heating, no trace, N <= 4096 "
+                             "and an even number of 128-replica blocks whose grid fits");
+        *out = true;
+        return HSB_OK;
+    }
+    if (use_pair(h, c)) {
+        *out = true;
+        return HSB_OK;
+    }
     const bool fits = c.schedule == 3 ? tc_resident_fits(h->Np, c.Rp)
                                       : tc_persistent_fits(h->Np, c.Rp);
     if (!fits && (c.schedule == 1 || c.schedule == 3))
@@ -805,8 +831,11 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
         a.nhpart = h->nhpart;
         a.nhflags = h->flags + nflags;
     }
-    // schedule 3: J resident on chip; otherwise J streamed every step
-    if (c.schedule == 3)
+    // the CTA-pair kernel where it applies; schedule 3: J resident on chip;
+    // otherwise J streamed every step
+    if (use_pair(h, c))
+        CK(launch_tc_fp8_pair(h->work, h->plan, a), "pair fp8 kernel");
+    else if (c.schedule == 3)
         CK(launch_tc_fp8_resident(h->work, h->plan, h->J8, a), "resident fp8 kernel");
     else
         CK(launch_tc_fp8_persistent(h->work, h->plan, a), "persistent fp8 kernel");

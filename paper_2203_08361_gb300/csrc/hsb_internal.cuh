@@ -127,6 +127,7 @@ struct TcPlan {
     CUtensorMap mapA3;     // 3-D J8 (128 B, rows, K chunks), box 128 x 128 x 2
     CUtensorMap mapB3[2];  // 3-D S8a / S8b, box 128 x 128 x 2
     CUtensorMap mapBw[2];  // 2-D S8a / S8b, box 128 B x 256 rows (per-step kernel)
+    CUtensorMap mapJ64;    // 2-D J8, box 128 B x 64 rows (CTA-pair kernel)
     int Np, Rp;            // Rp: replica capacity the maps were encoded for
 };
 
@@ -184,6 +185,12 @@ struct PersistArgs {
 bool tc_resident_fits(int Np, int Rp);
 cudaError_t launch_tc_fp8_resident(cudaStream_t st, const TcPlan *plan, const uint8_t *J8,
                                    const PersistArgs &a);
+
+// CTA-pair variant (hsb_pair.cu): F^T = S^T J with each pair of CTAs holding
+// 256 replicas x 128 spins; N <= 4096, Rp a multiple of 256, no Nose-Hoover,
+// no trace; same arguments otherwise.
+bool tc_pair_fits(int Np, int Rp);
+cudaError_t launch_tc_fp8_pair(cudaStream_t st, const TcPlan *plan, const PersistArgs &a);
 
 // True when the nblk x nrb grid of the persistent kernel can be co-resident.
 bool tc_persistent_fits(int Np, int Rp);

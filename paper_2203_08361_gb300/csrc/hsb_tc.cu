@@ -449,7 +449,8 @@ cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S
         !encode_u8_3d(&p->mapB3[0], S8a, (uint64_t)Rp, (uint64_t)Np, 128, 2) ||
         !encode_u8_3d(&p->mapB3[1], S8b, (uint64_t)Rp, (uint64_t)Np, 128, 2) ||
         !encode_u8(&p->mapBw[0], S8a, (uint64_t)Rp, (uint64_t)Np, kBN) ||
-        !encode_u8(&p->mapBw[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN)) {
+        !encode_u8(&p->mapBw[1], S8b, (uint64_t)Rp, (uint64_t)Np, kBN) ||
+        !encode_u8(&p->mapJ64, J8, (uint64_t)Np, (uint64_t)Np, 64)) {
         delete p;
         return cudaErrorInvalidValue;
     }

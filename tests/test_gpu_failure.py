@@ -1,8 +1,9 @@
 """Failure detection on the GPU without a GPU fault.
 
-Every spin-wait of the persistent kernel (mbarrier waits, the flag pollers)
+Every spin-wait of the persistent kernels (mbarrier waits, the flag pollers)
 gives up after a wall-clock budget (about 2 s), raises the CTA's abort flag
-and the error word, frees tensor memory and returns.  The test hook makes one
+and the error word, waits (bounded) for the copies and MMAs it issued, frees
+tensor memory and returns.  The test hook makes one
 tile skip the publication of its sign operand: the other tiles' waits run
 out, the run returns HSB_E_TIMEOUT, and the handle and the context stay
 usable: the next run on the same handle equals a run before the failure.
@@ -20,11 +21,12 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_dropped_publication_times_out_and_the_handle_stays_usable():
+@pytest.mark.parametrize("schedule", ["persistent", "pair"])
+def test_dropped_publication_times_out_and_the_handle_stays_usable(schedule):
     J = synth.sk_pm1(512, 7)
     R, steps, seed = 256, 40, 5
     p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=10,
-                   schedule="persistent")
+                   schedule=schedule)
     with hsb.Solver(J) as s:
         s1, e1 = s.run(p, R, steps, seed)
         hsb.debug_drop_publication(s.h, 1)
