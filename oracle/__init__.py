@@ -20,7 +20,16 @@ Parity status of each function (what pins it, in tests/test_oracle_pins.py):
                       normal modes, replica independence, determinism,
                       ties keep the earliest evaluation (J = 0), the traced
                       times k = m*trace_every < Ns (ragged count)
-  kinetic_sum      -- exact rational arithmetic (Python fractions)
+  kinetic_sum      -- binary32: exact rational arithmetic (Python fractions:
+                      the exact sum of squares rounded once), subnormal,
+                      tiny and large momenta, order independence;
+                      binary64: exact sums of exactly representable squares,
+                      the i-ascending order (an input whose two orders
+                      round differently), the error bound of a sum of N
+                      terms
+  kinetic_sum q24  -- (test double of the CUDA kernels' sum) exact rational
+                      arithmetic of its own definition, within its stated
+                      distance of the plain sum
   run, Nose-Hoover -- large-M reduction to constant heating gamma = -xi0,
                       the conserved quantity M xi^2 + S - N T ln S of the
                       force-free thermostat, time average of T_inst equal to
@@ -82,6 +91,7 @@ class Params(C.Structure):
         ("nh_T", C.c_double),
         ("nh_M", C.c_double),
         ("nh_xi0", C.c_double),
+        ("nh_sum", C.c_int),
     ]
 
 
@@ -118,9 +128,10 @@ def _load():
         lib.oracle_is_pm1.restype = C.c_int
         lib.oracle_is_pm1.argtypes = [P, C.c_int]
         for sfx in ("f64", "f32"):
-            ks = getattr(lib, f"oracle_kinetic_sum_{sfx}")
-            ks.restype = C.c_double
-            ks.argtypes = [P, C.c_int]
+            for name in (f"oracle_kinetic_sum_{sfx}", f"oracle_kinetic_sum_q24_{sfx}"):
+                ks = getattr(lib, name)
+                ks.restype = C.c_double
+                ks.argtypes = [P, C.c_int]
         for sfx, real in (("f64", C.c_double), ("f32", C.c_float)):
             st = getattr(lib, f"oracle_step_{sfx}")
             st.restype = C.c_int
@@ -219,12 +230,16 @@ def num_evals(steps: int, eval_every: int) -> int:
     return int(_load().oracle_num_evals(steps, eval_every))
 
 
-def kinetic_sum(y, precision: str = "f32") -> float:
-    """S = sum_i y_i^2 of Eq. (eq_NH) as the Nose-Hoover update forms it (each
-    y_i rounded to a multiple of 2^-24, squares summed exactly, one rounding)."""
+def kinetic_sum(y, precision: str = "f32", q24: bool = False) -> float:
+    """S = sum_i y_i^2 of Eq. (eq_NH) by its definition: for binary32
+    momenta the exact sum of the exact squares rounded once to binary64, for
+    binary64 momenta the binary64 sum (i ascending).  q24=True gives instead
+    the test double of the CUDA kernels' sum (each y_i rounded to a multiple
+    of 2^-24, squares summed exactly, one rounding)."""
     real = _real(precision)
     y = np.ascontiguousarray(y, dtype=real).ravel()
-    fn = getattr(_load(), f"oracle_kinetic_sum_{precision}")
+    name = f"oracle_kinetic_sum_q24_{precision}" if q24 else f"oracle_kinetic_sum_{precision}"
+    fn = getattr(_load(), name)
     return float(fn(_ptr(y), int(y.shape[0])))
 
 
@@ -263,15 +278,17 @@ def make_params(form: int, c0: float, dt: float, gamma: float, a0: float = 1.0,
                 init_half_width: float = 1.0, eval_every: int = 100, instance: int = 0,
                 force_plain_sum: bool = False, trace_every: int = 0,
                 nose_hoover: bool = False, nh_T: float = 0.0, nh_M: float = 1.0,
-                nh_xi0: float = 0.0) -> Params:
+                nh_xi0: float = 0.0, nh_sum_q24: bool = False) -> Params:
     """Run parameters; nose_hoover=True replaces the constant heating gamma by
     the dynamic xi of Eqs. (eq_NH1), (eq_NH) with temperature nh_T, mass nh_M
-    and xi(t_0) = nh_xi0."""
+    and xi(t_0) = nh_xi0.  nh_sum_q24=True forms S with the test double of
+    the CUDA kernels' 2^-24 fixed-point sum instead of the plain definition."""
     return Params(form=int(form), eval_every=int(eval_every), a0=float(a0), c0=float(c0),
                   dt=float(dt), gamma=float(gamma), init_half_width=float(init_half_width),
                   instance=int(instance), force_plain_sum=int(bool(force_plain_sum)),
                   trace_every=int(trace_every), thermostat=1 if nose_hoover else 0,
-                  nh_T=float(nh_T), nh_M=float(nh_M), nh_xi0=float(nh_xi0))
+                  nh_T=float(nh_T), nh_M=float(nh_M), nh_xi0=float(nh_xi0),
+                  nh_sum=1 if nh_sum_q24 else 0)
 
 
 def num_traced(steps: int, trace_every: int) -> int:

@@ -52,12 +52,14 @@
  *       S = sum_i y_i(t_{k+1})^2
  *       xi_{k+1} = xi_k + (dt/M) (S - N T)  (h = dt/M and N T in binary64,
  *                                            each operation rounded once)
- *     S is formed in fixed point so that it does not depend on the order of
- *     summation: each y_i is rounded to the nearest multiple of 2^-24 (ties to
- *     even; exact for |y_i| >= 1/2 in binary32), q_i = 2^24 y_i is squared
- *     exactly as an integer, the squares are added exactly as 128-bit
- *     integers, and 2^-48 times the total is rounded once to binary64
- *     (oracle_kinetic_sum).  |y_i| < 256.
+ *     S is the plain sum of squares (oracle_kinetic_sum): for binary32
+ *     momenta the exact sum of the exact squares, rounded once to binary64
+ *     (it does not depend on the order of the terms); for binary64 momenta
+ *     the binary64 sum, i ascending.  The CUDA kernels form S from momenta
+ *     rounded to multiples of 2^-24; oracle_kinetic_sum_q24 restates that
+ *     as a test double (oracle_params.nh_sum = 1) for bit-exact trajectory
+ *     checks, and the kernels are compared with the plain definition within
+ *     the bound that quantisation implies.
  *
  * Precision: every routine exists twice, in binary64 ("_f64", the reference
  * for tolerance checks) and in binary32 ("_f32", the paper's own single
@@ -205,6 +207,94 @@ int oracle_is_pm1(const float *J, int N)
     return 1;
 }
 
+/* Exact sum of the squares of binary32 values, rounded once to binary64
+ * (round to nearest, ties to even).  A nonzero binary32 value is
+ * v = m 2^(e-24) with an integer m < 2^24 (frexpf: |v| = f 2^e, f in
+ * [1/2, 1), m = f 2^24 exactly), so v^2 = m^2 2^(2e-48) is an integer
+ * multiple of 2^-298, the square of the least binary32 subnormal 2^-149.  The
+ * squares are added as integers in units of 2^-298 in a 640-bit accumulator
+ * (a finite binary32 value has e <= 128, so one square stays below 2^554 and
+ * 2^24 of them below 2^578).  The total X is rounded once: with its top bit
+ * at position t, bits t-52 .. t form the significand, bit t-53 is the
+ * rounding bit, any lower set bit is sticky, and the result is the rounded
+ * significand times 2^(t-52-298) (X itself when it has at most 53 bits). */
+#define SQ_LIMBS 10
+
+/* acc += sq 2^sh for sq < 2^48, sh >= 0 */
+static void sq_add(uint64_t acc[SQ_LIMBS], uint64_t sq, int sh)
+{
+    const int limb = sh / 64, bit = sh % 64;
+    const uint64_t part[2] = {sq << bit, bit ? sq >> (64 - bit) : 0};
+    uint64_t carry = 0;
+    for (int l = limb; l < SQ_LIMBS; ++l) {
+        const uint64_t a = l - limb < 2 ? part[l - limb] : 0;
+        const uint64_t s1 = acc[l] + a;
+        const uint64_t c1 = s1 < a ? 1u : 0u;
+        const uint64_t s2 = s1 + carry;
+        const uint64_t c2 = s2 < carry ? 1u : 0u;
+        acc[l] = s2;
+        carry = c1 | c2;
+        if (l > limb && !carry)
+            break;
+    }
+}
+
+static int sq_bit(const uint64_t acc[SQ_LIMBS], int b)
+{
+    return (int)((acc[b / 64] >> (b % 64)) & 1u);
+}
+
+double oracle_exact_square_sum_f32(const float *y, int N)
+{
+    uint64_t acc[SQ_LIMBS];
+    memset(acc, 0, sizeof acc);
+    for (int i = 0; i < N; ++i) {
+        const float v = fabsf(y[i]);
+        if (v == 0.0f)
+            continue;
+        int e = 0;
+        const float f = frexpf(v, &e);
+        const uint64_t m = (uint64_t)ldexpf(f, 24);
+        /* v^2 = m^2 2^(2e + 250) units of 2^-298.  For a subnormal v the
+         * shift can be negative; m then ends in enough zero bits that the
+         * right shift drops zeros only. */
+        uint64_t sq = m * m;
+        int sh = 2 * e + 250;
+        if (sh < 0) {
+            sq >>= -sh;
+            sh = 0;
+        }
+        sq_add(acc, sq, sh);
+    }
+    int t = -1;
+    for (int b = 64 * SQ_LIMBS - 1; b >= 0; --b)
+        if (sq_bit(acc, b)) {
+            t = b;
+            break;
+        }
+    if (t < 0)
+        return 0.0;
+    uint64_t sig = 0;
+    const int low = t >= 52 ? t - 52 : 0;
+    for (int b = t; b >= low; --b)
+        sig = (sig << 1) | (uint64_t)sq_bit(acc, b);
+    if (t <= 52)
+        return ldexp((double)sig, -298);  /* exact */
+    int expo = t - 52 - 298;
+    const int round = sq_bit(acc, t - 53);
+    int sticky = 0;
+    for (int b = t - 54; b >= 0 && !sticky; --b)
+        sticky = sq_bit(acc, b);
+    if (round && (sticky || (sig & 1u))) {
+        sig += 1;
+        if (sig >> 53) {
+            sig >>= 1;
+            expo += 1;
+        }
+    }
+    return ldexp((double)sig, expo);
+}
+
 /* Run parameters of the whole-trajectory driver. */
 typedef struct {
     int form;               /* 0: ballistic, Eq. (eq_fb); 1: discrete, Eq. (eq_fd) */
@@ -222,6 +312,9 @@ typedef struct {
     double nh_T;            /* Nose-Hoover temperature T */
     double nh_M;            /* Nose-Hoover mass M */
     double nh_xi0;          /* xi(t_0) */
+    int nh_sum;             /* Nose-Hoover S: 0 the plain definition (oracle_kinetic_sum),
+                               1 the CUDA kernels' 2^-24 fixed point (test double,
+                               oracle_kinetic_sum_q24) */
 } oracle_params;
 
 /* Number of traced times of a run: t_k for k = m*trace_every < Ns. */

@@ -89,13 +89,39 @@ static void SFX(update)(int N, REAL *x, REAL *y, const REAL *f, REAL c0, REAL pk
     }
 }
 
-/* S = sum_i y_i^2 of the Nose-Hoover equation (eq_NH) in fixed point: each
- * y_i is scaled by 2^24 (exact) and rounded to the nearest integer q_i, ties
- * to even (nearbyint in the default rounding mode); the squares q_i^2 (exact
- * in 64 bits for |y_i| < 256) are added exactly to a 128-bit unsigned integer,
- * and 2^-48 times the total is converted once to binary64 (correctly
- * rounded).  The result is independent of the order of the terms. */
+/* S = sum_i y_i^2 of the Nose-Hoover equation (eq_NH), by its definition,
+ * for the state of this precision:
+ *   binary32 -- every square y_i^2 is exact in binary64 (two 24-bit
+ *               significands), the squares are added exactly
+ *               (oracle_exact_square_sum_f32) and the total is rounded once
+ *               to binary64;
+ *   binary64 -- the plain binary64 sum, i ascending, each square and each
+ *               addition rounded once. */
 double SFX(oracle_kinetic_sum)(const REAL *y, int N)
+{
+    if (sizeof(REAL) == sizeof(float))
+        return oracle_exact_square_sum_f32((const float *)y, N);
+    {
+        double s = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double v = (double)y[i];
+            const double sq = v * v;
+            s = s + sq;
+        }
+        return s;
+    }
+}
+
+/* TEST DOUBLE of the CUDA kernels' kinetic sum (not the paper's quantity):
+ * each y_i scaled by 2^24 (exact) and rounded to the nearest integer q_i,
+ * ties to even (nearbyint in the default rounding mode); the squares q_i^2
+ * (exact in 64 bits for |y_i| < 256) added exactly to a 128-bit unsigned
+ * integer; 2^-48 times the total converted once to binary64.  Independent of
+ * the order of the terms.  It differs from the plain sum by at most
+ * 2^-24 sum_i |y_i| + N 2^-50 before the final rounding.  Runs select it
+ * with oracle_params.nh_sum = 1, to check the kernels' trajectories bit for
+ * bit; the plain definition above is the oracle proper. */
+double SFX(oracle_kinetic_sum_q24)(const REAL *y, int N)
 {
     unsigned __int128 acc = 0;
     for (int i = 0; i < N; ++i) {
@@ -250,7 +276,8 @@ int SFX(oracle_run)(const float *J, int N, const oracle_params *p, int steps, ui
                     const REAL gk = (REAL)(-xi * p->dt);
                     SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);
                     /* xi_{k+1} from the updated momenta, Eq. (eq_NH) */
-                    const double s2 = SFX(oracle_kinetic_sum)(y, N);
+                    const double s2 = p->nh_sum == 1 ? SFX(oracle_kinetic_sum_q24)(y, N)
+                                                     : SFX(oracle_kinetic_sum)(y, N);
                     xi = xi + nh_h * (s2 - nh_NT);
                 } else {
                     SFX(update)(N, x, y, f, c0, pk[k], dt, q, g);

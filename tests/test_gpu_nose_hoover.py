@@ -1,14 +1,23 @@
 """GPU parity of Nose-Hoover SB (Eqs. eq_NH1, eq_NH) against the CPU oracle.
 
 The friction -xi_r y replaces the constant heating term; xi_r advances after
-each step from S_r = sum_i y_i^2, which both sides form in exact fixed point
-(each term rounded to a multiple of 2^-64, exact 128-bit sum, one rounding),
-so the result does not depend on summation order and trajectories, xi and
-best spins equal the binary32 oracle bit for bit.  Runs on plain FP32 (any
-couplings) and on both FP8 schedules (+/-1 couplings): the persistent kernel,
-whose tiles exchange their sums of q^2 through a second set of flags each
-step, and the one-launch-per-step kernel with a separate xi update, with
-ragged spin and replica tails.
+each step from S_r = sum_i y_i^2.  The oracle forms S by its definition: the
+exact sum of the exact squares of the binary32 momenta, rounded once to
+binary64.  The CUDA kernels form it from momenta rounded to multiples of
+2^-24 (squares exact in 64-bit integers, an exact 128-bit sum, one rounding),
+which does not depend on the order of the terms and differs from the exact
+sum by at most 2^-24 sum_i |y_i| + N 2^-50.  So:
+  - one step from the seeded state: positions, momenta, spins and energies
+    equal the oracle's bit for bit, and xi(t_1) is within the bound that
+    distance implies;
+  - whole runs (the trajectories are chaotic, so a last-bit difference in xi
+    grows): positions, momenta, xi, best spins and energies equal, bit for
+    bit, the oracle run with the test double of the kernels' sum
+    (nh_sum_q24), whose own pins fix it to its definition.
+Runs on plain FP32 (any couplings) and on both FP8 schedules (+/-1
+couplings): the persistent kernel, whose tiles exchange their sums of q^2
+through a second set of flags each step, and the one-launch-per-step kernel
+with a separate xi update, with ragged spin and replica tails.
 """
 import numpy as np
 import pytest
@@ -27,10 +36,57 @@ def _nh(n):
     return dict(nh_T=0.3, nh_M=20.0 * n, nh_xi0=-0.05)
 
 
-def _nh_oracle(J, form, c1, dt, eval_every, trace_every=0, **nh):
+def _nh_oracle(J, form, c1, dt, eval_every, trace_every=0, q24=True, **nh):
+    # q24=True: S from the test double of the kernels' sum (whole runs);
+    # q24=False: the plain definition (the oracle proper)
     c0 = oracle.c0_from_c1(J, c1)
     return oracle.make_params(form, c0, dt, 0.0, eval_every=eval_every, trace_every=trace_every,
-                              nose_hoover=True, **nh)
+                              nose_hoover=True, nh_sum_q24=q24, **nh)
+
+
+@pytest.mark.parametrize("kind,form,prec,schedule,n,R", [
+    ("pm1", "discrete", "fp8", "persistent", 1000, 300),
+    ("pm1", "discrete", "fp8", "per_step", 257, 130),
+    ("pm1", "discrete", "fp32", "auto", 300, 130),
+    ("gauss", "ballistic", "fp32", "auto", 300, 130),
+])
+def test_nose_hoover_one_step_against_the_plain_definition(kind, form, prec, schedule, n, R):
+    # One step from the seeded state: the update uses xi0, so x, y and the
+    # evaluated spins and energies equal the plain oracle's bit for bit; xi_1
+    # = xi0 + (dt/M)(S - N T) differs only through S.  The kernels' S lies
+    # within D = 2^-24 sum |y_i| + N 2^-50 of the exact sum before its one
+    # rounding, and the oracle's is the exact sum rounded once; the binary64
+    # operations after it add at most an ulp each.
+    J = synth.sk_pm1(n, 70 + n) if kind == "pm1" else synth.sk_gauss(n, 70 + n)
+    fcode = 0 if form == "ballistic" else 1
+    c1 = 0.7 if form == "discrete" else 0.9
+    NH = _nh(n)
+    p = hsb.params(form, prec, c1=c1, dt=1.1, eval_every=0, schedule=schedule,
+                   thermostat="nose_hoover", **NH)
+    with hsb.Solver(J) as s:
+        spins, energy = s.run(p, R, 1, 9)
+        x, y = s.get_state(R)
+        xi = s.get_xi(R)
+    ref = oracle.run(J, _nh_oracle(J, fcode, c1, 1.1, 0, q24=False, **NH), 1, 9, range(R),
+                     "f32")
+    np.testing.assert_array_equal(x, ref["x"])
+    np.testing.assert_array_equal(y, ref["y"])
+    np.testing.assert_array_equal(spins, ref["best_s"])
+    if kind == "pm1":
+        np.testing.assert_array_equal(energy, ref["best_e"])
+    else:
+        np.testing.assert_allclose(energy, ref["best_e"], rtol=1e-12, atol=1e-9)
+    h = 1.1 / NH["nh_M"]
+    NT = n * NH["nh_T"]
+    y64 = ref["y"].astype(np.float64)
+    S = (y64 * y64).sum(axis=1)
+    D = 2.0**-24 * np.abs(y64).sum(axis=1) + n * 2.0**-50 + 2.0**-52 * S
+    bound = h * (D + 2.0**-51 * (S + NT)) + 2.0**-51 * (np.abs(h * (S - NT)) + np.abs(xi))
+    dev = np.abs(xi - ref["xi"])
+    assert np.all(dev <= bound), (dev.max(), bound.min())
+    # the bound is far below the step xi takes, so it tells a wrong S apart
+    step = np.abs(ref["xi"] - NH["nh_xi0"])
+    assert np.median(bound) < 1e-3 * np.median(step)
 
 
 @pytest.mark.parametrize("kind,form,prec,schedule,n,R", [

@@ -102,8 +102,22 @@ MUTANTS = [
     ("friction with the wrong sign", IMPL,
      "const REAL gk = (REAL)(-xi * p->dt);", "const REAL gk = (REAL)(xi * p->dt);"),
     ("xi reads the momenta before the update", IMPL,
-     "SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);\n                    /* xi_{k+1} from the updated momenta, Eq. (eq_NH) */\n                    const double s2 = SFX(oracle_kinetic_sum)(y, N);",
-     "const double s2 = SFX(oracle_kinetic_sum)(y, N);\n                    SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);"),
+     "SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);\n                    /* xi_{k+1} from the updated momenta, Eq. (eq_NH) */\n                    const double s2 = p->nh_sum == 1 ? SFX(oracle_kinetic_sum_q24)(y, N)\n                                                     : SFX(oracle_kinetic_sum)(y, N);",
+     "const double s2 = p->nh_sum == 1 ? SFX(oracle_kinetic_sum_q24)(y, N)\n                                                     : SFX(oracle_kinetic_sum)(y, N);\n                    SFX(update)(N, x, y, f, c0, pk[k], dt, q, gk);"),
+    ("Nose-Hoover runs take the kernels' quantised sum", IMPL,
+     "const double s2 = p->nh_sum == 1 ?", "const double s2 = p->nh_sum != 1 ?"),
+    ("binary64 kinetic sum in descending order", IMPL,
+     "for (int i = 0; i < N; ++i) {\n            const double v = (double)y[i];",
+     "for (int i = N - 1; i >= 0; --i) {\n            const double v = (double)y[i];"),
+    ("exact square sum drops subnormal momenta", MAIN,
+     "        if (sh < 0) {\n            sq >>= -sh;\n            sh = 0;\n        }",
+     "        if (sh < 0)\n            continue;"),
+    ("exact square sum truncated, not rounded", MAIN,
+     "if (round && (sticky || (sig & 1u))) {", "if (0) {"),
+    ("exact square sum rounds ties up", MAIN,
+     "if (round && (sticky || (sig & 1u))) {", "if (round) {"),
+    ("exact square sum drops the carry between limbs", MAIN,
+     "        carry = c1 | c2;", "        carry = 0;"),
     ("N dropped from N T", IMPL,
      "const double nh_NT = (double)N * p->nh_T;", "const double nh_NT = p->nh_T;"),
     ("thermostat step M / dt in place of dt / M", IMPL,

@@ -606,7 +606,7 @@ def test_nose_hoover_xi_reads_the_updated_momenta(xi0):
     # the momentum update.  Force-free and unpumped (J = 0, a0 = 0), one step
     # only scales y by 1 - xi0 dt.  With N T = S(t_0), a xi read from the old
     # momenta would not move; read from the new ones it moves against xi0 by
-    # (dt / M) ((1 - xi0 dt)^2 - 1) S(t_0), up to the 2^-24 quantisation of S.
+    # (dt / M) ((1 - xi0 dt)^2 - 1) S(t_0), up to the rounding of S.
     n, dt, M = 64, 0.5, 7.0  # dt / M not a power of two: its products round
     J = np.zeros((n, n), np.float32)
     x0, y0 = oracle.init_values(11, 0, [0], n, 1.0)
@@ -624,11 +624,64 @@ def test_nose_hoover_xi_reads_the_updated_momenta(xi0):
     assert out["xi"][0] == xi0 + (dt / M) * (S1 - n * (S0 / n))
 
 
-def test_nose_hoover_kinetic_sum_is_the_exact_fixed_point_sum():
-    # S of Eq. (eq_NH) as formed by the update: each y_i rounded to the
+def test_kinetic_sum_binary32_is_the_exact_sum_of_squares_rounded_once():
+    # S of Eq. (eq_NH) for binary32 momenta: the exact sum of the exact
+    # squares, rounded once to binary64.  Reference: Python's exact rationals
+    # (float() of a Fraction is correctly rounded, ties to even).
+    from fractions import Fraction
+    rng = np.random.default_rng(4)
+    t = 2.0 ** -27   # t^2 = 2^-54: two of them put 1 + 2^-53 on a tie
+    cases = [
+        rng.uniform(-1, 1, 1000).astype(np.float32),
+        # tiny, subnormal and large momenta, zeros of both signs
+        np.float32([2.0**-24, 3 * 2.0**-26, 2.0**-25, 1e-12, 7e-8, -2.0**-40, 0.0, -0.0,
+                    255.9, 1e-40, -3e-45, 2.0**-149]),
+        np.concatenate([rng.uniform(-1, 1, 300), rng.uniform(-1e-6, 1e-6, 300),
+                        rng.uniform(-1e-30, 1e-30, 50),
+                        rng.uniform(-200, 200, 40)]).astype(np.float32),
+        np.float32([1.0] * 70000),              # carries across 64-bit limbs
+        np.float32([1.0, t, t]),                # a tie: rounds to even (1.0)
+        np.float32([1.0, t, t, 2.0**-80]),      # just above the tie: rounds up
+        np.float32([1.0, t, t, t]),             # 1 + 1.5 2^-53: rounds up
+        np.float32([3e38, -3e38, 1e-45]),       # the largest binary32 magnitudes
+        np.float32([1e-40, -3e-45, 2.0**-149, 5e-39]),   # subnormals alone
+        np.float32([]),
+    ]
+    for y in cases:
+        exact = sum((Fraction(float(v)) ** 2 for v in y), Fraction(0))
+        want = float(exact)
+        assert oracle.kinetic_sum(y, "f32") == want
+        assert oracle.kinetic_sum(y[::-1].copy(), "f32") == want   # order-free
+    assert oracle.kinetic_sum(np.float32([1.0, t, t]), "f32") == 1.0
+    assert oracle.kinetic_sum(np.float32([1.0, t, t, 2.0**-80]), "f32") == 1.0 + 2.0**-52
+
+
+def test_kinetic_sum_binary64_is_the_plain_sum_in_ascending_order():
+    # For binary64 momenta S is the plain binary64 sum, i ascending, one
+    # rounding per square and per addition.  Three squares of 2^-54 before
+    # 1.0 add up to 1.5 2^-53 first and then round 1 + 1.5 2^-53 up; after
+    # 1.0 each is lost to rounding.  Squares and partial sums that are exact
+    # give the exact sum; otherwise the error stays within the bound of a
+    # sum of N rounded terms.
+    from fractions import Fraction
+    t = 2.0 ** -27
+    assert oracle.kinetic_sum(np.array([t, t, t, 1.0]), "f64") == 1.0 + 2.0 ** -52
+    assert oracle.kinetic_sum(np.array([1.0, t, t, t]), "f64") == 1.0
+    ints = np.arange(-40.0, 41.0)
+    assert oracle.kinetic_sum(ints, "f64") == float(np.sum(ints.astype(np.int64) ** 2))
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal(5000)
+    exact = sum((Fraction(float(v)) ** 2 for v in y), Fraction(0))
+    got = oracle.kinetic_sum(y, "f64")
+    assert abs(Fraction(got) - exact) <= exact * len(y) * Fraction(2, 2**53)
+
+
+def test_kinetic_sum_q24_test_double_is_its_fixed_point_definition():
+    # The test double of the CUDA kernels' sum: each y_i rounded to the
     # nearest multiple of 2^-24, the squares summed exactly, 2^-48 times the
     # total rounded once.  Reference: Python's exact rationals (round() to
-    # nearest even, float() correctly rounded).
+    # nearest even, float() correctly rounded).  It stays within
+    # 2^-24 sum |y_i| + N 2^-50 of the plain sum before its final rounding.
     from fractions import Fraction
     rng = np.random.default_rng(4)
     cases = [
@@ -642,10 +695,8 @@ def test_nose_hoover_kinetic_sum_is_the_exact_fixed_point_sum():
     for y in cases:
         units = sum(round(Fraction(float(v)) * 2**24) ** 2 for v in y)
         want = float(Fraction(units, 2**48))
-        assert oracle.kinetic_sum(y) == want
-        # order does not matter
-        assert oracle.kinetic_sum(y[::-1].copy()) == want
-        # and it is the plain sum of squares up to the 2^-24 quantisation of y
+        assert oracle.kinetic_sum(y, q24=True) == want
+        assert oracle.kinetic_sum(y[::-1].copy(), q24=True) == want
         exact = sum(Fraction(float(v)) ** 2 for v in y)
         bound = sum(abs(Fraction(float(v))) for v in y) * Fraction(1, 2**24) \
             + Fraction(len(y), 2**50) + abs(exact) * Fraction(1, 2**53)
