@@ -58,6 +58,9 @@ struct __align__(8) GShared {
     uint64_t step_done;     // epilogue finished a step (or the initial state)
     uint64_t acc_full[2];
     uint64_t acc_empty[2];
+    uint64_t drain;         // one arrival per MMA warp once its MMAs have completed
+    int last_use[kGStages]; // last use of each J stage a copy was issued for
+    int s_loads;            // copies of the resident S issued
     uint32_t tmem_base;
     int abort;
     int inst;               // current instance index (-1: none left)
@@ -141,6 +144,10 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
             ptx::mbar_init(&sh->acc_full[b], 2);  // one arrival per MMA warp
             ptx::mbar_init(&sh->acc_empty[b], 1);
         }
+        ptx::mbar_init(&sh->drain, 2);
+        for (int s = 0; s < kGStages; ++s)
+            sh->last_use[s] = -1;
+        sh->s_loads = 0;
         sh->abort = 0;
         ptx::mbar_init_fence();
     }
@@ -196,6 +203,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                                 fail = true;
                                 break;
                             }
+                            atomicMax(&sh->last_use[s], (int)(g / kGStages));  // for the drain
                             ptx::mbar_expect_tx(&sh->full[s], (uint32_t)kGStageA);
                             ptx::tma_load_3d(sA + (size_t)s * kGStageA, &in.mapA, 0, mb * kTM,
                                              2 * p, &sh->full[s]);
@@ -220,6 +228,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     ++sdone;
                     if (lane == 0) {
                         ptx::fence_proxy_async_global();
+                        ++sh->s_loads;  // for the drain
                         ptx::mbar_expect_tx(&sh->s_full, (uint32_t)(BN * Np));
                         ptx::tma_load_3d(sS, &in.mapS[k & 1], 0, 0, 0, &sh->s_full);
                     }
@@ -451,6 +460,21 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
             break;
     }
 
+    // drain before tensor memory and shared memory are given up (every exit
+    // path): the last copy into each J stage and the last resident S have
+    // landed and every MMA has completed, each wait bounded
+    if (warp == 2 || warp == 3)
+        commit_elect(&sh->drain);
+    __syncthreads();
+    if (threadIdx.x < kGStages) {
+        const int u = sh->last_use[threadIdx.x];
+        if (u >= 0)
+            ptx::mbar_drain(&sh->full[threadIdx.x], (uint32_t)u & 1u, a.err);
+    }
+    if (threadIdx.x == 32 && sh->s_loads > 0)
+        ptx::mbar_drain(&sh->s_full, (uint32_t)(sh->s_loads - 1) & 1u, a.err);
+    if (warp == 2 || warp == 3)
+        ptx::mbar_drain(&sh->drain, 0u, a.err);
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();

@@ -102,6 +102,8 @@ struct __align__(8) PShared {
     uint64_t empty[kPStages];
     uint64_t accfull;     // one arrival per MMA warp
     uint64_t tmem_empty;  // every epilogue warp has read the accumulator(s)
+    uint64_t drain;       // one arrival per MMA warp once its MMAs have completed
+    int last_use[kPStages];  // last use of each stage a copy was issued for
     uint32_t tmem_base;
     int abort;
     uint64_t ring[kOrder];  // slot g % kOrder named: one arrival per use
@@ -280,6 +282,9 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         }
         ptx::mbar_init(&sh->accfull, kMmaWarps);
         ptx::mbar_init(&sh->tmem_empty, kEpiWarps);
+        ptx::mbar_init(&sh->drain, kMmaWarps);
+        for (int s = 0; s < kPStages; ++s)
+            sh->last_use[s] = -1;
         for (int r = 0; r < kOrder; ++r)
             ptx::mbar_init(&sh->ring[r], 1);
         sh->abort = 0;
@@ -387,6 +392,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err))
                     break;
                 ptx::fence_proxy_async_global();
+                atomicMax(&sh->last_use[s], g / kPStages);  // for the drain
                 if (!split || iw == 0) {
                     // the stage's one arrival; both boxes count against it
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
@@ -445,6 +451,7 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
             else if (lane == 0)
                 ptx::mbar_arrive(&sh->accfull);  // no pair of this pass for this warp
         }
+        commit_elect(&sh->drain);  // arrives once this warp's MMAs have completed
     } else {
         // ---------------------------------------------------------- epilogue
         const int ew = warp - kFirstEpi;    // 0..15
@@ -796,6 +803,19 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         }
     }
 
+    // drain before tensor memory and shared memory are given up (every exit
+    // path): the last copy into each stage has landed and every MMA has
+    // completed, each wait bounded.  A stage whose last use was never armed
+    // (its arming warp gave up first) waits out the bound, with the error
+    // word set.
+    __syncthreads();
+    if (threadIdx.x < kPStages) {
+        const int u = sh->last_use[threadIdx.x];
+        if (u >= 0)
+            ptx::mbar_drain(&sh->full[threadIdx.x], (uint32_t)u & 1u, a.err);
+    }
+    if (warp >= kFirstMma && warp < kFirstEpi)
+        ptx::mbar_drain(&sh->drain, 0u, a.err);
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();

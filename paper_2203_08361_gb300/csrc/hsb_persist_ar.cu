@@ -64,6 +64,8 @@ struct __align__(8) RShared {
     uint64_t a_full;
     uint64_t accfull;
     uint64_t tmem_empty;
+    uint64_t drain;       // arrives once every MMA issued has completed
+    int last_use[kRStages];  // last use of each stage a copy was issued for
     uint32_t tmem_base;
     int abort;
     int stage_chunk[kRStages];
@@ -137,6 +139,9 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
         ptx::mbar_init(&sh->a_full, 1);
         ptx::mbar_init(&sh->accfull, 1);
         ptx::mbar_init(&sh->tmem_empty, 1);
+        ptx::mbar_init(&sh->drain, 1);
+        for (int s = 0; s < kRStages; ++s)
+            sh->last_use[s] = -1;
         sh->abort = 0;
         sh->avail = 0;
         ptx::mbar_init_fence();
@@ -297,6 +302,7 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
                     }
                     sh->stage_chunk[s] = kc;
                     ptx::fence_proxy_async_global();
+                    atomicMax(&sh->last_use[s], g / kRStages);  // for the drain
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)kRStageB);
                     ptx::tma_load_2d(sB + (size_t)s * kRStageB, mapB, kc * 128, r0, &sh->full[s]);
                 }
@@ -351,6 +357,7 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
                     break;
                 ptx::mma_commit(&sh->accfull);
             }
+            ptx::mma_commit(&sh->drain);  // arrives once every MMA issued has completed
         }
     } else {
         // ---------------------------------------------------------- epilogue
@@ -465,6 +472,19 @@ tc_fp8_resident_kernel(const __grid_constant__ CUtensorMap tmapA,
         }
     }
 
+    // drain before tensor memory and shared memory are given up (every exit
+    // path): the resident chunks and the last copy into each stage have
+    // landed and every MMA has completed, each wait bounded
+    __syncthreads();
+    if (threadIdx.x < kRStages) {
+        const int u = sh->last_use[threadIdx.x];
+        if (u >= 0)
+            ptx::mbar_drain(&sh->full[threadIdx.x], (uint32_t)u & 1u, a.err);
+    }
+    if (threadIdx.x == 32 && nsm > 0)
+        ptx::mbar_drain(&sh->a_full, 0u, a.err);
+    if (threadIdx.x == 96)
+        ptx::mbar_drain(&sh->drain, 0u, a.err);
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();

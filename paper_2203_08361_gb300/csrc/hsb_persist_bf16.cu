@@ -85,6 +85,8 @@ struct __align__(8) QShared {
     uint64_t empty[kQStages];
     uint64_t accfull;     // one arrival per accumulator
     uint64_t tmem_empty;  // one arrival per epilogue warp
+    uint64_t drain;       // one arrival per MMA warp once its MMAs have completed
+    int last_use[kQStages];  // last use of each stage a copy was issued for
     uint32_t tmem_base;
     int abort;
     float red[4][kQN];    // per-quadrant energy partials (energy-only pass)
@@ -199,6 +201,9 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
         }
         ptx::mbar_init(&sh->accfull, 2);
         ptx::mbar_init(&sh->tmem_empty, kQEpiWarps);
+        ptx::mbar_init(&sh->drain, 2);
+        for (int s = 0; s < kQStages; ++s)
+            sh->last_use[s] = -1;
         sh->abort = 0;
         ptx::mbar_init_fence();
     }
@@ -251,6 +256,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                             fail = true;
                             break;
                         }
+                        atomicMax(&sh->last_use[s], (int)(g / kQStages));  // for the drain
                         if (isJ) {
                             ptx::mbar_expect_tx(&sh->full[s],
                                                 (uint32_t)(kQStageA + kBPlanes * kQPlane));
@@ -313,6 +319,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
             else if (lane == 0)
                 ptx::mbar_arrive(&sh->accfull);  // no load of this pass for this accumulator
         }
+        commit_elect(&sh->drain);  // arrives once this warp's MMAs have completed
     } else {
         // ---------------------------------------------------------- epilogue
         const int ew = warp - kQFirstEpi;
@@ -481,6 +488,18 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
         }
     }
 
+    // drain before tensor memory and shared memory are given up (every exit
+    // path): the last copy into each stage has landed and every MMA has
+    // completed, each wait bounded.  A stage whose last use was never armed
+    // (the J issuer gave up first) waits out the bound, with the error word set.
+    __syncthreads();
+    if (threadIdx.x < kQStages) {
+        const int u = sh->last_use[threadIdx.x];
+        if (u >= 0)
+            ptx::mbar_drain(&sh->full[threadIdx.x], (uint32_t)u & 1u, a.err);
+    }
+    if (warp == 2 || warp == 3)
+        ptx::mbar_drain(&sh->drain, 0u, a.err);
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();

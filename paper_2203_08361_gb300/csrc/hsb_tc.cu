@@ -68,6 +68,8 @@ struct __align__(8) TcShared {
     uint64_t empty[kStages];
     uint64_t accfull[2];
     uint64_t accempty[2];
+    uint64_t drain;          // arrives once every MMA issued has completed
+    int last_use[kStages];   // last use of each stage a copy was issued for
     uint32_t tmem_base;
     int abort;
     float red[4][kBN];
@@ -155,6 +157,9 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
             ptx::mbar_init(&sh->accfull[b], 1);
             ptx::mbar_init(&sh->accempty[b], kEpiWarps);
         }
+        ptx::mbar_init(&sh->drain, 1);
+        for (int s = 0; s < kStages; ++s)
+            sh->last_use[s] = -1;
         sh->abort = 0;
         ptx::mbar_init_fence();
     }
@@ -188,6 +193,7 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                 const uint32_t ph = (uint32_t)(g / kStages) & 1u;
                 if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, err))
                     break;
+                atomicMax(&sh->last_use[s], g / kStages);  // for the drain
                 if (isA) {
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kStageA + kStageB));
                     ptx::tma_load_2d(sA + (size_t)s * kStageA, &tmapA, kc * kBK, mb * kBM,
@@ -231,6 +237,7 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                 break;
             commit_elect(&sh->accfull[b]);
         }
+        commit_elect(&sh->drain);  // arrives once every MMA issued has completed
     } else {
         // ---------------------------------------------------------- epilogue
         const int ew = warp - kFirstEpi;           // 0..7
@@ -356,6 +363,18 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
         }
     }
 
+    // drain before tensor memory and shared memory are given up (every exit
+    // path): the last copy into each stage has landed and every MMA has
+    // completed, each wait bounded.  A stage whose last use was never armed
+    // (the J issuer gave up first) waits out the bound, with the error word set.
+    __syncthreads();
+    if (threadIdx.x < kStages) {
+        const int u = sh->last_use[threadIdx.x];
+        if (u >= 0)
+            ptx::mbar_drain(&sh->full[threadIdx.x], (uint32_t)u & 1u, err);
+    }
+    if (warp == kMmaWarp)
+        ptx::mbar_drain(&sh->drain, 0u, err);
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
