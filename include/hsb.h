@@ -305,7 +305,11 @@ HSB_API hsb_status hsb_run_stats(hsb_handle h, long long *kernel_launches);
  * Every intermediate buffer lives in one file-scope device array of about
  * 2.6 MB that each GPU loading the library holds until the process exits.
  * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make that
+ * first call before any stream capture.  The kept address belongs to the
+ * device's context of that time: after cudaDeviceReset, or once the primary
+ * context has been destroyed and created again, it no longer names the array,
+ * so do not call this entry point on that device again in the process.
  * All calls share the array and it keeps the previous call's contents (the
  * call rewrites every part it reads first): calls whose work overlaps on the
  * GPU -- on different streams, or from different threads -- race and give

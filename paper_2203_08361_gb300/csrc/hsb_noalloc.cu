@@ -52,7 +52,9 @@ std::mutex g_setup_mutex;
 void *g_scratch_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the first call on a device performs this set-up).
+// per device (the first call on a device performs this set-up) and kept for
+// the life of the process: it belongs to the context current at that time, so
+// it is stale after cudaDeviceReset (stated in hsb.h).
 cudaError_t scratch_address(int dev, unsigned char **out)
 {
     std::lock_guard<std::mutex> lock(g_setup_mutex);

@@ -189,3 +189,87 @@ int main(void)
     torch = pytest.importorskip("torch")
     want = 0 if torch.cuda.is_available() else 8  # HSB_OK or HSB_E_NODEVICE
     assert f"create: {want}" in r.stdout
+
+
+@pytest.mark.gpu
+def test_a_c_program_runs_the_library_and_advances_a_worked_step(tmp_path):
+    # A plain C11 client on a device: hsb_run on the antiferromagnetic
+    # triangle (J = -1 on every pair), whose energies Eq. (eq_Ising) gives by
+    # hand (tests/golden/worked_steps.json: 3 with no pair cut, -1 otherwise);
+    # and hsb_advance over the hand-derived two-spin discrete step of the
+    # same file (k = 0, so p_0 = a0; c0 = dt = 1/2, gamma dt = 1/8): the
+    # positions and momenta it prints must be the worked values exactly.
+    import json
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    hsb.load()
+    libdir = os.path.dirname(hsb.LIB_PATH)
+    with open(os.path.join(ROOT, "tests", "golden", "worked_steps.json")) as fh:
+        golden = json.load(fh)
+    step = next(c for c in golden["cases"] if c["name"] == "dsb_n2_no_wall")
+    tri = next(c for c in golden["energies"]["cases"] if c["name"] == "antiferro_triangle")
+    src = tmp_path / "runner.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "hsb.h"
+int main(void)
+{
+    float J[9] = {0, -1, -1, -1, 0, -1, -1, -1, 0};
+    hsb_handle h;
+    if (hsb_create(J, 3, &h) != HSB_OK)
+        return 10;
+    hsb_params p;
+    hsb_params_default(&p);
+    p.eval_every = 5;
+    enum { R = 8 };
+    int8_t spins[R * 3];
+    double energy[R];
+    if (hsb_run(h, &p, R, 60, 7, spins, energy) != HSB_OK)
+        return 11;
+    for (int r = 0; r < R; ++r)
+        printf("run %d %d %d %.17g\n", spins[3 * r], spins[3 * r + 1], spins[3 * r + 2],
+               energy[r]);
+    hsb_destroy(h);
+
+    float J2[4] = {0, 1, 1, 0};
+    if (hsb_create(J2, 2, &h) != HSB_OK)
+        return 12;
+    hsb_params_default(&p);
+    p.form = HSB_DISCRETE;
+    p.prec = HSB_PREC_FP32;
+    p.a0 = 1.0;
+    p.c0 = 0.5;
+    p.dt = 0.5;
+    p.gamma = 0.25;
+    float x[2] = {0.5f, -0.25f}, y[2] = {0.125f, 0.0f};
+    if (hsb_advance(h, &p, 1, 4, 0, 1, x, y) != HSB_OK)
+        return 13;
+    printf("step %.9g %.9g %.9g %.9g\n", x[0], x[1], y[0], y[1]);
+    hsb_destroy(h);
+    return 0;
+}
+""")
+    exe = tmp_path / "runner"
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Werror", "-pedantic", "-I", inc, str(src),
+                        "-L", libdir, "-lhsb", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    lines = r.stdout.split("\n")
+    runs = [ln.split()[1:] for ln in lines if ln.startswith("run ")]
+    assert len(runs) == 8
+    hand = {tuple(s): e for s, e in zip(tri["states"], tri["E"])}
+    for fields in runs:
+        s = tuple(int(v) for v in fields[:3])
+        e = float(fields[3])
+        # the energy of a state and of its global flip are equal
+        key = s if s in hand else tuple(-v for v in s)
+        assert e == hand[key], (s, e)
+        assert e == tri["E_ground"]  # 60 heated steps find a frustrated ground state
+    got = [float(v) for v in next(ln for ln in lines if ln.startswith("step ")).split()[1:]]
+    assert got == step["x_next"] + step["y_next"]

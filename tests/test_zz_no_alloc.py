@@ -1,13 +1,16 @@
 """hsb_run_fp32_noalloc, the entry point that allocates nothing (it works in a
-fixed scratch array the library holds), against hsb_run on the plain FP32
-path: two calls in a row, each on a different instance, must give the same
-best spins and energies (exact integers for +/-1 couplings; for general
-couplings the no-alloc path sums the final energies in binary64 and hsb_run
-in exact fixed point, so they agree to 1e-12 relative).  This file is
-collected last on purpose."""
+fixed scratch array the library holds), for callers that cannot allocate
+device memory on demand: against hsb_run on the plain FP32 path, two calls in
+a row, each on a different instance, must give the same best spins and
+energies (exact integers for +/-1 couplings; for general couplings the
+no-alloc path sums the final energies in binary64 and hsb_run in exact fixed
+point, so they agree to 1e-12 relative), and both equal the binary32 oracle.
+A call made while every device allocation of the library is capped at one
+byte succeeds: it allocates nothing.  This file is collected last on purpose."""
 import numpy as np
 import pytest
 
+import oracle
 import paper_2203_08361_gb300 as hsb
 import synth
 
@@ -43,6 +46,37 @@ def test_no_alloc_run_matches_hsb_run_on_two_calls_in_a_row():
         np.testing.assert_array_equal(got_s, want_s)
         exact = bool(np.all(np.isin(J, (-1.0, 0.0, 1.0))))
         np.testing.assert_allclose(got_e, want_e, rtol=0 if exact else 1e-12, atol=0)
+        # and the binary32 oracle on sampled replicas
+        rows = [0, 1, R - 1]
+        op = oracle.make_params(0 if form == "ballistic" else 1, c0, 1.1, gamma, eval_every=ev)
+        ref = oracle.run(J, op, steps, 9, rows, "f32")
+        np.testing.assert_array_equal(got_s[rows], ref["best_s"])
+        np.testing.assert_allclose(got_e[rows], ref["best_e"], rtol=0 if exact else 1e-12,
+                                   atol=0)
+
+
+def test_no_alloc_run_allocates_nothing():
+    # every device allocation the library makes goes through one wrapper that
+    # honours the cap; with the cap at one byte the call still succeeds
+    torch = pytest.importorskip("torch")
+    stream = torch.cuda.Stream()
+    J = synth.sk_pm1(256, 8)
+    p = hsb.params("discrete", "fp32", c0=0.7 / 16.0, dt=1.1, gamma=0.06, eval_every=20)
+    want_s, want_e = _noalloc(torch, J, p, 64, 60, 2, stream)  # set-up before the cap
+    dJ = torch.from_numpy(J).to("cuda")
+    spins = torch.empty((64, 256), dtype=torch.int8, device="cuda")
+    energy = torch.empty(64, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    try:
+        hsb.debug_alloc_cap(1)
+        with torch.cuda.stream(stream):
+            hsb.run_fp32_noalloc(dJ.data_ptr(), 256, p, 64, 60, 2, spins.data_ptr(),
+                                 energy.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+    finally:
+        hsb.debug_alloc_cap(0)
+    np.testing.assert_array_equal(spins.cpu().numpy(), want_s)
+    np.testing.assert_array_equal(energy.cpu().numpy(), want_e)
 
 
 def test_no_alloc_rejects_sizes_beyond_its_scratch():
