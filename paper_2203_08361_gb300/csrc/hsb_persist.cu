@@ -572,14 +572,19 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                     sh->gnh[et] = __double2float_rn(__dmul_rn(-x, a.dt64));
                 }
             }
-            // x and y of the first 16 columns: the MMA does not write them
+            // x and y of the first 16 columns (the MMA does not write them)
+            // and v = p_k x of their update, formed in the MMA's shadow
             uint32_t xpre[16], ypre[16];
+            uint64_t vpre[8];
             ptx::tmem_ld16(tmem + lane_off + kColX + c0, xpre);
             ptx::tmem_ld16(tmem + lane_off + kColY + c0, ypre);
-            const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err) &&
-                            ok_nh;
             ptx::tmem_ld_wait(xpre);
             ptx::tmem_ld_wait(ypre);
+#pragma unroll
+            for (int j = 0; j < 16; j += 2)
+                vpre[j / 2] = f2_fma(pk2, f2_pack_bits(xpre[j], xpre[j + 1]), k2.z);
+            const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err) &&
+                            ok_nh;
             if (epi_bar_or(!ok)) {
                 left = true;
                 break;
@@ -588,11 +593,16 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
 
             if (!final_pass) {
                 // ---- phase 1: only sgn(x') = sgn(x~), published before the
-                // rest of the update (the next step of every tile waits for it)
+                // rest of the update (the next step of every tile waits for
+                // it).  The operations are those of the update up to p = q yt;
+                // x~ = fl(x + p) is negative exactly when p < -x (a nonzero
+                // sum of two binary32 values does not round to zero, a zero
+                // sum rounds to +0).
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const uint32_t col0 = (uint32_t)(c0 + h * 16);
                     uint32_t f[16], xr[16], yr[16];
+                    uint64_t v[8];
                     load_force(tmem + lane_off + col0, two_acc, f);
                     if (h == 0) {
 #pragma unroll
@@ -600,19 +610,31 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                             xr[j] = xpre[j];
                             yr[j] = ypre[j];
                         }
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            v[j] = vpre[j];
                     } else {
                         ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
                         ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
                         ptx::tmem_ld_wait(xr);
                         ptx::tmem_ld_wait(yr);
+#pragma unroll
+                        for (int j = 0; j < 16; j += 2)
+                            v[j / 2] = f2_fma(pk2, f2_pack_bits(xr[j], xr[j + 1]), k2.z);
                     }
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
-                        const uint64_t xt =
-                            sb_position2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
-                                         f2_pack_bits(yr[j], yr[j + 1]), pk2, k2);
-                        srow[(col0 + j) * kPTileRow] = live ? fp8_sign(f2_lo(xt)) : (uint8_t)0;
-                        srow[(col0 + j + 1) * kPTileRow] = live ? fp8_sign(f2_hi(xt)) : (uint8_t)0;
+                        const uint64_t u = f2_fma(k2.c0, f2_pack_bits(f[j], f[j + 1]), k2.z);
+                        const uint64_t w = f2_sub(u, v[j / 2]);
+                        const uint64_t wd = f2_fma(w, k2.dt, k2.z);
+                        const uint64_t yt = f2_add(f2_pack_bits(yr[j], yr[j + 1]), wd);
+                        const uint64_t qy = f2_fma(k2.q, yt, k2.z);
+                        const bool n0 = f2_lo(qy) < -__uint_as_float(xr[j]);
+                        const bool n1 = f2_hi(qy) < -__uint_as_float(xr[j + 1]);
+                        srow[(col0 + j) * kPTileRow] =
+                            live ? (n0 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
+                        srow[(col0 + j + 1) * kPTileRow] =
+                            live ? (n1 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
                     }
                 }
                 // this warp's 32 replicas x 32 spins of S(t_{k+1}): 16-byte
