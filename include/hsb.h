@@ -83,7 +83,14 @@ typedef enum {
     HSB_PREC_FP8 = 2,
     /* tcgen05 tensor cores, J = J_hi + J_lo and x = x_hi + x_lo in BF16,
        J_hi x_hi + J_lo x_hi + J_hi x_lo accumulated in FP32 */
-    HSB_PREC_BF16X3 = 3
+    HSB_PREC_BF16X3 = 3,
+    /* tcgen05 tensor cores (kind::mxf4, block-scaled with unit UE8M0 scales),
+       J and sgn(x) in packed FP4 e2m1 (+1 = 0x2, -1 = 0xA), FP32
+       accumulation.  Exact (integer forces), so trajectories equal the FP8
+       ones bit for bit.  Discrete form with J in {-1,0,+1} only, one kernel
+       launch per step (schedule 0 or 2, else HSB_E_UNSUPPORTED); never
+       picked by AUTO. */
+    HSB_PREC_FP4 = 4
 } hsb_prec;
 
 typedef struct {

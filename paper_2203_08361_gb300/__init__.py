@@ -19,13 +19,13 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhsb.so")
 
 HSB_BALLISTIC, HSB_DISCRETE = 0, 1
-HSB_PREC_AUTO, HSB_PREC_FP32, HSB_PREC_FP8, HSB_PREC_BF16X3 = 0, 1, 2, 3
+HSB_PREC_AUTO, HSB_PREC_FP32, HSB_PREC_FP8, HSB_PREC_BF16X3, HSB_PREC_FP4 = 0, 1, 2, 3, 4
 HSB_E_INVAL, HSB_E_NOMEM, HSB_E_TIMEOUT, HSB_E_UNSUPPORTED = 1, 4, 6, 7
 HSB_HEAT_CONSTANT, HSB_HEAT_NOSE_HOOVER = 0, 1
 STATUS = {0: "HSB_OK", 1: "HSB_E_INVAL", 2: "HSB_E_ASYM", 3: "HSB_E_DIAG", 4: "HSB_E_NOMEM",
           5: "HSB_E_CUDA", 6: "HSB_E_TIMEOUT", 7: "HSB_E_UNSUPPORTED", 8: "HSB_E_NODEVICE"}
 PREC = {"auto": HSB_PREC_AUTO, "fp32": HSB_PREC_FP32, "fp8": HSB_PREC_FP8,
-        "bf16x3": HSB_PREC_BF16X3}
+        "bf16x3": HSB_PREC_BF16X3, "fp4": HSB_PREC_FP4}
 FORM = {"ballistic": HSB_BALLISTIC, "discrete": HSB_DISCRETE}
 SCHEDULE = {"auto": 0, "persistent": 1, "per_step": 2, "resident": 3, "pair": 4}
 THERMOSTAT = {"constant": HSB_HEAT_CONSTANT, "nose_hoover": HSB_HEAT_NOSE_HOOVER}

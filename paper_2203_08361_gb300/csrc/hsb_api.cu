@@ -127,11 +127,15 @@ struct hsb_ctx {
     cudaStream_t own = nullptr;      // private stream (default work stream, capture stream)
     float *J32 = nullptr;            // [Np][Np]
     uint8_t *J8 = nullptr;           // [Np][Np], FP8 e4m3, created on first FP8 run
+    uint8_t *J4 = nullptr;           // [Np][Kp/2], packed e2m1, created on first FP4 run
+    int Kp = 0;                      // Np rounded up to 256 (FP4 row length in values)
     // run buffers, sized for Rcap padded replicas
     int Rcap = 0;
     float *X[2] = {nullptr, nullptr};
     float *Y = nullptr;
     uint8_t *S8[2] = {nullptr, nullptr};
+    uint8_t *S4[2] = {nullptr, nullptr};  // [Rcap][Kp/2] packed e2m1 operand (FP4 runs)
+    TcPlan *plan4 = nullptr;              // tensor maps of J4 and S4
     float *Epart = nullptr;
     float *Tpart = nullptr;  // [nblk][Rp] sums of y^2 for the trace
     double *trace = nullptr; // [n_traced][3] {min E, mean E, mean T_inst}
@@ -196,6 +200,13 @@ void free_run_buffers(hsb_ctx *h)
         tc_plan_destroy(h->plan);
         h->plan = nullptr;
     }
+    if (h->plan4) {
+        tc_plan_destroy(h->plan4);
+        h->plan4 = nullptr;
+    }
+    cudaFree(h->S4[0]);
+    cudaFree(h->S4[1]);
+    h->S4[0] = h->S4[1] = nullptr;
     if (h->bplan) {
         bf16_plan_destroy(h->bplan);
         h->bplan = nullptr;
@@ -290,6 +301,26 @@ hsb_status ensure_fp8(hsb_ctx *h)
     return HSB_OK;
 }
 
+hsb_status ensure_fp4(hsb_ctx *h)
+{
+    if (!h->J4) {
+        CK(dev_alloc(&h->J4, (size_t)h->Np * (h->Kp / 2)), "cudaMalloc J4");
+        CK(launch_j_to_fp4(h->work, h->J32, h->Np, h->Kp, h->J4), "j_to_fp4");
+    }
+    for (int b = 0; b < 2; ++b)
+        if (!h->S4[b]) {
+            CK(dev_alloc(&h->S4[b], (size_t)h->Rcap * (h->Kp / 2)), "cudaMalloc S4");
+            CK(cudaMemsetAsync(h->S4[b], 0, (size_t)h->Rcap * (h->Kp / 2), h->work),
+               "memset S4");
+        }
+    if (!h->plan4) {
+        CK(tc_fp4_plan_create(&h->plan4, h->J4, h->S4[0], h->S4[1], h->Np, h->Kp, h->Rcap),
+           "tc_fp4_plan_create");
+        h->buffers_gen++;  // as for the FP8 plan: captured loops name these maps
+    }
+    return HSB_OK;
+}
+
 hsb_status ensure_bf16(hsb_ctx *h)
 {
     const size_t np = (size_t)h->Np;
@@ -348,11 +379,18 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
     if (prec == HSB_PREC_FP8 && !(p->form == HSB_DISCRETE && h->pm1))
         return set_error(HSB_E_UNSUPPORTED,
                          "FP8 needs the discrete form and couplings in {-1, 0, +1}");
+    if (prec == HSB_PREC_FP4 && !(p->form == HSB_DISCRETE && h->pm1))
+        return set_error(HSB_E_UNSUPPORTED,
+                         "FP4 needs the discrete form and couplings in {-1, 0, +1}");
+    if (prec == HSB_PREC_FP4 && p->schedule != 0 && p->schedule != 2)
+        return set_error(HSB_E_UNSUPPORTED, "FP4 runs one kernel launch per step (schedule 0 "
+                                            "or 2)");
     if (prec == HSB_PREC_BF16X3 && !tc_bf16_persistent_fits(h->Np, Rp_))
         return set_error(HSB_E_UNSUPPORTED,
                          "BF16X3 runs as one persistent kernel; its %d x %d grid does not fit",
                          h->Np / kTileM, Rp_ / kTileR);
-    if (prec != HSB_PREC_FP32 && prec != HSB_PREC_FP8 && prec != HSB_PREC_BF16X3)
+    if (prec != HSB_PREC_FP32 && prec != HSB_PREC_FP8 && prec != HSB_PREC_BF16X3 &&
+        prec != HSB_PREC_FP4)
         return set_error(HSB_E_INVAL, "unknown precision %d", p->prec);
     if (p->trace_every > 0 && prec == HSB_PREC_BF16X3)
         return set_error(HSB_E_UNSUPPORTED, "the trace needs the FP32 or FP8 precision");
@@ -425,6 +463,14 @@ hsb_status enqueue_step(hsb_ctx *h, cudaStream_t st, const RunCfg &c, int k, int
             CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[cur], nullptr,
                                   h->Ebest, h->Sbest),
                "best kernel");
+    } else if (c.prec == HSB_PREC_FP4) {  // S4[cur] -> S4[cur^1], X and Y in place
+        CK(launch_tc_fp4_step(st, h->plan4, cur, en, false, h->N, c.Rp, h->X[0], h->Y, c.pk[k],
+                              c.c, h->Epart, tpart, h->S4[cur ^ 1], h->err, gv),
+           "fp4 step kernel");
+        if (ev)
+            CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, nullptr,
+                                  h->Ebest, h->Sbest, h->S4[cur], h->Kp),
+               "best kernel");
     } else {  // FP8: S8[cur] -> S8[cur^1], X and Y in place
         CK(launch_tc_fp8_step(st, h->plan, cur, en, false, h->N, c.Rp, h->X[0], h->Y, c.pk[k],
                               c.c, h->Epart, tpart, h->S8[cur ^ 1], h->err, gv),
@@ -458,6 +504,13 @@ hsb_status enqueue_final(hsb_ctx *h, cudaStream_t st, const RunCfg &c)
         CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, h->X[cur], nullptr,
                               h->Ebest, h->Sbest),
            "best kernel");
+    } else if (c.prec == HSB_PREC_FP4) {
+        CK(launch_tc_fp4_step(st, h->plan4, cur, true, true, h->N, c.Rp, h->X[0], h->Y, 0.f, c.c,
+                              h->Epart, nullptr, nullptr, h->err),
+           "fp4 energy kernel");
+        CK(launch_best_update(st, h->Epart, nblk, h->N, h->Np, c.R, c.Rp, nullptr, nullptr,
+                              h->Ebest, h->Sbest, h->S4[cur], h->Kp),
+           "best kernel");
     } else {
         CK(launch_tc_fp8_step(st, h->plan, cur, true, true, h->N, c.Rp, h->X[0], h->Y, 0.f, c.c,
                               h->Epart, nullptr, nullptr, h->err),
@@ -490,6 +543,8 @@ long long count_launches(const hsb_ctx *h, const RunCfg &c)
     }
     if (!h->pm1)
         n += 1;
+    if (c.prec == HSB_PREC_FP4)
+        n += 1;  // sign of x0 packed into the e2m1 operand
     if (c.thermo)
         n += 1 + c.steps;  // xi init, one xi update per step
     return n;
@@ -533,6 +588,11 @@ hsb_status prepare(hsb_ctx *h, const RunCfg &c)
         return s;
     if (c.prec == HSB_PREC_FP8) {
         s = ensure_fp8(h);
+        if (s != HSB_OK)
+            return s;
+    }
+    if (c.prec == HSB_PREC_FP4) {
+        s = ensure_fp4(h);
         if (s != HSB_OK)
             return s;
     }
@@ -1047,6 +1107,9 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
     CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R, c.Rp,
                    h->X[0], h->Y, c.prec == HSB_PREC_FP8 ? h->S8[0] : nullptr, h->Ebest),
        "init kernel");
+    if (c.prec == HSB_PREC_FP4)
+        CK(launch_sign_to_fp4(h->work, h->X[0], h->N, h->Np, h->Kp, c.Rp, h->S4[0]),
+           "fp4 sign kernel");
     if (c.thermo)
         CK(launch_nh_init(h->work, c.R, c.Rp, c.nh_xi0, c.dt64, h->xi, h->gvec), "xi init");
     h->have_xi = c.thermo != 0;
@@ -1254,6 +1317,7 @@ hsb_status hsb_create(const float *J, int N, hsb_handle *out)
     cudaGetDevice(&h->device);
     h->N = N;
     h->Np = round_up(N, kTileM);
+    h->Kp = round_up(h->Np, 256);
     h->pm1 = pm1;
     h->sigma = sqrt(sum2 / ((double)N * (double)(N - 1)));
     h->jscale = energy_scale_exp(maxabs);
@@ -1309,6 +1373,7 @@ void hsb_destroy(hsb_handle h)
     free_run_buffers(h);
     cudaFree(h->J32);
     cudaFree(h->J8);
+    cudaFree(h->J4);
     cudaFree(h->Jcat);
     cudaFree(h->trace);
     cudaFree(h->err);
@@ -1492,6 +1557,9 @@ hsb_status hsb_advance(hsb_handle h, const hsb_params *p, int R, int steps, int 
     if (c.prec == HSB_PREC_FP8)
         CK(launch_sign_to_fp8(h->work, h->X[0], h->N, h->Np, c.Rp, h->S8[k_begin & 1]),
            "sign kernel");
+    if (c.prec == HSB_PREC_FP4)
+        CK(launch_sign_to_fp4(h->work, h->X[0], h->N, h->Np, h->Kp, c.Rp, h->S4[k_begin & 1]),
+           "fp4 sign kernel");
     if (c.prec == HSB_PREC_BF16X3) {
         CK(launch_split_state(h->work, h->X[0], h->N, h->Np, c.Rp, c.form, h->Xcat[0]),
            "split state");
@@ -1657,6 +1725,18 @@ hsb_status hsb_set_couplings(hsb_handle h, const float *J)
             }
             cudaFree(h->J8);
             h->J8 = nullptr;
+        }
+    }
+    if (h->J4) {
+        if (pm1) {
+            CK(launch_j_to_fp4(h->work, h->J32, h->Np, h->Kp, h->J4), "j_to_fp4");
+        } else {
+            if (h->plan4) {
+                tc_plan_destroy(h->plan4);
+                h->plan4 = nullptr;
+            }
+            cudaFree(h->J4);
+            h->J4 = nullptr;
         }
     }
     if (h->Jcat)

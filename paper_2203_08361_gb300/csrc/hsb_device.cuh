@@ -38,6 +38,11 @@ __device__ __forceinline__ float init_uniform(uint64_t s_inst, uint32_t r, uint3
     return __fmul_rn(v, scale);
 }
 
+// e2m1 (FP4) codes of +1 and -1 (sign 0/1, exponent 01, mantissa 0), packed
+// two per byte with the even index in the low nibble; 0 is 0x0.
+constexpr uint32_t kFp4PlusOne = 0x2;
+constexpr uint32_t kFp4MinusOne = 0xA;
+
 // sgn(x) as an FP8 byte; +1 for x >= 0 (including -0.0).
 __device__ __forceinline__ uint8_t fp8_sign(float x)
 {

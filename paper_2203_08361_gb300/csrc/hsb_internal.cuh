@@ -90,10 +90,12 @@ cudaError_t launch_trace_reduce_many(cudaStream_t st, const float *Epart, const 
                                      unsigned *tickets, double *out);
 
 // Best tracking after an evaluation: E_r = -1/2 sum_blocks Epart; if E_r <
-// Ebest[r] store it with the spins sgn(x) read from X (fp32) or S8 (fp8).
+// Ebest[r] store it with the spins sgn(x) read from X (fp32), S8 (fp8) or the
+// packed S4 (fp4, rows of Kp/2 bytes).
 cudaError_t launch_best_update(cudaStream_t st, const float *Epart, int nblk, int N, int Np,
                                int R, int Rp, const float *X, const uint8_t *S8,
-                               double *Ebest, int8_t *Sbest);
+                               double *Ebest, int8_t *Sbest, const uint8_t *S4 = nullptr,
+                               int Kp = 0);
 
 // Energy of the final best spins in binary64 (Eq. (eq_Ising)) for general J.
 cudaError_t launch_final_energy_f64(cudaStream_t st, const float *J32, int N, int Np, int R,
@@ -129,6 +131,7 @@ struct TcPlan {
     CUtensorMap mapBw[2];  // 2-D S8a / S8b, box 128 B x 256 rows (per-step kernel)
     CUtensorMap mapJ64;    // 2-D J8, box 128 B x 64 rows (CTA-pair kernel)
     int Np, Rp;            // Rp: replica capacity the maps were encoded for
+    int Kp = 0;            // FP4 plans: row length in e2m1 values (Np rounded up to 256)
 };
 
 // tcgen05 FP8 step: F = J8 * S8cur^T on the tensor cores (FP32 accumulation
@@ -142,6 +145,23 @@ cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, 
                                bool energy_only, int N, int Rp, float *X, float *Y, float pk,
                                StepConsts c, float *Epart, float *Tpart, uint8_t *S8next,
                                int *err, const float *gvec = nullptr);
+
+// The same step with packed FP4 e2m1 operands (tcgen05 kind::mxf4, unit
+// block scales): J4 [Np][Kp/2] and S4 [Rcap][Kp/2] bytes, two values per byte
+// (+1 = 0x2, -1 = 0xA, 0 = 0x0, the even index in the low nibble), Kp = Np
+// rounded up to 256 with zero padding.  Only mapA and mapBw[2] (box 192 rows)
+// of an FP4 plan are encoded; it serves launch_tc_fp4_step alone.
+cudaError_t tc_fp4_plan_create(TcPlan **out, const uint8_t *J4, const uint8_t *S4a,
+                               const uint8_t *S4b, int Np, int Kp, int Rp);
+cudaError_t launch_tc_fp4_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
+                               bool energy_only, int N, int Rp, float *X, float *Y, float pk,
+                               StepConsts c, float *Epart, float *Tpart, uint8_t *S4next,
+                               int *err, const float *gvec = nullptr);
+// float32 couplings (+/-1/0) -> packed e2m1 J4 [Np][Kp/2]; sgn(X) -> packed
+// S4 [Rp][Kp/2] (padded spins and the K padding 0).
+cudaError_t launch_j_to_fp4(cudaStream_t st, const float *J32, int Np, int Kp, uint8_t *J4);
+cudaError_t launch_sign_to_fp4(cudaStream_t st, const float *X, int N, int Np, int Kp, int Rp,
+                               uint8_t *S4);
 
 // ---- hsb_persist.cu --------------------------------------------------------
 // Arguments of the persistent FP8 kernel: `nsteps` updates starting at global

@@ -136,7 +136,7 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap *map)
 // byte offset >> 4 (bits 32-45), the fixed value 1 (bits 46-47) and swizzle
 // mode 2 = 128-byte (bits 61-63).  Advancing K inside the 128-byte row adds
 // the byte offset to the start address.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+__host__ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
     d |= (uint64_t)1u << 16;
@@ -151,6 +151,35 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 __host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N)
 {
     return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of the block-scaled kind::mxf4 (PTX ISA, tcgen05
+// instruction descriptor for .kind::mxf4): bits 0-2 sparsity (0: dense),
+// bits 4-5 scale-factor id of B (0), bits 7-9 A format and 10-12 B format
+// (E2M1 = 1), bits 13-14 negation (0), bits 15-16 K-major A and B (0), N >> 3
+// at bits 17-22, scale-factor type at bit 23 (1: UE8M0), M >> 4 at bits
+// 24-28, scale-factor id of A at bits 29-30 (0), bit 31 (0: K = 64).
+__host__ __device__ constexpr uint32_t idesc_mxf4_e2m1(int M, int N)
+{
+    return (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | (1u << 23) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+// Block-scaled MMA with packed e2m1 operands (32 bytes = 64 K elements per
+// operand row), scale factors of A and B read from tensor memory, issued by
+// one elected lane of a converged warp.
+__device__ __forceinline__ void mma_mxf4_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                               uint32_t idesc, uint32_t tmem_sfa,
+                                               uint32_t tmem_sfb, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %3, 0;\n\t"
+        "@e tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %4, "
+        "[%5], [%6], p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(idesc), "r"(tmem_sfa), "r"(tmem_sfb)
+        : "memory");
 }
 
 __device__ __forceinline__ void mma_fp8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,

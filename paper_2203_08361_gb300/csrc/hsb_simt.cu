@@ -552,7 +552,8 @@ cudaError_t launch_trace_reduce(cudaStream_t st, const float *Epart, const float
 __global__ void best_update_kernel(const float *__restrict__ Epart, int nblk, int N, int Np,
                                    int Rp, const float *__restrict__ X,
                                    const uint8_t *__restrict__ S8, double *__restrict__ Ebest,
-                                   int8_t *__restrict__ Sbest)
+                                   int8_t *__restrict__ Sbest, const uint8_t *__restrict__ S4,
+                                   int Kp)
 {
     const int r = blockIdx.x;
     __shared__ int take;
@@ -572,6 +573,9 @@ __global__ void best_update_kernel(const float *__restrict__ Epart, int nblk, in
         int8_t sp;
         if (X)
             sp = X[(size_t)r * Np + i] >= 0.f ? 1 : -1;
+        else if (S4)
+            sp = ((S4[(size_t)r * (Kp / 2) + (i >> 1)] >> (4 * (i & 1))) & 15u) == kFp4PlusOne ? 1
+                                                                                           : -1;
         else
             sp = S8[(size_t)r * Np + i] == kFp8PlusOne ? 1 : -1;
         Sbest[(size_t)r * N + i] = sp;
@@ -580,9 +584,9 @@ __global__ void best_update_kernel(const float *__restrict__ Epart, int nblk, in
 
 cudaError_t launch_best_update(cudaStream_t st, const float *Epart, int nblk, int N, int Np,
                                int R, int Rp, const float *X, const uint8_t *S8,
-                               double *Ebest, int8_t *Sbest)
+                               double *Ebest, int8_t *Sbest, const uint8_t *S4, int Kp)
 {
-    best_update_kernel<<<R, 256, 0, st>>>(Epart, nblk, N, Np, Rp, X, S8, Ebest, Sbest);
+    best_update_kernel<<<R, 256, 0, st>>>(Epart, nblk, N, Np, Rp, X, S8, Ebest, Sbest, S4, Kp);
     return cudaGetLastError();
 }
 
@@ -776,6 +780,62 @@ cudaError_t launch_j_to_fp8(cudaStream_t st, const float *J32, int Np, uint8_t *
     if (blocks > 152 * 16)
         blocks = 152 * 16;
     j_to_fp8_kernel<<<blocks, 256, 0, st>>>(J32, total, J8);
+    return cudaGetLastError();
+}
+
+// Packed e2m1 operands: two values per byte, the even index in the low nibble.
+__device__ __forceinline__ uint32_t fp4_nibble_of_coupling(float v)
+{
+    return v > 0.f ? kFp4PlusOne : (v < 0.f ? kFp4MinusOne : 0u);
+}
+
+__global__ void j_to_fp4_kernel(const float *__restrict__ J, int Np, int Kp, size_t total,
+                                uint8_t *__restrict__ J4)
+{
+    const int bpr = Kp / 2;  // bytes per row
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t row = e / bpr;
+        const int j = 2 * (int)(e % bpr);
+        const uint32_t lo = j < Np ? fp4_nibble_of_coupling(J[row * Np + j]) : 0u;
+        const uint32_t hi = j + 1 < Np ? fp4_nibble_of_coupling(J[row * Np + j + 1]) : 0u;
+        J4[e] = (uint8_t)(lo | (hi << 4));
+    }
+}
+
+cudaError_t launch_j_to_fp4(cudaStream_t st, const float *J32, int Np, int Kp, uint8_t *J4)
+{
+    const size_t total = (size_t)Np * (Kp / 2);
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    j_to_fp4_kernel<<<blocks, 256, 0, st>>>(J32, Np, Kp, total, J4);
+    return cudaGetLastError();
+}
+
+__global__ void sign_to_fp4_kernel(const float *__restrict__ X, int N, int Np, int Kp,
+                                   size_t total, uint8_t *__restrict__ S4)
+{
+    const int bpr = Kp / 2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = e / bpr;
+        const int i = 2 * (int)(e % bpr);
+        const uint32_t lo = i < N ? (X[r * Np + i] >= 0.f ? kFp4PlusOne : kFp4MinusOne) : 0u;
+        const uint32_t hi =
+            i + 1 < N ? (X[r * Np + i + 1] >= 0.f ? kFp4PlusOne : kFp4MinusOne) : 0u;
+        S4[e] = (uint8_t)(lo | (hi << 4));
+    }
+}
+
+cudaError_t launch_sign_to_fp4(cudaStream_t st, const float *X, int N, int Np, int Kp, int Rp,
+                               uint8_t *S4)
+{
+    const size_t total = (size_t)Rp * (Kp / 2);
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 16)
+        blocks = 152 * 16;
+    sign_to_fp4_kernel<<<blocks, 256, 0, st>>>(X, N, Np, Kp, total, S4);
     return cudaGetLastError();
 }
 

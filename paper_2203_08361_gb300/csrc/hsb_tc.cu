@@ -49,20 +49,34 @@ namespace hsb {
 namespace {
 
 constexpr int kBM = 128;            // spins per tile (MMA M, tensor-memory lanes)
-constexpr int kBN = 256;            // replicas per tile (MMA N, accumulator columns)
+constexpr int kBN = 256;            // replicas per FP8 tile (MMA N, accumulator columns)
+constexpr int kBN4 = 192;           // replicas per FP4 tile: two accumulators and the
+                                    // unit block scales fit the 512 tensor-memory columns
 constexpr int kBK = 128;            // K bytes per stage (one 128-byte swizzle row)
-constexpr int kStages = 4;
+constexpr int kStages = 4;          // even: every stage is served by one issuer pair
 constexpr int kStageA = kBM * kBK;  // 16 KB
-constexpr int kStageB = kBN * kBK;  // 32 KB
 constexpr int kIssuers = 4;
 constexpr int kMmaWarp = kIssuers;
 constexpr int kFirstEpi = kMmaWarp + 1;
 constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 32 * kFirstEpi + kEpiThreads;
-constexpr uint32_t kTmemCols = 2 * kBN;  // two accumulators
-constexpr uint32_t kIdesc = ptx::idesc_e4m3_f32(kBM, kBN);
+constexpr uint32_t kTmemCols = 512;  // two accumulators (+ the FP4 block scales)
 
+// FP8: kind::f8f6f4 e4m3, K = 32 per instruction.  FP4: kind::mxf4 with packed
+// e2m1 operands (+1 = 0x2, -1 = 0xA, 0 = 0x0, element 2j in the low nibble of
+// byte j), K = 64 per instruction, block scales UE8M0 1.0 read from tensor
+// memory; both take 32 bytes of each operand row per instruction.
+template <bool FP4>
+struct StepShape {
+    static constexpr int BN = FP4 ? kBN4 : kBN;
+    static constexpr int StageB = BN * kBK;
+    static constexpr uint32_t ColScale = 2 * BN;  // FP4 block scales (16 columns)
+    static constexpr uint32_t Idesc =
+        FP4 ? ptx::idesc_mxf4_e2m1(kBM, BN) : ptx::idesc_e4m3_f32(kBM, BN);
+};
+
+template <int BN>
 struct __align__(8) TcShared {
     uint64_t full[kStages];
     uint64_t empty[kStages];
@@ -72,13 +86,21 @@ struct __align__(8) TcShared {
     int last_use[kStages];   // last use of each stage a copy was issued for
     uint32_t tmem_base;
     int abort;
-    float red[4][kBN];
-    float tred[4][kBN];
+    float red[4][BN];
+    float tred[4][BN];
 };
 
-constexpr size_t kSmemBytes = 1024 /* alignment slack */ + (size_t)kStages * (kStageA + kStageB) +
-                              sizeof(TcShared);
-static_assert(kSmemBytes <= 232448, "shared memory per CTA is limited to 227 KB");
+template <bool FP4>
+constexpr size_t step_smem_bytes()
+{
+    return 1024 /* alignment slack */ +
+           (size_t)kStages * (kStageA + StepShape<FP4>::StageB) +
+           sizeof(TcShared<StepShape<FP4>::BN>);
+}
+static_assert(step_smem_bytes<false>() <= 232448, "shared memory per CTA is limited to 227 KB");
+static_assert(step_smem_bytes<true>() <= 232448, "shared memory per CTA is limited to 227 KB");
+static_assert(2 * kBN <= (int)kTmemCols && 2 * kBN4 + 32 <= (int)kTmemCols,
+              "accumulators and block scales exceed tensor memory");
 
 __device__ __forceinline__ bool epi_bar_or(bool pred)
 {
@@ -103,16 +125,21 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *a
     return __all_sync(0xFFFFFFFFu, ok);
 }
 
+template <bool FP4>
 __device__ __forceinline__ void mma_elect(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t accumulate)
+                                          uint32_t accumulate, uint32_t tmem_scale)
 {
-    asm volatile(
-        "{\n\t.reg .pred p, e;\n\t"
-        "elect.sync _|e, 0xffffffff;\n\t"
-        "setp.ne.b32 p, %3, 0;\n\t"
-        "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %4, p;\n\t}" ::"r"(tmem_d),
-        "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(kIdesc)
-        : "memory");
+    if (FP4)
+        ptx::mma_mxf4_elect(tmem_d, adesc, bdesc, StepShape<true>::Idesc, tmem_scale, tmem_scale,
+                            accumulate);
+    else
+        asm volatile(
+            "{\n\t.reg .pred p, e;\n\t"
+            "elect.sync _|e, 0xffffffff;\n\t"
+            "setp.ne.b32 p, %3, 0;\n\t"
+            "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %4, p;\n\t}" ::"r"(tmem_d),
+            "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(StepShape<false>::Idesc)
+            : "memory");
 }
 
 __device__ __forceinline__ void commit_elect(uint64_t *bar)
@@ -127,24 +154,29 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
 
 }  // namespace
 
+// Snext: the next step's operand, FP8 bytes [Rp][Np] or packed FP4 [Rp][Kp/2]
+// (Kp = Np rounded up to 256: Kp/2 bytes per row, the padding zero).
+template <bool FP4>
 __global__ void __launch_bounds__(kThreads, 1)
-tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
-                   const __grid_constant__ CUtensorMap tmapB, int N, int Np, int Rp, int nrb,
-                   int ntiles, float *__restrict__ X, float *__restrict__ Y,
-                   uint8_t *__restrict__ S8next, float pk, StepConsts c, int energy,
-                   int energy_only, float *__restrict__ Epart, float *__restrict__ Tpart,
-                   int *__restrict__ err, const float *__restrict__ gvec)
+tc_step_kernel(const __grid_constant__ CUtensorMap tmapA,
+               const __grid_constant__ CUtensorMap tmapB, int N, int Np, int Kp, int Rp, int nrb,
+               int ntiles, float *__restrict__ X, float *__restrict__ Y,
+               uint8_t *__restrict__ Snext, float pk, StepConsts c, int energy, int energy_only,
+               float *__restrict__ Epart, float *__restrict__ Tpart, int *__restrict__ err,
+               const float *__restrict__ gvec)
 {
+    constexpr int kBN = StepShape<FP4>::BN;  // replicas per tile
+    constexpr int kStageB = StepShape<FP4>::StageB;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = base;
     uint8_t *sB = base + (size_t)kStages * kStageA;
-    TcShared *sh = reinterpret_cast<TcShared *>(sB + (size_t)kStages * kStageB);
+    TcShared<kBN> *sh = reinterpret_cast<TcShared<kBN> *>(sB + (size_t)kStages * kStageB);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int nk = Np / kBK;
+    const int nk = (FP4 ? Kp / 2 : Np) / kBK;  // 128-byte K chunks of a row
     // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
     const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
@@ -173,6 +205,22 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
+    if (FP4) {
+        // unit block scales: UE8M0 0x7F (2^0) in 16 columns of every lane; the
+        // scale reads of every instruction fall inside them
+        if (warp >= kFirstEpi && warp < kFirstEpi + 4) {
+            uint32_t one[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                one[j] = 0x7F7F7F7Fu;
+            ptx::tmem_st16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + StepShape<FP4>::ColScale,
+                           one);
+            ptx::tmem_st_wait();
+        }
+        ptx::tc_fence_before();
+        __syncthreads();
+        ptx::tc_fence_after();
+    }
 
     if (warp < kIssuers) {
         // ------------------------------------------------------- TMA issuers
@@ -229,8 +277,9 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                 const uint64_t bd = bdesc0 + (uint64_t)((s * kStageB) >> 4);
 #pragma unroll
                 for (int kk = 0; kk < kBK / 32; ++kk)
-                    mma_elect(dcol, ad + (uint64_t)((kk * 32) >> 4), bd + (uint64_t)((kk * 32) >> 4),
-                              (kc | kk) != 0 ? 1u : 0u);
+                    mma_elect<FP4>(dcol, ad + (uint64_t)((kk * 32) >> 4),
+                                   bd + (uint64_t)((kk * 32) >> 4), (kc | kk) != 0 ? 1u : 0u,
+                                   tmem + StepShape<FP4>::ColScale);
                 commit_elect(&sh->empty[s]);
             }
             if (!ok)
@@ -309,7 +358,17 @@ tc_fp8_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                                 sb_update(fj, x0, y0, pk, cr, xn, yn);
                                 X[e] = xn;
                                 Y[e] = yn;
-                                S8next[e] = live ? fp8_sign(xn) : (uint8_t)0;
+                                if (FP4) {
+                                    // spins i (even lane) and i + 1 share a byte
+                                    const uint32_t nib =
+                                        live ? (xn >= 0.f ? kFp4PlusOne : kFp4MinusOne) : 0u;
+                                    const uint32_t up = __shfl_down_sync(0xFFFFFFFFu, nib, 1);
+                                    if ((lane & 1) == 0)
+                                        Snext[(size_t)r * (Kp / 2) + (i >> 1)] =
+                                            (uint8_t)(nib | (up << 4));
+                                } else {
+                                    Snext[e] = live ? fp8_sign(xn) : (uint8_t)0;
+                                }
                             }
                         }
                         tv[u] = term;
@@ -473,9 +532,37 @@ cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S
         delete p;
         return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaFuncSetAttribute(tc_fp8_step_kernel,
+    cudaError_t e = cudaFuncSetAttribute(tc_step_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kSmemBytes);
+                                         (int)step_smem_bytes<false>());
+    if (e != cudaSuccess) {
+        delete p;
+        return e;
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+cudaError_t tc_fp4_plan_create(TcPlan **out, const uint8_t *J4, const uint8_t *S4a,
+                               const uint8_t *S4b, int Np, int Kp, int Rp)
+{
+    *out = nullptr;
+    if (Np % kBM != 0 || Kp % 256 != 0 || Kp < Np || Rp % 128 != 0)
+        return cudaErrorInvalidValue;
+    TcPlan *p = new TcPlan();
+    p->Np = Np;
+    p->Rp = Rp;
+    p->Kp = Kp;
+    // rows of Kp/2 bytes; a 128-byte box row holds 256 e2m1 values
+    if (!encode_u8(&p->mapA, J4, (uint64_t)Np, (uint64_t)Kp / 2, kBM) ||
+        !encode_u8(&p->mapBw[0], S4a, (uint64_t)Rp, (uint64_t)Kp / 2, kBN4) ||
+        !encode_u8(&p->mapBw[1], S4b, (uint64_t)Rp, (uint64_t)Kp / 2, kBN4)) {
+        delete p;
+        return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(tc_step_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_smem_bytes<true>());
     if (e != cudaSuccess) {
         delete p;
         return e;
@@ -486,15 +573,19 @@ cudaError_t tc_fp8_plan_create(TcPlan **out, const uint8_t *J8, const uint8_t *S
 
 void tc_plan_destroy(TcPlan *p) { delete p; }
 
-cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
-                               bool energy_only, int N, int Rp, float *X, float *Y, float pk,
-                               StepConsts c, float *Epart, float *Tpart, uint8_t *S8next,
-                               int *err, const float *gvec)
+namespace {
+
+template <bool FP4>
+cudaError_t launch_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
+                        bool energy_only, int N, int Rp, float *X, float *Y, float pk,
+                        StepConsts c, float *Epart, float *Tpart, uint8_t *Snext, int *err,
+                        const float *gvec)
 {
     // Rp (this run's padded replica count) may be below the capacity the
     // tensor maps were encoded for; Epart rows are Rp long.  A last tile that
-    // reaches past Rp reads operand rows that are never stored back.
-    if (!plan || Rp % 128 != 0 || Rp > plan->Rp)
+    // reaches past Rp reads operand rows that are never stored back (past the
+    // capacity the copy fills zeros).
+    if (!plan || Rp % 128 != 0 || Rp > plan->Rp || (FP4 && plan->Kp < plan->Np))
         return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -502,13 +593,34 @@ cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, 
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess)
         return e;
-    const int nrb = (Rp + kBN - 1) / kBN;
+    constexpr int bn = StepShape<FP4>::BN;
+    const int nrb = (Rp + bn - 1) / bn;
     const int ntiles = (plan->Np / kBM) * nrb;
     const int grid = ntiles < sms ? ntiles : sms;
-    tc_fp8_step_kernel<<<grid, kThreads, kSmemBytes, st>>>(
-        plan->mapA, plan->mapBw[parity & 1], N, plan->Np, Rp, nrb, ntiles, X, Y, S8next, pk, c,
-        energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err, gvec);
+    tc_step_kernel<FP4><<<grid, kThreads, step_smem_bytes<FP4>(), st>>>(
+        plan->mapA, plan->mapBw[parity & 1], N, plan->Np, plan->Kp, Rp, nrb, ntiles, X, Y, Snext,
+        pk, c, energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err, gvec);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
+                               bool energy_only, int N, int Rp, float *X, float *Y, float pk,
+                               StepConsts c, float *Epart, float *Tpart, uint8_t *S8next,
+                               int *err, const float *gvec)
+{
+    return launch_step<false>(st, plan, parity, energy, energy_only, N, Rp, X, Y, pk, c, Epart,
+                              Tpart, S8next, err, gvec);
+}
+
+cudaError_t launch_tc_fp4_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
+                               bool energy_only, int N, int Rp, float *X, float *Y, float pk,
+                               StepConsts c, float *Epart, float *Tpart, uint8_t *S4next,
+                               int *err, const float *gvec)
+{
+    return launch_step<true>(st, plan, parity, energy, energy_only, N, Rp, X, Y, pk, c, Epart,
+                             Tpart, S4next, err, gvec);
 }
 
 }  // namespace hsb

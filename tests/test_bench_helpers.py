@@ -54,7 +54,7 @@ def test_every_workload_definition_builds_valid_parameters():
             "eval_every", "trace_every", "peak", "dtype"}
     for key, w in bench.OTHER.items():
         assert need <= set(w), key
-        assert w["peak"] in ("fp8", "bf16") and w["kind"] in ("single", "batch")
+        assert w["peak"] in ("fp8", "fp4", "bf16") and w["kind"] in ("single", "batch")
         p = hsb.params(w["form"], w["prec"], c1=w["c1"], dt=w["dt"], gamma=w["gamma"],
                        eval_every=w["eval_every"], trace_every=w["trace_every"],
                        **w.get("nh", {}))

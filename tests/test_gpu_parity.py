@@ -1,6 +1,6 @@
 """GPU parity: the CUDA path, called through the C ABI, against the CPU oracle.
 
-Discrete form with +/-1 couplings (FP8 tensor cores and plain FP32): positions,
+Discrete form with +/-1 couplings (FP8 and FP4 tensor cores, plain FP32): positions,
 momenta, best spins and best energies equal the binary32 oracle bit for bit.
 Plain FP32 for every form and coupling type: bit for bit as well (both sides
 form the force with fused multiply-adds over j ascending).  Sizes span several
@@ -32,7 +32,8 @@ def _assert_same(got_x, got_y, spins, energy, ref, rows=None):
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "resident"),
-                                           ("fp8", "per_step"), ("fp32", "auto")])
+                                           ("fp8", "per_step"), ("fp4", "per_step"),
+                                           ("fp32", "auto")])
 @pytest.mark.parametrize("n,R", [(128, 128), (300, 40), (257, 130), (2, 3), (700, 300),
                                  (1100, 130), (2048, 128)])
 def test_discrete_pm1_bit_exact(prec, schedule, n, R):
@@ -86,7 +87,8 @@ def test_small_ballistic_pm1_workload_fp32():
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "resident"),
-                                           ("fp8", "per_step"), ("fp32", "auto")])
+                                           ("fp8", "per_step"), ("fp4", "per_step"),
+                                           ("fp32", "auto")])
 def test_one_step_and_split_runs(prec, schedule):
     n, R, steps = 260, 70, 50
     J = synth.sk_pm1(n, 4)
@@ -108,8 +110,9 @@ def test_one_step_and_split_runs(prec, schedule):
         np.testing.assert_array_equal(ya, yb)
 
 
+@pytest.mark.parametrize("prec", ["fp8", "fp4"])
 @pytest.mark.parametrize("n", [2000, 16384])
-def test_fp8_force_is_the_exact_integer_product(n):
+def test_fp8_force_is_the_exact_integer_product(n, prec):
     # With a0 = 2^-40, c0 = 1, dt = 2^-20 and y = 0, one step leaves
     # y' = fl(fl(f - p x) dt) with |p x| < 2^-60, so round(y'/dt) = f, the force.
     # Replica 0 has x = 2^-30 J[0, :] (x_0 = 0 counts as +1), so f_0 = N - 1.
@@ -119,7 +122,7 @@ def test_fp8_force_is_the_exact_integer_product(n):
     x0 = (rng.choice([-1.0, 1.0], size=(R, n)) * 2.0**-30).astype(np.float32)
     x0[0] = (J[0] * 2.0**-30).astype(np.float32)
     y0 = np.zeros((R, n), np.float32)
-    p = hsb.params("discrete", "fp8", a0=2.0**-40, c0=1.0, dt=2.0**-20, gamma=0.0)
+    p = hsb.params("discrete", prec, a0=2.0**-40, c0=1.0, dt=2.0**-20, gamma=0.0)
     with hsb.Solver(J) as s:
         x1, y1 = s.advance(p, 4, 0, 1, x0, y0)
     f = np.rint(y1.astype(np.float64) / 2.0**-20).astype(np.int64)
@@ -263,7 +266,7 @@ def _dilute_pm1(n, seed, p_zero=0.5):
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
-                                           ("fp32", "auto")])
+                                           ("fp4", "per_step"), ("fp32", "auto")])
 @pytest.mark.parametrize("n,R,steps,ev", [
     (129, 1, 1, 0),       # one replica, one step, final evaluation only
     (129, 1, 37, 0),      # final evaluation only (the 700-spin protocol)
@@ -283,7 +286,7 @@ def test_edge_cases_bit_exact(prec, schedule, n, R, steps, ev):
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
-                                           ("fp32", "auto")])
+                                           ("fp4", "per_step"), ("fp32", "auto")])
 def test_diluted_couplings_bit_exact(prec, schedule):
     n, R, steps, seed, ev = 500, 70, 120, 4, 30
     J = _dilute_pm1(n, 8)
