@@ -11,15 +11,19 @@
 // in tensor memory is exact and the force equals the integer J sgn(x).
 //
 // A persistent grid, one CTA per SM, walks tiles of 128 spins x 256
-// replicas, replica blocks fastest, so that the CTAs running at one time share
-// a few row blocks of J in L2 (J streams from HBM about once per step) and
-// every S chunk is reused by all of them.  Per CTA:
+// replicas (FP4: 192) band by band: the replica blocks are cut into as few
+// bands as keep a band's S rows within an L2 budget, and inside a band the
+// replica blocks run fastest, so that the CTAs running at one time share a
+// few row blocks of J in L2 (J streams from HBM once per band and step) and
+// the band's S rows stay in L2 for all row blocks.  x and y go through L2
+// with an evict-first policy.  Per CTA:
 //   warps 0-3  TMA issuers: warps 0 and 1 load the J box (128 rows x 128 B)
 //              of even and odd K chunks, warps 2 and 3 the S box (256 rows x
-//              128 B), into a ring of four 48 KB stages.  Copies from one
-//              thread complete one after another, so four issuing threads
-//              keep the ring full; every stage is always served by the same
-//              two issuers, so their parity waits see each phase in order;
+//              128 B), into a ring of four 48 KB stages (FP4: 40 KB).
+//              Copies from one thread complete one after another, so four
+//              issuing threads keep the ring full; every stage is always
+//              served by the same two issuers, so their parity waits see each
+//              phase in order;
 //   warp 4     MMA: tcgen05.mma kind::f8f6f4, M = 128, N = 256, K = 32,
 //              issued from an elected lane of the converged warp (a 128 x 256
 //              x 32 instruction keeps the tensor core busy even from one warp)
@@ -53,7 +57,6 @@ constexpr int kBN = 256;            // replicas per FP8 tile (MMA N, accumulator
 constexpr int kBN4 = 192;           // replicas per FP4 tile: two accumulators and the
                                     // unit block scales fit the 512 tensor-memory columns
 constexpr int kBK = 128;            // K bytes per stage (one 128-byte swizzle row)
-constexpr int kStages = 4;          // even: every stage is served by one issuer pair
 constexpr int kStageA = kBM * kBK;  // 16 KB
 constexpr int kIssuers = 4;
 constexpr int kMmaWarp = kIssuers;
@@ -62,6 +65,9 @@ constexpr int kEpiWarps = 8;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kThreads = 32 * kFirstEpi + kEpiThreads;
 constexpr uint32_t kTmemCols = 512;  // two accumulators (+ the FP4 block scales)
+// S rows of one replica band: the band stays in L2 while J and x, y stream
+// past it (data read by SMs of both dies may be held in both halves of L2)
+constexpr size_t kSBandBytes = (size_t)40 << 20;
 
 // FP8: kind::f8f6f4 e4m3, K = 32 per instruction.  FP4: kind::mxf4 with packed
 // e2m1 operands (+1 = 0x2, -1 = 0xA, 0 = 0x0, element 2j in the low nibble of
@@ -71,12 +77,13 @@ template <bool FP4>
 struct StepShape {
     static constexpr int BN = FP4 ? kBN4 : kBN;
     static constexpr int StageB = BN * kBK;
+    static constexpr int Stages = 4;
     static constexpr uint32_t ColScale = 2 * BN;  // FP4 block scales (16 columns)
     static constexpr uint32_t Idesc =
         FP4 ? ptx::idesc_mxf4_e2m1(kBM, BN) : ptx::idesc_e4m3_f32(kBM, BN);
 };
 
-template <int BN>
+template <int BN, int kStages>
 struct __align__(8) TcShared {
     uint64_t full[kStages];
     uint64_t empty[kStages];
@@ -94,8 +101,8 @@ template <bool FP4>
 constexpr size_t step_smem_bytes()
 {
     return 1024 /* alignment slack */ +
-           (size_t)kStages * (kStageA + StepShape<FP4>::StageB) +
-           sizeof(TcShared<StepShape<FP4>::BN>);
+           (size_t)StepShape<FP4>::Stages * (kStageA + StepShape<FP4>::StageB) +
+           sizeof(TcShared<StepShape<FP4>::BN, StepShape<FP4>::Stages>);
 }
 static_assert(step_smem_bytes<false>() <= 232448, "shared memory per CTA is limited to 227 KB");
 static_assert(step_smem_bytes<true>() <= 232448, "shared memory per CTA is limited to 227 KB");
@@ -154,25 +161,43 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
 
 }  // namespace
 
+// Tile t -> (row block mb, replica block rb).  The replica blocks are cut
+// into bands of `band` blocks (the last band may be narrower) taken one after
+// another; inside a band the tiles run row block by row block with the band's
+// replica blocks fastest.  The CTAs running at one time then share the J rows
+// of a few row blocks, and the band's S rows, which every row block reads,
+// stay in L2 while the row blocks pass.
+__device__ __forceinline__ void tile_coords(int t, int nmb, int nrb, int band, int &mb, int &rb)
+{
+    const int per = nmb * band;
+    const int k = t / per;
+    const int rem = t - k * per;
+    const int w = min(band, nrb - k * band);
+    mb = rem / w;
+    rb = k * band + (rem - mb * w);
+}
+
 // Snext: the next step's operand, FP8 bytes [Rp][Np] or packed FP4 [Rp][Kp/2]
 // (Kp = Np rounded up to 256: Kp/2 bytes per row, the padding zero).
 template <bool FP4>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                const __grid_constant__ CUtensorMap tmapB, int N, int Np, int Kp, int Rp, int nrb,
-               int ntiles, float *__restrict__ X, float *__restrict__ Y,
+               int band, int ntiles, float *__restrict__ X, float *__restrict__ Y,
                uint8_t *__restrict__ Snext, float pk, StepConsts c, int energy, int energy_only,
                float *__restrict__ Epart, float *__restrict__ Tpart, int *__restrict__ err,
                const float *__restrict__ gvec)
 {
     constexpr int kBN = StepShape<FP4>::BN;  // replicas per tile
     constexpr int kStageB = StepShape<FP4>::StageB;
+    constexpr int kStages = StepShape<FP4>::Stages;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = base;
     uint8_t *sB = base + (size_t)kStages * kStageA;
-    TcShared<kBN> *sh = reinterpret_cast<TcShared<kBN> *>(sB + (size_t)kStages * kStageB);
+    TcShared<kBN, kStages> *sh =
+        reinterpret_cast<TcShared<kBN, kStages> *>(sB + (size_t)kStages * kStageB);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -224,20 +249,24 @@ tc_step_kernel(const __grid_constant__ CUtensorMap tmapA,
 
     if (warp < kIssuers) {
         // ------------------------------------------------------- TMA issuers
-        // Global chunk counter g runs over the K chunks of this CTA's tiles;
-        // issuer warp w takes g with g % 2 == w % 2 (stages w % 2, w % 2 + 2)
-        // and loads J (w < 2) or S (w >= 2).  The J issuer posts the stage's
-        // expected bytes (its one arrival); both boxes count against it.
+        // Global chunk counter g runs over the K chunks of this CTA's tiles
+        // and fills stage g % kStages.  Issuer warp w serves the stages s
+        // with s % 2 == w % 2 (always the same ones, so its parity waits see
+        // every phase of them in order) and loads J (w < 2) or S (w >= 2).
+        // The J issuer posts the stage's expected bytes (its one arrival);
+        // both boxes count against it.
         if (lane == 0) {
             const bool isA = warp < 2;
             const int total = my_tiles * nk;
-            for (int g = warp & 1; g < total; g += 2) {
+            for (int g = 0; g < total; ++g) {
+                const int s = g % kStages;
+                if ((s & 1) != (warp & 1))
+                    continue;
                 const int j = g / nk;
                 const int kc = g - j * nk;
                 const int tile = blockIdx.x + j * gridDim.x;
-                const int mb = tile / nrb;
-                const int rb = tile - mb * nrb;
-                const int s = g % kStages;
+                int mb, rb;
+                tile_coords(tile, Np / kBM, nrb, band, mb, rb);
                 const uint32_t ph = (uint32_t)(g / kStages) & 1u;
                 if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, err))
                     break;
@@ -295,11 +324,15 @@ tc_step_kernel(const __grid_constant__ CUtensorMap tmapA,
         const int et = threadIdx.x - 32 * kFirstEpi;
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const bool reduce = energy || energy_only || Tpart;
+        // x and y are read and written once per step: their lines go first
+        // from L2, so that the S rows of the band, re-read by every row
+        // block, stay
+        const uint64_t stream_once = ptx::l2_evict_first_policy();
         for (int j = 0; j < my_tiles; ++j) {
             const int b = j & 1;
             const int tile = blockIdx.x + j * gridDim.x;
-            const int mb = tile / nrb;
-            const int rb = tile - mb * nrb;
+            int mb, rb;
+            tile_coords(tile, Np / kBM, nrb, band, mb, rb);
             const int m0 = mb * kBM;
             const int r0 = rb * kBN;
             const int i = m0 + q * 32 + lane;      // spin of this thread
@@ -313,8 +346,8 @@ tc_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                 for (int jj = 0; jj < 32; ++jj) {
                     const int r = r0 + col0 + jj;
                     const size_t e = (size_t)(r < Rp ? r : 0) * Np + i;
-                    xv[jj] = X[e];
-                    yv[jj] = energy_only ? 0.f : Y[e];
+                    xv[jj] = ptx::ld_f32_hint(X + e, stream_once);
+                    yv[jj] = energy_only ? 0.f : ptx::ld_f32_hint(Y + e, stream_once);
                 }
             };
             fetch(cbase);
@@ -356,8 +389,8 @@ tc_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                                     cr.g = __ldg(gvec + r);
                                 float xn, yn;
                                 sb_update(fj, x0, y0, pk, cr, xn, yn);
-                                X[e] = xn;
-                                Y[e] = yn;
+                                ptx::st_f32_hint(X + e, xn, stream_once);
+                                ptx::st_f32_hint(Y + e, yn, stream_once);
                                 if (FP4) {
                                     // spins i (even lane) and i + 1 share a byte
                                     const uint32_t nib =
@@ -597,9 +630,14 @@ cudaError_t launch_step(cudaStream_t st, const TcPlan *plan, int parity, bool en
     const int nrb = (Rp + bn - 1) / bn;
     const int ntiles = (plan->Np / kBM) * nrb;
     const int grid = ntiles < sms ? ntiles : sms;
+    // replica bands whose S rows fit the L2 budget, as few as possible
+    const size_t srow = FP4 ? (size_t)plan->Kp / 2 : (size_t)plan->Np;
+    const size_t sbytes = (size_t)nrb * bn * srow;
+    const int nbands = (int)((sbytes + kSBandBytes - 1) / kSBandBytes);
+    const int band = (nrb + nbands - 1) / nbands;
     tc_step_kernel<FP4><<<grid, kThreads, step_smem_bytes<FP4>(), st>>>(
-        plan->mapA, plan->mapBw[parity & 1], N, plan->Np, plan->Kp, Rp, nrb, ntiles, X, Y, Snext,
-        pk, c, energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err, gvec);
+        plan->mapA, plan->mapBw[parity & 1], N, plan->Np, plan->Kp, Rp, nrb, band, ntiles, X, Y,
+        Snext, pk, c, energy ? 1 : 0, energy_only ? 1 : 0, Epart, Tpart, err, gvec);
     return cudaGetLastError();
 }
 

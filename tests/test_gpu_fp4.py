@@ -62,10 +62,12 @@ def test_fp4_equals_fp8_at_full_size_and_sampled_replicas_match_the_oracle():
 
 
 def test_fp4_large_instance_with_trace_equals_fp8():
-    # N = 16384 (the large streamed instance), 384 replicas (two 192-row
-    # tiles), 12 steps with the per-step trace; replica 0 against the oracle
+    # N = 16384, R = 4096 (the large streamed instance), 12 steps with the
+    # per-step trace.  The FP8 sign operand (67 MB) is walked in two replica
+    # bands, the FP4 one (34 MB) in one: all replicas agree, and replicas at
+    # both ends of each band match the oracle.
     J = synth.sk_pm1(16384, 3)
-    R, steps, seed = 384, 12, 2
+    R, steps, seed = 4096, 12, 2
     with hsb.Solver(J) as s:
         a = _run(s, "fp4", R, steps, seed, eval_every=5, trace_every=1)
         ta = s.get_trace()
@@ -74,9 +76,12 @@ def test_fp4_large_instance_with_trace_equals_fp8():
     for u, v in zip(a, b):
         np.testing.assert_array_equal(u, v)
     np.testing.assert_array_equal(ta, tb)
-    ref = oracle.run(J, _op(J, 5), steps, seed, [0, 383], "f32")
-    np.testing.assert_array_equal(a[2][[0, 383]], ref["x"])
-    np.testing.assert_array_equal(a[3][[0, 383]], ref["y"])
+    rows = [0, 2047, 2048, 4095]
+    ref = oracle.run(J, _op(J, 5), steps, seed, rows, "f32", nthreads=0)
+    np.testing.assert_array_equal(a[2][rows], ref["x"])
+    np.testing.assert_array_equal(a[3][rows], ref["y"])
+    np.testing.assert_array_equal(a[0][rows], ref["best_s"])
+    np.testing.assert_array_equal(a[1][rows], ref["best_e"])
 
 
 def test_fp4_nose_hoover_equals_fp8():
