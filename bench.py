@@ -509,6 +509,10 @@ OTHER = {
                     kind="single", N=16384, J="pm1", J_seed=3, R=4096, sb_steps=10000,
                     form="discrete", prec="fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
                     trace_every=1, peak="fp8", dtype="fp8"),
+    "sk2000_fp4": dict(name="HdSB SK +/-1 N=2000 R=1024 2000 steps FP4 e2m1 (persistent)",
+                       kind="single", N=2000, J="pm1", J_seed=1, R=1024, sb_steps=2000,
+                       form="discrete", prec="fp4", c1=0.7, dt=1.1, gamma=0.06, eval_every=100,
+                       trace_every=0, peak="fp4", dtype="fp4"),
     "sk16384_fp4": dict(name="HdSB SK +/-1 N=16384 R=4096 10000 steps FP4 e2m1 with per-step "
                              "trace", kind="single", N=16384, J="pm1", J_seed=3, R=4096,
                         sb_steps=10000, form="discrete", prec="fp4", c1=0.7, dt=1.1, gamma=0.06,

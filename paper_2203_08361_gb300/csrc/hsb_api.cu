@@ -382,9 +382,10 @@ hsb_status resolve(const hsb_ctx *h, const hsb_params *p, int R, int steps, RunC
     if (prec == HSB_PREC_FP4 && !(p->form == HSB_DISCRETE && h->pm1))
         return set_error(HSB_E_UNSUPPORTED,
                          "FP4 needs the discrete form and couplings in {-1, 0, +1}");
-    if (prec == HSB_PREC_FP4 && p->schedule != 0 && p->schedule != 2)
-        return set_error(HSB_E_UNSUPPORTED, "FP4 runs one kernel launch per step (schedule 0 "
-                                            "or 2)");
+    if (prec == HSB_PREC_FP4 && p->schedule != 0 && p->schedule != 1 && p->schedule != 2)
+        return set_error(HSB_E_UNSUPPORTED,
+                         "FP4 runs the persistent kernel or one launch per step (schedule 0, "
+                         "1 or 2)");
     if (prec == HSB_PREC_BF16X3 && !tc_bf16_persistent_fits(h->Np, Rp_))
         return set_error(HSB_E_UNSUPPORTED,
                          "BF16X3 runs as one persistent kernel; its %d x %d grid does not fit",
@@ -747,10 +748,19 @@ bool use_pair(const hsb_ctx *h, const RunCfg &c)
     return tc_pair_fits(h->Np, c.Rp);
 }
 
-// Whether the FP8 step loop runs as one persistent kernel.
+// Whether the FP8 (or FP4) step loop runs as one persistent kernel.
 hsb_status use_persistent(const hsb_ctx *h, const RunCfg &c, bool *out)
 {
     *out = false;
+    if (c.prec == HSB_PREC_FP4 && c.schedule != 2) {
+        const bool fits = tc_fp4_persistent_fits(h->Np, c.Rp);
+        if (!fits && c.schedule == 1)
+            return set_error(HSB_E_UNSUPPORTED,
+                             "the persistent kernel's %d x %d grid does not fit on the device",
+                             h->Np / kTileM, c.Rp / kTileR);
+        *out = fits;
+        return HSB_OK;
+    }
     if (c.prec != HSB_PREC_FP8 || c.schedule == 2)
         return HSB_OK;
     if (c.schedule == 4) {
@@ -893,7 +903,12 @@ hsb_status enqueue_persistent(hsb_ctx *h, const RunCfg &c, int k_begin, int nste
     }
     // the CTA-pair kernel where it applies; schedule 3: J resident on chip;
     // otherwise J streamed every step
-    if (use_pair(h, c))
+    if (c.prec == HSB_PREC_FP4) {
+        a.S8a = h->S4[0];
+        a.S8b = h->S4[1];
+        a.Kp = h->Kp;
+        CK(launch_tc_fp4_persistent(h->work, h->plan4, a), "persistent fp4 kernel");
+    } else if (use_pair(h, c))
         CK(launch_tc_fp8_pair(h->work, h->plan, a), "pair fp8 kernel");
     else if (c.schedule == 3)
         CK(launch_tc_fp8_resident(h->work, h->plan, h->J8, a), "resident fp8 kernel");
@@ -1076,8 +1091,12 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
             return s;
         CK(cudaMemsetAsync(h->err, 0, sizeof(int), h->work), "memset err");
         CK(launch_init(h->work, seed, p->instance, (float)p->init_half_width, h->N, h->Np, c.R,
-                       c.Rp, h->X[0], h->Y, h->S8[0], h->Ebest),
+                       c.Rp, h->X[0], h->Y, c.prec == HSB_PREC_FP8 ? h->S8[0] : nullptr,
+                       h->Ebest),
            "init kernel");
+        if (c.prec == HSB_PREC_FP4)
+            CK(launch_sign_to_fp4(h->work, h->X[0], h->N, h->Np, h->Kp, c.Rp, h->S4[0]),
+               "fp4 sign kernel");
         if (c.thermo)
             CK(launch_nh_init(h->work, c.R, c.Rp, c.nh_xi0, c.dt64, h->xi, h->gvec), "xi init");
         s = enqueue_persistent(h, c, 0, c.steps, true, 0);
@@ -1090,7 +1109,8 @@ hsb_status enqueue_run(hsb_ctx *h, const RunCfg &c, uint64_t seed, const hsb_par
         // init, (xi init), the step loop, best selection, trace entries in
         // launches of at most 65535
         const long long ntr = c.trace_every > 0 ? (c.steps - 1) / c.trace_every + 1 : 0;
-        h->launches = 3 + (c.thermo ? 1 : 0) + (ntr + 65534) / 65535;
+        h->launches = 3 + (c.thermo ? 1 : 0) + (c.prec == HSB_PREC_FP4 ? 1 : 0) +
+                      (ntr + 65534) / 65535;
         h->have_xi = c.thermo != 0;
         return HSB_OK;
     }

@@ -149,8 +149,9 @@ cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, 
 // The same step with packed FP4 e2m1 operands (tcgen05 kind::mxf4, unit
 // block scales): J4 [Np][Kp/2] and S4 [Rcap][Kp/2] bytes, two values per byte
 // (+1 = 0x2, -1 = 0xA, 0 = 0x0, the even index in the low nibble), Kp = Np
-// rounded up to 256 with zero padding.  Only mapA and mapBw[2] (box 192 rows)
-// of an FP4 plan are encoded; it serves launch_tc_fp4_step alone.
+// rounded up to 256 with zero padding.  Only mapA (J4, box 128 rows), mapB[2]
+// (S4, box 128 rows: persistent kernel) and mapBw[2] (S4, box 192 rows:
+// per-step kernel) of an FP4 plan are encoded.
 cudaError_t tc_fp4_plan_create(TcPlan **out, const uint8_t *J4, const uint8_t *S4a,
                                const uint8_t *S4b, int Np, int Kp, int Rp);
 cudaError_t launch_tc_fp4_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,
@@ -199,6 +200,9 @@ struct PersistArgs {
     // in trE / trT [m][nblk][Rp] (binary32)
     int trace_every;
     float *trE, *trT;
+    // FP4 operands (launch_tc_fp4_persistent): S8a / S8b hold packed e2m1
+    // rows of Kp / 2 bytes, Kp = Np rounded up to 256
+    int Kp;
 };
 
 // Resident-J variant (hsb_persist_ar.cu): N <= 2048, same arguments.
@@ -215,6 +219,10 @@ cudaError_t launch_tc_fp8_pair(cudaStream_t st, const TcPlan *plan, const Persis
 // True when the nblk x nrb grid of the persistent kernel can be co-resident.
 bool tc_persistent_fits(int Np, int Rp);
 cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const PersistArgs &a);
+// The same step loop with packed e2m1 operands (kind::mxf4, unit block
+// scales): the FP4 plan's maps, S8a / S8b pointing at the S4 buffers.
+bool tc_fp4_persistent_fits(int Np, int Rp);
+cudaError_t launch_tc_fp4_persistent(cudaStream_t st, const TcPlan *plan, const PersistArgs &a);
 cudaError_t launch_select_best(cudaStream_t st, const float *Epart, const uint8_t *Snap,
                                int n_evals, int nblk, int N, int Np, int R, int Rp,
                                double *Ebest, int8_t *Sbest);

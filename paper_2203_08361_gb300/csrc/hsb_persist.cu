@@ -76,10 +76,18 @@ namespace {
 constexpr int kPM = 128;
 constexpr int kPN = 128;
 constexpr int kPK = 128;
-constexpr int kPChunks = 2;  // K chunks of 128 per stage
-constexpr int kPStages = 3;
-constexpr int kPStageA = kPChunks * kPM * kPK;
-constexpr int kPStageB = kPChunks * kPN * kPK;
+constexpr int kPChunks = 2;  // FP8: K chunks of 128 per stage
+// One load covers a pair of 128-spin K chunks: in FP8 two 16 KB boxes of each
+// operand (3-D maps), in FP4 one 128-byte row of 256 packed e2m1 values per
+// operand row (2-D maps), so the FP4 stages are half as large and twice as
+// many.
+template <bool FP4>
+struct PShape {
+    static constexpr int Stages = FP4 ? 6 : 3;
+    static constexpr int StageA = (FP4 ? 1 : kPChunks) * kPM * kPK;
+    static constexpr int StageB = (FP4 ? 1 : kPChunks) * kPN * kPK;
+};
+constexpr int kPStagesMax = 6;
 constexpr int kPTileRow = kPM + 16;          // padded row of the sign tile (bytes)
 constexpr int kPTileS = kPN * kPTileRow;     // FP8 sign tile [replica][spin]
 constexpr int kIssuers = 2;
@@ -95,15 +103,18 @@ constexpr uint32_t kColAcc0 = 0;
 constexpr uint32_t kColAcc1 = 128;                 // used when kMmaWarps == 2
 constexpr uint32_t kColX = 128 * kMmaWarps;
 constexpr uint32_t kColY = kColX + 128;
+constexpr uint32_t kColSF = kColY + 128;           // FP4: unit block scales (16 columns)
 constexpr uint32_t kIdesc = ptx::idesc_e4m3_f32(kPM, kPN);
+constexpr uint32_t kIdesc4 = ptx::idesc_mxf4_e2m1(kPM, kPN);
+static_assert(kColSF + 16 <= kPTmemCols, "tensor memory columns");
 
 struct __align__(8) PShared {
-    uint64_t full[kPStages];
-    uint64_t empty[kPStages];
+    uint64_t full[kPStagesMax];
+    uint64_t empty[kPStagesMax];
     uint64_t accfull;     // one arrival per MMA warp
     uint64_t tmem_empty;  // every epilogue warp has read the accumulator(s)
     uint64_t drain;       // one arrival per MMA warp once its MMAs have completed
-    int last_use[kPStages];  // last use of each stage a copy was issued for
+    int last_use[kPStagesMax];  // last use of each stage a copy was issued for
     uint32_t tmem_base;
     int abort;
     uint64_t ring[kOrder];  // slot g % kOrder named: one arrival per use
@@ -119,9 +130,14 @@ struct __align__(8) PShared {
     float trt[4][kPN];
 };
 
-constexpr size_t kPSmem =
-    1024 + (size_t)kPStages * (kPStageA + kPStageB) + kPTileS + sizeof(PShared);
-static_assert(kPSmem <= 232448, "shared memory per CTA is limited to 227 KB");
+template <bool FP4>
+constexpr size_t persist_smem()
+{
+    return 1024 + (size_t)PShape<FP4>::Stages * (PShape<FP4>::StageA + PShape<FP4>::StageB) +
+           kPTileS + sizeof(PShared);
+}
+static_assert(persist_smem<false>() <= 232448, "shared memory per CTA is limited to 227 KB");
+static_assert(persist_smem<true>() <= 232448, "shared memory per CTA is limited to 227 KB");
 static_assert(kPThreads <= 1024, "too many threads per CTA");
 
 // Barrier among the epilogue warps that also ORs a predicate over them, so
@@ -251,12 +267,17 @@ __device__ __forceinline__ double nh_u128_q48_to_double(uint64_t hi, uint64_t lo
 
 }  // namespace
 
-template <bool kNH>
-__global__ void __launch_bounds__(kPThreads, 1)
-tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
-                         const __grid_constant__ CUtensorMap tmapB0,
-                         const __grid_constant__ CUtensorMap tmapB1, const PersistArgs a)
+// The step loop of one tile.  kFP4: J and S in packed e2m1 (rows of Kp/2
+// bytes), kind::mxf4 MMAs with unit block scales, the sign tile published as
+// nibbles; otherwise FP8 e4m3 and kind::f8f6f4.
+template <bool kNH, bool kFP4>
+__device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
+                                                const CUtensorMap *tmapB0,
+                                                const CUtensorMap *tmapB1, const PersistArgs &a)
 {
+    constexpr int kPStages = PShape<kFP4>::Stages;
+    constexpr int kPStageA = PShape<kFP4>::StageA;
+    constexpr int kPStageB = PShape<kFP4>::StageB;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -291,9 +312,9 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         ptx::mbar_init_fence();
     }
     if (warp == 1 && lane == 0) {
-        ptx::prefetch_tmap(&tmapA);
-        ptx::prefetch_tmap(&tmapB0);
-        ptx::prefetch_tmap(&tmapB1);
+        ptx::prefetch_tmap(tmapA);
+        ptx::prefetch_tmap(tmapB0);
+        ptx::prefetch_tmap(tmapB1);
     }
     if (warp == kFirstMma)
         ptx::tmem_alloc(&sh->tmem_base, kPTmemCols);
@@ -301,6 +322,21 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
+    if (kFP4) {
+        // unit block scales (UE8M0 0x7F = 2^0) in 16 columns of every lane,
+        // before the first MMA reads them
+        if (warp >= kFirstEpi && warp < kFirstEpi + 4) {
+            uint32_t one[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                one[j] = 0x7F7F7F7Fu;
+            ptx::tmem_st16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + kColSF, one);
+            ptx::tmem_st_wait();
+        }
+        ptx::tc_fence_before();
+        __syncthreads();
+        ptx::tc_fence_after();
+    }
 
     if (warp == 0) {
         // ------------------------------------------------------------ poller
@@ -396,13 +432,21 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 if (!split || iw == 0) {
                     // the stage's one arrival; both boxes count against it
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
-                    ptx::tma_load_3d(sA + (size_t)s * kPStageA, &tmapA, 0, m0, 2 * pp,
-                                     &sh->full[s]);
+                    if (kFP4)
+                        ptx::tma_load_2d(sA + (size_t)s * kPStageA, tmapA, pp * kPK, m0,
+                                         &sh->full[s]);
+                    else
+                        ptx::tma_load_3d(sA + (size_t)s * kPStageA, tmapA, 0, m0, 2 * pp,
+                                         &sh->full[s]);
                 }
                 if (!split || iw == 1) {
-                    const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? &tmapB1 : &tmapB0;
-                    ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp,
-                                     &sh->full[s]);
+                    const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? tmapB1 : tmapB0;
+                    if (kFP4)
+                        ptx::tma_load_2d(sB + (size_t)s * kPStageB, mapB, pp * kPK, r0,
+                                         &sh->full[s]);
+                    else
+                        ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp,
+                                         &sh->full[s]);
                 }
             }
         }
@@ -433,13 +477,23 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                 ptx::tc_fence_after();
                 const uint64_t ad = adesc0 + (uint64_t)((s * kPStageA) >> 4);
                 const uint64_t bd = bdesc0 + (uint64_t)((s * kPStageB) >> 4);
-#pragma unroll
-                for (int c = 0; c < kPChunks; ++c) {
+                if (kFP4) {
+                    // one 128-byte row of K per operand row: four K = 64 MMAs
 #pragma unroll
                     for (int kk = 0; kk < kPK / 32; ++kk)
-                        mma_fp8_elect(dcol, ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4),
-                                      bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4),
-                                      (mine | c | kk) != 0 ? 1u : 0u);
+                        ptx::mma_mxf4_elect(dcol, ad + (uint64_t)((kk * 32) >> 4),
+                                            bd + (uint64_t)((kk * 32) >> 4), kIdesc4,
+                                            tmem + kColSF, tmem + kColSF,
+                                            (mine | kk) != 0 ? 1u : 0u);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < kPChunks; ++c) {
+#pragma unroll
+                        for (int kk = 0; kk < kPK / 32; ++kk)
+                            mma_fp8_elect(dcol, ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4),
+                                          bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4),
+                                          (mine | c | kk) != 0 ? 1u : 0u);
+                    }
                 }
                 commit_elect(&sh->empty[s]);
                 ++mine;
@@ -489,8 +543,10 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         bool nh_bad = false;
 
         bool left = false;
-        // this spin's byte in row `col` of the sign tile
+        // this spin's byte in row `col` of the sign tile (FP4: the byte of
+        // this spin pair, written by its even lane)
         uint8_t *srow = sS + q * 32 + lane;
+        uint8_t *srow4 = sS + q * 16 + (lane >> 1);
         const StepConsts2 k2 = step_consts2(a.c);
         float pk_next = a.nsteps > 0 ? a.pk[a.k_begin] : 0.f;
         for (int kl = 0; kl < passes; ++kl) {
@@ -631,23 +687,44 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
                         const uint64_t qy = f2_fma(k2.q, yt, k2.z);
                         const bool n0 = f2_lo(qy) < -__uint_as_float(xr[j]);
                         const bool n1 = f2_hi(qy) < -__uint_as_float(xr[j + 1]);
-                        srow[(col0 + j) * kPTileRow] =
-                            live ? (n0 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
-                        srow[(col0 + j + 1) * kPTileRow] =
-                            live ? (n1 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
+                        if (kFP4) {
+                            // spins 2m (even lane) and 2m + 1 share a byte
+                            const uint32_t b0 = live ? (n0 ? kFp4MinusOne : kFp4PlusOne) : 0u;
+                            const uint32_t b1 = live ? (n1 ? kFp4MinusOne : kFp4PlusOne) : 0u;
+                            const uint32_t u0 = __shfl_down_sync(0xFFFFFFFFu, b0, 1);
+                            const uint32_t u1 = __shfl_down_sync(0xFFFFFFFFu, b1, 1);
+                            if ((lane & 1) == 0) {
+                                srow4[(col0 + j) * kPTileRow] = (uint8_t)(b0 | (u0 << 4));
+                                srow4[(col0 + j + 1) * kPTileRow] = (uint8_t)(b1 | (u1 << 4));
+                            }
+                        } else {
+                            srow[(col0 + j) * kPTileRow] =
+                                live ? (n0 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
+                            srow[(col0 + j + 1) * kPTileRow] =
+                                live ? (n1 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
+                        }
                     }
                 }
-                // this warp's 32 replicas x 32 spins of S(t_{k+1}): 16-byte
-                // stores, two per lane, into the other operand buffer
+                // this warp's 32 replicas x 32 spins of S(t_{k+1}) into the
+                // other operand buffer with 16-byte stores: FP8 two per lane
+                // (32-byte row segments), FP4 one (16 bytes of packed pairs)
                 __syncwarp();
-                uint8_t *dst = (((a.par0 + kl + 1) & 1) ? a.S8b : a.S8a) +
-                               (size_t)(r0 + c0) * a.Np + m0 + q * 32;
-#pragma unroll
-                for (int v = lane; v < 64; v += 32) {
-                    const int row = v >> 1, off = (v & 1) * 16;
+                uint8_t *sdst = ((a.par0 + kl + 1) & 1) ? a.S8b : a.S8a;
+                if (kFP4) {
+                    const size_t pitch = (size_t)a.Kp / 2;
                     const uint4 val =
-                        *reinterpret_cast<const uint4 *>(sS + (c0 + row) * kPTileRow + q * 32 + off);
-                    *reinterpret_cast<uint4 *>(dst + (size_t)row * a.Np + off) = val;
+                        *reinterpret_cast<const uint4 *>(sS + (c0 + lane) * kPTileRow + q * 16);
+                    *reinterpret_cast<uint4 *>(sdst + (size_t)(r0 + c0 + lane) * pitch +
+                                               (m0 + q * 32) / 2) = val;
+                } else {
+                    uint8_t *dst = sdst + (size_t)(r0 + c0) * a.Np + m0 + q * 32;
+#pragma unroll
+                    for (int v = lane; v < 64; v += 32) {
+                        const int row = v >> 1, off = (v & 1) * 16;
+                        const uint4 val = *reinterpret_cast<const uint4 *>(
+                            sS + (c0 + row) * kPTileRow + q * 32 + off);
+                        *reinterpret_cast<uint4 *>(dst + (size_t)row * a.Np + off) = val;
+                    }
                 }
                 epi_bar();
                 if (et == 0 && !(mb == a.drop_mb && rb == 0)) {
@@ -845,6 +922,24 @@ tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
         ptx::tmem_dealloc(tmem, kPTmemCols);
 }
 
+template <bool kNH>
+__global__ void __launch_bounds__(kPThreads, 1)
+tc_fp8_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
+                         const __grid_constant__ CUtensorMap tmapB0,
+                         const __grid_constant__ CUtensorMap tmapB1, const PersistArgs a)
+{
+    persistent_body<kNH, false>(&tmapA, &tmapB0, &tmapB1, a);
+}
+
+template <bool kNH>
+__global__ void __launch_bounds__(kPThreads, 1)
+tc_fp4_persistent_kernel(const __grid_constant__ CUtensorMap tmapA,
+                         const __grid_constant__ CUtensorMap tmapB0,
+                         const __grid_constant__ CUtensorMap tmapB1, const PersistArgs a)
+{
+    persistent_body<kNH, true>(&tmapA, &tmapB0, &tmapB1, a);
+}
+
 // Best evaluation of each replica: E_e = -1/2 sum_b Epart[e][b][r] (binary64,
 // blocks in order); the first strictly lowest wins; its snapshot is copied.
 __global__ void select_best_kernel(const float *__restrict__ Epart,
@@ -878,7 +973,10 @@ __global__ void select_best_kernel(const float *__restrict__ Epart,
 
 // ------------------------------------------------------------- host side ---
 
-bool tc_persistent_fits(int Np, int Rp)
+namespace {
+
+template <bool FP4>
+bool persistent_fits(int Np, int Rp)
 {
     const int nblk = Np / kPM;
     const int nrb = Rp / kPN;
@@ -888,15 +986,47 @@ bool tc_persistent_fits(int Np, int Rp)
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return false;
-    // both instantiations have the same block size and shared memory
-    if (cudaFuncSetAttribute(tc_fp8_persistent_kernel<false>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPSmem) != cudaSuccess)
+    // both instantiations of a precision have the same block size and shared memory
+    auto kern = FP4 ? tc_fp4_persistent_kernel<false> : tc_fp8_persistent_kernel<false>;
+    const size_t smem = persist_smem<FP4>();
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return false;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_fp8_persistent_kernel<false>,
-                                                      kPThreads, kPSmem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPThreads, smem) !=
+        cudaSuccess)
         return false;
     return (long long)nblk * nrb <= (long long)per_sm * sms;
 }
+
+template <bool FP4>
+cudaError_t launch_persistent(cudaStream_t st, const CUtensorMap &mA, const CUtensorMap &mB0,
+                              const CUtensorMap &mB1, const PersistArgs &a)
+{
+    auto kern = FP4 ? (a.nh ? tc_fp4_persistent_kernel<true> : tc_fp4_persistent_kernel<false>)
+                    : (a.nh ? tc_fp8_persistent_kernel<true> : tc_fp8_persistent_kernel<false>);
+    const size_t smem = persist_smem<FP4>();
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.nblk, a.nrb, 1);
+    cfg.blockDim = dim3(kPThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, mA, mB0, mB1, a);
+}
+
+}  // namespace
+
+bool tc_persistent_fits(int Np, int Rp) { return persistent_fits<false>(Np, Rp); }
+
+bool tc_fp4_persistent_fits(int Np, int Rp) { return persistent_fits<true>(Np, Rp); }
 
 cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const PersistArgs &a)
 {
@@ -904,23 +1034,17 @@ cudaError_t launch_tc_fp8_persistent(cudaStream_t st, const TcPlan *plan, const 
         return cudaErrorInvalidValue;
     if (a.nh && (!a.xi || !a.nhpart || !a.nhflags || !a.final_pass))
         return cudaErrorInvalidValue;
-    auto kern = a.nh ? tc_fp8_persistent_kernel<true> : tc_fp8_persistent_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kPSmem);
-    if (e != cudaSuccess)
-        return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(a.nblk, a.nrb, 1);
-    cfg.blockDim = dim3(kPThreads, 1, 1);
-    cfg.dynamicSmemBytes = kPSmem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, plan->mapA3, plan->mapB3[0],
-                              plan->mapB3[1], a);
+    return launch_persistent<false>(st, plan->mapA3, plan->mapB3[0], plan->mapB3[1], a);
+}
+
+cudaError_t launch_tc_fp4_persistent(cudaStream_t st, const TcPlan *plan, const PersistArgs &a)
+{
+    if (!plan || a.Np != plan->Np || a.Rp > plan->Rp || a.Rp % kPN != 0 || a.nblk > 32 ||
+        a.Kp != plan->Kp || a.Kp < a.Np || a.Kp % 256 != 0)
+        return cudaErrorInvalidValue;
+    if (a.nh && (!a.xi || !a.nhpart || !a.nhflags || !a.final_pass))
+        return cudaErrorInvalidValue;
+    return launch_persistent<true>(st, plan->mapA, plan->mapB[0], plan->mapB[1], a);
 }
 
 cudaError_t launch_select_best(cudaStream_t st, const float *Epart, const uint8_t *Snap,

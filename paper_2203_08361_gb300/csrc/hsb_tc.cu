@@ -68,6 +68,7 @@ constexpr uint32_t kTmemCols = 512;  // two accumulators (+ the FP4 block scales
 // S rows of one replica band: the band stays in L2 while J and x, y stream
 // past it (data read by SMs of both dies may be held in both halves of L2)
 constexpr size_t kSBandBytes = (size_t)40 << 20;
+constexpr bool kRotateK = true;
 
 // FP8: kind::f8f6f4 e4m3, K = 32 per instruction.  FP4: kind::mxf4 with packed
 // e2m1 operands (+1 = 0x2, -1 = 0xA, 0 = 0x0, element 2j in the low nibble of
@@ -267,16 +268,21 @@ tc_step_kernel(const __grid_constant__ CUtensorMap tmapA,
                 const int tile = blockIdx.x + j * gridDim.x;
                 int mb, rb;
                 tile_coords(tile, Np / kBM, nrb, band, mb, rb);
+                // each tile starts its K loop at its own chunk, so the CTAs
+                // that share J rows or S rows do not ask for the same lines
+                // at the same time (the partial forces are exact integers:
+                // the summation order does not matter)
+                const int kq = kRotateK ? (kc + tile) % nk : kc;
                 const uint32_t ph = (uint32_t)(g / kStages) & 1u;
                 if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, err))
                     break;
                 atomicMax(&sh->last_use[s], g / kStages);  // for the drain
                 if (isA) {
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kStageA + kStageB));
-                    ptx::tma_load_2d(sA + (size_t)s * kStageA, &tmapA, kc * kBK, mb * kBM,
+                    ptx::tma_load_2d(sA + (size_t)s * kStageA, &tmapA, kq * kBK, mb * kBM,
                                      &sh->full[s]);
                 } else {
-                    ptx::tma_load_2d(sB + (size_t)s * kStageB, &tmapB, kc * kBK, rb * kBN,
+                    ptx::tma_load_2d(sB + (size_t)s * kStageB, &tmapB, kq * kBK, rb * kBN,
                                      &sh->full[s]);
                 }
             }
@@ -588,6 +594,8 @@ cudaError_t tc_fp4_plan_create(TcPlan **out, const uint8_t *J4, const uint8_t *S
     p->Kp = Kp;
     // rows of Kp/2 bytes; a 128-byte box row holds 256 e2m1 values
     if (!encode_u8(&p->mapA, J4, (uint64_t)Np, (uint64_t)Kp / 2, kBM) ||
+        !encode_u8(&p->mapB[0], S4a, (uint64_t)Rp, (uint64_t)Kp / 2, 128) ||
+        !encode_u8(&p->mapB[1], S4b, (uint64_t)Rp, (uint64_t)Kp / 2, 128) ||
         !encode_u8(&p->mapBw[0], S4a, (uint64_t)Rp, (uint64_t)Kp / 2, kBN4) ||
         !encode_u8(&p->mapBw[1], S4b, (uint64_t)Rp, (uint64_t)Kp / 2, kBN4)) {
         delete p;

@@ -12,7 +12,7 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _batch_vs_single(sizes, R, steps, ev, seed, check_oracle=()):
+def _batch_vs_single(sizes, R, steps, ev, seed, check_oracle=(), oracle_rows=None):
     Js = [synth.sk_pm1(n, 500 + b) for b, n in enumerate(sizes)]
     solvers = [hsb.Solver(J) for J in Js]
     p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=ev)
@@ -28,9 +28,10 @@ def _batch_vs_single(sizes, R, steps, ev, seed, check_oracle=()):
             J = Js[b]
             op = oracle.make_params(1, oracle.c0_from_c1(J, 0.7), 1.1, 0.06, eval_every=ev,
                                     instance=b)
-            ref = oracle.run(J, op, steps, seed, range(R), "f32")
-            np.testing.assert_array_equal(out[b][0], ref["best_s"])
-            np.testing.assert_array_equal(out[b][1], ref["best_e"])
+            rows = list(range(R)) if oracle_rows is None else list(oracle_rows)
+            ref = oracle.run(J, op, steps, seed, rows, "f32", nthreads=0)
+            np.testing.assert_array_equal(out[b][0][rows], ref["best_s"])
+            np.testing.assert_array_equal(out[b][1][rows], ref["best_e"])
     finally:
         for s in solvers:
             s.close()
@@ -51,9 +52,12 @@ def test_batch_more_instances_than_ctas_per_cta_reuse():
 
 def test_batch_uneven_workload_full_size():
     # 256 SK instances, N uniform in [100, 2000], R = 64, 2000 steps, eval every
-    # 100: one batched launch against 256 separate runs.
-    sizes = synth.batch_sizes(256, 4)
-    _batch_vs_single(sizes, 64, 2000, 100, 9, check_oracle=(sizes.index(min(sizes)),))
+    # 100: one batched launch against 256 separate runs; the smallest and the
+    # largest instance against the oracle on replicas at both ends
+    sizes = [int(v) for v in synth.batch_sizes(256, 4)]
+    _batch_vs_single(sizes, 64, 2000, 100, 9,
+                     check_oracle=(sizes.index(min(sizes)), sizes.index(max(sizes))),
+                     oracle_rows=(0, 1, 62, 63))
 
 
 @pytest.mark.parametrize("kind", ["gauss", "nose_hoover"])

@@ -1,5 +1,6 @@
-"""GPU parity of the FP4 schedule (packed e2m1 J and sgn(x), tcgen05 kind::mxf4
-with unit UE8M0 block scales, FP32 accumulation, one launch per step).
+"""GPU parity of the FP4 path (packed e2m1 J and sgn(x), tcgen05 kind::mxf4
+with unit UE8M0 block scales, FP32 accumulation), on the persistent kernel
+(the automatic choice where its grid fits) and one launch per step.
 
 The products of +/-1 and 0 codes are exact, the per-instruction partial sums
 are integers below 2^24, so the force equals the FP8 path's and the binary32
@@ -45,14 +46,18 @@ def test_fp4_ragged_replica_tiles_bit_exact(n, R):
 
 
 def test_fp4_equals_fp8_at_full_size_and_sampled_replicas_match_the_oracle():
-    # N = 2000, R = 1024 (the benchmark's workload), 300 steps
+    # N = 2000, R = 1024 (the benchmark's workload), 300 steps: FP4 on the
+    # persistent kernel and one launch per step, FP8 on both
     J = synth.sk_pm1(2000, 1)
     R, steps, seed = 1024, 300, 3
     with hsb.Solver(J) as s:
-        a = _run(s, "fp4", R, steps, seed, eval_every=100)
-        b = _run(s, "fp8", R, steps, seed, eval_every=100, schedule="per_step")
-    for u, v in zip(a, b):
-        np.testing.assert_array_equal(u, v)
+        a = _run(s, "fp4", R, steps, seed, eval_every=100, schedule="persistent")
+        others = [_run(s, "fp4", R, steps, seed, eval_every=100, schedule="per_step"),
+                  _run(s, "fp8", R, steps, seed, eval_every=100, schedule="per_step"),
+                  _run(s, "fp8", R, steps, seed, eval_every=100, schedule="persistent")]
+    for b in others:
+        for u, v in zip(a, b):
+            np.testing.assert_array_equal(u, v)
     rows = [0, 191, 192, 1023]
     ref = oracle.run(J, _op(J, 100), steps, seed, rows, "f32")
     np.testing.assert_array_equal(a[2][rows], ref["x"])
@@ -82,6 +87,20 @@ def test_fp4_large_instance_with_trace_equals_fp8():
     np.testing.assert_array_equal(a[3][rows], ref["y"])
     np.testing.assert_array_equal(a[0][rows], ref["best_s"])
     np.testing.assert_array_equal(a[1][rows], ref["best_e"])
+
+
+@pytest.mark.parametrize("n,R", [(700, 256), (2000, 1024), (257, 129)])
+def test_fp4_persistent_trace_equals_fp8(n, R):
+    J = synth.sk_pm1(n, 12)
+    steps, seed = 120, 6
+    with hsb.Solver(J) as s:
+        a = _run(s, "fp4", R, steps, seed, eval_every=30, trace_every=1, schedule="persistent")
+        ta = s.get_trace()
+        b = _run(s, "fp8", R, steps, seed, eval_every=30, trace_every=1, schedule="persistent")
+        tb = s.get_trace()
+    for u, v in zip(a, b):
+        np.testing.assert_array_equal(u, v)
+    np.testing.assert_array_equal(ta, tb)
 
 
 def test_fp4_nose_hoover_equals_fp8():
@@ -130,12 +149,15 @@ def test_fp4_device_run_advance_and_set_couplings():
 def test_fp4_is_refused_where_it_does_not_apply():
     J = synth.sk_pm1(300, 3)
     with hsb.Solver(J) as s:
-        for form, kw in (("ballistic", {}), ("discrete", {"schedule": "persistent"}),
-                         ("discrete", {"schedule": "resident"}),
+        for form, kw in (("ballistic", {}), ("discrete", {"schedule": "resident"}),
                          ("discrete", {"schedule": "pair"})):
             with pytest.raises(hsb.HsbError) as e:
                 s.run(hsb.params(form, "fp4", **kw), 256, 10, 0)
             assert e.value.status == hsb.HSB_E_UNSUPPORTED
+    with hsb.Solver(synth.sk_pm1(4200, 0)) as s:  # 33 row blocks: no persistent grid
+        with pytest.raises(hsb.HsbError) as e:
+            s.run(hsb.params("discrete", "fp4", schedule="persistent"), 128, 4, 0)
+        assert e.value.status == hsb.HSB_E_UNSUPPORTED
     with hsb.Solver(synth.sk_gauss(300, 3)) as s:
         with pytest.raises(hsb.HsbError) as e:
             s.run(hsb.params("discrete", "fp4"), 64, 10, 0)

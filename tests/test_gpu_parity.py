@@ -32,7 +32,7 @@ def _assert_same(got_x, got_y, spins, energy, ref, rows=None):
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "resident"),
-                                           ("fp8", "per_step"), ("fp4", "per_step"),
+                                           ("fp8", "per_step"), ("fp4", "per_step"), ("fp4", "persistent"),
                                            ("fp32", "auto")])
 @pytest.mark.parametrize("n,R", [(128, 128), (300, 40), (257, 130), (2, 3), (700, 300),
                                  (1100, 130), (2048, 128)])
@@ -87,7 +87,7 @@ def test_small_ballistic_pm1_workload_fp32():
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "resident"),
-                                           ("fp8", "per_step"), ("fp4", "per_step"),
+                                           ("fp8", "per_step"), ("fp4", "per_step"), ("fp4", "persistent"),
                                            ("fp32", "auto")])
 def test_one_step_and_split_runs(prec, schedule):
     n, R, steps = 260, 70, 50
@@ -266,7 +266,7 @@ def _dilute_pm1(n, seed, p_zero=0.5):
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
-                                           ("fp4", "per_step"), ("fp32", "auto")])
+                                           ("fp4", "per_step"), ("fp4", "persistent"), ("fp32", "auto")])
 @pytest.mark.parametrize("n,R,steps,ev", [
     (129, 1, 1, 0),       # one replica, one step, final evaluation only
     (129, 1, 37, 0),      # final evaluation only (the 700-spin protocol)
@@ -286,7 +286,7 @@ def test_edge_cases_bit_exact(prec, schedule, n, R, steps, ev):
 
 
 @pytest.mark.parametrize("prec,schedule", [("fp8", "persistent"), ("fp8", "per_step"),
-                                           ("fp4", "per_step"), ("fp32", "auto")])
+                                           ("fp4", "per_step"), ("fp4", "persistent"), ("fp32", "auto")])
 def test_diluted_couplings_bit_exact(prec, schedule):
     n, R, steps, seed, ev = 500, 70, 120, 4, 30
     J = _dilute_pm1(n, 8)
