@@ -130,42 +130,6 @@ __device__ __forceinline__ bool warp_wait_cl(uint64_t *bar, uint32_t parity, int
     return __all_sync(0xFFFFFFFFu, ok);
 }
 
-// Shared-memory pass counters of the poller: a release store (cta scope) and
-// a bounded acquire wait for "count >= want".  A counter, unlike the parity
-// wait of an mbarrier, stays correct when the waiter is several passes ahead
-// of the poller (an issuer whose stage is free early, few K chunks).
-__device__ __forceinline__ void st_release_cta_shared(int *p, int v)
-{
-    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(ptx::smem_u32(p)), "r"(v)
-                 : "memory");
-}
-
-__device__ __forceinline__ int ld_acquire_cta_shared(const int *p)
-{
-    int v;
-    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(ptx::smem_u32(p))
-                 : "memory");
-    return v;
-}
-
-__device__ __forceinline__ bool wait_ready(const int *cnt, int want, int *abort, int *err)
-{
-    if (ld_acquire_cta_shared(cnt) >= want)
-        return true;
-    const unsigned long long t0 = ptx::globaltimer();
-    for (unsigned it = 1;; ++it) {
-        if (ld_acquire_cta_shared(cnt) >= want)
-            return true;
-        if (*(volatile int *)abort)
-            return false;
-        if ((it & 15u) == 0 && ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
-            *(volatile int *)abort = 1;
-            atomicExch(err, kErrTimeout);
-            return false;
-        }
-    }
-}
-
 // 0xFF in byte i of the result for each set bit i (i < 4) of b, else 0x00
 // (the four bits spread to bytes by one multiplication, no carries).
 __device__ __forceinline__ uint32_t byte_mask4(uint32_t b)
@@ -270,7 +234,7 @@ tc_fp8_pair_kernel(const __grid_constant__ CUtensorMap tmapJ,
                                           i0 + (int)h * kQJRows, full_c);
                 } else {
                     // chunk c of this CTA's replicas for pass kl is published
-                    if (!wait_ready(&sh->rdy[c], kl + 1, &sh->abort, a.err))
+                    if (!ptx::wait_count(&sh->rdy[c], kl + 1, &sh->abort, a.err))
                         break;
                     ptx::fence_proxy_async_global();
                     const CUtensorMap *mapS = ((a.par0 + kl) & 1) ? &tmapS1 : &tmapS0;
@@ -308,7 +272,7 @@ tc_fp8_pair_kernel(const __grid_constant__ CUtensorMap tmapJ,
                 if (pending)
                     ready = ptx::ld_acquire_gpu(&a.flags[flag_index(lane, rho, a.nrb)]) >= kl;
                 if (ready) {
-                    st_release_cta_shared(&sh->rdy[lane], kl + 1);
+                    ptx::st_release_cta_shared(&sh->rdy[lane], kl + 1);
                     pending = false;
                 }
                 if (!__any_sync(0xFFFFFFFFu, ready)) {

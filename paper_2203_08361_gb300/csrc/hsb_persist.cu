@@ -13,19 +13,24 @@
 // every row block), so the roles are arranged to shorten it:
 //   warp 0      poller: reads the per-tile "published" flags of the step's
 //               operand (one flag per 128-spin chunk, all lanes at once) and
-//               appends the K-chunk pairs, in the order they become ready, to
-//               a ring in shared memory, arriving on the slot's mbarrier (the
-//               FP8 products are exact integers, so the summation order does
-//               not change the force);
-//   warps 1-2   TMA issuers: load g of the ring fills stage g % 3 with two
-//               32 KB 3-D boxes (J and S, 128 x 128 x 2 bytes).  Bulk copies
-//               from one thread complete one after another: the boxes of the
-//               first two loads of a pass come from both warps in parallel,
-//               later loads alternate whole between the warps;
-//   warp 3      MMA: issues tcgen05.mma (kind::f8f6f4, M = N = 128, K = 32)
-//               from an elected lane of the converged warp (warp-uniform
-//               operands issue faster than from one divergent thread).  With
-//               kMmaWarps = 2, pair t goes to warp 3 + t % 2 and its own
+//               raises the pass counter of each load unit (a pair of 128-spin
+//               K chunks) whose chunks are both published;
+//   warps 1-2   TMA issuers: load g fills stage g % 3 (FP4: g % 6) with the
+//               unit's K slices of J (128 rows, warp 1) and of S (warp 2):
+//               one 3-D box of 128 x 128 x 2 bytes each in FP8, one 2-D box
+//               of 128 x 128 bytes in FP4.  Every
+//               tile takes its units in a fixed order starting from its own,
+//               so the J slice of a load does not wait for any publication:
+//               warp 1 copies it as soon as the stage is free and the first
+//               loads of a pass have their J before the signs arrive; warp 2
+//               copies the S slice once the unit's counter allows (the FP8
+//               and FP4 products are exact integers, so the order of the K
+//               slices does not change the force);
+//   warp 3      MMA: issues tcgen05.mma (kind::f8f6f4, M = N = 128, K = 32;
+//               FP4 kind::mxf4, K = 64) from an elected lane of the converged
+//               warp (warp-uniform operands issue faster than from one
+//               divergent thread).  With kMmaWarps = 2, load t goes to warp
+//               3 + t % 2 and its own
 //               accumulator (split K); the partial forces are exact integers,
 //               so their binary32 sum is the exact force;
 //   warps 4-19  epilogue, four warps per 32-lane quadrant (32 replicas each,
@@ -76,18 +81,20 @@ namespace {
 constexpr int kPM = 128;
 constexpr int kPN = 128;
 constexpr int kPK = 128;
-constexpr int kPChunks = 2;  // FP8: K chunks of 128 per stage
-// One load covers a pair of 128-spin K chunks: in FP8 two 16 KB boxes of each
-// operand (3-D maps), in FP4 one 128-byte row of 256 packed e2m1 values per
-// operand row (2-D maps), so the FP4 stages are half as large and twice as
-// many.
+// One load covers a pair of 128-spin K chunks of each operand's 128 rows: in
+// FP8 one 3-D box of two 128-byte slices (32 KB), in FP4 one 128-byte slice
+// of 256 packed e2m1 values (16 KB), so the FP4 stages are half as large and
+// twice as many.  (Boxes of one 128-byte FP8 slice, twice as many copies,
+// made the FP8 step loop slower.)
 template <bool FP4>
 struct PShape {
+    static constexpr int Slices = FP4 ? 1 : 2;  // 128-byte K slices per load
     static constexpr int Stages = FP4 ? 6 : 3;
-    static constexpr int StageA = (FP4 ? 1 : kPChunks) * kPM * kPK;
-    static constexpr int StageB = (FP4 ? 1 : kPChunks) * kPN * kPK;
+    static constexpr int StageA = Slices * kPM * kPK;
+    static constexpr int StageB = Slices * kPN * kPK;
 };
 constexpr int kPStagesMax = 6;
+constexpr int kMaxLoads = 32;  // loads per pass (one flag lane per chunk, nblk <= 32)
 constexpr int kPTileRow = kPM + 16;          // padded row of the sign tile (bytes)
 constexpr int kPTileS = kPN * kPTileRow;     // FP8 sign tile [replica][spin]
 constexpr int kIssuers = 2;
@@ -97,7 +104,6 @@ constexpr int kFirstEpi = kFirstMma + kMmaWarps;
 constexpr int kEpiWarps = 16;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kPThreads = 32 * kFirstEpi + kEpiThreads;
-constexpr int kOrder = 32;                   // ring of pair ids in load order
 constexpr uint32_t kPTmemCols = 512;
 constexpr uint32_t kColAcc0 = 0;
 constexpr uint32_t kColAcc1 = 128;                 // used when kMmaWarps == 2
@@ -114,11 +120,10 @@ struct __align__(8) PShared {
     uint64_t accfull;     // one arrival per MMA warp
     uint64_t tmem_empty;  // every epilogue warp has read the accumulator(s)
     uint64_t drain;       // one arrival per MMA warp once its MMAs have completed
-    int last_use[kPStagesMax];  // last use of each stage a copy was issued for
     uint32_t tmem_base;
     int abort;
-    uint64_t ring[kOrder];  // slot g % kOrder named: one arrival per use
-    int order[kOrder];    // pair of load g at order[g % kOrder]
+    int rdy[kMaxLoads];     // load unit u is published for passes < rdy[u] (poller)
+    int copies[kPStagesMax][2];  // uses of each stage copied: [stage][J, S] (drain)
     float red[4][kPN];    // per-quadrant energy partials
     // Nose-Hoover (kNH): xi of the tile's replicas, the friction factor of
     // the current pass, and 22-bit chunk sums of q^2 over the tile's rows
@@ -293,7 +298,13 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
     const int m0 = mb * kPM;
     const int r0 = rb * kPN;
     const int nblk = a.nblk;
-    const int npairs = (nblk + 1) >> 1;
+    // loads of a pass: unit u covers K chunks 2u, 2u + 1; a chunk past the
+    // end reads as zero.  Every tile takes the units in the order u0, u0 + 1,
+    // ... cyclically from its own (the first published, by this CTA), so
+    // tiles sharing rows ask for different lines at a time
+    constexpr int kCpl = 2;
+    const int nload = (nblk + kCpl - 1) / kCpl;
+    const int u0 = mb / kCpl;
     const int passes = a.nsteps + a.final_pass;
 
     if (threadIdx.x == 0) {
@@ -305,9 +316,9 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
         ptx::mbar_init(&sh->tmem_empty, kEpiWarps);
         ptx::mbar_init(&sh->drain, kMmaWarps);
         for (int s = 0; s < kPStages; ++s)
-            sh->last_use[s] = -1;
-        for (int r = 0; r < kOrder; ++r)
-            ptx::mbar_init(&sh->ring[r], 1);
+            sh->copies[s][0] = sh->copies[s][1] = 0;
+        for (int u = 0; u < kMaxLoads; ++u)
+            sh->rdy[u] = 0;
         sh->abort = 0;
         ptx::mbar_init_fence();
     }
@@ -340,15 +351,15 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
 
     if (warp == 0) {
         // ------------------------------------------------------------ poller
-        // K chunks are fetched in pairs (2p, 2p+1); a chunk past the end reads
-        // as zero, so an odd chunk count adds zero products only.  A pair is
-        // appended once both of its chunks are published for the pass.
-        int G = 0;
+        // lane c reads the flag of chunk c (tile (c, rb)) for each pass; once
+        // every chunk of a load unit is published, lane u raises the unit's
+        // pass counter, which the S issuer waits on
         bool fail = false;
+        const uint32_t all_units = nload >= 32 ? 0xFFFFFFFFu : ((1u << nload) - 1u);
         for (int kl = 0; kl < passes && !fail; ++kl) {
             uint32_t pending = nblk >= 32 ? 0xFFFFFFFFu : ((1u << nblk) - 1u);
             uint32_t have = 0;
-            uint32_t left = npairs >= 32 ? 0xFFFFFFFFu : ((1u << npairs) - 1u);
+            uint32_t left = all_units;
             const unsigned long long t0 = ptx::globaltimer();
             int idle = 0;
             while (left) {
@@ -358,32 +369,17 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                 const uint32_t rmask = __ballot_sync(0xFFFFFFFFu, ready);
                 have |= rmask;
                 pending &= ~rmask;
-                uint32_t pmask = 0;
-                for (int pp = 0; pp < npairs; ++pp) {
-                    const uint32_t need = (2 * pp + 1 < nblk) ? (3u << (2 * pp)) : (1u << (2 * pp));
-                    if (((left >> pp) & 1u) && (have & need) == need)
-                        pmask |= 1u << pp;
+                bool unit = false;
+                if ((left >> lane) & 1u) {
+                    const uint32_t need =
+                        2 * lane + 1 < nblk ? (3u << (2 * lane)) : (1u << (2 * lane));
+                    unit = (have & need) == need;
                 }
-                if (pmask) {
-                    if (lane == 0) {
-                        // own pair first, then the following ones cyclically
-                        const int p0 = mb >> 1;
-                        for (int t = 0; t < npairs; ++t) {
-                            int pp = p0 + t;
-                            if (pp >= npairs)
-                                pp -= npairs;
-                            if ((pmask >> pp) & 1u) {
-                                // the arrival (release) makes the entry visible
-                                // to the issuers waiting on the slot
-                                sh->order[G % kOrder] = pp;
-                                ptx::mbar_arrive(&sh->ring[G % kOrder]);
-                                ++G;
-                            }
-                        }
-                    }
-                    G = __shfl_sync(0xFFFFFFFFu, G, 0);
-                    left &= ~pmask;
-                } else {
+                if (unit)
+                    ptx::st_release_cta_shared(&sh->rdy[lane], kl + 1);
+                const uint32_t umask = __ballot_sync(0xFFFFFFFFu, unit);
+                left &= ~umask;
+                if (!umask && left) {
                     int give_up = 0;
                     if (lane == 0) {
                         // the clock is read every 16th idle poll (a read costs ~0.1 us)
@@ -405,50 +401,52 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
         }
     } else if (warp <= kIssuers) {
         // ------------------------------------------------------- TMA issuers
-        // Copies from one thread complete one after another.  The first two
-        // loads of a pass are on the critical path, so their J boxes come
-        // from warp 1 and their S boxes from warp 2, in parallel; the later
-        // loads alternate whole between the warps (J and S from one thread).
+        // Both issuers serve every load g in order (stage g % kPStages).  Warp
+        // 1 copies the J slice as soon as the stage is free (J does not wait
+        // for the step's signs, so a pass's first loads have their J before
+        // its signs are published) and posts the stage's expected bytes (its
+        // one arrival); warp 2 copies the S slice once the unit is published.
+        // A copy of S that lands first takes the transaction count below zero
+        // until then: it cannot belong to the previous use, whose MMAs had
+        // completed before the stage was free.
         if (lane == 0) {
-            const int iw = warp - 1;
-            const int total = passes * npairs;
+            const bool jl = warp == 1;
+            const int total = passes * nload;
+            int used = 0;
             for (int g = 0; g < total; ++g) {
-                const int kl = g / npairs;
-                const int t = g - kl * npairs;
-                const bool split = t < 2;
-                if (!split && (t & 1) != iw)
-                    continue;
-                // the poller has named load g (use g / kOrder of the slot)
-                if (!ptx::mbar_wait(&sh->ring[g % kOrder], (uint32_t)(g / kOrder) & 1u, &sh->abort,
-                                    a.err))
-                    break;
-                const int pp = *(volatile int *)&sh->order[g % kOrder];
+                const int kl = g / nload;
+                int u = u0 + (g - kl * nload);
+                if (u >= nload)
+                    u -= nload;
                 const int s = g % kPStages;
                 const uint32_t ph = (uint32_t)(g / kPStages) & 1u;
                 if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err))
                     break;
-                ptx::fence_proxy_async_global();
-                atomicMax(&sh->last_use[s], g / kPStages);  // for the drain
-                if (!split || iw == 0) {
-                    // the stage's one arrival; both boxes count against it
+                if (jl) {
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
                     if (kFP4)
-                        ptx::tma_load_2d(sA + (size_t)s * kPStageA, tmapA, pp * kPK, m0,
+                        ptx::tma_load_2d(sA + (size_t)s * kPStageA, tmapA, u * kPK, m0,
                                          &sh->full[s]);
                     else
-                        ptx::tma_load_3d(sA + (size_t)s * kPStageA, tmapA, 0, m0, 2 * pp,
+                        ptx::tma_load_3d(sA + (size_t)s * kPStageA, tmapA, 0, m0, 2 * u,
                                          &sh->full[s]);
-                }
-                if (!split || iw == 1) {
+                } else {
+                    if (!ptx::wait_count(&sh->rdy[u], kl + 1, &sh->abort, a.err))
+                        break;
+                    ptx::fence_proxy_async_global();
                     const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? tmapB1 : tmapB0;
                     if (kFP4)
-                        ptx::tma_load_2d(sB + (size_t)s * kPStageB, mapB, pp * kPK, r0,
+                        ptx::tma_load_2d(sB + (size_t)s * kPStageB, mapB, u * kPK, r0,
                                          &sh->full[s]);
                     else
-                        ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * pp,
+                        ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * u,
                                          &sh->full[s]);
                 }
+                used = g + 1;
             }
+            // the uses of each stage this thread copied, for the drain
+            for (int s = 0; s < kPStages; ++s)
+                sh->copies[s][jl ? 0 : 1] = used > s ? (used - 1 - s) / kPStages + 1 : 0;
         }
     } else if (warp < kFirstEpi) {
         // --------------------------------------------------------------- MMA
@@ -466,8 +464,8 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
             }
             bool ok = true;
             int mine = 0;
-            for (int t = mw; t < npairs; t += kMmaWarps) {
-                const int g = kl * npairs + t;
+            for (int t = mw; t < nload; t += kMmaWarps) {
+                const int g = kl * nload + t;
                 const int s = g % kPStages;
                 const uint32_t ph = (uint32_t)(g / kPStages) & 1u;
                 if (!warp_wait(&sh->full[s], ph, &sh->abort, a.err)) {
@@ -477,22 +475,20 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                 ptx::tc_fence_after();
                 const uint64_t ad = adesc0 + (uint64_t)((s * kPStageA) >> 4);
                 const uint64_t bd = bdesc0 + (uint64_t)((s * kPStageB) >> 4);
-                if (kFP4) {
-                    // one 128-byte row of K per operand row: four K = 64 MMAs
+                // each 128-byte K slice of the operand rows: four MMAs of 32
+                // bytes (K = 32 e4m3 or K = 64 e2m1 values)
 #pragma unroll
-                    for (int kk = 0; kk < kPK / 32; ++kk)
-                        ptx::mma_mxf4_elect(dcol, ad + (uint64_t)((kk * 32) >> 4),
-                                            bd + (uint64_t)((kk * 32) >> 4), kIdesc4,
-                                            tmem + kColSF, tmem + kColSF,
-                                            (mine | kk) != 0 ? 1u : 0u);
-                } else {
+                for (int c = 0; c < PShape<kFP4>::Slices; ++c) {
 #pragma unroll
-                    for (int c = 0; c < kPChunks; ++c) {
-#pragma unroll
-                        for (int kk = 0; kk < kPK / 32; ++kk)
-                            mma_fp8_elect(dcol, ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4),
-                                          bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4),
-                                          (mine | c | kk) != 0 ? 1u : 0u);
+                    for (int kk = 0; kk < kPK / 32; ++kk) {
+                        const uint64_t ak = ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4);
+                        const uint64_t bk = bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4);
+                        const uint32_t acc = (mine | c | kk) != 0 ? 1u : 0u;
+                        if (kFP4)
+                            ptx::mma_mxf4_elect(dcol, ak, bk, kIdesc4, tmem + kColSF,
+                                                tmem + kColSF, acc);
+                        else
+                            mma_fp8_elect(dcol, ak, bk, acc);
                     }
                 }
                 commit_elect(&sh->empty[s]);
@@ -514,7 +510,7 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
         const int et = threadIdx.x - 32 * kFirstEpi;  // 0..511
         const int i = m0 + q * 32 + lane;   // spin of this thread
         const bool live = i < a.N;
-        const bool two_acc = kMmaWarps > 1 && npairs > 1;  // a second accumulator has pairs
+        const bool two_acc = kMmaWarps > 1 && nload > 1;  // a second accumulator has loads
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const size_t plane = (size_t)a.Rp * a.Np;
 
@@ -907,11 +903,24 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
     // completed, each wait bounded.  A stage whose last use was never armed
     // (its arming warp gave up first) waits out the bound, with the error
     // word set.
+    // A use whose S slice was never copied (the S issuer gave up first) is
+    // completed here with a stand-in for its bytes; a use never armed (only
+    // possible when J gave up first) is armed for what was copied.
     __syncthreads();
     if (threadIdx.x < kPStages) {
-        const int u = sh->last_use[threadIdx.x];
-        if (u >= 0)
-            ptx::mbar_drain(&sh->full[threadIdx.x], (uint32_t)u & 1u, a.err);
+        const int st = threadIdx.x;
+        const int jc = sh->copies[st][0], sc = sh->copies[st][1];
+        const int U = jc > sc ? jc : sc;
+        if (U > 0) {
+            const uint32_t landing = (jc >= U ? kPStageA : 0) + (sc >= U ? kPStageB : 0);
+            if (jc >= U) {
+                if (landing < (uint32_t)(kPStageA + kPStageB))
+                    ptx::mbar_complete_tx(&sh->full[st], (uint32_t)(kPStageA + kPStageB) - landing);
+            } else {
+                ptx::mbar_expect_tx(&sh->full[st], landing);
+            }
+            ptx::mbar_drain(&sh->full[st], (uint32_t)(U - 1) & 1u, a.err);
+        }
     }
     if (warp >= kFirstMma && warp < kFirstEpi)
         ptx::mbar_drain(&sh->drain, 0u, a.err);

@@ -94,6 +94,41 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// Shared-memory pass counters: a release store (cta scope) and a bounded
+// acquire wait for "count >= want".  A counter, unlike the parity wait of an
+// mbarrier, stays correct when the waiter is several passes ahead.
+__device__ __forceinline__ void st_release_cta_shared(int *p, int v)
+{
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v)
+                 : "memory");
+}
+
+__device__ __forceinline__ int ld_acquire_cta_shared(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p))
+                 : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool wait_count(const int *cnt, int want, int *abort, int *err)
+{
+    if (ld_acquire_cta_shared(cnt) >= want)
+        return true;
+    const unsigned long long t0 = globaltimer();
+    for (unsigned it = 1;; ++it) {
+        if (ld_acquire_cta_shared(cnt) >= want)
+            return true;
+        if (*(volatile int *)abort)
+            return false;
+        if ((it & 15u) == 0 && globaltimer() - t0 > kWaitBudgetNs) {
+            *(volatile int *)abort = 1;
+            atomicExch(err, kErrTimeout);
+            return false;
+        }
+    }
+}
+
 // L2 cache policies (createpolicy, the whole access range): evict_first for
 // data streamed once per launch, so that lines other CTAs re-read stay.
 __device__ __forceinline__ uint64_t l2_evict_first_policy()
