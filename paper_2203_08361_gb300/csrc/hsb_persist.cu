@@ -6,11 +6,14 @@
 // (eq_Ising) evaluated every `eval_every` steps and at the end (K2000 study).
 //
 // Each CTA owns one tile of 128 spins x 128 replicas for the whole run.  The
-// tile's positions x and momenta y stay in tensor memory next to the FP32
-// accumulator (columns 0-127 accumulator, 128-255 x, 256-383 y; lane = spin),
-// so a step moves only J and the FP8 spin operand S = sgn(x) through L2.  One
-// step of a tile is a dependency chain (the force needs the sign tiles of
-// every row block), so the roles are arranged to shorten it:
+// force is formed transposed, F^T = S^T J (the MMA's M dimension is the
+// tile's replicas, N its spins), so the tile's positions x and momenta y stay
+// in tensor memory next to the FP32 accumulator with lane = replica and
+// column = spin (columns 0-127 accumulator, 128-255 x, 256-383 y, FP4 block
+// scales at 384), and an epilogue thread owns 32 consecutive spins of one
+// replica.  A step moves only J and the sign operand S = sgn(x) through L2.
+// One step of a tile is a dependency chain (the force needs the sign tiles
+// of every row block), so the roles are arranged to shorten it:
 //   warp 0      poller: reads the per-tile "published" flags of the step's
 //               operand (one flag per 128-spin chunk, all lanes at once) and
 //               raises the pass counter of each load unit (a pair of 128-spin
@@ -18,7 +21,9 @@
 //   warps 1-2   TMA issuers: load g fills stage g % 3 (FP4: g % 6) with the
 //               unit's K slices of J (128 rows, warp 1) and of S (warp 2):
 //               one 3-D box of 128 x 128 x 2 bytes each in FP8, one 2-D box
-//               of 128 x 128 bytes in FP4.  Every
+//               of 128 x 128 bytes in FP4; lane l of each warp serves stage
+//               l, and the lanes that may copy do so in one instruction (in
+//               parallel, where one thread's copies are serial).  Every
 //               tile takes its units in a fixed order starting from its own,
 //               so the J slice of a load does not wait for any publication:
 //               warp 1 copies it as soon as the stage is free and the first
@@ -33,16 +38,17 @@
 //               3 + t % 2 and its own
 //               accumulator (split K); the partial forces are exact integers,
 //               so their binary32 sum is the exact force;
-//   warps 4-19  epilogue, four warps per 32-lane quadrant (32 replicas each,
-//               moved through tensor memory 16 columns at a time), in two
-//               phases.  Phase 1 computes only x~ (sgn(x') = sgn(x~), the
-//               walls keep the sign), writes sgn as FP8 into a padded
-//               shared-memory tile that each warp copies to the other operand
-//               buffer with 16-byte stores, and one thread releases the
+//   warps 4-19  epilogue, four warps per 32-lane quadrant (32 replicas) of
+//               tensor memory, one per 32-spin column group, in two phases.
+//               Phase 1 computes only x~ (sgn(x') = sgn(x~), the walls keep
+//               the sign) and writes each thread's 32 signs straight from
+//               registers as one row segment of the other operand buffer (FP8
+//               two 16-byte stores, FP4 one), then one thread releases the
 //               tile's flag at gpu scope.  Phase 2, while the flags travel,
 //               repeats the pinned update in full and stores x' and y' in
 //               tensor memory; on evaluation steps it also forms the
-//               per-replica partial sums of s_i f_i and a snapshot of
+//               per-replica partial sums of s_i f_i (in-thread over its 32
+//               spins, then over the four column groups) and a snapshot of
 //               s = sgn(x(t_k)).  Each warp then releases the accumulator.
 // A final pass after the last update evaluates E(t_Ns).  The best evaluation
 // per replica is chosen afterwards by select_best_kernel.
@@ -95,8 +101,6 @@ struct PShape {
 };
 constexpr int kPStagesMax = 6;
 constexpr int kMaxLoads = 32;  // loads per pass (one flag lane per chunk, nblk <= 32)
-constexpr int kPTileRow = kPM + 16;          // padded row of the sign tile (bytes)
-constexpr int kPTileS = kPN * kPTileRow;     // FP8 sign tile [replica][spin]
 constexpr int kIssuers = 2;
 constexpr int kMmaWarps = 1;  // 2 splits K over two accumulators
 constexpr int kFirstMma = 1 + kIssuers;
@@ -139,7 +143,7 @@ template <bool FP4>
 constexpr size_t persist_smem()
 {
     return 1024 + (size_t)PShape<FP4>::Stages * (PShape<FP4>::StageA + PShape<FP4>::StageB) +
-           kPTileS + sizeof(PShared);
+           sizeof(PShared);
 }
 static_assert(persist_smem<false>() <= 232448, "shared memory per CTA is limited to 227 KB");
 static_assert(persist_smem<true>() <= 232448, "shared memory per CTA is limited to 227 KB");
@@ -233,11 +237,29 @@ __device__ __forceinline__ void load_force(uint32_t tcol, bool two_acc, uint32_t
     ptx::tmem_ld_wait(f);
 }
 
+// 0xFF in byte i of the result for each set bit i (i < 4) of b, else 0x00
+// (the four bits spread to bytes by one multiplication, no carries).
+__device__ __forceinline__ uint32_t byte_mask4(uint32_t b)
+{
+    return (((b & 15u) * 0x204081u) & 0x01010101u) * 0xFFu;
+}
+
+// 0xF in nibble i of the result for each set bit i (i < 8) of b, else 0x0.
+__device__ __forceinline__ uint32_t nibble_mask8(uint32_t b)
+{
+    uint32_t m = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+        m |= ((b >> i) & 1u) * (0xFu << (4 * i));
+    return m;
+}
+
 // q^2 for q = round(2^24 y) (exact scaling, round to nearest even), |y| < 256
-// (else *bad), split into 22-bit chunks; each chunk summed over the warp's 32
-// rows stays below 2^27.  Lane `owner` keeps the three sums of this column.
-__device__ __forceinline__ void nh_sum_square(float y, bool owner, unsigned &s0, unsigned &s1,
-                                              unsigned &s2, bool &bad)
+// (else *bad), split into 22-bit chunks added to s0, s1, s2; over the 32
+// spins of a thread each chunk sum stays below 2^27, over a tile's 128 spins
+// below 2^29.
+__device__ __forceinline__ void nh_square_chunks(float y, unsigned &s0, unsigned &s1,
+                                                 unsigned &s2, bool &bad)
 {
     const float s = fabsf(y * 16777216.0f);
     uint64_t v = 0;
@@ -247,14 +269,9 @@ __device__ __forceinline__ void nh_sum_square(float y, bool owner, unsigned &s0,
     } else {
         bad = true;  // also NaN
     }
-    const unsigned c0 = __reduce_add_sync(0xFFFFFFFFu, (unsigned)(v & 0x3FFFFFu));
-    const unsigned c1 = __reduce_add_sync(0xFFFFFFFFu, (unsigned)((v >> 22) & 0x3FFFFFu));
-    const unsigned c2 = __reduce_add_sync(0xFFFFFFFFu, (unsigned)(v >> 44));
-    if (owner) {
-        s0 = c0;
-        s1 = c1;
-        s2 = c2;
-    }
+    s0 += (unsigned)(v & 0x3FFFFFu);
+    s1 += (unsigned)((v >> 22) & 0x3FFFFFu);
+    s2 += (unsigned)(v >> 44);
 }
 
 // (hi 2^64 + lo) 2^-48 rounded once to binary64 (see nh_update_kernel).
@@ -288,8 +305,7 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint8_t *sA = base;
     uint8_t *sB = base + (size_t)kPStages * kPStageA;
-    uint8_t *sS = sB + (size_t)kPStages * kPStageB;
-    PShared *sh = reinterpret_cast<PShared *>(sS + kPTileS);
+    PShared *sh = reinterpret_cast<PShared *>(sB + (size_t)kPStages * kPStageB);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -399,8 +415,8 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                 }
             }
         }
-    } else if (warp <= kIssuers) {
-        // ------------------------------------------------------- TMA issuers
+    } else if (warp <= kIssuers && !kFP4) {
+        // ------------------------------------------------- TMA issuers (FP8)
         // Both issuers serve every load g in order (stage g % kPStages).  Warp
         // 1 copies the J slice as soon as the stage is free (J does not wait
         // for the step's signs, so a pass's first loads have their J before
@@ -424,23 +440,15 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                     break;
                 if (jl) {
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
-                    if (kFP4)
-                        ptx::tma_load_2d(sA + (size_t)s * kPStageA, tmapA, u * kPK, m0,
-                                         &sh->full[s]);
-                    else
-                        ptx::tma_load_3d(sA + (size_t)s * kPStageA, tmapA, 0, m0, 2 * u,
-                                         &sh->full[s]);
+                    ptx::tma_load_3d(sA + (size_t)s * kPStageA, tmapA, 0, m0, 2 * u,
+                                     &sh->full[s]);
                 } else {
                     if (!ptx::wait_count(&sh->rdy[u], kl + 1, &sh->abort, a.err))
                         break;
                     ptx::fence_proxy_async_global();
                     const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? tmapB1 : tmapB0;
-                    if (kFP4)
-                        ptx::tma_load_2d(sB + (size_t)s * kPStageB, mapB, u * kPK, r0,
-                                         &sh->full[s]);
-                    else
-                        ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * u,
-                                         &sh->full[s]);
+                    ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * u,
+                                     &sh->full[s]);
                 }
                 used = g + 1;
             }
@@ -448,6 +456,82 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
             for (int s = 0; s < kPStages; ++s)
                 sh->copies[s][jl ? 0 : 1] = used > s ? (used - 1 - s) / kPStages + 1 : 0;
         }
+    } else if (warp <= kIssuers) {
+        // ------------------------------------------------- TMA issuers (FP4)
+        // Lane l of each issuer warp owns stage l: the loads g = l, l + S,
+        // l + 2S, ... (S = kPStages), so it sees every phase of its stage in
+        // order.  Copies from one thread complete one after another, so in
+        // each round the lanes whose next copy may go issue it together in
+        // one instruction, and those copies proceed in parallel (for the
+        // six 16 KB FP4 stages this is faster than one thread per warp; for
+        // the three 32 KB FP8 stages it is not).  Warp 1
+        // copies the J slices as soon as a stage is free (J does not wait for
+        // the step's signs, so a pass's first loads have their J before its
+        // signs are published) and posts the stage's expected bytes (its one
+        // arrival); warp 2 copies the S slices once the unit is published.  A
+        // copy of S that lands first takes the transaction count below zero
+        // until then: it cannot belong to the previous use, whose MMAs had
+        // completed before the stage was free.
+        const bool jl = warp == 1;
+        const int total = passes * nload;
+        int g = lane;  // this lane's next load
+        int used = 0;
+        unsigned long long t0 = 0;
+        int idle = 0;
+        while (true) {
+            const bool active = lane < kPStages && g < total;
+            if (!__any_sync(0xFFFFFFFFu, active))
+                break;
+            bool go = false;
+            int kl = 0, u = 0;
+            if (active) {
+                kl = g / nload;
+                u = u0 + (g - kl * nload);
+                if (u >= nload)
+                    u -= nload;
+                // a non-blocking test: a suspended lane would hold back the
+                // copies of the others
+                go = ptx::mbar_test_wait(&sh->empty[lane], ((uint32_t)(g / kPStages) & 1u) ^ 1u);
+                if (go && !jl)
+                    go = ptx::ld_acquire_cta_shared(&sh->rdy[u]) >= kl + 1;
+            }
+            if (go) {
+                if (jl) {
+                    ptx::mbar_expect_tx(&sh->full[lane], (uint32_t)(kPStageA + kPStageB));
+                    ptx::tma_load_2d(sA + (size_t)lane * kPStageA, tmapA, u * kPK, m0,
+                                     &sh->full[lane]);
+                } else {
+                    ptx::fence_proxy_async_global();
+                    const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? tmapB1 : tmapB0;
+                    ptx::tma_load_2d(sB + (size_t)lane * kPStageB, mapB, u * kPK, r0,
+                                     &sh->full[lane]);
+                }
+                g += kPStages;
+                ++used;
+            }
+            if (__any_sync(0xFFFFFFFFu, go)) {
+                t0 = 0;
+                continue;
+            }
+            // no copy could go this round: bounded wait for progress
+            int give_up = 0;
+            if (lane == 0) {
+                if (*(volatile int *)&sh->abort) {
+                    give_up = 1;
+                } else if (t0 == 0) {
+                    t0 = ptx::globaltimer();
+                } else if ((++idle & 15) == 0 && ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
+                    *(volatile int *)&sh->abort = 1;
+                    atomicExch(a.err, kErrTimeout);
+                    give_up = 1;
+                }
+            }
+            if (__shfl_sync(0xFFFFFFFFu, give_up, 0))
+                break;
+        }
+        // the uses of its stage this lane copied, for the drain
+        if (lane < kPStages)
+            sh->copies[lane][jl ? 0 : 1] = used;
     } else if (warp < kFirstEpi) {
         // --------------------------------------------------------------- MMA
         // descriptors of stage 0; a stage or K step further is a plain add on
@@ -481,14 +565,16 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                 for (int c = 0; c < PShape<kFP4>::Slices; ++c) {
 #pragma unroll
                     for (int kk = 0; kk < kPK / 32; ++kk) {
-                        const uint64_t ak = ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4);
-                        const uint64_t bk = bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4);
+                        // A = the S slice (replicas), B = the J slice (spins):
+                        // the accumulator holds F^T, lane = replica
+                        const uint64_t sk = bd + (uint64_t)((c * kPN * kPK + kk * 32) >> 4);
+                        const uint64_t jk = ad + (uint64_t)((c * kPM * kPK + kk * 32) >> 4);
                         const uint32_t acc = (mine | c | kk) != 0 ? 1u : 0u;
                         if (kFP4)
-                            ptx::mma_mxf4_elect(dcol, ak, bk, kIdesc4, tmem + kColSF,
+                            ptx::mma_mxf4_elect(dcol, sk, jk, kIdesc4, tmem + kColSF,
                                                 tmem + kColSF, acc);
                         else
-                            mma_fp8_elect(dcol, ak, bk, acc);
+                            mma_fp8_elect(dcol, sk, jk, acc);
                     }
                 }
                 commit_elect(&sh->empty[s]);
@@ -504,28 +590,50 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
         commit_elect(&sh->drain);  // arrives once this warp's MMAs have completed
     } else {
         // ---------------------------------------------------------- epilogue
+        // The force is formed transposed (lane = replica, column = spin), so
+        // a thread owns 32 consecutive spins of one replica: its signs are
+        // one contiguous row segment of the next operand, stored straight
+        // from registers.
         const int ew = warp - kFirstEpi;    // 0..15
         const int q = warp & 3;             // tensor-memory lane quadrant
-        const int c0 = (ew >> 2) * 32;      // first of this warp's 32 replica columns
+        const int cg = ew >> 2;             // spin column group (32 spins)
         const int et = threadIdx.x - 32 * kFirstEpi;  // 0..511
-        const int i = m0 + q * 32 + lane;   // spin of this thread
-        const bool live = i < a.N;
+        const int rl = q * 32 + lane;       // replica of this thread within the tile
+        const int r = r0 + rl;
+        const int ib = m0 + cg * 32;        // first of this thread's 32 spins
+        const uint32_t col0 = (uint32_t)(cg * 32);
         const bool two_acc = kMmaWarps > 1 && nload > 1;  // a second accumulator has loads
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
         const size_t plane = (size_t)a.Rp * a.Np;
+        // live spins of this thread's 32 (padded spins publish a zero code)
+        const uint32_t live = ib + 32 <= a.N ? 0xFFFFFFFFu
+                              : ib >= a.N   ? 0u
+                                            : ((1u << (a.N - ib)) - 1u);
+        uint8_t *const srow_a = a.S8a + (kFP4 ? (size_t)r * (a.Kp / 2) + ib / 2
+                                              : (size_t)r * a.Np + ib);
+        uint8_t *const srow_b = a.S8b + (kFP4 ? (size_t)r * (a.Kp / 2) + ib / 2
+                                              : (size_t)r * a.Np + ib);
 
         // initial state of the tile into tensor memory
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             uint32_t xr[16], yr[16];
+            const float4 *xs = reinterpret_cast<const float4 *>(a.X + (size_t)r * a.Np + ib + 16 * h);
+            const float4 *ys = reinterpret_cast<const float4 *>(a.Y + (size_t)r * a.Np + ib + 16 * h);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const size_t e = (size_t)(r0 + c0 + h * 16 + j) * a.Np + i;
-                xr[j] = __float_as_uint(a.X[e]);
-                yr[j] = __float_as_uint(a.Y[e]);
+            for (int v = 0; v < 4; ++v) {
+                const float4 xv = xs[v], yv = ys[v];
+                xr[4 * v] = __float_as_uint(xv.x);
+                xr[4 * v + 1] = __float_as_uint(xv.y);
+                xr[4 * v + 2] = __float_as_uint(xv.z);
+                xr[4 * v + 3] = __float_as_uint(xv.w);
+                yr[4 * v] = __float_as_uint(yv.x);
+                yr[4 * v + 1] = __float_as_uint(yv.y);
+                yr[4 * v + 2] = __float_as_uint(yv.z);
+                yr[4 * v + 3] = __float_as_uint(yv.w);
             }
-            ptx::tmem_st16(tmem + lane_off + kColX + c0 + h * 16, xr);
-            ptx::tmem_st16(tmem + lane_off + kColY + c0 + h * 16, yr);
+            ptx::tmem_st16(tmem + lane_off + kColX + col0 + 16 * h, xr);
+            ptx::tmem_st16(tmem + lane_off + kColY + col0 + 16 * h, yr);
         }
         ptx::tmem_st_wait();
         if (kNH && et < kPN) {
@@ -539,10 +647,6 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
         bool nh_bad = false;
 
         bool left = false;
-        // this spin's byte in row `col` of the sign tile (FP4: the byte of
-        // this spin pair, written by its even lane)
-        uint8_t *srow = sS + q * 32 + lane;
-        uint8_t *srow4 = sS + q * 16 + (lane >> 1);
         const StepConsts2 k2 = step_consts2(a.c);
         float pk_next = a.nsteps > 0 ? a.pk[a.k_begin] : 0.f;
         for (int kl = 0; kl < passes; ++kl) {
@@ -624,12 +728,12 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                     sh->gnh[et] = __double2float_rn(__dmul_rn(-x, a.dt64));
                 }
             }
-            // x and y of the first 16 columns (the MMA does not write them)
-            // and v = p_k x of their update, formed in the MMA's shadow
+            // x and y of the first 16 spins (the MMA does not write them) and
+            // v = p_k x of their update, formed in the MMA's shadow
             uint32_t xpre[16], ypre[16];
             uint64_t vpre[8];
-            ptx::tmem_ld16(tmem + lane_off + kColX + c0, xpre);
-            ptx::tmem_ld16(tmem + lane_off + kColY + c0, ypre);
+            ptx::tmem_ld16(tmem + lane_off + kColX + col0, xpre);
+            ptx::tmem_ld16(tmem + lane_off + kColY + col0, ypre);
             ptx::tmem_ld_wait(xpre);
             ptx::tmem_ld_wait(ypre);
 #pragma unroll
@@ -644,18 +748,22 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
             ptx::tc_fence_after();
 
             if (!final_pass) {
-                // ---- phase 1: only sgn(x') = sgn(x~), published before the
-                // rest of the update (the next step of every tile waits for
-                // it).  The operations are those of the update up to p = q yt;
-                // x~ = fl(x + p) is negative exactly when p < -x (a nonzero
-                // sum of two binary32 values does not round to zero, a zero
-                // sum rounds to +0).
+                // ---- phase 1: only sgn(x') = sgn(x~) of this thread's 32
+                // spins, published before the rest of the update (the next
+                // step of every tile waits for it).  The operations are those
+                // of the update up to p = q yt; x~ = fl(x + p) is negative
+                // exactly when p < -x (a nonzero sum of two binary32 values
+                // does not round to zero, a zero sum rounds to +0).  FP8: one
+                // sign byte per spin (+1 = 0x38, -1 = 0xB8), two 16-byte
+                // stores; FP4: one e2m1 code per spin, spins 2m and 2m + 1 in
+                // the low and high nibble of a byte, one 16-byte store.
+                uint8_t *dst = ((a.par0 + kl + 1) & 1) ? srow_b : srow_a;
+                uint32_t w4[4];  // FP4: the 16 bytes of both halves
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const uint32_t col0 = (uint32_t)(c0 + h * 16);
                     uint32_t f[16], xr[16], yr[16];
                     uint64_t v[8];
-                    load_force(tmem + lane_off + col0, two_acc, f);
+                    load_force(tmem + lane_off + col0 + 16 * h, two_acc, f);
                     if (h == 0) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
@@ -666,14 +774,18 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                         for (int j = 0; j < 8; ++j)
                             v[j] = vpre[j];
                     } else {
-                        ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
-                        ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
+                        ptx::tmem_ld16(tmem + lane_off + kColX + col0 + 16, xr);
+                        ptx::tmem_ld16(tmem + lane_off + kColY + col0 + 16, yr);
                         ptx::tmem_ld_wait(xr);
                         ptx::tmem_ld_wait(yr);
 #pragma unroll
                         for (int j = 0; j < 16; j += 2)
                             v[j / 2] = f2_fma(pk2, f2_pack_bits(xr[j], xr[j + 1]), k2.z);
                     }
+                    // the negative spins' sign bits placed in their codes:
+                    // FP8 bit 7 of byte j (0x38 -> 0xB8), FP4 bit 3 of
+                    // nibble j (0x2 -> 0xA); m = all ones when negative
+                    uint32_t negw[kFP4 ? 2 : 4] = {};
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         const uint64_t u = f2_fma(k2.c0, f2_pack_bits(f[j], f[j + 1]), k2.z);
@@ -681,47 +793,39 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                         const uint64_t wd = f2_fma(w, k2.dt, k2.z);
                         const uint64_t yt = f2_add(f2_pack_bits(yr[j], yr[j + 1]), wd);
                         const uint64_t qy = f2_fma(k2.q, yt, k2.z);
-                        const bool n0 = f2_lo(qy) < -__uint_as_float(xr[j]);
-                        const bool n1 = f2_hi(qy) < -__uint_as_float(xr[j + 1]);
+                        const uint32_t mk0 = 0u - (uint32_t)(f2_lo(qy) < -__uint_as_float(xr[j]));
+                        const uint32_t mk1 =
+                            0u - (uint32_t)(f2_hi(qy) < -__uint_as_float(xr[j + 1]));
                         if (kFP4) {
-                            // spins 2m (even lane) and 2m + 1 share a byte
-                            const uint32_t b0 = live ? (n0 ? kFp4MinusOne : kFp4PlusOne) : 0u;
-                            const uint32_t b1 = live ? (n1 ? kFp4MinusOne : kFp4PlusOne) : 0u;
-                            const uint32_t u0 = __shfl_down_sync(0xFFFFFFFFu, b0, 1);
-                            const uint32_t u1 = __shfl_down_sync(0xFFFFFFFFu, b1, 1);
-                            if ((lane & 1) == 0) {
-                                srow4[(col0 + j) * kPTileRow] = (uint8_t)(b0 | (u0 << 4));
-                                srow4[(col0 + j + 1) * kPTileRow] = (uint8_t)(b1 | (u1 << 4));
-                            }
+                            negw[j / 8] |= (mk0 & (0x8u << (4 * (j % 8)))) |
+                                           (mk1 & (0x8u << (4 * ((j + 1) % 8))));
                         } else {
-                            srow[(col0 + j) * kPTileRow] =
-                                live ? (n0 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
-                            srow[(col0 + j + 1) * kPTileRow] =
-                                live ? (n1 ? kFp8MinusOne : kFp8PlusOne) : (uint8_t)0;
+                            negw[j / 4] |= (mk0 & (0x80u << (8 * (j % 4)))) |
+                                           (mk1 & (0x80u << (8 * ((j + 1) % 4))));
                         }
                     }
-                }
-                // this warp's 32 replicas x 32 spins of S(t_{k+1}) into the
-                // other operand buffer with 16-byte stores: FP8 two per lane
-                // (32-byte row segments), FP4 one (16 bytes of packed pairs)
-                __syncwarp();
-                uint8_t *sdst = ((a.par0 + kl + 1) & 1) ? a.S8b : a.S8a;
-                if (kFP4) {
-                    const size_t pitch = (size_t)a.Kp / 2;
-                    const uint4 val =
-                        *reinterpret_cast<const uint4 *>(sS + (c0 + lane) * kPTileRow + q * 16);
-                    *reinterpret_cast<uint4 *>(sdst + (size_t)(r0 + c0 + lane) * pitch +
-                                               (m0 + q * 32) / 2) = val;
-                } else {
-                    uint8_t *dst = sdst + (size_t)(r0 + c0) * a.Np + m0 + q * 32;
+                    const uint32_t lv = (live >> (16 * h)) & 0xFFFFu;
+                    if (kFP4) {
 #pragma unroll
-                    for (int v = lane; v < 64; v += 32) {
-                        const int row = v >> 1, off = (v & 1) * 16;
-                        const uint4 val = *reinterpret_cast<const uint4 *>(
-                            sS + (c0 + row) * kPTileRow + q * 32 + off);
-                        *reinterpret_cast<uint4 *>(dst + (size_t)row * a.Np + off) = val;
+                        for (int m = 0; m < 2; ++m) {
+                            uint32_t wd4 = 0x22222222u | negw[m];
+                            if (lv != 0xFFFFu)  // padded spins publish 0
+                                wd4 &= nibble_mask8((lv >> (8 * m)) & 0xFFu);
+                            w4[2 * h + m] = wd4;
+                        }
+                    } else {
+                        uint32_t wv[4];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            wv[m] = 0x38383838u | negw[m];
+                            if (lv != 0xFFFFu)  // padded spins publish 0
+                                wv[m] &= byte_mask4((lv >> (4 * m)) & 0xFu);
+                        }
+                        *reinterpret_cast<uint4 *>(dst + 16 * h) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
                     }
                 }
+                if (kFP4)
+                    *reinterpret_cast<uint4 *>(dst) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
                 epi_bar();
                 if (et == 0 && !(mb == a.drop_mb && rb == 0)) {
                     // every epilogue thread's S stores precede the barrier; the
@@ -731,92 +835,60 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                 }
             }
 
-            // ---- phase 2: energy of s(t_k) on evaluation passes, and the full
-            // update of x and y in tensor memory (off the critical path: the
-            // next force needs the flags of every tile first)
+            // ---- phase 2: energy of s(t_k) on evaluation passes, the trace
+            // sums on traced passes, and the full update of x and y in tensor
+            // memory (off the critical path: the next force needs the flags of
+            // every tile first)
+            float gfr = 0.f;  // Nose-Hoover friction factor of this replica
+            if (kNH)
+                gfr = sh->gnh[rl];
+            int esum = 0;     // sum of s_i f_i over this thread's spins (exact)
+            float ysum = 0.f; // sum of y_i(t_k)^2 over them (trace)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const uint32_t col0 = (uint32_t)(c0 + h * 16);
                 uint32_t f[16], xr[16], yr[16];
-                ptx::tmem_ld16(tmem + lane_off + kColX + col0, xr);
-                ptx::tmem_ld16(tmem + lane_off + kColY + col0, yr);
-                load_force(tmem + lane_off + col0, two_acc, f);
+                ptx::tmem_ld16(tmem + lane_off + kColX + col0 + 16 * h, xr);
+                ptx::tmem_ld16(tmem + lane_off + kColY + col0 + 16 * h, yr);
+                load_force(tmem + lane_off + col0 + 16 * h, two_acc, f);
                 ptx::tmem_ld_wait(xr);
                 ptx::tmem_ld_wait(yr);
-                if (tm >= 0) {
-                    // s_i f_i is an exact integer: one redux per column (lane j
-                    // keeps column col0 + j); y_i^2 through the transposed
-                    // butterfly (lane l ends with column (l >> 1) & 15)
-                    int emine = 0;
-                    float tv[16];
+                if (e >= 0 || tm >= 0) {
+                    uint32_t sb[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const float fj = __uint_as_float(f[j]);
+                        const bool lv = (live >> (16 * h + j)) & 1u;
                         const float x0 = __uint_as_float(xr[j]);
-                        const int term = live ? (x0 >= 0.f ? (int)fj : -(int)fj) : 0;
-                        const int sum = __reduce_add_sync(0xFFFFFFFFu, term);
-                        if (lane == j)
-                            emine = sum;
-                        const float y0 = __uint_as_float(yr[j]);
-                        tv[j] = __fmul_rn(y0, y0);  // y_i(t_k)^2 (Eq. eq_TInst)
-                    }
-#pragma unroll
-                    for (int m = 16, n = 8; m >= 2; m >>= 1, n >>= 1) {
-                        const bool up = (lane & m) != 0;
-#pragma unroll
-                        for (int kk = 0; kk < n; ++kk) {
-                            const float sa = up ? tv[kk] : tv[kk + n];
-                            const float ra = __shfl_xor_sync(0xFFFFFFFFu, sa, m);
-                            tv[kk] = (up ? tv[kk + n] : tv[kk]) + ra;
+                        const int fj = (int)__uint_as_float(f[j]);  // exact integer force
+                        esum += lv ? (x0 >= 0.f ? fj : -fj) : 0;
+                        if (tm >= 0) {
+                            const float y0 = __uint_as_float(yr[j]);
+                            ysum = __fadd_rn(ysum, __fmul_rn(y0, y0));  // y_i(t_k)^2 (Eq. eq_TInst)
                         }
+                        sb[j >> 2] |= (lv ? (uint32_t)fp8_sign(x0) : 0u) << (8 * (j & 3));
                     }
-                    const float tsum = tv[0] + __shfl_xor_sync(0xFFFFFFFFu, tv[0], 1);
-                    if (lane < 16)
-                        sh->tre[q][col0 + lane] = emine;
-                    if ((lane & 1) == 0)
-                        sh->trt[q][col0 + ((lane >> 1) & 15)] = tsum;
-                }
-                if (e >= 0) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = col0 + j;
-                        const float fj = __uint_as_float(f[j]);
-                        const float x0 = __uint_as_float(xr[j]);
-                        float term = live ? (x0 >= 0.f ? fj : -fj) : 0.f;
-#pragma unroll
-                        for (int off = 16; off > 0; off >>= 1)
-                            term += __shfl_xor_sync(0xFFFFFFFFu, term, off);
-                        if (lane == 0)
-                            sh->red[q][col] = term;
-                        a.Snap[(size_t)e * plane + (size_t)(r0 + col) * a.Np + i] =
-                            live ? fp8_sign(x0) : (uint8_t)0;
-                    }
+                    if (e >= 0)
+                        *reinterpret_cast<uint4 *>(a.Snap + (size_t)e * plane + (size_t)r * a.Np +
+                                                   ib + 16 * h) =
+                            make_uint4(sb[0], sb[1], sb[2], sb[3]);
                 }
                 if (!final_pass) {
-                    // two replicas per packed binary32 operation
+                    StepConsts2 kn = k2;
+                    if (kNH)
+                        kn.g = f2_pack(gfr, gfr);  // per-replica friction in place of gamma dt
+                    // two spins per packed binary32 operation
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         float xn0, xn1;
                         uint64_t yn;
-                        if (kNH) {
-                            // per-replica friction factor in place of gamma dt
-                            StepConsts2 kn = k2;
-                            kn.g = f2_pack(sh->gnh[col0 + j], sh->gnh[col0 + j + 1]);
-                            sb_update2(f2_pack_bits(f[j], f[j + 1]),
-                                       f2_pack_bits(xr[j], xr[j + 1]),
-                                       f2_pack_bits(yr[j], yr[j + 1]), pk2, kn, xn0, xn1, yn);
-                        } else {
-                            sb_update2(f2_pack_bits(f[j], f[j + 1]),
-                                       f2_pack_bits(xr[j], xr[j + 1]),
-                                       f2_pack_bits(yr[j], yr[j + 1]), pk2, k2, xn0, xn1, yn);
-                        }
+                        sb_update2(f2_pack_bits(f[j], f[j + 1]), f2_pack_bits(xr[j], xr[j + 1]),
+                                   f2_pack_bits(yr[j], yr[j + 1]), pk2, kn, xn0, xn1, yn);
                         xr[j] = __float_as_uint(xn0);
                         xr[j + 1] = __float_as_uint(xn1);
                         yr[j] = (uint32_t)yn;
                         yr[j + 1] = (uint32_t)(yn >> 32);
                     }
-                    ptx::tmem_st16(tmem + lane_off + kColX + col0, xr);
-                    ptx::tmem_st16(tmem + lane_off + kColY + col0, yr);
+                    ptx::tmem_st16(tmem + lane_off + kColX + col0 + 16 * h, xr);
+                    ptx::tmem_st16(tmem + lane_off + kColY + col0 + 16 * h, yr);
                 }
             }
             ptx::tc_fence_before();
@@ -826,6 +898,13 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
             if (lane == 0)
                 ptx::mbar_arrive(&sh->tmem_empty);  // this warp has read the accumulator
             if (e >= 0 || tm >= 0) {
+                // the four spin column groups' sums of each replica
+                if (e >= 0)
+                    sh->red[cg][rl] = (float)esum;
+                if (tm >= 0) {
+                    sh->tre[cg][rl] = esum;
+                    sh->trt[cg][rl] = ysum;
+                }
                 epi_bar();
                 if (et < kPN && e >= 0) {
                     const float s = sh->red[0][et] + sh->red[1][et] + sh->red[2][et] + sh->red[3][et];
@@ -840,23 +919,23 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
             }
             if (kNH && !final_pass) {
                 // this tile's sums of q^2 of y(t_{k+1}) (in tensor memory; the
-                // accumulator is already released): slot kl % 3, then the flag
-                // lane l ends with the sums of column c0 + l; one warp-wide
-                // atomic per chunk adds them to the tile's sums
+                // accumulator is already released): slot kl % 3, then the
+                // flag.  Each thread sums the 22-bit chunks of q^2 over its 32
+                // spins (each chunk sum below 2^27); one shared-memory atomic
+                // per chunk adds them to the replica's sums
                 unsigned s0 = 0u, s1 = 0u, s2 = 0u;
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     uint32_t yr[16];
-                    ptx::tmem_ld16(tmem + lane_off + kColY + (uint32_t)(c0 + h * 16), yr);
+                    ptx::tmem_ld16(tmem + lane_off + kColY + col0 + 16 * h, yr);
                     ptx::tmem_ld_wait(yr);
 #pragma unroll
                     for (int j = 0; j < 16; ++j)
-                        nh_sum_square(__uint_as_float(yr[j]), lane == h * 16 + j, s0, s1, s2,
-                                      nh_bad);
+                        nh_square_chunks(__uint_as_float(yr[j]), s0, s1, s2, nh_bad);
                 }
-                atomicAdd(&sh->nhacc[0][c0 + lane], s0);
-                atomicAdd(&sh->nhacc[1][c0 + lane], s1);
-                atomicAdd(&sh->nhacc[2][c0 + lane], s2);
+                atomicAdd(&sh->nhacc[0][rl], s0);
+                atomicAdd(&sh->nhacc[1][rl], s1);
+                atomicAdd(&sh->nhacc[2][rl], s2);
                 epi_bar();  // every warp's atomics are in
                 if (et < kPN) {
                     const uint64_t c0 = sh->nhacc[0][et], c1 = sh->nhacc[1][et],
@@ -885,14 +964,19 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 uint32_t xr[16], yr[16];
-                ptx::tmem_ld16(tmem + lane_off + kColX + c0 + h * 16, xr);
-                ptx::tmem_ld16(tmem + lane_off + kColY + c0 + h * 16, yr);
+                ptx::tmem_ld16(tmem + lane_off + kColX + col0 + 16 * h, xr);
+                ptx::tmem_ld16(tmem + lane_off + kColY + col0 + 16 * h, yr);
                 ptx::tmem_ld_wait();
+                float4 *xd = reinterpret_cast<float4 *>(a.X + (size_t)r * a.Np + ib + 16 * h);
+                float4 *yd = reinterpret_cast<float4 *>(a.Y + (size_t)r * a.Np + ib + 16 * h);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const size_t eidx = (size_t)(r0 + c0 + h * 16 + j) * a.Np + i;
-                    a.X[eidx] = __uint_as_float(xr[j]);
-                    a.Y[eidx] = __uint_as_float(yr[j]);
+                for (int v = 0; v < 4; ++v) {
+                    xd[v] = make_float4(__uint_as_float(xr[4 * v]), __uint_as_float(xr[4 * v + 1]),
+                                        __uint_as_float(xr[4 * v + 2]),
+                                        __uint_as_float(xr[4 * v + 3]));
+                    yd[v] = make_float4(__uint_as_float(yr[4 * v]), __uint_as_float(yr[4 * v + 1]),
+                                        __uint_as_float(yr[4 * v + 2]),
+                                        __uint_as_float(yr[4 * v + 3]));
                 }
             }
         }
