@@ -149,9 +149,10 @@ cudaError_t launch_tc_fp8_step(cudaStream_t st, const TcPlan *plan, int parity, 
 // The same step with packed FP4 e2m1 operands (tcgen05 kind::mxf4, unit
 // block scales): J4 [Np][Kp/2] and S4 [Rcap][Kp/2] bytes, two values per byte
 // (+1 = 0x2, -1 = 0xA, 0 = 0x0, the even index in the low nibble), Kp = Np
-// rounded up to 256 with zero padding.  Only mapA (J4, box 128 rows), mapB[2]
-// (S4, box 128 rows: persistent kernel) and mapBw[2] (S4, box 192 rows:
-// per-step kernel) of an FP4 plan are encoded.
+// rounded up to 256 with zero padding.  Only mapA (J4, box 128 rows) and
+// mapBw[2] (S4, box 192 rows) for the per-step kernel and mapA3 / mapB3[2]
+// (3-D, two 128-byte slices, 128 rows) for the persistent kernel are encoded
+// in an FP4 plan.
 cudaError_t tc_fp4_plan_create(TcPlan **out, const uint8_t *J4, const uint8_t *S4a,
                                const uint8_t *S4b, int Np, int Kp, int Rp);
 cudaError_t launch_tc_fp4_step(cudaStream_t st, const TcPlan *plan, int parity, bool energy,

@@ -16,14 +16,12 @@
 // of every row block), so the roles are arranged to shorten it:
 //   warp 0      poller: reads the per-tile "published" flags of the step's
 //               operand (one flag per 128-spin chunk, all lanes at once) and
-//               raises the pass counter of each load unit (a pair of 128-spin
-//               K chunks) whose chunks are both published;
-//   warps 1-2   TMA issuers: load g fills stage g % 3 (FP4: g % 6) with the
-//               unit's K slices of J (128 rows, warp 1) and of S (warp 2):
-//               one 3-D box of 128 x 128 x 2 bytes each in FP8, one 2-D box
-//               of 128 x 128 bytes in FP4; lane l of each warp serves stage
-//               l, and the lanes that may copy do so in one instruction (in
-//               parallel, where one thread's copies are serial).  Every
+//               raises the pass counter of each load unit (the 128-spin K
+//               chunks of two 128-byte slices: two in FP8, four in FP4) whose
+//               chunks are all published;
+//   warps 1-2   TMA issuers: load g fills stage g % 3 with the unit's two
+//               128-byte K slices of J (128 rows, warp 1) and of S (warp 2),
+//               one 3-D box of 128 x 128 x 2 bytes each.  Every
 //               tile takes its units in a fixed order starting from its own,
 //               so the J slice of a load does not wait for any publication:
 //               warp 1 copies it as soon as the stage is free and the first
@@ -87,19 +85,19 @@ namespace {
 constexpr int kPM = 128;
 constexpr int kPN = 128;
 constexpr int kPK = 128;
-// One load covers a pair of 128-spin K chunks of each operand's 128 rows: in
-// FP8 one 3-D box of two 128-byte slices (32 KB), in FP4 one 128-byte slice
-// of 256 packed e2m1 values (16 KB), so the FP4 stages are half as large and
-// twice as many.  (Boxes of one 128-byte FP8 slice, twice as many copies,
-// made the FP8 step loop slower.)
+// One load is one 3-D box of two 128-byte K slices of each operand's 128
+// rows (32 KB per operand): 256 spins in FP8, 512 packed e2m1 values in FP4.
+// Three stages of 64 KB.  (Stages of one slice, twice as many copies, were
+// slower for both precisions, also with one issuing lane per stage.)
 template <bool FP4>
 struct PShape {
-    static constexpr int Slices = FP4 ? 1 : 2;  // 128-byte K slices per load
-    static constexpr int Stages = FP4 ? 6 : 3;
+    static constexpr int Slices = 2;  // 128-byte K slices per load
+    static constexpr int Stages = 3;
     static constexpr int StageA = Slices * kPM * kPK;
     static constexpr int StageB = Slices * kPN * kPK;
+    static constexpr int ChunksPerLoad = Slices * (FP4 ? 2 : 1);  // 128-spin chunks
 };
-constexpr int kPStagesMax = 6;
+constexpr int kPStagesMax = 3;
 constexpr int kMaxLoads = 32;  // loads per pass (one flag lane per chunk, nblk <= 32)
 constexpr int kIssuers = 2;
 constexpr int kMmaWarps = 1;  // 2 splits K over two accumulators
@@ -314,11 +312,11 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
     const int m0 = mb * kPM;
     const int r0 = rb * kPN;
     const int nblk = a.nblk;
-    // loads of a pass: unit u covers K chunks 2u, 2u + 1; a chunk past the
-    // end reads as zero.  Every tile takes the units in the order u0, u0 + 1,
+    // loads of a pass: unit u covers K chunks kCpl u .. kCpl u + kCpl - 1; a
+    // chunk past the end reads as zero.  Every tile takes the units in the order u0, u0 + 1,
     // ... cyclically from its own (the first published, by this CTA), so
     // tiles sharing rows ask for different lines at a time
-    constexpr int kCpl = 2;
+    constexpr int kCpl = PShape<kFP4>::ChunksPerLoad;
     const int nload = (nblk + kCpl - 1) / kCpl;
     const int u0 = mb / kCpl;
     const int passes = a.nsteps + a.final_pass;
@@ -387,8 +385,9 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                 pending &= ~rmask;
                 bool unit = false;
                 if ((left >> lane) & 1u) {
-                    const uint32_t need =
-                        2 * lane + 1 < nblk ? (3u << (2 * lane)) : (1u << (2 * lane));
+                    const int c0 = kCpl * lane;
+                    const int nc = nblk - c0 < kCpl ? nblk - c0 : kCpl;
+                    const uint32_t need = ((1u << nc) - 1u) << c0;
                     unit = (have & need) == need;
                 }
                 if (unit)
@@ -415,8 +414,8 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                 }
             }
         }
-    } else if (warp <= kIssuers && !kFP4) {
-        // ------------------------------------------------- TMA issuers (FP8)
+    } else if (warp <= kIssuers) {
+        // ------------------------------------------------------- TMA issuers
         // Both issuers serve every load g in order (stage g % kPStages).  Warp
         // 1 copies the J slice as soon as the stage is free (J does not wait
         // for the step's signs, so a pass's first loads have their J before
@@ -440,15 +439,15 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
                     break;
                 if (jl) {
                     ptx::mbar_expect_tx(&sh->full[s], (uint32_t)(kPStageA + kPStageB));
-                    ptx::tma_load_3d(sA + (size_t)s * kPStageA, tmapA, 0, m0, 2 * u,
-                                     &sh->full[s]);
+                    ptx::tma_load_3d(sA + (size_t)s * kPStageA, tmapA, 0, m0,
+                                     PShape<kFP4>::Slices * u, &sh->full[s]);
                 } else {
                     if (!ptx::wait_count(&sh->rdy[u], kl + 1, &sh->abort, a.err))
                         break;
                     ptx::fence_proxy_async_global();
                     const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? tmapB1 : tmapB0;
-                    ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0, 2 * u,
-                                     &sh->full[s]);
+                    ptx::tma_load_3d(sB + (size_t)s * kPStageB, mapB, 0, r0,
+                                     PShape<kFP4>::Slices * u, &sh->full[s]);
                 }
                 used = g + 1;
             }
@@ -456,82 +455,6 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
             for (int s = 0; s < kPStages; ++s)
                 sh->copies[s][jl ? 0 : 1] = used > s ? (used - 1 - s) / kPStages + 1 : 0;
         }
-    } else if (warp <= kIssuers) {
-        // ------------------------------------------------- TMA issuers (FP4)
-        // Lane l of each issuer warp owns stage l: the loads g = l, l + S,
-        // l + 2S, ... (S = kPStages), so it sees every phase of its stage in
-        // order.  Copies from one thread complete one after another, so in
-        // each round the lanes whose next copy may go issue it together in
-        // one instruction, and those copies proceed in parallel (for the
-        // six 16 KB FP4 stages this is faster than one thread per warp; for
-        // the three 32 KB FP8 stages it is not).  Warp 1
-        // copies the J slices as soon as a stage is free (J does not wait for
-        // the step's signs, so a pass's first loads have their J before its
-        // signs are published) and posts the stage's expected bytes (its one
-        // arrival); warp 2 copies the S slices once the unit is published.  A
-        // copy of S that lands first takes the transaction count below zero
-        // until then: it cannot belong to the previous use, whose MMAs had
-        // completed before the stage was free.
-        const bool jl = warp == 1;
-        const int total = passes * nload;
-        int g = lane;  // this lane's next load
-        int used = 0;
-        unsigned long long t0 = 0;
-        int idle = 0;
-        while (true) {
-            const bool active = lane < kPStages && g < total;
-            if (!__any_sync(0xFFFFFFFFu, active))
-                break;
-            bool go = false;
-            int kl = 0, u = 0;
-            if (active) {
-                kl = g / nload;
-                u = u0 + (g - kl * nload);
-                if (u >= nload)
-                    u -= nload;
-                // a non-blocking test: a suspended lane would hold back the
-                // copies of the others
-                go = ptx::mbar_test_wait(&sh->empty[lane], ((uint32_t)(g / kPStages) & 1u) ^ 1u);
-                if (go && !jl)
-                    go = ptx::ld_acquire_cta_shared(&sh->rdy[u]) >= kl + 1;
-            }
-            if (go) {
-                if (jl) {
-                    ptx::mbar_expect_tx(&sh->full[lane], (uint32_t)(kPStageA + kPStageB));
-                    ptx::tma_load_2d(sA + (size_t)lane * kPStageA, tmapA, u * kPK, m0,
-                                     &sh->full[lane]);
-                } else {
-                    ptx::fence_proxy_async_global();
-                    const CUtensorMap *mapB = ((a.par0 + kl) & 1) ? tmapB1 : tmapB0;
-                    ptx::tma_load_2d(sB + (size_t)lane * kPStageB, mapB, u * kPK, r0,
-                                     &sh->full[lane]);
-                }
-                g += kPStages;
-                ++used;
-            }
-            if (__any_sync(0xFFFFFFFFu, go)) {
-                t0 = 0;
-                continue;
-            }
-            // no copy could go this round: bounded wait for progress
-            int give_up = 0;
-            if (lane == 0) {
-                if (*(volatile int *)&sh->abort) {
-                    give_up = 1;
-                } else if (t0 == 0) {
-                    t0 = ptx::globaltimer();
-                } else if ((++idle & 15) == 0 && ptx::globaltimer() - t0 > ptx::kWaitBudgetNs) {
-                    *(volatile int *)&sh->abort = 1;
-                    atomicExch(a.err, kErrTimeout);
-                    give_up = 1;
-                }
-            }
-            if (__shfl_sync(0xFFFFFFFFu, give_up, 0))
-                break;
-        }
-        // the uses of its stage this lane copied, for the drain
-        if (lane < kPStages)
-            sh->copies[lane][jl ? 0 : 1] = used;
     } else if (warp < kFirstEpi) {
         // --------------------------------------------------------------- MMA
         // descriptors of stage 0; a stage or K step further is a plain add on
@@ -1137,7 +1060,7 @@ cudaError_t launch_tc_fp4_persistent(cudaStream_t st, const TcPlan *plan, const 
         return cudaErrorInvalidValue;
     if (a.nh && (!a.xi || !a.nhpart || !a.nhflags || !a.final_pass))
         return cudaErrorInvalidValue;
-    return launch_persistent<true>(st, plan->mapA, plan->mapB[0], plan->mapB[1], a);
+    return launch_persistent<true>(st, plan->mapA3, plan->mapB3[0], plan->mapB3[1], a);
 }
 
 cudaError_t launch_select_best(cudaStream_t st, const float *Epart, const uint8_t *Snap,

@@ -594,8 +594,9 @@ cudaError_t tc_fp4_plan_create(TcPlan **out, const uint8_t *J4, const uint8_t *S
     p->Kp = Kp;
     // rows of Kp/2 bytes; a 128-byte box row holds 256 e2m1 values
     if (!encode_u8(&p->mapA, J4, (uint64_t)Np, (uint64_t)Kp / 2, kBM) ||
-        !encode_u8(&p->mapB[0], S4a, (uint64_t)Rp, (uint64_t)Kp / 2, 128) ||
-        !encode_u8(&p->mapB[1], S4b, (uint64_t)Rp, (uint64_t)Kp / 2, 128) ||
+        !encode_u8_3d(&p->mapA3, J4, (uint64_t)Np, (uint64_t)Kp / 2, kBM, 2) ||
+        !encode_u8_3d(&p->mapB3[0], S4a, (uint64_t)Rp, (uint64_t)Kp / 2, 128, 2) ||
+        !encode_u8_3d(&p->mapB3[1], S4b, (uint64_t)Rp, (uint64_t)Kp / 2, 128, 2) ||
         !encode_u8(&p->mapBw[0], S4a, (uint64_t)Rp, (uint64_t)Kp / 2, kBN4) ||
         !encode_u8(&p->mapBw[1], S4b, (uint64_t)Rp, (uint64_t)Kp / 2, kBN4)) {
         delete p;
