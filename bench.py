@@ -465,7 +465,7 @@ def run_gpu(args):
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": _traffic_for_current_kernel(),
                 "kernel": ("tc_fp8_persistent_kernel" if launches_adv == 1
-                           else "tc_fp8_step_kernel"),
+                           else "tc_step_kernel<0> (FP8, one launch per step)"),
                 "launches_per_loop": launches_adv, "launch_ms": launch_ms,
                 "peak_source": "FP8 dense, burst (the loop kernel runs alone at full clock): "
                                + peak_how,
