@@ -87,9 +87,9 @@ typedef enum {
     /* tcgen05 tensor cores (kind::mxf4, block-scaled with unit UE8M0 scales),
        J and sgn(x) in packed FP4 e2m1 (+1 = 0x2, -1 = 0xA), FP32
        accumulation.  Exact (integer forces), so trajectories equal the FP8
-       ones bit for bit.  Discrete form with J in {-1,0,+1} only, one kernel
-       launch per step (schedule 0 or 2, else HSB_E_UNSUPPORTED); never
-       picked by AUTO. */
+       ones bit for bit.  Discrete form with J in {-1,0,+1} only; the
+       persistent kernel or one kernel launch per step (schedule 0, 1 or 2,
+       else HSB_E_UNSUPPORTED); never picked by AUTO. */
     HSB_PREC_FP4 = 4
 } hsb_prec;
 
@@ -106,11 +106,12 @@ typedef struct {
     int trace_every;        /* >= 0; > 0 records, at t_k for k = m*trace_every < steps,
                                the minimum and mean Ising energy over replicas and
                                the mean instantaneous temperature (1/N) sum y^2
-                               (Eq. (eq_TInst)); see hsb_get_trace.  FP32 and FP8
-                               (persistent or one launch per step; not schedule 3);
+                               (Eq. (eq_TInst)); see hsb_get_trace.  FP32, FP8 and
+                               FP4 (persistent or one launch per step; not
+                               schedules 3 and 4);
                                BF16X3 returns HSB_E_UNSUPPORTED */
     uint32_t instance;      /* random stream of the instance (x0, y0) */
-    int schedule;           /* FP8 step loop: 0 = automatic (persistent kernel
+    int schedule;           /* FP8 / FP4 step loop: 0 = automatic (persistent kernel
                                when its grid fits on the device), 1 = persistent
                                kernel only (HSB_E_UNSUPPORTED if it cannot fit),
                                2 = one kernel launch per step, 3 = persistent
@@ -121,12 +122,13 @@ typedef struct {
                                trace, N <= 4096, R rounded up to 128 a multiple
                                of 256 and a grid that fits, else
                                HSB_E_UNSUPPORTED).  Automatic takes 1
-                               where its grid fits, then 4, then 2. */
+                               where its grid fits, then 4 (FP8), then 2.
+                               FP4 takes 0, 1 and 2 only. */
     int thermostat;         /* HSB_HEAT_CONSTANT: the constant heating rate gamma of
                                Eq. (eq_MomHeat) (HbSB / HdSB); HSB_HEAT_NOSE_HOOVER:
                                the dynamic xi of Eqs. (eq_NH1), (eq_NH), one per
                                replica, in place of -gamma (gamma is then unused).
-                               Nose-Hoover runs on FP32 and on FP8 (persistent or one
+                               Nose-Hoover runs on FP32, FP8 and FP4 (persistent or one
                                launch per step; AUTO never picks BF16X3 for it);
                                schedule 3 and hsb_advance* return HSB_E_UNSUPPORTED,
                                hsb_run_batch runs the instances one after another.
