@@ -531,6 +531,11 @@ OTHER = {
                           "steps, FP8, one batched launch", kind="batch", count=256, sizes_seed=4,
                      R=64, sb_steps=2000, form="discrete", prec="fp8", c1=0.7, dt=1.1,
                      gamma=0.06, eval_every=100, trace_every=0, peak="fp8", dtype="fp8"),
+    "batch256_fp4": dict(name="HdSB 256 SK +/-1 instances, N uniform in [100, 2000], R=64, "
+                              "2000 steps, FP4 e2m1, one batched launch", kind="batch",
+                         count=256, sizes_seed=4, R=64, sb_steps=2000, form="discrete",
+                         prec="fp4", c1=0.7, dt=1.1, gamma=0.06, eval_every=100, trace_every=0,
+                         peak="fp4", dtype="fp4"),
 }
 
 
@@ -676,19 +681,22 @@ def run_other(args, w):
                 "scope": "whole run (force, update, evaluations, final energies); "
                          "algorithmic 2 N^2 R per step"}
     if w["kind"] == "batch":
-        # The batch streams every instance's FP8 couplings each step (their sum
+        # The batch streams every instance's couplings each step (their sum
         # exceeds L2) and keeps x, y in global memory: per step and instance
-        # N^2 bytes of J, 16 N R bytes of x, y read and written, 2 N R bytes
-        # of the sign operand written and read back.  That traffic, not the
-        # tensor rate, bounds it.
-        nbytes = world * sum(J.shape[0] ** 2 + 18 * J.shape[0] * R for J in Js) * S
+        # N^2 bytes of FP8 J (N^2 / 2 packed e2m1), 16 N R bytes of x, y read
+        # and written, 2 N R bytes of the sign operand written and read back
+        # (N R in e2m1).  That traffic, not the tensor rate, bounds it.
+        jb, sb = (0.5, 1) if w["prec"] == "fp4" else (1.0, 2)
+        nbytes = world * sum(jb * J.shape[0] ** 2 + (16 + sb) * J.shape[0] * R for J in Js) * S
         hbm = float(mp.get("hbm_gbs", 6800.0))
         gbs = nbytes / t_run / 1e9
         roofline = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                     "frac": gbs / hbm, "traffic": None,
                     "peak_source": f"hbm_gbs of {src} peaks",
                     "scope": "whole batched launch; algorithmic bytes per step and instance "
-                             "N^2 (J, FP8) + 18 N R (x, y read and written, sign operand)",
+                             + ("N^2/2 (J, e2m1) + 17 N R" if w["prec"] == "fp4" else
+                                "N^2 (J, FP8) + 18 N R")
+                             + " (x, y read and written, sign operand)",
                     "tensor_frac": achieved / peak}
     if w["prec"] == "bf16x3":
         roofline["executed_tflops"] = 3.0 * achieved

@@ -1211,11 +1211,11 @@ struct BatchChoice {
 };
 
 struct BatchTuneKey {
-    int device, count, BN, log2bytes;
+    int device, count, BN, log2bytes, fp4;
     bool operator<(const BatchTuneKey &o) const
     {
-        return std::tie(device, count, BN, log2bytes) <
-               std::tie(o.device, o.count, o.BN, o.log2bytes);
+        return std::tie(device, count, BN, log2bytes, fp4) <
+               std::tie(o.device, o.count, o.BN, o.log2bytes, o.fp4);
     }
 };
 
@@ -1244,7 +1244,7 @@ float time_batch(cudaStream_t st, const BatchInst *d_insts, BatchArgs a, int cta
     float ms = -1.f;
     if (cudaMemsetAsync(a.queue, 0, sizeof(unsigned int), st) == cudaSuccess &&
         cudaEventRecord(e0, st) == cudaSuccess &&
-        launch_tc_fp8_batch(st, d_insts, a, ctas) == cudaSuccess &&
+        launch_tc_batch(st, d_insts, a, ctas) == cudaSuccess &&
         cudaEventRecord(e1, st) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
         cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -1838,12 +1838,13 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
             return set_error(HSB_E_INVAL, "hsb_run_batch: all handles must share one device");
     }
     // The batched kernel applies to the discrete form with +/-1 couplings in
-    // FP8; any other case runs the instances one after another.
+    // FP8 (AUTO) or FP4; any other case runs the instances one after another.
+    const bool fp4 = p->prec == HSB_PREC_FP4;
     bool batched = p->form == HSB_DISCRETE &&
-                   (p->prec == HSB_PREC_AUTO || p->prec == HSB_PREC_FP8) && p->trace_every == 0 &&
-                   p->thermostat == HSB_HEAT_CONSTANT;
+                   (p->prec == HSB_PREC_AUTO || p->prec == HSB_PREC_FP8 || fp4) &&
+                   p->trace_every == 0 && p->thermostat == HSB_HEAT_CONSTANT;
     for (int b = 0; b < count && batched; ++b)
-        batched = hs[b]->pm1 && batch_shape_ok(hs[b]->Np, R);
+        batched = hs[b]->pm1 && batch_shape_ok(hs[b]->Np, R, fp4);
     if (!batched) {
         for (int b = 0; b < count; ++b) {
             hsb_params pb = *p;
@@ -1862,7 +1863,8 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
     for (int b = 0; b < count; ++b) {
         hsb_ctx *h = hs[b];
         hsb_params pb = *p;
-        pb.prec = HSB_PREC_FP8;
+        pb.prec = fp4 ? HSB_PREC_FP4 : HSB_PREC_FP8;
+        pb.schedule = 0;
         pb.instance = p->instance + (uint32_t)b;
         RunCfg c;
         hsb_status s = resolve(h, &pb, R, steps, &c);
@@ -1877,8 +1879,8 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
         memset(&in, 0, sizeof in);
         in.X = h->X[0];
         in.Y = h->Y;
-        in.S8a = h->S8[0];
-        in.S8b = h->S8[1];
+        in.S8a = fp4 ? h->S4[0] : h->S8[0];
+        in.S8b = fp4 ? h->S4[1] : h->S8[1];
         in.Ebest = h->Ebest;
         in.Sbest = h->Sbest;
         in.c0 = c.c.c0;
@@ -1887,7 +1889,9 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
         in.R = R;
         in.BN = round_up(R, 32);
         in.instance = pb.instance;
-        CK(batch_fill_maps(&in, h->J8, h->S8[0], h->S8[1], h->Np, h->Rcap), "batch maps");
+        CK(batch_fill_maps(&in, fp4 ? h->J4 : h->J8, in.S8a, in.S8b, h->Np, h->Rcap,
+                           fp4 ? h->Kp : 0),
+           "batch maps");
     }
     // largest instances first
     std::vector<int> order((size_t)count);
@@ -1945,14 +1949,16 @@ hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, i
         double bytes = 0.0;
         for (int b = 0; b < count; ++b)
             bytes += (double)insts[(size_t)b].Np * insts[(size_t)b].Np;
-        const BatchTuneKey key{hs[0]->device, count, round_up(R, 32), (int)ceil(log2(bytes))};
+        a.fp4 = fp4 ? 1 : 0;
+        const BatchTuneKey key{hs[0]->device, count, round_up(R, 32), (int)ceil(log2(bytes)),
+                               a.fp4};
         const BatchChoice ch = tune_batch(key, st, d_insts, a, sms, count);
         a.allow_split = ch.split;
         e = cudaMemsetAsync(d_queue, 0, sizeof(unsigned int), st);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(hs[0]->err, 0, sizeof(int), st);
         if (e == cudaSuccess)
-            e = launch_tc_fp8_batch(st, d_insts, a, ch.ctas);
+            e = launch_tc_batch(st, d_insts, a, ch.ctas);
     }
     for (int b = 0; b < count && e == cudaSuccess; ++b) {
         hsb_ctx *h = hs[b];

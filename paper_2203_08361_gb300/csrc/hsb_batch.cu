@@ -1,6 +1,6 @@
-// hsb_batch.cu -- many heated discrete SB problems (+/-1 couplings, FP8) of
-// uneven size in one launch: a work queue of instances, one CTA per instance
-// at a time, largest first.
+// hsb_batch.cu -- many heated discrete SB problems (+/-1 couplings, FP8 or
+// packed FP4 e2m1 operands) of uneven size in one launch: a work queue of
+// instances, one CTA per instance at a time, largest first.
 //
 // Per instance the whole step loop (Kanao & Goto, arXiv 2203.08361: force
 // Eq. (eq_fd), Methods update, evaluations every `eval_every` steps and at the
@@ -26,6 +26,11 @@
 // loads, warp 2 alone otherwise; warp 2 also loads
 // the resident S of each step; warps 4-11 are the epilogue.  Every stage has one
 // producer and one consumer, so each mbarrier phase is awaited in order.
+// FP4 (kFP4): J and S packed two e2m1 values per byte (rows of Kp / 2 bytes,
+// Kp = Np rounded up to 256), so a 128-byte K slice holds 256 spins and a
+// load of two slices 512; kind::mxf4 MMAs (K = 64) with unit UE8M0 block
+// scales in tensor memory columns 496-511; the epilogue writes sgn(x') as
+// nibble pairs (two lanes, two spins, one byte).
 // Every wait is bounded; a wait that gives up raises the error word and the
 // CTA stops taking instances.
 #include <cuda.h>
@@ -50,6 +55,7 @@ constexpr int kGEpiWarps = 8;
 constexpr int kGEpiThreads = 32 * kGEpiWarps;
 constexpr int kGFirstEpi = 4;            // 2 J producers, 2 MMA warps
 constexpr int kGThreads = 32 * kGFirstEpi + kGEpiThreads;
+constexpr uint32_t kGColSF = 496;        // FP4 unit block scales (16 columns)
 
 struct __align__(8) GShared {
     uint64_t full[kGStages];
@@ -120,8 +126,9 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *a
 
 }  // namespace
 
+template <bool kFP4>
 __global__ void __launch_bounds__(kGThreads, 1)
-tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
+tc_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *base = reinterpret_cast<uint8_t *>(
@@ -157,6 +164,21 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
     __syncthreads();
     ptx::tc_fence_after();
     const uint32_t tmem = sh->tmem_base;
+    if (kFP4) {
+        // unit block scales (UE8M0 0x7F = 2^0) in 16 columns of every lane,
+        // before the first MMA reads them
+        if (warp >= kGFirstEpi && warp < kGFirstEpi + 4) {
+            uint32_t one[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                one[j] = 0x7F7F7F7Fu;
+            ptx::tmem_st16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + kGColSF, one);
+            ptx::tmem_st_wait();
+        }
+        ptx::tc_fence_before();
+        __syncthreads();
+        ptx::tc_fence_after();
+    }
 
     // running counters of each role, continued across instances
     uint32_t g = 0;       // J stages (producer, MMA)
@@ -174,7 +196,10 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
         const BatchInst &in = insts[idx];
         const int N = in.N, Np = in.Np, BN = in.BN, R = in.R;
         const int nblk = Np / kTM;
-        const int npairs = (nblk + 1) >> 1;
+        // 128-byte K slices of an operand row: Np / 128 (FP8), Kp / 256 (FP4)
+        const int nslice = kFP4 ? in.Kp / 256 : nblk;
+        const int npairs = (nslice + 1) >> 1;  // loads of two slices per row block
+        const size_t srow = kFP4 ? (size_t)in.Kp / 2 : (size_t)Np;  // operand row bytes
         const int passes = a.steps + 1;  // updates, then the final evaluation
 
         // K is split over the two MMA warps (each into its own accumulator,
@@ -182,7 +207,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
         // row block has at least two loads
         // (every kGStages consecutive loads include stages of both parities,
         // so each MMA warp gets at least one load of every row block)
-        const bool split = a.allow_split && BN <= 128 && npairs >= kGStages;
+        const bool split = a.allow_split && BN <= (kFP4 ? 96 : 128) && npairs >= kGStages;
 
         if (warp < 2) {
             // --------------------------------------------------- J producers
@@ -215,7 +240,8 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
             // (warp 2, without it), always in load order; warp 2 also loads
             // the resident S of each step (its MMAs cannot start before)
             const int pw = warp - 2;
-            const uint32_t idesc = ptx::idesc_e4m3_f32(kTM, BN);
+            const uint32_t idesc =
+                kFP4 ? ptx::idesc_mxf4_e2m1(kTM, BN) : ptx::idesc_e4m3_f32(kTM, BN);
             const uint64_t sdesc0 = ptx::sw128_desc(ptx::smem_u32(sS));
             const uint64_t adesc0 = ptx::sw128_desc(ptx::smem_u32(sA));
             bool ok = true;
@@ -229,7 +255,7 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     if (lane == 0) {
                         ptx::fence_proxy_async_global();
                         ++sh->s_loads;  // for the drain
-                        ptx::mbar_expect_tx(&sh->s_full, (uint32_t)(BN * Np));
+                        ptx::mbar_expect_tx(&sh->s_full, (uint32_t)(BN * srow));
                         ptx::tma_load_3d(sS, &in.mapS[k & 1], 0, 0, 0, &sh->s_full);
                     }
                     __syncwarp();
@@ -261,15 +287,22 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                         ptx::tc_fence_after();
                         for (int c = 0; c < 2; ++c) {
                             const int kc = 2 * p + c;
-                            if (kc >= nblk)
+                            if (kc >= nslice)
                                 break;
                             const uint64_t ad =
                                 adesc0 + (uint64_t)(((size_t)s * kGStageA + c * kTM * 128) >> 4);
                             const uint64_t bd = sdesc0 + (uint64_t)((kc * BN * 128) >> 4);
 #pragma unroll
-                            for (int kk = 0; kk < 4; ++kk)
-                                mma_fp8_elect(dcol, ad + (uint64_t)(kk * 2), bd + (uint64_t)(kk * 2),
-                                              idesc, (mine | c | kk) != 0 ? 1u : 0u);
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const uint32_t acc = (mine | c | kk) != 0 ? 1u : 0u;
+                                if (kFP4)
+                                    ptx::mma_mxf4_elect(dcol, ad + (uint64_t)(kk * 2),
+                                                        bd + (uint64_t)(kk * 2), idesc,
+                                                        tmem + kGColSF, tmem + kGColSF, acc);
+                                else
+                                    mma_fp8_elect(dcol, ad + (uint64_t)(kk * 2),
+                                                  bd + (uint64_t)(kk * 2), idesc, acc);
+                            }
                         }
                         commit_elect(&sh->empty[s]);
                         ++mine;
@@ -313,7 +346,22 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                 }
                 X[e] = x;
                 Y[e] = y;
-                S8a[e] = sg;
+                if (!kFP4)
+                    S8a[e] = sg;
+            }
+            if (kFP4) {
+                // packed e2m1 signs of the stored x (spins 2b and 2b + 1 of
+                // byte b; padded spins and the K padding 0)
+                gbar();
+                for (size_t e = et; e < (size_t)BN * srow; e += kGEpiThreads) {
+                    const int r = (int)(e / srow), i = 2 * (int)(e % srow);
+                    const uint32_t lo =
+                        i < N ? (X[(size_t)r * Np + i] >= 0.f ? kFp4PlusOne : kFp4MinusOne) : 0u;
+                    const uint32_t hi = i + 1 < N ? (X[(size_t)r * Np + i + 1] >= 0.f ? kFp4PlusOne
+                                                                                      : kFp4MinusOne)
+                                                  : 0u;
+                    S8a[e] = (uint8_t)(lo | (hi << 4));
+                }
             }
             for (int r = et; r < R; r += kGEpiThreads)
                 Ebest[r] = INFINITY;
@@ -411,8 +459,23 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                                 X[e + Np] = xo1;
                                 Y[e] = f2_lo(yo);
                                 Y[e + Np] = f2_hi(yo);
-                                Snew[e] = live ? fp8_sign(xo0) : (uint8_t)0;
-                                Snew[e + Np] = live ? fp8_sign(xo1) : (uint8_t)0;
+                                if (kFP4) {
+                                    // spins i (even lane) and i + 1 share a byte
+                                    const uint32_t n0 =
+                                        live ? (xo0 >= 0.f ? kFp4PlusOne : kFp4MinusOne) : 0u;
+                                    const uint32_t n1 =
+                                        live ? (xo1 >= 0.f ? kFp4PlusOne : kFp4MinusOne) : 0u;
+                                    const uint32_t u0 = __shfl_down_sync(0xFFFFFFFFu, n0, 1);
+                                    const uint32_t u1 = __shfl_down_sync(0xFFFFFFFFu, n1, 1);
+                                    if ((lane & 1) == 0) {
+                                        const size_t b = (size_t)(cbase + cb + j) * srow + i / 2;
+                                        Snew[b] = (uint8_t)(n0 | (u0 << 4));
+                                        Snew[b + srow] = (uint8_t)(n1 | (u1 << 4));
+                                    }
+                                } else {
+                                    Snew[e] = live ? fp8_sign(xo0) : (uint8_t)0;
+                                    Snew[e + Np] = live ? fp8_sign(xo1) : (uint8_t)0;
+                                }
                             }
                         }
 #pragma unroll
@@ -441,9 +504,13 @@ tc_fp8_batch_kernel(const BatchInst *__restrict__ insts, const BatchArgs a)
                     const int w = warp - kGFirstEpi;
                     for (int r = w; r < R; r += kGEpiWarps)
                         if (sh->improved[r])
-                            for (int i = lane; i < N; i += 32)
-                                Sbest[(size_t)r * N + i] =
-                                    Sold[(size_t)r * Np + i] == kFp8PlusOne ? (int8_t)1 : (int8_t)-1;
+                            for (int i = lane; i < N; i += 32) {
+                                const bool plus =
+                                    kFP4 ? ((Sold[(size_t)r * srow + i / 2] >> (4 * (i & 1))) &
+                                            15u) == kFp4PlusOne
+                                         : Sold[(size_t)r * Np + i] == kFp8PlusOne;
+                                Sbest[(size_t)r * N + i] = plus ? (int8_t)1 : (int8_t)-1;
+                            }
                     for (int r = et; r < kMaxBN; r += kGEpiThreads)
                         sh->esum[r] = 0;
                 }
@@ -524,33 +591,41 @@ bool encode_chunks(CUtensorMap *m, const void *ptr, uint64_t rows, uint64_t cols
 
 }  // namespace
 
-bool batch_shape_ok(int Np, int R)
+bool batch_shape_ok(int Np, int R, bool fp4)
 {
     const int BN = round_up(R, 32);
+    const int Kp = round_up(Np, 256);
+    if (fp4)  // two accumulators and the block scales in 512 columns
+        return R >= 1 && 2 * BN + 16 <= 512 && Np % kTM == 0 && Kp / 256 <= 256 &&
+               BN * (Kp / 2) <= kMaxS;
     return R >= 1 && BN <= kMaxBN && Np % kTM == 0 && Np / 128 <= 256 && BN * Np <= kMaxS;
 }
 
-cudaError_t batch_fill_maps(BatchInst *in, const uint8_t *J8, const uint8_t *S8a,
-                            const uint8_t *S8b, int Np, int Rcap)
+cudaError_t batch_fill_maps(BatchInst *in, const uint8_t *J, const uint8_t *Sa,
+                            const uint8_t *Sb, int Np, int Rcap, int Kp)
 {
     const int BN = in->BN;
-    if (!encode_chunks(&in->mapA, J8, (uint64_t)Np, (uint64_t)Np, kTM, 2) ||
-        !encode_chunks(&in->mapS[0], S8a, (uint64_t)Rcap, (uint64_t)Np, (uint32_t)BN,
-                       (uint32_t)(Np / 128)) ||
-        !encode_chunks(&in->mapS[1], S8b, (uint64_t)Rcap, (uint64_t)Np, (uint32_t)BN,
-                       (uint32_t)(Np / 128)))
+    // operand rows: Np bytes (FP8) or Kp / 2 bytes of packed e2m1 (Kp > 0)
+    const uint64_t cols = Kp > 0 ? (uint64_t)Kp / 2 : (uint64_t)Np;
+    if (!encode_chunks(&in->mapA, J, (uint64_t)Np, cols, kTM, 2) ||
+        !encode_chunks(&in->mapS[0], Sa, (uint64_t)Rcap, cols, (uint32_t)BN,
+                       (uint32_t)(cols / 128)) ||
+        !encode_chunks(&in->mapS[1], Sb, (uint64_t)Rcap, cols, (uint32_t)BN,
+                       (uint32_t)(cols / 128)))
         return cudaErrorInvalidValue;
+    in->Kp = Kp;
     return cudaSuccess;
 }
 
-cudaError_t launch_tc_fp8_batch(cudaStream_t st, const BatchInst *d_insts, const BatchArgs &a,
-                                int ctas)
+cudaError_t launch_tc_batch(cudaStream_t st, const BatchInst *d_insts, const BatchArgs &a,
+                            int ctas)
 {
-    cudaError_t e = cudaFuncSetAttribute(tc_fp8_batch_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
+    auto kern = a.fp4 ? tc_batch_kernel<true> : tc_batch_kernel<false>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGSmem);
     if (e != cudaSuccess)
         return e;
-    tc_fp8_batch_kernel<<<ctas, kGThreads, kGSmem, st>>>(d_insts, a);
+    kern<<<ctas, kGThreads, kGSmem, st>>>(d_insts, a);
     return cudaGetLastError();
 }
 

@@ -251,11 +251,12 @@ struct BatchInst {
     CUtensorMap mapA;     // J8 as (128 B, rows, K chunk), box 128 x 128 x 2
     CUtensorMap mapS[2];  // S8a / S8b as (128 B, rows, chunk), box 128 x BN x Np/128
     float *X, *Y;         // [Rcap][Np] state
-    uint8_t *S8a, *S8b;   // [Rcap][Np] FP8 operand ping/pong
+    uint8_t *S8a, *S8b;   // [Rcap][Np] FP8 (or [Rcap][Kp/2] packed e2m1) operand ping/pong
     double *Ebest;        // [R]
     int8_t *Sbest;        // [R][N]
     float c0;
     int N, Np, R, BN;     // BN = R rounded up to 32
+    int Kp;               // FP4: Np rounded up to 256 (operand rows of Kp / 2 bytes); 0 for FP8
     uint32_t instance;    // random stream of the instance
 };
 
@@ -270,12 +271,15 @@ struct BatchArgs {
     uint64_t seed;
     int *err;
     int allow_split;       // K may be split over the two MMA warps
+    int fp4;               // packed e2m1 operands (kind::mxf4) instead of FP8
 };
 
-bool batch_shape_ok(int Np, int R);
-cudaError_t batch_fill_maps(BatchInst *in, const uint8_t *J8, const uint8_t *S8a,
-                            const uint8_t *S8b, int Np, int Rcap);
-cudaError_t launch_tc_fp8_batch(cudaStream_t st, const BatchInst *d_insts, const BatchArgs &a,
-                                int ctas);
+bool batch_shape_ok(int Np, int R, bool fp4);
+// Kp = 0: FP8 J8 and operands [rows][Np]; Kp > 0: packed e2m1 J4 and
+// operands [rows][Kp/2].
+cudaError_t batch_fill_maps(BatchInst *in, const uint8_t *J, const uint8_t *Sa,
+                            const uint8_t *Sb, int Np, int Rcap, int Kp);
+cudaError_t launch_tc_batch(cudaStream_t st, const BatchInst *d_insts, const BatchArgs &a,
+                            int ctas);
 
 }  // namespace hsb

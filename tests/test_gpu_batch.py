@@ -1,7 +1,7 @@
-"""Batched heated discrete SB over many instances of uneven size (FP8, one
-launch): every instance's best spins and energies must equal those of a
-separate run of the same instance (same random stream), and the oracle's on
-sampled instances."""
+"""Batched heated discrete SB over many instances of uneven size (FP8 or packed
+FP4 e2m1 operands, one launch): every instance's best spins and energies must
+equal those of a separate run of the same instance (same random stream), and
+the oracle's on sampled instances; the FP4 batch equals the FP8 batch."""
 import numpy as np
 import pytest
 
@@ -12,14 +12,15 @@ import synth
 pytestmark = pytest.mark.gpu
 
 
-def _batch_vs_single(sizes, R, steps, ev, seed, check_oracle=(), oracle_rows=None):
+def _batch_vs_single(sizes, R, steps, ev, seed, check_oracle=(), oracle_rows=None,
+                     prec="fp8"):
     Js = [synth.sk_pm1(n, 500 + b) for b, n in enumerate(sizes)]
     solvers = [hsb.Solver(J) for J in Js]
-    p = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=ev)
+    p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=ev)
     try:
         out = hsb.run_batch([s.h for s in solvers], p, R, steps, seed)
         for b, s in enumerate(solvers):
-            pb = hsb.params("discrete", "fp8", c1=0.7, dt=1.1, gamma=0.06, eval_every=ev,
+            pb = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=ev,
                             instance=b)
             spins, energy = s.run(pb, R, steps, seed)
             np.testing.assert_array_equal(out[b][0], spins, err_msg=f"instance {b}")
@@ -38,10 +39,19 @@ def _batch_vs_single(sizes, R, steps, ev, seed, check_oracle=(), oracle_rows=Non
     return out
 
 
-def test_batch_small_uneven_instances():
-    # ragged sizes (one 128-row block up to several, odd block counts) and R
+@pytest.mark.parametrize("prec", ["fp8", "fp4"])
+def test_batch_small_uneven_instances(prec):
+    # ragged sizes (one 128-row block up to several, odd block counts; in FP4
+    # K paddings beyond the 128-spin padding) and R
     _batch_vs_single([100, 128, 257, 300, 511, 700, 129, 2, 640], 40, 150, 30, 3,
-                     check_oracle=(0, 2, 7))
+                     check_oracle=(0, 2, 7), prec=prec)
+
+
+@pytest.mark.parametrize("R", [1, 64, 96, 200])
+def test_batch_fp4_replica_widths(R):
+    # one accumulator per buffer up to 224 replica columns, K split over two
+    # MMA warps up to 96
+    _batch_vs_single([300, 1000, 513], R, 60, 20, 6, check_oracle=(0,), prec="fp4")
 
 
 def test_batch_more_instances_than_ctas_per_cta_reuse():
@@ -58,6 +68,26 @@ def test_batch_uneven_workload_full_size():
     _batch_vs_single(sizes, 64, 2000, 100, 9,
                      check_oracle=(sizes.index(min(sizes)), sizes.index(max(sizes))),
                      oracle_rows=(0, 1, 62, 63))
+
+
+def test_batch_fp4_equals_fp8_on_the_uneven_workload():
+    # 256 SK instances, N uniform in [100, 2000], R = 64, 300 steps: the FP4
+    # batch equals the FP8 batch for every instance
+    sizes = [int(v) for v in synth.batch_sizes(256, 4)]
+    Js = [synth.sk_pm1(n, 500 + b) for b, n in enumerate(sizes)]
+    solvers = [hsb.Solver(J) for J in Js]
+    try:
+        hs = [s.h for s in solvers]
+        out = {}
+        for prec in ("fp8", "fp4"):
+            p = hsb.params("discrete", prec, c1=0.7, dt=1.1, gamma=0.06, eval_every=100)
+            out[prec] = hsb.run_batch(hs, p, 64, 300, 9)
+        for b in range(len(sizes)):
+            np.testing.assert_array_equal(out["fp8"][b][0], out["fp4"][b][0], err_msg=f"{b}")
+            np.testing.assert_array_equal(out["fp8"][b][1], out["fp4"][b][1], err_msg=f"{b}")
+    finally:
+        for s in solvers:
+            s.close()
 
 
 @pytest.mark.parametrize("kind", ["gauss", "nose_hoover"])
