@@ -223,11 +223,14 @@ HSB_API hsb_status hsb_run_device(hsb_handle h, const hsb_params *p, int R, int 
  * host, R float64).  Instance b draws its initial state from the random
  * stream p->instance + b, so its result equals hsb_run on hs[b] with
  * instance = p->instance + b.  For the discrete form with couplings in
- * {-1, 0, +1} (FP8), R rounded up to 32 at most 256 and N rounded up to 128
- * times that at most 128 KiB, all instances run in one kernel launch that
- * takes them from a queue, largest first, one CTA per instance; otherwise
- * the instances run one after another.  All handles must be on one device;
- * the work is queued on hs[0]'s stream.  Blocks. */
+ * {-1, 0, +1}, constant heating and no trace, all instances run in one
+ * kernel launch that takes them from a queue, largest first, one CTA per
+ * instance, where the shape allows: with p->prec AUTO or FP8, R rounded up
+ * to 32 at most 256 and (N rounded up to 128) times that at most 128 KiB;
+ * with HSB_PREC_FP4 (packed e2m1 operands), R rounded up to 32 at most 224
+ * and (N rounded up to 256) / 2 times that at most 128 KiB.  Otherwise the
+ * instances run one after another.  All handles must be on one device; the
+ * work is queued on hs[0]'s stream.  Blocks. */
 HSB_API hsb_status hsb_run_batch(const hsb_handle *hs, int count, const hsb_params *p, int R,
                                  int steps, uint64_t seed, int8_t *const *best_spins,
                                  double *const *best_energy);
