@@ -130,6 +130,7 @@ struct TcPlan {
     CUtensorMap mapB3[2];  // 3-D S8a / S8b, box 128 x 128 x 2
     CUtensorMap mapBw[2];  // 2-D S8a / S8b, box 128 B x 256 rows (per-step kernel)
     CUtensorMap mapJ64;    // 2-D J8, box 128 B x 64 rows (CTA-pair kernel)
+    CUtensorMap mapBq[2];  // 2-D S a / b, box 128 B x BN/2 rows (CTA-pair per-step kernel)
     int Np, Rp;            // Rp: replica capacity the maps were encoded for
     int Kp = 0;            // FP4 plans: row length in e2m1 values (Np rounded up to 256)
 };

@@ -583,6 +583,22 @@ __device__ __forceinline__ void mma_fp8_pair_elect(uint32_t tmem_d, uint64_t ade
         : "memory");
 }
 
+// Block-scaled pair MMA with packed e2m1 operands (kind::mxf4, scale factors
+// of A and B read from tensor memory at the same columns in both CTAs).
+__device__ __forceinline__ void mma_mxf4_pair_elect(uint32_t tmem_d, uint64_t adesc,
+                                                    uint64_t bdesc, uint32_t idesc,
+                                                    uint32_t tmem_sf, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, e;\n\t"
+        "elect.sync _|e, 0xffffffff;\n\t"
+        "setp.ne.b32 p, %3, 0;\n\t"
+        "@e tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %4, "
+        "[%5], [%5], p;\n\t}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(accumulate), "r"(idesc), "r"(tmem_sf)
+        : "memory");
+}
+
 // One arrival on the mbarrier at cluster address `caddr` (either CTA of the
 // pair) when every pair MMA issued so far by the elected lane has completed.
 __device__ __forceinline__ void commit_pair_elect(uint32_t caddr)

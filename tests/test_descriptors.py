@@ -25,6 +25,8 @@ int main()
 {
     printf("mxf4_128_192 %u\n", hsb::ptx::idesc_mxf4_e2m1(128, 192));
     printf("mxf4_128_256 %u\n", hsb::ptx::idesc_mxf4_e2m1(128, 256));
+    printf("mxf4_256_192 %u\n", hsb::ptx::idesc_mxf4_e2m1(256, 192));
+    printf("e4m3_256_256 %u\n", hsb::ptx::idesc_e4m3_f32(256, 256));
     printf("e4m3_128_256 %u\n", hsb::ptx::idesc_e4m3_f32(128, 256));
     printf("e4m3_256_128 %u\n", hsb::ptx::idesc_e4m3_f32(256, 128));
     printf("sw128_at_9216 %llu\n", (unsigned long long)hsb::ptx::sw128_desc(9216u));
@@ -88,7 +90,8 @@ E4M3 = 0  # element format code of e4m3 in the f8f6f4 descriptor
 F32 = 1   # accumulator format code of f32
 
 
-@pytest.mark.parametrize("key,M,N", [("mxf4_128_192", 128, 192), ("mxf4_128_256", 128, 256)])
+@pytest.mark.parametrize("key,M,N", [("mxf4_128_192", 128, 192), ("mxf4_128_256", 128, 256),
+                                     ("mxf4_256_192", 256, 192)])
 def test_mxf4_instruction_descriptor_fields(values, key, M, N):
     f = decode_block_scaled_idesc(values[key])
     assert f == {
@@ -100,7 +103,8 @@ def test_mxf4_instruction_descriptor_fields(values, key, M, N):
     }
 
 
-@pytest.mark.parametrize("key,M,N", [("e4m3_128_256", 128, 256), ("e4m3_256_128", 256, 128)])
+@pytest.mark.parametrize("key,M,N", [("e4m3_128_256", 128, 256), ("e4m3_256_128", 256, 128),
+                                     ("e4m3_256_256", 256, 256)])
 def test_f8f6f4_instruction_descriptor_fields(values, key, M, N):
     f = decode_f8f6f4_idesc(values[key])
     assert f == {
