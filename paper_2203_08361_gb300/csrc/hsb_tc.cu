@@ -164,6 +164,22 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
 
 }  // namespace
 
+// bit k of b (k < 8) to bit 4k: one bit per nibble
+__device__ __forceinline__ uint32_t spread8_nibbles(uint32_t b)
+{
+    uint32_t x = b & 0xFFu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    return (x | (x << 3)) & 0x11111111u;
+}
+
+// bit k of b (k < 4) to bit 8k: one bit per byte (the four partial products
+// of the multiplication occupy distinct bits, so nothing carries)
+__device__ __forceinline__ uint32_t spread4_bytes(uint32_t b)
+{
+    return ((b & 0xFu) * 0x00204081u) & 0x01010101u;
+}
+
 // Tile t -> (row block mb, replica block rb).  The replica blocks are cut
 // into bands of `band` blocks (the last band may be narrower) taken one after
 // another; inside a band the tiles run row block by row block with the band's
@@ -200,7 +216,8 @@ __device__ __forceinline__ bool epilogue_tile(
 {
     const uint32_t lane_off = (uint32_t)(q * 32) << 16;
     const int m0 = mb * kBM;
-    const int i = valid ? m0 + q * 32 + lane : 0;  // spin of this thread
+    const int i0 = m0 + q * 32;                  // first spin of this warp
+    const int i = valid ? i0 + lane : 0;         // spin of this thread
     const bool live = valid && i < N;
     // x and y of one 32-column chunk, fetched before any store of the
     // chunk (the first chunk before the accumulator wait): all loads
@@ -223,56 +240,71 @@ __device__ __forceinline__ bool epilogue_tile(
     if (epi_bar_or(!ok))
         return false;
     ptx::tc_fence_after();
+    const StepConsts2 k2 = step_consts2(c);
+    const uint64_t pk2 = f2_pack(pk, pk);
+    const uint32_t livem = __ballot_sync(0xFFFFFFFFu, live);  // bit l: spin i0 + l is live
     for (int cb = 0; cb < kBN / 2 / 32; ++cb) {
         const int col0 = cbase + cb * 32;
+        const int rc = r0 + col0;  // replica of the chunk's first column
         uint32_t fr[32];
         ptx::tmem_ld32(tmem + lane_off + (uint32_t)(b * kBN + col0), fr);
         if (cb > 0)
             fetch(col0);
         ptx::tmem_ld_wait();
+        uint32_t negm = 0u;  // lane l: bit s set when spin i0 + s of replica rc + l is negative
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
             // partial sums over this warp's 32 spins of 16 columns:
             // s_i f_i (evaluations) and y_i(t_k)^2 (trace)
             float tv[16], t2v[16];
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < 16; u += 2) {
                 const int jj = hh * 16 + u;
-                const int r = r0 + col0 + jj;
-                const float fj = __uint_as_float(fr[jj]);
-                float term = 0.f, t2 = 0.f;
-                if (r < Rp && valid) {
-                    const size_t e = (size_t)r * Np + i;
-                    const float x0 = xv[jj];
-                    if (energy || energy_only)
-                        term = live ? (x0 >= 0.f ? fj : -fj) : 0.f;
-                    if (!energy_only) {
-                        const float y0 = yv[jj];
-                        if (Tpart)
-                            t2 = __fmul_rn(y0, y0);  // y_i(t_k)^2 (Eq. eq_TInst)
-                        // per-replica friction of the Nose-Hoover thermostat
-                        StepConsts cr = c;
-                        if (gvec)
-                            cr.g = __ldg(gvec + r);
-                        float xn, yn;
-                        sb_update(fj, x0, y0, pk, cr, xn, yn);
-                        ptx::st_f32_hint(X + e, xn, stream_once);
-                        ptx::st_f32_hint(Y + e, yn, stream_once);
-                        if (FP4) {
-                            // spins i (even lane) and i + 1 share a byte
-                            const uint32_t nib =
-                                live ? (xn >= 0.f ? kFp4PlusOne : kFp4MinusOne) : 0u;
-                            const uint32_t up = __shfl_down_sync(0xFFFFFFFFu, nib, 1);
-                            if ((lane & 1) == 0)
-                                Snext[(size_t)r * (Kp / 2) + (i >> 1)] =
-                                    (uint8_t)(nib | (up << 4));
-                        } else {
-                            Snext[e] = live ? fp8_sign(xn) : (uint8_t)0;
-                        }
-                    }
+                const int r = rc + jj;
+                const bool in0 = valid && r < Rp;  // uniform over the warp
+                const bool in1 = valid && r + 1 < Rp;
+                const float f0 = __uint_as_float(fr[jj]), f1 = __uint_as_float(fr[jj + 1]);
+                const float x0 = xv[jj], x1 = xv[jj + 1];
+                float e0 = 0.f, e1 = 0.f, s0 = 0.f, s1 = 0.f;
+                if (energy || energy_only) {
+                    e0 = (live && in0) ? (x0 >= 0.f ? f0 : -f0) : 0.f;
+                    e1 = (live && in1) ? (x1 >= 0.f ? f1 : -f1) : 0.f;
                 }
-                tv[u] = term;
-                t2v[u] = t2;
+                if (!energy_only) {
+                    const float y0 = yv[jj], y1 = yv[jj + 1];
+                    if (Tpart) {
+                        s0 = in0 ? __fmul_rn(y0, y0) : 0.f;  // y_i(t_k)^2 (Eq. eq_TInst)
+                        s1 = in1 ? __fmul_rn(y1, y1) : 0.f;
+                    }
+                    // two replicas per packed binary32 operation (the same
+                    // bits as two scalar updates); the per-replica friction
+                    // of the Nose-Hoover thermostat in place of gamma dt
+                    StepConsts2 kr = k2;
+                    if (gvec)
+                        kr.g = f2_pack(in0 ? __ldg(gvec + r) : 0.f, in1 ? __ldg(gvec + r + 1) : 0.f);
+                    float xn0, xn1;
+                    uint64_t yn;
+                    sb_update2(f2_pack(f0, f1), f2_pack(x0, x1), f2_pack(yv[jj], yv[jj + 1]), pk2,
+                               kr, xn0, xn1, yn);
+                    const size_t e = (size_t)r * Np + i;
+                    if (in0) {
+                        ptx::st_f32_hint(X + e, xn0, stream_once);
+                        ptx::st_f32_hint(Y + e, __uint_as_float((uint32_t)yn), stream_once);
+                    }
+                    if (in1) {
+                        ptx::st_f32_hint(X + e + Np, xn1, stream_once);
+                        ptx::st_f32_hint(Y + e + Np, __uint_as_float((uint32_t)(yn >> 32)),
+                                         stream_once);
+                    }
+                    const uint32_t b0 = __ballot_sync(0xFFFFFFFFu, !(xn0 >= 0.f));
+                    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, !(xn1 >= 0.f));
+                    negm = lane == jj ? b0 : negm;
+                    negm = lane == jj + 1 ? b1 : negm;
+                }
+                tv[u] = e0;
+                tv[u + 1] = e1;
+                t2v[u] = s0;
+                t2v[u + 1] = s1;
             }
             if (reduce) {
                 // transposed butterfly: after the exchanges over lane
@@ -299,6 +331,30 @@ __device__ __forceinline__ bool epilogue_tile(
                     sh->red[q][col] = ta;
                     sh->tred[q][col] = tb;
                 }
+            }
+        }
+        // lane l writes the next operand's codes of replica rc + l for this
+        // warp's 32 spins (padded spins 0): FP8 one byte per spin (32 bytes),
+        // FP4 one nibble per spin, spin 2m in the low nibble of byte m (16 bytes)
+        if (!energy_only && valid && rc + lane < Rp) {
+            const uint32_t neg = negm & livem;
+            if (FP4) {
+                uint32_t w[4];
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+                    w[m] = (spread8_nibbles(livem >> (8 * m)) * kFp4PlusOne) |
+                           (spread8_nibbles(neg >> (8 * m)) << 3);
+                *reinterpret_cast<uint4 *>(Snext + (size_t)(rc + lane) * (Kp / 2) + (i0 >> 1)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                uint32_t w[8];
+#pragma unroll
+                for (int m = 0; m < 8; ++m)
+                    w[m] = (spread4_bytes(livem >> (4 * m)) * kFp8PlusOne) |
+                           (spread4_bytes(neg >> (4 * m)) << 7);
+                uint4 *dst = reinterpret_cast<uint4 *>(Snext + (size_t)(rc + lane) * Np + i0);
+                dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
             }
         }
     }
