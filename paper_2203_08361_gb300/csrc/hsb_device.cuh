@@ -49,6 +49,35 @@ __device__ __forceinline__ uint8_t fp8_sign(float x)
     return x >= 0.f ? kFp8PlusOne : kFp8MinusOne;
 }
 
+// ---- bit spreading for the sign codes (host and device) --------------------
+// bit k of b (k < 4) to bit 8k: one bit per byte (the four partial products
+// of the multiplication occupy distinct bits, so nothing carries)
+__host__ __device__ __forceinline__ uint32_t spread4_bytes(uint32_t b)
+{
+    return ((b & 0xFu) * 0x00204081u) & 0x01010101u;
+}
+
+// bit k of b (k < 8) to bit 4k: one bit per nibble
+__host__ __device__ __forceinline__ uint32_t spread8_nibbles(uint32_t b)
+{
+    uint32_t x = b & 0xFFu;
+    x = (x | (x << 12)) & 0x000F000Fu;
+    x = (x | (x << 6)) & 0x03030303u;
+    return (x | (x << 3)) & 0x11111111u;
+}
+
+// 0xFF in byte i of the result for each set bit i (i < 4) of b, else 0x00
+__host__ __device__ __forceinline__ uint32_t byte_mask4(uint32_t b)
+{
+    return spread4_bytes(b) * 0xFFu;
+}
+
+// 0xF in nibble i of the result for each set bit i (i < 8) of b, else 0x0
+__host__ __device__ __forceinline__ uint32_t nibble_mask8(uint32_t b)
+{
+    return spread8_nibbles(b) * 0xFu;
+}
+
 // One spin update (Methods):
 //   y~  = y + {-(a0 - a(t_k)) x + c0 f} dt        Eq. (eq_SyEuY)
 //   x~  = x + a0 y~ dt                             Eq. (eq_SyEuX)

@@ -130,13 +130,6 @@ __device__ __forceinline__ bool warp_wait_cl(uint64_t *bar, uint32_t parity, int
     return __all_sync(0xFFFFFFFFu, ok);
 }
 
-// 0xFF in byte i of the result for each set bit i (i < 4) of b, else 0x00
-// (the four bits spread to bytes by one multiplication, no carries).
-__device__ __forceinline__ uint32_t byte_mask4(uint32_t b)
-{
-    return (((b & 15u) * 0x204081u) & 0x01010101u) * 0xFFu;
-}
-
 __device__ __forceinline__ uint32_t pack4(uint8_t b0, uint8_t b1, uint8_t b2, uint8_t b3)
 {
     return (uint32_t)b0 | ((uint32_t)b1 << 8) | ((uint32_t)b2 << 16) | ((uint32_t)b3 << 24);

@@ -235,23 +235,6 @@ __device__ __forceinline__ void load_force(uint32_t tcol, bool two_acc, uint32_t
     ptx::tmem_ld_wait(f);
 }
 
-// 0xFF in byte i of the result for each set bit i (i < 4) of b, else 0x00
-// (the four bits spread to bytes by one multiplication, no carries).
-__device__ __forceinline__ uint32_t byte_mask4(uint32_t b)
-{
-    return (((b & 15u) * 0x204081u) & 0x01010101u) * 0xFFu;
-}
-
-// 0xF in nibble i of the result for each set bit i (i < 8) of b, else 0x0.
-__device__ __forceinline__ uint32_t nibble_mask8(uint32_t b)
-{
-    uint32_t m = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-        m |= ((b >> i) & 1u) * (0xFu << (4 * i));
-    return m;
-}
-
 // q^2 for q = round(2^24 y) (exact scaling, round to nearest even), |y| < 256
 // (else *bad), split into 22-bit chunks added to s0, s1, s2; over the 32
 // spins of a thread each chunk sum stays below 2^27, over a tile's 128 spins

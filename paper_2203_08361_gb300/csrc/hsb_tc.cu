@@ -164,22 +164,6 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
 
 }  // namespace
 
-// bit k of b (k < 8) to bit 4k: one bit per nibble
-__device__ __forceinline__ uint32_t spread8_nibbles(uint32_t b)
-{
-    uint32_t x = b & 0xFFu;
-    x = (x | (x << 12)) & 0x000F000Fu;
-    x = (x | (x << 6)) & 0x03030303u;
-    return (x | (x << 3)) & 0x11111111u;
-}
-
-// bit k of b (k < 4) to bit 8k: one bit per byte (the four partial products
-// of the multiplication occupy distinct bits, so nothing carries)
-__device__ __forceinline__ uint32_t spread4_bytes(uint32_t b)
-{
-    return ((b & 0xFu) * 0x00204081u) & 0x01010101u;
-}
-
 // Tile t -> (row block mb, replica block rb).  The replica blocks are cut
 // into bands of `band` blocks (the last band may be narrower) taken one after
 // another; inside a band the tiles run row block by row block with the band's

@@ -2,7 +2,8 @@
 
 A host-only program (nvcc, no GPU) prints the instruction descriptors of the
 FP8 (kind::f8f6f4) and FP4 (kind::mxf4, block-scaled) MMAs, the 128-byte
-swizzled shared-memory matrix descriptor and the operand codes of +1 and -1.
+swizzled shared-memory matrix descriptor, the operand codes of +1 and -1 and
+the bit-spreading helpers that assemble the sign codes of 4 or 8 spins.
 The test decodes each field with the bit layout of the PTX ISA's tcgen05
 descriptor tables, written out here independently of the library's helpers,
 and the operand codes with the OCP MX element formats (e4m3, e2m1, UE8M0).
@@ -34,6 +35,12 @@ int main()
     printf("fp4_minus %u\n", (unsigned)hsb::kFp4MinusOne);
     printf("fp8_plus %u\n", (unsigned)hsb::kFp8PlusOne);
     printf("fp8_minus %u\n", (unsigned)hsb::kFp8MinusOne);
+    for (unsigned b = 0; b < 256; ++b) {
+        printf("spread4_%u %u\n", b, hsb::spread4_bytes(b));
+        printf("spread8_%u %u\n", b, hsb::spread8_nibbles(b));
+        printf("bmask4_%u %u\n", b, hsb::byte_mask4(b));
+        printf("nmask8_%u %u\n", b, hsb::nibble_mask8(b));
+    }
     return 0;
 }
 """
@@ -154,3 +161,35 @@ def test_operand_codes_of_plus_and_minus_one(values):
     # the decoders themselves: every e2m1 code, and e4m3 extremes
     assert [decode_e2m1(c) for c in range(8)] == [0, 0.5, 1, 1.5, 2, 3, 4, 6]
     assert decode_e4m3(0x7E) == 448.0 and decode_e4m3(0x01) == 2.0 ** -9
+
+
+def spread(b, nbits, width):
+    """Bit k of b (k < nbits) moved to bit width * k."""
+    return sum(((b >> k) & 1) << (width * k) for k in range(nbits))
+
+
+def test_sign_code_bit_spreading(values):
+    # every argument below 256; only its low 4 (bytes) or 8 (nibbles) bits count
+    for b in range(256):
+        assert values[f"spread4_{b}"] == spread(b & 0xF, 4, 8), b
+        assert values[f"spread8_{b}"] == spread(b, 8, 4), b
+        assert values[f"bmask4_{b}"] == spread(b & 0xF, 4, 8) * 0xFF, b
+        assert values[f"nmask8_{b}"] == spread(b, 8, 4) * 0xF, b
+
+
+def test_sign_codes_of_four_and_eight_spins(values):
+    # the one-step epilogue's codes: FP8 byte j = 0x38 | 0x80 for a negative
+    # live spin j, 0 for a padded one; FP4 nibble j likewise with 0x2 | 0x8
+    for live in range(16):
+        for neg in range(16):
+            w = values[f"spread4_{live}"] * 0x38 | values[f"spread4_{neg & live}"] << 7
+            want = bytes((0xB8 if (neg >> j) & (live >> j) & 1 else 0x38) if (live >> j) & 1
+                         else 0 for j in range(4))
+            assert w.to_bytes(4, "little") == want
+    for live in (0x00, 0xFF, 0x0F, 0xA5, 0x80):
+        for neg in (0x00, 0xFF, 0x3C, 0x81):
+            w = values[f"spread8_{live}"] * 0x2 | values[f"spread8_{neg & live}"] << 3
+            for j in range(8):
+                code = (w >> (4 * j)) & 0xF
+                want = (0xA if (neg >> j) & 1 else 0x2) if (live >> j) & 1 else 0
+                assert code == want
