@@ -645,8 +645,12 @@ __device__ __forceinline__ void persistent_body(const CUtensorMap *tmapA,
 #pragma unroll
             for (int j = 0; j < 16; j += 2)
                 vpre[j / 2] = f2_fma(pk2, f2_pack_bits(xpre[j], xpre[j + 1]), k2.z);
-            const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err) &&
-                            ok_nh;
+            // one warp waits for the accumulator; the others block at the
+            // barrier after it, leaving the schedulers to the poller, the
+            // issuers and the MMA warp while the force is formed
+            const bool ok =
+                (ew != 0 || ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err)) &&
+                ok_nh;
             if (epi_bar_or(!ok)) {
                 left = true;
                 break;
