@@ -114,7 +114,9 @@ typedef struct {
     int schedule;           /* FP8 / FP4 step loop: 0 = automatic (persistent kernel
                                when its grid fits on the device), 1 = persistent
                                kernel only (HSB_E_UNSUPPORTED if it cannot fit),
-                               2 = one kernel launch per step, 3 = persistent
+                               2 = one kernel launch per step (on CTA pairs,
+                               tcgen05 cta_group::2, once N rounded up to 128
+                               reaches 1024), 3 = persistent
                                kernel with the CTA's rows of J held on chip for
                                the whole run (N <= 2048, else
                                HSB_E_UNSUPPORTED), 4 = persistent kernel run by
