@@ -120,7 +120,7 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
 // Bounded wait by every lane; false in all lanes if any gave up.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, int *abort, int *err)
 {
-    const bool ok = ptx::mbar_wait(bar, parity, abort, err);
+    const bool ok = ptx::mbar_wait<false>(bar, parity, abort, err);
     return __all_sync(0xFFFFFFFFu, ok);
 }
 
@@ -252,7 +252,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
                         const int c = 2 * kb + h;
                         const int s = (int)(g % kQStages);
                         const uint32_t ph = (g / kQStages) & 1u;
-                        if (!ptx::mbar_wait(&sh->empty[s], ph ^ 1u, &sh->abort, a.err)) {
+                        if (!ptx::mbar_wait<false>(&sh->empty[s], ph ^ 1u, &sh->abort, a.err)) {
                             fail = true;
                             break;
                         }
@@ -361,7 +361,7 @@ tc_bf16x3_persistent_kernel(const __grid_constant__ CUtensorMap tmapJ,
             uint32_t xpre[16], ypre[16];
             ptx::tmem_ld16(tmem + lane_off + kQColX + c0, xpre);
             ptx::tmem_ld16(tmem + lane_off + kQColY + c0, ypre);
-            const bool ok = ptx::mbar_wait(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
+            const bool ok = ptx::mbar_wait<false>(&sh->accfull, (uint32_t)kl & 1u, &sh->abort, a.err);
             ptx::tmem_ld_wait(xpre);
             ptx::tmem_ld_wait(ypre);
             if (qbar_or(!ok)) {
