@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libhsb.so")
 SOURCES = ["hsb_api.cu", "hsb_simt.cu", "hsb_tc.cu", "hsb_persist.cu", "hsb_pair.cu", "hsb_persist_ar.cu", "hsb_persist_bf16.cu", "hsb_batch.cu", "hsb_noalloc.cu"]
-HEADERS = ["hsb_internal.cuh", "hsb_device.cuh", "hsb_ptx.cuh"]
+HEADERS = ["hsb_internal.cuh", "hsb_device.cuh", "hsb_ptx.cuh", "hsb_sched.cuh"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -47,6 +47,7 @@
 #include "hsb_device.cuh"
 #include "hsb_internal.cuh"
 #include "hsb_ptx.cuh"
+#include "hsb_sched.cuh"
 
 namespace hsb {
 
@@ -164,21 +165,6 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
 
 }  // namespace
 
-// Tile t -> (row block mb, replica block rb).  The replica blocks are cut
-// into bands of `band` blocks (the last band may be narrower) taken one after
-// another; inside a band the tiles run row block by row block with the band's
-// replica blocks fastest.  The CTAs running at one time then share the J rows
-// of a few row blocks, and the band's S rows, which every row block reads,
-// stay in L2 while the row blocks pass.
-__device__ __forceinline__ void tile_coords(int t, int nmb, int nrb, int band, int &mb, int &rb)
-{
-    const int per = nmb * band;
-    const int k = t / per;
-    const int rem = t - k * per;
-    const int w = min(band, nrb - k * band);
-    mb = rem / w;
-    rb = k * band + (rem - mb * w);
-}
 
 // Epilogue of one tile in the eight epilogue warps (lane = spin; each warp
 // takes half of the tile's replica columns, 32 at a time): the accumulator,

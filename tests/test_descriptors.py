@@ -2,8 +2,9 @@
 
 A host-only program (nvcc, no GPU) prints the instruction descriptors of the
 FP8 (kind::f8f6f4) and FP4 (kind::mxf4, block-scaled) MMAs, the 128-byte
-swizzled shared-memory matrix descriptor, the operand codes of +1 and -1 and
-the bit-spreading helpers that assemble the sign codes of 4 or 8 spins.
+swizzled shared-memory matrix descriptor, the operand codes of +1 and -1,
+the bit-spreading helpers that assemble the sign codes of 4 or 8 spins and
+the band-order tile map of the one-step kernels.
 The test decodes each field with the bit layout of the PTX ISA's tcgen05
 descriptor tables, written out here independently of the library's helpers,
 and the operand codes with the OCP MX element formats (e4m3, e2m1, UE8M0).
@@ -22,6 +23,7 @@ PROGRAM = r"""
 #include <stdio.h>
 #include "hsb_ptx.cuh"
 #include "hsb_device.cuh"
+#include "hsb_sched.cuh"
 int main()
 {
     printf("mxf4_128_192 %u\n", hsb::ptx::idesc_mxf4_e2m1(128, 192));
@@ -35,6 +37,34 @@ int main()
     printf("fp4_minus %u\n", (unsigned)hsb::kFp4MinusOne);
     printf("fp8_plus %u\n", (unsigned)hsb::kFp8PlusOne);
     printf("fp8_minus %u\n", (unsigned)hsb::kFp8MinusOne);
+    // the band-order tile map of the one-step kernels over (nmb, nrb, band):
+    // every tile once; prints the count of shapes where it is not a bijection
+    int bad_maps = 0, shapes = 0;
+    for (int nmb = 1; nmb <= 70; nmb += 3)
+        for (int nrb = 1; nrb <= 40; ++nrb)
+            for (int band = 1; band <= nrb; band += (band < 8 ? 1 : 5)) {
+                static unsigned char seen[70 * 40];
+                const int ntiles = nmb * nrb;
+                for (int i = 0; i < ntiles; ++i)
+                    seen[i] = 0;
+                bool ok = true;
+                for (int t = 0; t < ntiles; ++t) {
+                    int mb = -1, rb = -1;
+                    hsb::tile_coords(t, nmb, nrb, band, mb, rb);
+                    if (mb < 0 || mb >= nmb || rb < 0 || rb >= nrb || seen[mb * nrb + rb]++)
+                        ok = false;
+                }
+                bad_maps += !ok;
+                ++shapes;
+            }
+    printf("tile_map_shapes %d\n", shapes);
+    printf("tile_map_bad %d\n", bad_maps);
+    // one shape in full: nmb = 3, nrb = 5, band = 2 (bands of 2, 2, 1 blocks)
+    for (int t = 0; t < 15; ++t) {
+        int mb, rb;
+        hsb::tile_coords(t, 3, 5, 2, mb, rb);
+        printf("tile_3_5_2_%d %d\n", t, mb * 5 + rb);
+    }
     for (unsigned b = 0; b < 256; ++b) {
         printf("spread4_%u %u\n", b, hsb::spread4_bytes(b));
         printf("spread8_%u %u\n", b, hsb::spread8_nibbles(b));
@@ -193,3 +223,14 @@ def test_sign_codes_of_four_and_eight_spins(values):
                 code = (w >> (4 * j)) & 0xF
                 want = (0xA if (neg >> j) & 1 else 0x2) if (live >> j) & 1 else 0
                 assert code == want
+
+
+def test_band_order_tile_map(values):
+    # t -> (row block, replica block) visits every tile of the grid once
+    assert values["tile_map_shapes"] > 1000
+    assert values["tile_map_bad"] == 0
+    # bands of two replica blocks, the last of one: inside a band the row
+    # blocks run in order with the band's replica blocks fastest
+    order = [values[f"tile_3_5_2_{t}"] for t in range(15)]
+    want = [mb * 5 + rb for band in ((0, 1), (2, 3), (4,)) for mb in range(3) for rb in band]
+    assert order == want
