@@ -168,9 +168,12 @@ __device__ __forceinline__ void commit_elect(uint64_t *bar)
 
 // Epilogue of one tile in the eight epilogue warps (lane = spin; each warp
 // takes half of the tile's replica columns, 32 at a time): the accumulator,
-// x and y from global memory, the pinned update, x' and y' in place, sgn(x')
-// as the next operand; on evaluation steps the per-replica partial sums of
-// s_i f_i and, with a trace, of y_i(t_k)^2, through a transposed butterfly.
+// x and y from global memory, the pinned update (two replicas per packed
+// binary32 operation), x' and y' in place, sgn(x') as the next operand (the
+// signs of a replica column gathered by one ballot; lane l then stores the
+// codes of column l as one row segment); on evaluation steps the
+// per-replica partial sums of s_i f_i and, with a trace, of y_i(t_k)^2,
+// through a transposed butterfly.
 // kPair: the tile belongs to a CTA pair, whose even CTA completes this CTA's
 // accumulator barrier and receives its release (cluster address accempty_c).
 // valid = false (a pair's row block past Np): the accumulator is waited for
